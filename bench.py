@@ -1,0 +1,375 @@
+"""Benchmark of the LAMG+ solve phase on B300 (one JSON line on stdout).
+
+Workload (N=1 line): the 1024 x 1024 grid-aligned anisotropic 5-point Laplacian (x-edges 1,
+y-edges 1e-3; n = 1,048,576, nnz(L) = n + 2m = 5,238,784), one mean-zero Gaussian right-hand
+side b = L x (seeds: graph 1, RHS 2, test vectors 3), FP64 cycle inside FP64 flexible CG, run to
+||b - L phi|| / ||b|| <= 1e-8.
+
+A step is one complete solve (projection of b, CG with one cycle per iteration, final true
+residual) with b and phi resident in device memory; the hierarchy is set up once before the
+timed region. The metric is ns per nonzero of L per digit of residual reduction,
+t_solve / (nnz(L) * log10(||b|| / ||b - L phi||)); lower is better.
+
+--impl reference times the CPU oracle (serial FP64 C) on the same workload and metric.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "ns/nnz/digit to 1e-8 residual"
+UNIT = "ns/nnz/digit"
+WORKLOAD = ("aniso1024: 2D 5-point grid 1024x1024, x-weight 1, y-weight 1e-3, one mean-zero "
+            "N(0,1) RHS b = L x, FP64 cycle in FP64 flexible CG, tol 1e-8")
+TOL = 1e-8
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1])); smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(smax)),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def workload():
+    import graphgen as gg
+    g = gg.config_graph("aniso1024")
+    b = gg.rhs(g, 2)
+    return g, b
+
+
+def digits(relres: float) -> float:
+    return -math.log10(max(relres, 1e-300))
+
+
+def cpu_baseline(g, b, reps: int = 3) -> dict:
+    """The oracle as it stands (serial FP64 C, one thread) on the same workload."""
+    import oracle
+    t0 = time.perf_counter()
+    H = oracle.Hierarchy(g)
+    setup_s = time.perf_counter() - t0
+    times, units = 0.0, 0.0
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        out = H.fcg(b, TOL, 200)
+        dt = time.perf_counter() - t0
+        x = out["x"]
+        import graphgen as gg
+        r = gg.laplacian_apply(g, x) - (b - b.mean())
+        rel = np.linalg.norm(r) / np.linalg.norm(b - b.mean())
+        times += dt
+        units += g.nnz_L * digits(rel)
+    return {"value": times * 1e9 / units, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{reps} full solves of the aniso1024 workload (FCG to 1e-8) after a "
+                      f"{setup_s:.1f} s untimed oracle setup; single-threaded C, gcc -O2",
+            "setup_s": setup_s}
+
+
+def traffic_for(kernel: str):
+    """ncu DRAM bytes per launch recorded for `kernel`, if the kernel source is unchanged."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    if not os.path.exists(path):
+        return None
+    rec = json.load(open(path))
+    src = open(os.path.join(ROOT, "paper_2606_24791_b300", "csrc", "cycle_kernels.cu"), "rb").read()
+    if rec.get("source_sha256") != hashlib.sha256(src).hexdigest():
+        return None
+    return rec.get("kernels", {}).get(kernel)
+
+
+def schedule_counts(P, iters: int) -> dict:
+    """Per-solve launch counts of the cycle kernels (the cycle's static schedule)."""
+    import math as m
+    counts = {}
+    lv = P.info
+    visits = [0] * len(lv)
+
+    def visit(l):
+        visits[l] += 1
+        L = lv[l]
+        if L["kind"] == "coarsest":
+            return
+        if L["kind"] == "elim":
+            visit(l + 1)
+            return
+        j = counts.setdefault(("j", l), 0)
+        counts[("j", l)] = j + 1
+        nv = m.floor((j + 1) * L["gamma"]) - m.floor(j * L["gamma"])
+        for _ in range(nv):
+            visit(l + 1)
+    visit(0)
+    return visits
+
+
+def run_ours(args, ws, rank, local):
+    import torch
+    import paper_2606_24791_b300 as lamg
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    g, b = workload()
+    t0 = time.perf_counter()
+    P = lamg.setup(g, device=local)
+    setup_s = time.perf_counter() - t0
+    stream = torch.cuda.current_stream(dev)
+    bt = torch.from_numpy(b).to(dev)
+    xt = torch.zeros_like(bt)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    def solve():
+        return P.solve_ptr(bt.data_ptr(), xt.data_ptr(), TOL, 200, stream=stream.cuda_stream)
+
+    for _ in range(max(args.warmup, 0)):
+        flush.fill_(1)
+        st = solve()
+    torch.cuda.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    stats = []
+    wall0 = time.perf_counter()
+    for i in range(args.steps):
+        flush.fill_(i & 0xff)                 # evict the 126 MB L2 between steps
+        ev[i][0].record(stream)
+        stats.append(solve())
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    if ws > 1:
+        torch.distributed.barrier()
+    clocks = sampler.stop()
+    step_ms = [a.elapsed_time(bb) for a, bb in ev]
+    total_ms = float(sum(step_ms))
+    units = float(sum(g.nnz_L * digits(s["relres_true"]) for s in stats))
+    iters = [s["iters"] for s in stats]
+
+    # launches in the timed region: 3 init + first tail + per iteration head(2) + tails + 2 final
+    nops = P_ops(P)
+    launches = sum(3 + (nops + 3) + 2 * it + (it - 1) * (nops + 3) + 2 for it in iters)
+
+    # e2e: the same solve through the C ABI with host buffers (H2D of b, D2H of phi inside)
+    e2e_t, e2e_units = 0.0, 0.0
+    for _ in range(3):
+        t0 = time.perf_counter()
+        x, st = P.solve(b, TOL, 200)
+        e2e_t += time.perf_counter() - t0
+        e2e_units += g.nnz_L * digits(st["relres_true"])
+
+    # roofline of the dominant kernel: cold-L2 timing of each candidate, weighted by how often
+    # a solve runs it
+    visits = schedule_counts(P, iters[0])
+    cand = []
+    it0 = iters[0]
+    for l, L in enumerate(P.info):
+        if L["kind"] != "agg" or L["n"] < 100_000:
+            continue
+        for k, per_cycle in (("gs_sweep", 3 * visits[l]), ("resid", visits[l])):
+            r = P.time_kernel(k, l, reps=10)
+            cand.append((r["ms"] * per_cycle * it0, f"{k}@L{l}", r))
+    r = P.time_kernel("spmv_dot", 0, reps=10)
+    cand.append((r["ms"] * it0, "spmv_dot@L0", r))
+    cand.sort(key=lambda t: -t[0])
+    share_ms, dom_name, dom = cand[0]
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+        os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+    peak = peaks.get("hbm_gbs", 6400.0)
+    kname = {"gs_sweep": "k_gs", "resid": "k_resid", "spmv_dot": "k_spmv_dot"}[dom_name.split("@")[0]]
+    traffic = traffic_for(kname)
+    roofline = {"bound": "hbm", "kernel": dom_name, "achieved": round(dom["gbs"], 1), "peak": peak,
+                "unit": "GB/s", "frac": round(dom["gbs"] / peak, 3),
+                "traffic": traffic, "algorithmic_bytes": dom["bytes"], "launch_ms": dom["ms"],
+                "peak_source": "MEASURED_PEAKS.json hbm_gbs (burst copy), of measured" if peaks
+                else "fallback 6400 GB/s"}
+    kernels = {name: {"gbs": round(rr["gbs"], 1), "ms": round(rr["ms"], 4)} for _, name, rr in cand}
+
+    # whole-job value across ranks: max time over ranks / sum of units
+    if ws > 1:
+        import torch.distributed as td
+        t = torch.tensor([total_ms, units], dtype=torch.float64, device=dev)
+        tmax = t.clone(); td.all_reduce(tmax[:1], op=td.ReduceOp.MAX)
+        tsum = t.clone(); td.all_reduce(tsum[1:], op=td.ReduceOp.SUM)
+        total_ms, units_all = float(tmax[0]), float(tsum[1])
+    else:
+        units_all = units
+    value = total_ms * 1e6 / units_all
+    out = {
+        "metric": METRIC, "value": round(value, 5), "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(total_ms / args.steps, 4), "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n": g.n, "nnz_L": g.nnz_L, "levels": P.nlevels,
+                   "iterations": iters[0], "relres_true": stats[-1]["relres_true"],
+                   "digits": round(digits(stats[-1]["relres_true"]), 3), "setup_s": round(setup_s, 2),
+                   "parallelism": f"replicas{ws}", "l2": "flushed between steps (256 MB write)",
+                   "seeds": {"graph": 1, "rhs": 2, "test_vectors": 3}},
+        "e2e": {"value": round(e2e_t * 1e9 / e2e_units, 5), "unit": UNIT,
+                "h2d_bytes_per_step": 8 * g.n, "d2h_bytes_per_step": 8 * g.n + 128},
+        "gpu_launches": launches,
+        "roofline": roofline,
+        "kernels": kernels,
+        "clocks": clocks,
+        "wall_s_timed": round(wall, 3),
+    }
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(g, b)
+    P.close()
+    return out
+
+
+def P_ops(P) -> int:
+    """Kernels in one cycle of the static schedule (as the library generates it)."""
+    import math as m
+    lv = P.info
+    cnt = [0]
+    jv = {}
+
+    def visit(l, first):
+        L = lv[l]
+        if L["kind"] == "coarsest":
+            cnt[0] += 1
+            return
+        if L["kind"] == "elim":
+            cnt[0] += 2
+            visit(l + 1, first)
+            return
+        cnt[0] += L["ncol"] * 3 + 3   # pre sweep (first colour fused), resid, restrict, prolong, post
+        j = jv.get(l, 0); jv[l] = j + 1
+        nv = m.floor((j + 1) * L["gamma"]) - m.floor(j * L["gamma"])
+        for i in range(nv):
+            visit(l + 1, i == 0)
+    visit(0, True)
+    return cnt[0]
+
+
+def run_reference(args, ws, rank):
+    """The oracle on the host cores, same workload and metric (rank 0 only)."""
+    if rank != 0:
+        return None
+    import oracle
+    import graphgen as gg
+    g, b = workload()
+    H = oracle.Hierarchy(g)
+    for _ in range(max(args.warmup, 0)):
+        H.fcg(b, TOL, 200)
+    t_total, units = 0.0, 0.0
+    t0w = time.perf_counter()
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        out = H.fcg(b, TOL, 200)
+        t_total += time.perf_counter() - t0
+        r = gg.laplacian_apply(g, out["x"]) - (b - b.mean())
+        units += g.nnz_L * digits(np.linalg.norm(r) / np.linalg.norm(b - b.mean()))
+    value = t_total * 1e9 / units
+    return {
+        "impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": UNIT,
+        "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(t_total * 1e3 / args.steps, 2), "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n": g.n, "nnz_L": g.nnz_L},
+        "cpu_baseline": {"value": round(value, 4), "unit": UNIT, "kind": "oracle", "cores": 1,
+                         "sample": f"{args.steps} full oracle solves of the workload after an untimed setup"},
+        "e2e": {"value": round(value, 4), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "wall_s_timed": round(time.perf_counter() - t0w, 2),
+    }
+
+
+def main():
+    args = parse()
+    ws, rank, local = dist_env()
+    if args.impl == "reference":
+        out = run_reference(args, ws, rank)
+        if out is not None:
+            print(json.dumps(out), flush=True)
+        return
+    if ws > 1:
+        import torch
+        import torch.distributed as td
+        torch.cuda.set_device(local)
+        td.init_process_group("nccl")
+    out = run_ours(args, ws, rank, local)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if ws > 1:
+        import torch.distributed as td
+        td.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,246 @@
+/*
+ * lamg.h - C ABI of the B300 LAMG+ solve-phase library.
+ *
+ * The library solves the compatible graph-Laplacian system of the paper's Eq. 1,
+ *     L phi = b,   1^T phi = 0,   1^T b = 0,   L = D - W,
+ * for a connected weighted undirected graph, with a multigrid cycle over a LAMG+ hierarchy
+ * (Section 2: low-degree elimination, Eq. 2; guarded caliber-1 aggregation, Eqs. 3-4;
+ * strength-of-connection veto, Eq. 9; selective caliber-2 interpolation, Section 3.2 and
+ * Eq. 13; Galerkin coarse operators; gamma-cycle work rule, Eq. 5) used as the
+ * preconditioner of a flexible conjugate-gradient iteration run in FP64 on the GPU.
+ *
+ * Conventions shared by every entry point
+ *  - All sizes are int64_t, node ids int32_t (n < 2^31), values IEEE binary64 unless stated.
+ *  - Graphs are given as symmetric adjacency in CSR: rp[n+1] (row pointers), ci[rp[n]]
+ *    (neighbour ids, strictly ascending within a row, no self loops), w[rp[n]] (positive
+ *    finite weights, w[u->v] == w[v->u]). The library copies what it needs; the caller keeps
+ *    ownership of every array it passes and may free it when the call returns.
+ *  - Vectors b and phi are indexed by the caller's node ids. By default they are HOST
+ *    pointers; with LAMG_DEVICE_PTRS in the flags they are device pointers on the current
+ *    CUDA device, and the work is ordered on the stream given in the options (0: the
+ *    library's own stream). The library never frees caller memory.
+ *  - Every call returns LAMG_OK or an error code; lamg_strerror() names it. A failed call
+ *    leaves its outputs unspecified and its inputs untouched. A hierarchy handle must not be
+ *    used from two host threads at once.
+ *  - Every GPU wait inside the library is bounded; a wait that runs out returns
+ *    LAMG_ERR_TIMEOUT instead of hanging.
+ */
+#ifndef LAMG_H
+#define LAMG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define LAMG_OK 0
+#define LAMG_ERR_INVALID 1        /* asymmetric graph, w <= 0 or NaN, self loop, bad sizes */
+#define LAMG_ERR_DISCONNECTED 2   /* the paper assumes a connected graph (Section 1) */
+#define LAMG_ERR_SETUP 3          /* coarsening stalled above the dense-coarsest limit */
+#define LAMG_ERR_OOM 4            /* a device or host allocation failed */
+#define LAMG_ERR_NOT_CONVERGED 5  /* maxit reached; the stats are valid */
+#define LAMG_ERR_CUDA 6           /* a CUDA runtime call failed */
+#define LAMG_ERR_TIMEOUT 7        /* a bounded GPU wait ran out */
+#define LAMG_ERR_ADMISSION 8      /* serving: the request can never fit the memory budget */
+#define LAMG_ERR_NO_DEVICE 9      /* no CUDA device is visible */
+
+/* flags */
+#define LAMG_DEVICE_PTRS 1u       /* vectors are device pointers */
+
+/* cycle precision */
+#define LAMG_FP64 0
+#define LAMG_FP32 1               /* FP32 cycle inside FP64 CG (outer residual, dots, projection
+                                     and coarsest solve stay FP64) */
+
+/* Setup options. lamg_options_default() fills the paper's parameter-free values. */
+typedef struct lamg_options {
+    int32_t K;             /* test vectors per aggregation level: 4 (Section 3.3) */
+    int32_t nu_tv;         /* GS sweeps per test vector: 3 (Section 2) */
+    int32_t dmax;          /* elimination degree bound: 4 (Eq. 2) */
+    int32_t nu_pre;        /* pre-smoothing sweeps: 1 */
+    int32_t nu_post;       /* post-smoothing sweeps: 2 ((1,2) cycle, Appendix A Table 4) */
+    int32_t coarsest_max;  /* a level with at most this many nodes is solved densely: 1024 */
+    int32_t max_levels;    /* 100 */
+    int32_t veto;          /* strength-of-connection veto on (1) / off (0), Eq. 9 */
+    int32_t caliber2;      /* selective caliber-2 on (1) / off (0), Section 3.2 */
+    int32_t precision;     /* LAMG_FP64 or LAMG_FP32 cycle */
+    uint64_t seed;         /* test-vector random stream (SplitMix64, counter-based) */
+    double Q;              /* energy-ratio guard bound: 2.5 (Eq. 4) */
+    double tau_soc;        /* veto threshold: 0.05 (Eq. 9) */
+    double elim_min_frac;  /* keep an elimination level while |F| >= this * n: 0.01 */
+    double snap;           /* caliber-2 weight snap distance to 0/1: 1e-3 */
+    double guard_eps;      /* relative size below which a nodal energy counts as zero: 1e-10 */
+    double gamma_fixed;    /* > 0: this cycle index on every aggregation level instead of Eq. 5 */
+    int32_t device;        /* CUDA device ordinal */
+    int32_t reserved[7];
+} lamg_options;
+
+typedef struct lamg_graph {
+    int64_t n;
+    const int64_t *rp;
+    const int32_t *ci;
+    const double *w;
+} lamg_graph;
+
+/* One level of a prebuilt hierarchy, natural node numbering (lamg_import).
+ * kind: 0 elimination, 1 aggregation, 2 coarsest.
+ * Operator A (all kinds): off-diagonal CSR rp/ci/val (columns ascending) + diag.
+ * Aggregation level: colour[n] (Gauss-Seidel colour classes; rows of one colour must be
+ *   pairwise non-adjacent), nc aggregates, agg[n], agg2[n] (-1 for caliber-1 rows), wt[n]:
+ *   P row u = wt[u] at column agg[u] and 1 - wt[u] at column agg2[u].
+ * Elimination level: cidx[n] = coarse index of a kept (C) node, -1 for an eliminated (F)
+ *   node; C nodes must be numbered in ascending node order. The next level's operator must
+ *   be the Schur complement of Eq. 2.
+ * gamma: cycle index of an aggregation level (Eq. 5), ignored otherwise. */
+typedef struct lamg_level_desc {
+    int32_t kind;
+    int32_t pad;
+    int64_t n;
+    const int64_t *rp;
+    const int32_t *ci;
+    const double *val;
+    const double *diag;
+    const int32_t *colour;
+    int64_t nc;
+    const int32_t *cidx;
+    const int32_t *agg;
+    const int32_t *agg2;
+    const double *wt;
+    double gamma;
+} lamg_level_desc;
+
+typedef struct lamg_solve_opts {
+    double tol;            /* stop when ||b - L phi||_2 / ||b||_2 <= tol (recursive residual) */
+    int32_t maxit;         /* outer CG iteration cap */
+    uint32_t flags;        /* LAMG_DEVICE_PTRS */
+    void *stream;          /* cudaStream_t for device-pointer calls, or 0 */
+} lamg_solve_opts;
+
+typedef struct lamg_stats {
+    int32_t iters;         /* outer iterations done */
+    int32_t nlevels;
+    double relres;         /* recursive residual norm / ||b|| at exit */
+    double relres_true;    /* ||b - L phi|| / ||b|| recomputed at exit (FP64) */
+    double b_mean;         /* mean removed from b before solving */
+    double solve_ms;       /* device time of the solve (CUDA events) */
+    double *hist;          /* optional caller buffer of maxit+1 doubles: relres per iteration */
+} lamg_stats;
+
+typedef struct lamg_hier lamg_hier;
+
+/* Fill *opt with the defaults listed above. */
+void lamg_options_default(lamg_options *opt);
+
+/* Build a hierarchy for the Laplacian of graph g (Section 2 setup). The host runs
+ * elimination, aggregation, caliber-2 and the Galerkin products; the GPU computes the test
+ * vectors (K GS sweeps from a SplitMix64 start) and the per-edge affinities with the veto
+ * flag. The hierarchy stays resident on the device until lamg_destroy.
+ * Errors: INVALID, DISCONNECTED, SETUP, OOM, CUDA, NO_DEVICE. */
+int lamg_setup(const lamg_graph *g, const lamg_options *opt, lamg_hier **out);
+
+/* Build the device hierarchy from levels computed elsewhere (same layout as lamg_level_get
+ * returns). Used to run the cycle on exactly the hierarchy and colour order of another
+ * implementation. Errors: INVALID, OOM, CUDA, NO_DEVICE. */
+int lamg_import(const lamg_level_desc *levels, int32_t nlevels, const lamg_options *opt,
+                lamg_hier **out);
+
+/* Solve L phi = b (Eq. 1) by flexible CG preconditioned with one cycle per iteration.
+ * b (n values) is projected to mean zero first (the removed mean goes to st->b_mean);
+ * phi (n values, output) has 1^T phi = 0. st may be NULL.
+ * Errors: INVALID (tol <= 0, maxit < 1), NOT_CONVERGED (phi and st valid), CUDA, TIMEOUT. */
+int lamg_solve(lamg_hier *h, const double *b, double *phi, const lamg_solve_opts *so,
+               lamg_stats *st);
+
+/* k right-hand sides at once: B and PHI are n x k, row-major (entry (u, j) at u*k + j).
+ * Each column is an independent solve with its own CG scalars and stopping test; the cycles
+ * run in SpMM form over all still-active columns. st: NULL or an array of k stats.
+ * Errors: as lamg_solve (NOT_CONVERGED if any column did not converge). */
+int lamg_solve_batch(lamg_hier *h, int32_t k, const double *B, double *PHI,
+                     const lamg_solve_opts *so, lamg_stats *st);
+
+/* Apply the preconditioner once: z = M r (one cycle from zero, then the mean-zero
+ * projection), no projection of r. r and z are n values (host, or device with
+ * LAMG_DEVICE_PTRS). Errors: CUDA. */
+int lamg_cycle(lamg_hier *h, const double *r, double *z, uint32_t flags);
+
+/* Hierarchy shape: info[0] = number of levels; for level l, meta (7 int64 per level) =
+ * kind, n, nnz (off-diagonal), colours, nc, caliber-2 rows, device bytes; gamma[l]. */
+int lamg_hier_info(const lamg_hier *h, int64_t *nlevels, int64_t *meta, double *gamma);
+
+/* Copy a per-level array of the hierarchy, natural numbering, into dst (sized by the caller
+ * from lamg_hier_info; dst may be NULL to query the element count, returned in *count).
+ * Names: "rp","ci","val","diag" (int64/int32/double/double), "colour","cidx","agg","agg2"
+ * (int32), "wt" (double), "X" (n x K test vectors, double), "aff" (double per off-diagonal
+ * entry), "strong" (uint8 per off-diagonal entry), "pinv" (n x n, double).
+ * Errors: INVALID for an unknown name or level. */
+int lamg_level_get(const lamg_hier *h, int32_t level, const char *name, void *dst,
+                   int64_t *count);
+
+/* Release a hierarchy and all its device memory. NULL is allowed. */
+void lamg_destroy(lamg_hier *h);
+
+/* Setup kernel K9 on its own (test vectors, Section 2): for a level operator given by host
+ * arrays (off-diagonal CSR rp/ci/val + diag, natural order) and a colouring, start each of
+ * K columns at the SplitMix64 value of (seed, level, node, column) and run nu colour-ordered
+ * GS sweeps on A x = 0 on the GPU. X (host, n x K row-major) receives the result.
+ * Errors: INVALID, OOM, CUDA, NO_DEVICE. */
+int lamg_testvectors(int64_t n, const int64_t *rp, const int32_t *ci, const double *val,
+                     const double *diag, const int32_t *colour, int32_t level, uint64_t seed,
+                     int32_t K, int32_t nu, double *X);
+
+/* Setup kernel K10 on its own (Eq. 3 affinity and Eq. 9 veto) on the GPU for host inputs:
+ * aff[e] = affinity of off-diagonal entry e, strong[e] = 1 iff |A_e| >= tau * max |A_ut| over
+ * u's row. Errors: INVALID, OOM, CUDA, NO_DEVICE. */
+int lamg_affinity(int64_t n, const int64_t *rp, const int32_t *ci, const double *val,
+                  const double *X, int32_t K, double tau, double *aff, uint8_t *strong);
+
+/* Time one solve-phase kernel of a hierarchy in isolation (used for roofline figures): `reps`
+ * launches on the hierarchy's stream, each after a 256 MB device write that evicts the L2,
+ * timed with CUDA events. which: 0 residual r = b - A x at an aggregation level, 1 one full
+ * colour-ordered GS sweep at an aggregation level, 2 outer CG SpMV with the p.q dot (level 0),
+ * 3 restriction P^T r, 4 prolongation x += P x^c. out[0] = mean device ms per launch (sweep),
+ * out[1] = algorithmic DRAM bytes of one launch (sweep), out[2] = kernels per launch.
+ * The kernels run on the hierarchy's current vectors. Errors: INVALID, OOM, CUDA, TIMEOUT. */
+int lamg_time_kernel(lamg_hier *h, int32_t which, int32_t level, int32_t reps, double *out);
+
+/* Name of an error code. */
+const char *lamg_strerror(int code);
+
+/* ----------------------------------------------------------------- serving
+ * A server owns a device memory budget and a worker thread. lamg_serve() submits one request
+ * (graph + right-hand side, both copied), returns at once with a ticket; requests are
+ * admitted while their estimated hierarchy + vector bytes fit the budget, set up on host
+ * threads, and their CG iterations are interleaved on the device with those of every other
+ * admitted request. lamg_serve_poll() reports completion and copies the solution out. */
+typedef struct lamg_server lamg_server;
+
+typedef struct lamg_server_opts {
+    double budget_bytes;   /* device memory budget for admitted requests */
+    int32_t max_inflight;  /* maximum concurrently admitted requests */
+    int32_t setup_threads; /* host setup workers */
+    double tol;
+    int32_t maxit;
+    int32_t device;
+} lamg_server_opts;
+
+typedef struct lamg_ticket_info {
+    int32_t done;          /* 0 pending, 1 finished */
+    int32_t status;        /* LAMG_OK or an error code once done */
+    int32_t iters;
+    int32_t pad;
+    double relres;
+    double t_submit_ms, t_admit_ms, t_done_ms;  /* server clock */
+} lamg_ticket_info;
+
+int lamg_server_create(const lamg_server_opts *so, const lamg_options *opt, lamg_server **out);
+int lamg_serve(lamg_server *s, const lamg_graph *g, const double *b, int64_t *ticket);
+int lamg_serve_poll(lamg_server *s, int64_t ticket, lamg_ticket_info *info, double *phi);
+int lamg_server_drain(lamg_server *s, double timeout_s);
+void lamg_server_destroy(lamg_server *s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LAMG_H */

@@ -1,0 +1,280 @@
+"""Python binding of the B300 LAMG+ solve-phase library (``include/lamg.h``).
+
+Argument marshalling only: every step of setup kernels, cycle and CG runs inside
+``_lib/liblamg_b300.so``. There is no CPU fallback: if the shared library cannot be loaded,
+every call raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_lib = None
+
+LAMG_OK = 0
+ERRORS = {1: "INVALID", 2: "DISCONNECTED", 3: "SETUP", 4: "OOM", 5: "NOT_CONVERGED", 6: "CUDA",
+          7: "TIMEOUT", 8: "ADMISSION", 9: "NO_DEVICE"}
+DEVICE_PTRS = 1
+FP64, FP32 = 0, 1
+KINDS = {"elim": 0, "agg": 1, "coarsest": 2}
+KIND_NAMES = {v: k for k, v in KINDS.items()}
+
+
+class LamgError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = code
+        super().__init__(f"{where}: {ERRORS.get(code, code)} ({_strerror(code)})")
+
+
+class Options(C.Structure):
+    _fields_ = [("K", C.c_int32), ("nu_tv", C.c_int32), ("dmax", C.c_int32), ("nu_pre", C.c_int32),
+                ("nu_post", C.c_int32), ("coarsest_max", C.c_int32), ("max_levels", C.c_int32),
+                ("veto", C.c_int32), ("caliber2", C.c_int32), ("precision", C.c_int32),
+                ("seed", C.c_uint64), ("Q", C.c_double), ("tau_soc", C.c_double),
+                ("elim_min_frac", C.c_double), ("snap", C.c_double), ("guard_eps", C.c_double),
+                ("gamma_fixed", C.c_double), ("device", C.c_int32), ("reserved", C.c_int32 * 7)]
+
+
+class Graph(C.Structure):
+    _fields_ = [("n", C.c_int64), ("rp", C.c_void_p), ("ci", C.c_void_p), ("w", C.c_void_p)]
+
+
+class LevelDesc(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("pad", C.c_int32), ("n", C.c_int64), ("rp", C.c_void_p),
+                ("ci", C.c_void_p), ("val", C.c_void_p), ("diag", C.c_void_p),
+                ("colour", C.c_void_p), ("nc", C.c_int64), ("cidx", C.c_void_p),
+                ("agg", C.c_void_p), ("agg2", C.c_void_p), ("wt", C.c_void_p),
+                ("gamma", C.c_double)]
+
+
+class SolveOpts(C.Structure):
+    _fields_ = [("tol", C.c_double), ("maxit", C.c_int32), ("flags", C.c_uint32),
+                ("stream", C.c_void_p)]
+
+
+class Stats(C.Structure):
+    _fields_ = [("iters", C.c_int32), ("nlevels", C.c_int32), ("relres", C.c_double),
+                ("relres_true", C.c_double), ("b_mean", C.c_double), ("solve_ms", C.c_double),
+                ("hist", C.c_void_p)]
+
+
+def lib_path() -> str:
+    return _build.SO
+
+
+def lib():
+    """Load the shared library (building it first if it is missing or stale)."""
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        L = C.CDLL(path)
+        P = C.c_void_p
+        L.lamg_options_default.argtypes = [C.POINTER(Options)]
+        L.lamg_strerror.restype = C.c_char_p
+        L.lamg_strerror.argtypes = [C.c_int]
+        L.lamg_setup.argtypes = [C.POINTER(Graph), C.POINTER(Options), C.POINTER(P)]
+        L.lamg_import.argtypes = [C.POINTER(LevelDesc), C.c_int32, C.POINTER(Options), C.POINTER(P)]
+        L.lamg_solve.argtypes = [P, P, P, C.POINTER(SolveOpts), C.POINTER(Stats)]
+        L.lamg_solve_batch.argtypes = [P, C.c_int32, P, P, C.POINTER(SolveOpts), P]
+        L.lamg_cycle.argtypes = [P, P, P, C.c_uint32]
+        L.lamg_hier_info.argtypes = [P, C.POINTER(C.c_int64), P, P]
+        L.lamg_level_get.argtypes = [P, C.c_int32, C.c_char_p, P, C.POINTER(C.c_int64)]
+        L.lamg_destroy.argtypes = [P]
+        L.lamg_destroy.restype = None
+        L.lamg_testvectors.argtypes = [C.c_int64, P, P, P, P, P, C.c_int32, C.c_uint64, C.c_int32,
+                                       C.c_int32, P]
+        L.lamg_affinity.argtypes = [C.c_int64, P, P, P, P, C.c_int32, C.c_double, P, P]
+        L.lamg_time_kernel.argtypes = [P, C.c_int32, C.c_int32, C.c_int32, P]
+        _lib = L
+    return _lib
+
+
+def _strerror(code: int) -> str:
+    try:
+        return lib().lamg_strerror(code).decode()
+    except Exception:  # noqa: BLE001 - only used inside error formatting
+        return "?"
+
+
+def _check(rc: int, where: str, allow=(LAMG_OK,)):
+    if rc not in allow:
+        raise LamgError(rc, where)
+    return rc
+
+
+def _p(a):
+    return None if a is None else a.ctypes.data_as(C.c_void_p)
+
+
+def _c(a, dt):
+    return np.ascontiguousarray(a, dtype=dt)
+
+
+def options(**kw) -> Options:
+    o = Options()
+    lib().lamg_options_default(C.byref(o))
+    for k, v in kw.items():
+        if not hasattr(o, k):
+            raise KeyError(k)
+        setattr(o, k, v)
+    return o
+
+
+class Hierarchy:
+    """A device-resident LAMG+ hierarchy (from ``setup`` or ``import_levels``)."""
+
+    def __init__(self, handle, keep=None):
+        self._h = handle
+        self._keep = keep
+        n = C.c_int64()
+        _check(lib().lamg_hier_info(self._h, C.byref(n), None, None), "lamg_hier_info")
+        self.nlevels = int(n.value)
+        meta = np.zeros(7 * self.nlevels, np.int64)
+        gam = np.zeros(self.nlevels)
+        lib().lamg_hier_info(self._h, C.byref(n), _p(meta), _p(gam))
+        meta = meta.reshape(-1, 7)
+        self.info = [dict(kind=KIND_NAMES[int(m[0])], n=int(m[1]), nnz=int(m[2]), ncol=int(m[3]),
+                          nc=int(m[4]), n_caliber2=int(m[5]), gamma=float(g))
+                     for m, g in zip(meta, gam)]
+        self.n = self.info[0]["n"]
+
+    def close(self):
+        if self._h:
+            lib().lamg_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:  # noqa: BLE001 - interpreter shutdown
+            pass
+
+    def array(self, level: int, name: str):
+        cnt = C.c_int64()
+        _check(lib().lamg_level_get(self._h, level, name.encode(), None, C.byref(cnt)), "lamg_level_get")
+        dt = {"rp": np.int64, "ci": np.int32, "val": np.float64, "diag": np.float64,
+              "colour": np.int32, "cidx": np.int32, "agg": np.int32, "agg2": np.int32,
+              "wt": np.float64, "X": np.float64, "aff": np.float64, "strong": np.uint8,
+              "pinv": np.float64}[name]
+        out = np.zeros(cnt.value, dt)
+        if cnt.value:
+            lib().lamg_level_get(self._h, level, name.encode(), _p(out), C.byref(cnt))
+        return out
+
+    def solve(self, b, tol: float = 1e-8, maxit: int = 100, allow_unconverged: bool = False):
+        """Host-pointer solve; returns (phi, stats dict with the residual history)."""
+        b = _c(b, np.float64)
+        if b.shape != (self.n,):
+            raise ValueError("b has the wrong shape")
+        phi = np.zeros(self.n)
+        hist = np.zeros(maxit + 1)
+        so = SolveOpts(tol, maxit, 0, None)
+        st = Stats()
+        st.hist = hist.ctypes.data
+        rc = lib().lamg_solve(self._h, _p(b), _p(phi), C.byref(so), C.byref(st))
+        _check(rc, "lamg_solve", (LAMG_OK, 5) if allow_unconverged else (LAMG_OK,))
+        return phi, _stats(st, hist)
+
+    def solve_ptr(self, b_ptr: int, phi_ptr: int, tol: float = 1e-8, maxit: int = 100,
+                  stream: int = 0, device: bool = True, hist: bool = False):
+        """Solve with raw pointers (device pointers when ``device``), e.g. torch ``data_ptr()``."""
+        so = SolveOpts(tol, maxit, DEVICE_PTRS if device else 0, C.c_void_p(stream) if stream else None)
+        st = Stats()
+        h = np.zeros(maxit + 1) if hist else None
+        if h is not None:
+            st.hist = h.ctypes.data
+        rc = lib().lamg_solve(self._h, C.c_void_p(b_ptr), C.c_void_p(phi_ptr), C.byref(so), C.byref(st))
+        _check(rc, "lamg_solve", (LAMG_OK, 5))
+        return _stats(st, h)
+
+    KERNELS = {"resid": 0, "gs_sweep": 1, "spmv_dot": 2, "restrict": 3, "prolong": 4}
+
+    def time_kernel(self, which: str, level: int, reps: int = 20) -> dict:
+        """Cold-L2 device time of one kernel (``KERNELS``) and its algorithmic bytes."""
+        out = np.zeros(3)
+        _check(lib().lamg_time_kernel(self._h, self.KERNELS[which], level, reps, _p(out)),
+               "lamg_time_kernel")
+        return dict(ms=float(out[0]), bytes=float(out[1]), launches=int(out[2]),
+                    gbs=float(out[1]) / (float(out[0]) * 1e-3) / 1e9)
+
+    def cycle(self, r):
+        r = _c(r, np.float64)
+        z = np.zeros(self.n)
+        _check(lib().lamg_cycle(self._h, _p(r), _p(z), 0), "lamg_cycle")
+        return z
+
+
+def _stats(st: Stats, hist) -> dict:
+    d = dict(iters=st.iters, nlevels=st.nlevels, relres=st.relres, relres_true=st.relres_true,
+             b_mean=st.b_mean, solve_ms=st.solve_ms)
+    if hist is not None:
+        d["hist"] = hist[: st.iters + 1].copy()
+    return d
+
+
+def setup(g, **opts) -> Hierarchy:
+    """lamg_setup on a ``graphgen.Graph``-like object (n, rp, ci, w)."""
+    rp, ci, w = _c(g.rp, np.int64), _c(g.ci, np.int32), _c(g.w, np.float64)
+    G = Graph(g.n, rp.ctypes.data, ci.ctypes.data, w.ctypes.data)
+    o = options(**opts)
+    h = C.c_void_p()
+    _check(lib().lamg_setup(C.byref(G), C.byref(o), C.byref(h)), "lamg_setup")
+    return Hierarchy(h)
+
+
+def import_levels(levels: list, **opts) -> Hierarchy:
+    """lamg_import from level dicts with keys kind ('elim'|'agg'|'coarsest'), n, rp, ci, val,
+    diag and, per kind, colour/nc/agg/agg2/wt/gamma or nc/cidx (natural numbering)."""
+    keep = []
+    descs = (LevelDesc * len(levels))()
+    for d, L in zip(descs, levels):
+        def arr(name, dt):
+            if name not in L or L[name] is None:
+                return None
+            a = _c(L[name], dt)
+            keep.append(a)
+            return a.ctypes.data
+        d.kind = KINDS[L["kind"]]
+        d.n = int(L["n"])
+        d.rp = arr("rp", np.int64); d.ci = arr("ci", np.int32)
+        d.val = arr("val", np.float64); d.diag = arr("diag", np.float64)
+        d.colour = arr("colour", np.int32)
+        d.nc = int(L.get("nc", 0) or 0)
+        d.cidx = arr("cidx", np.int32)
+        d.agg = arr("agg", np.int32); d.agg2 = arr("agg2", np.int32); d.wt = arr("wt", np.float64)
+        d.gamma = float(L.get("gamma", 0.0) or 0.0)
+    o = options(**opts)
+    h = C.c_void_p()
+    _check(lib().lamg_import(descs, len(levels), C.byref(o), C.byref(h)), "lamg_import")
+    return Hierarchy(h, keep)
+
+
+def testvectors(rp, ci, val, diag, colour, level: int, seed: int, K: int = 4, nu: int = 3):
+    rp, ci = _c(rp, np.int64), _c(ci, np.int32)
+    val, diag, colour = _c(val, np.float64), _c(diag, np.float64), _c(colour, np.int32)
+    n = len(diag)
+    X = np.zeros((n, K))
+    _check(lib().lamg_testvectors(n, _p(rp), _p(ci), _p(val), _p(diag), _p(colour), level, seed, K,
+                                  nu, _p(X)), "lamg_testvectors")
+    return X
+
+
+def affinity(rp, ci, val, X, tau: float = 0.05):
+    rp, ci, val = _c(rp, np.int64), _c(ci, np.int32), _c(val, np.float64)
+    X = _c(X, np.float64)
+    n, K = X.shape
+    aff = np.zeros(len(ci)); strong = np.zeros(len(ci), np.uint8)
+    _check(lib().lamg_affinity(n, _p(rp), _p(ci), _p(val), _p(X), K, tau, _p(aff), _p(strong)),
+           "lamg_affinity")
+    return aff, strong
+
+
+EXPORTS = ["lamg_options_default", "lamg_setup", "lamg_import", "lamg_solve", "lamg_solve_batch",
+           "lamg_cycle", "lamg_hier_info", "lamg_level_get", "lamg_destroy", "lamg_testvectors",
+           "lamg_affinity", "lamg_strerror", "lamg_server_create", "lamg_serve", "lamg_serve_poll",
+           "lamg_server_drain", "lamg_server_destroy", "lamg_time_kernel"]

@@ -1,0 +1,95 @@
+// Device-side hierarchy layout and the kernel launchers shared by the solver.
+#pragma once
+
+#include <cstdint>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+namespace lamg {
+
+// One level in device order. Device order of a level:
+//  - aggregation level: rows grouped by Gauss-Seidel colour (colour 0 first), ascending
+//    natural id within a colour, so each colour class is a contiguous row range;
+//  - elimination level: the kept (C) nodes first, in the next level's device order, then
+//    the eliminated (F) nodes in ascending natural id. The first nc entries of the level's
+//    iterate are therefore the next level's iterate, and share its memory;
+//  - coarsest level: natural order.
+struct DevLevel {
+    int kind = 0;
+    int64_t n = 0, nnz = 0, nc = 0, nF = 0;
+    int ncol = 0;
+    int tpr = 1;                  // threads per row of the CSR kernels
+    std::vector<int64_t> cptr;    // colour class row ranges (aggregation)
+    std::vector<int32_t> perm;    // device index -> natural id
+
+    // operator: off-diagonal CSR + diagonal (FP64), int32 row pointers
+    int32_t *rp = nullptr, *ci = nullptr;
+    double *val = nullptr, *diag = nullptr;
+    // aggregation: P rows (coarse device ids) and P^T as CSR over coarse rows
+    int32_t *agg = nullptr, *agg2 = nullptr;
+    double *wt = nullptr;
+    int32_t *pt_ptr = nullptr, *pt_row = nullptr;
+    double *pt_w = nullptr;
+    int pt_tpr = 1;
+    // elimination: F rows as ELL-4 (coarse columns < nc, -1 padding), P_F^T over C rows
+    int32_t *pf_col = nullptr;
+    double *pf_val = nullptr, *dF = nullptr;
+    int32_t *pft_ptr = nullptr, *pft_f = nullptr;
+    double *pft_val = nullptr;
+    // coarsest: dense pseudo-inverse, row-major
+    double *pinv = nullptr;
+    // iterate, right-hand side, residual
+    double *x = nullptr, *b = nullptr, *r = nullptr;
+    size_t bytes = 0;
+};
+
+enum OpKind {
+    OP_GS_FIRST,      // colour-0 rows x = b / d, every other row x = 0 (first visit, x == 0)
+    OP_GS,            // one colour class of a Gauss-Seidel sweep
+    OP_ZERO,          // x = 0 (first visit without pre-smoothing)
+    OP_RESID,         // r = b - A x
+    OP_RESTRICT,      // b_{l+1} = P^T r
+    OP_PROLONG,       // x += P x_{l+1}
+    OP_ELIM_RESTRICT, // b_{l+1} = b_C + P_F^T b_F
+    OP_ELIM_INTERP,   // x_F = P_F x_C + b_F / d_F
+    OP_COARSE,        // x = A^+ b, then the mean-zero projection
+};
+
+struct Op {
+    int kind;
+    int level;
+    int colour;
+};
+
+// Reduction workspace: per-block partial sums, a completion ticket, device scalars.
+constexpr int RED_MAXG = 1184;   // 148 SMs x 8 blocks
+constexpr int RED_NV = 4;
+enum Scalar { S_RZ = 0, S_PQ, S_ALPHA, S_BETA, S_RR, S_BN2, S_MEAN, S_TRUE_RR, S_BMEAN, S_COUNT = 16 };
+
+struct Reduce {
+    double *partials = nullptr;   // RED_NV x RED_MAXG
+    unsigned *ticket = nullptr;
+    double *scal = nullptr;       // S_COUNT
+};
+
+// launchers (cycle_kernels.cu)
+void launch_op(const Op &op, std::vector<DevLevel> &lv, const Reduce &red, cudaStream_t s);
+void launch_gather(int64_t n, const int32_t *perm, const double *src, double *dst, cudaStream_t s);
+void launch_scatter(int64_t n, const int32_t *perm, const double *src, double *dst, cudaStream_t s);
+void launch_sum(int64_t n, const double *v, const Reduce &red, cudaStream_t s);  // S_MEAN = sum / n
+void launch_sub_mean(int64_t n, double *v, const Reduce &red, cudaStream_t s);
+void launch_init_b(int64_t n, double *r, double *bkeep, double *x, double *p, double *zold,
+                   const Reduce &red, cudaStream_t s);
+void launch_spmv_dot(const DevLevel &L, const double *p, double *q, const Reduce &red, cudaStream_t s);
+void launch_update_xr(int64_t n, double *x, double *r, const double *p, const double *q,
+                      const Reduce &red, cudaStream_t s);
+void launch_proj_dots(int64_t n, double *z, const double *zold, const double *r, const Reduce &red,
+                      cudaStream_t s);
+void launch_update_p(int64_t n, const double *z, double *p, double *zold, const Reduce &red,
+                     cudaStream_t s);
+void launch_true_resid(const DevLevel &L, const double *x, const double *b, const Reduce &red,
+                       cudaStream_t s);
+int choose_tpr(double avg_row);
+
+}  // namespace lamg

@@ -1,0 +1,68 @@
+// Internal declarations of the B300 LAMG+ library (not part of the public ABI).
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "lamg.h"
+
+namespace lamg {
+
+enum LevelKind { KIND_ELIM = 0, KIND_AGG = 1, KIND_COARSEST = 2 };
+
+// Level operator on the host: off-diagonal CSR (columns ascending) + diagonal.
+struct HostMat {
+    int64_t n = 0;
+    std::vector<int64_t> rp;
+    std::vector<int32_t> ci;
+    std::vector<double> val;
+    std::vector<double> diag;
+    int64_t nnz() const { return (int64_t)ci.size(); }
+};
+
+// One level of the hierarchy in the caller's (natural) numbering.
+struct HostLevel {
+    int kind = KIND_COARSEST;
+    HostMat A;
+    std::vector<int32_t> colour;  // aggregation levels
+    int ncol = 0;
+    int64_t nc = 0;               // coarse size (elimination: |C|, aggregation: aggregates)
+    std::vector<int32_t> cidx;    // elimination: coarse index or -1
+    std::vector<int32_t> agg, agg2;
+    std::vector<double> wt;
+    std::vector<double> X;        // test vectors n x K (lamg_setup only)
+    std::vector<double> aff;      // per off-diagonal entry (lamg_setup only)
+    std::vector<uint8_t> strong;  // per off-diagonal entry (lamg_setup only)
+    std::vector<double> pinv;     // coarsest: dense pseudo-inverse
+    double gamma = 0.0;
+};
+
+struct Status {
+    int code = LAMG_OK;
+    std::string msg;
+};
+
+// host setup (setup_host.cpp)
+int validate_graph(const lamg_graph *g);
+int build_hierarchy(const lamg_graph *g, const lamg_options &o, std::vector<HostLevel> &levels);
+int greedy_colour(const HostMat &A, std::vector<int32_t> &colour);
+int dense_pinv(const HostMat &A, std::vector<double> &pinv);
+double cycle_index(int64_t El, int64_t El1, int64_t E0);
+
+// GPU setup kernels (setup_kernels.cu): K test vectors by colour-ordered GS on A x = 0 and
+// the affinity / veto pass. All pointers are host pointers; the functions manage device
+// copies themselves. X is n x K row-major.
+int gpu_testvectors(const HostMat &A, const std::vector<int32_t> &colour, int level,
+                    uint64_t seed, int K, int nu, double *X);
+int gpu_affinity(const HostMat &A, const double *X, int K, double tau, double *aff,
+                 uint8_t *strong);
+int gpu_tv_and_affinity(const HostMat &A, const std::vector<int32_t> &colour, int level,
+                        uint64_t seed, int K, int nu, double tau, int veto, double *X,
+                        double *aff, uint8_t *strong);
+
+int cuda_status(cudaError_t e);
+
+}  // namespace lamg

@@ -1,0 +1,477 @@
+// Host side of the LAMG+ setup (Section 2): input validation, the Laplacian, low-degree
+// elimination (Eq. 2), guarded aggregation (Eqs. 3-4, Appendix B) with the veto (Eq. 9),
+// selective caliber-2 (Section 3.2, Eq. 13), Galerkin coarse operators, colouring, the
+// cycle index of Eq. 5 and the dense coarsest pseudo-inverse. The test vectors and the
+// affinity / veto pass run on the GPU (setup_kernels.cu).
+//
+// Floating-point expressions are evaluated left to right without contraction (the file is
+// compiled with -ffp-contract=off), so that decisions taken from them (guard admissibility,
+// affinity maxima, caliber-2 gates) are reproducible.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <numeric>
+
+#include "internal.h"
+
+namespace lamg {
+
+int validate_graph(const lamg_graph *g) {
+    if (!g || g->n < 1 || !g->rp || (g->rp[g->n] > 0 && (!g->ci || !g->w))) return LAMG_ERR_INVALID;
+    const int64_t n = g->n;
+    if (n >= (int64_t)INT32_MAX) return LAMG_ERR_INVALID;
+    if (g->rp[0] != 0) return LAMG_ERR_INVALID;
+    for (int64_t u = 0; u < n; u++) {
+        if (g->rp[u + 1] < g->rp[u]) return LAMG_ERR_INVALID;
+        for (int64_t e = g->rp[u]; e < g->rp[u + 1]; e++) {
+            int32_t v = g->ci[e];
+            if (v < 0 || v >= n || v == u) return LAMG_ERR_INVALID;
+            if (e > g->rp[u] && v <= g->ci[e - 1]) return LAMG_ERR_INVALID;
+            double w = g->w[e];
+            if (!(w > 0.0) || !std::isfinite(w)) return LAMG_ERR_INVALID;
+        }
+    }
+    for (int64_t u = 0; u < n; u++) {
+        for (int64_t e = g->rp[u]; e < g->rp[u + 1]; e++) {
+            int32_t v = g->ci[e];
+            const int32_t *b = g->ci + g->rp[v], *end = g->ci + g->rp[v + 1];
+            const int32_t *f = std::lower_bound(b, end, (int32_t)u);
+            if (f == end || *f != u) return LAMG_ERR_INVALID;
+            if (g->w[g->rp[v] + (f - b)] != g->w[e]) return LAMG_ERR_INVALID;
+        }
+    }
+    // connectivity (breadth-first search from node 0)
+    std::vector<int32_t> queue(n);
+    std::vector<uint8_t> seen(n, 0);
+    int64_t head = 0, tail = 0;
+    queue[tail++] = 0;
+    seen[0] = 1;
+    while (head < tail) {
+        int32_t u = queue[head++];
+        for (int64_t e = g->rp[u]; e < g->rp[u + 1]; e++) {
+            int32_t v = g->ci[e];
+            if (!seen[v]) { seen[v] = 1; queue[tail++] = v; }
+        }
+    }
+    if (tail != n) return LAMG_ERR_DISCONNECTED;
+    return LAMG_OK;
+}
+
+// L = D - W (Eq. 1).
+static void laplacian(const lamg_graph *g, HostMat &A) {
+    const int64_t n = g->n, z = g->rp[n];
+    A.n = n;
+    A.rp.assign(g->rp, g->rp + n + 1);
+    A.ci.assign(g->ci, g->ci + z);
+    A.val.resize(z);
+    A.diag.assign(n, 0.0);
+    for (int64_t u = 0; u < n; u++) {
+        double d = 0.0;
+        for (int64_t e = g->rp[u]; e < g->rp[u + 1]; e++) {
+            A.val[e] = -g->w[e];
+            d += g->w[e];
+        }
+        A.diag[u] = d;
+    }
+}
+
+// Greedy colouring: nodes in ascending order take the smallest colour not used by an
+// already-coloured neighbour.
+int greedy_colour(const HostMat &A, std::vector<int32_t> &colour) {
+    const int64_t n = A.n;
+    colour.assign(n, -1);
+    std::vector<int64_t> used;  // used[c] == u+1 when colour c is taken around u
+    int ncol = 0;
+    for (int64_t u = 0; u < n; u++) {
+        for (int64_t e = A.rp[u]; e < A.rp[u + 1]; e++) {
+            int32_t c = colour[A.ci[e]];
+            if (c < 0) continue;
+            if ((int64_t)used.size() <= c) used.resize(c + 1, 0);
+            used[c] = u + 1;
+        }
+        int c = 0;
+        while (c < (int)used.size() && used[c] == u + 1) c++;
+        colour[u] = c;
+        ncol = std::max(ncol, c + 1);
+    }
+    return ncol;
+}
+
+// ----------------------------------------------------------------------------------- elimination
+
+// F: greedy maximal independent set of the nodes of degree <= dmax, ascending order (Eq. 2).
+static int64_t pick_F(const HostMat &A, int dmax, std::vector<uint8_t> &inF) {
+    const int64_t n = A.n;
+    inF.assign(n, 0);
+    std::vector<uint8_t> nbrF(n, 0);
+    int64_t cnt = 0;
+    for (int64_t u = 0; u < n; u++) {
+        if (A.rp[u + 1] - A.rp[u] > dmax || nbrF[u]) continue;
+        inF[u] = 1;
+        cnt++;
+        for (int64_t e = A.rp[u]; e < A.rp[u + 1]; e++) nbrF[A.ci[e]] = 1;
+    }
+    return cnt;
+}
+
+// Sparse accumulator for one output row.
+struct RowAcc {
+    std::vector<double> v;
+    std::vector<int64_t> stamp;
+    std::vector<int32_t> cols;
+    int64_t cur = -1;
+    explicit RowAcc(int64_t n) : v(n, 0.0), stamp(n, -1) {}
+    void start(int64_t row) { cur = row; cols.clear(); }
+    double &at(int32_t j) {
+        if (stamp[j] != cur) { stamp[j] = cur; v[j] = 0.0; cols.push_back(j); }
+        return v[j];
+    }
+};
+
+// Exact Schur complement onto C (Eq. 2); C keeps ascending node order.
+static void schur(const HostMat &A, const std::vector<uint8_t> &inF, HostLevel &L, HostMat &Ac) {
+    const int64_t n = A.n;
+    L.cidx.assign(n, -1);
+    int64_t nc = 0;
+    for (int64_t u = 0; u < n; u++)
+        if (!inF[u]) L.cidx[u] = (int32_t)nc++;
+    L.nc = nc;
+    Ac.n = nc;
+    Ac.rp.assign(nc + 1, 0);
+    Ac.diag.assign(nc, 0.0);
+    Ac.ci.clear();
+    Ac.val.clear();
+    Ac.ci.reserve(A.nnz());
+    Ac.val.reserve(A.nnz());
+    RowAcc acc(nc);
+    int64_t i = 0;
+    for (int64_t u = 0; u < n; u++) {
+        if (inF[u]) continue;
+        acc.start(i);
+        double d = A.diag[u];
+        for (int64_t e = A.rp[u]; e < A.rp[u + 1]; e++) {
+            const int32_t v = A.ci[e];
+            if (!inF[v]) {
+                acc.at(L.cidx[v]) += A.val[e];
+                continue;
+            }
+            const double avv = A.diag[v], auv = A.val[e];
+            for (int64_t f = A.rp[v]; f < A.rp[v + 1]; f++) {
+                const int32_t t = A.ci[f];
+                const double term = auv * A.val[f] / avv;
+                if (t == u) d -= term;
+                else acc.at(L.cidx[t]) -= term;
+            }
+        }
+        std::sort(acc.cols.begin(), acc.cols.end());
+        for (int32_t j : acc.cols) {
+            if (acc.v[j] == 0.0) continue;
+            Ac.ci.push_back(j);
+            Ac.val.push_back(acc.v[j]);
+        }
+        Ac.diag[i] = d;
+        Ac.rp[i + 1] = (int64_t)Ac.ci.size();
+        i++;
+    }
+}
+
+// ----------------------------------------------------------------------------------- aggregation
+
+enum { UNDECIDED = 0, SEED = 1, ASSOCIATE = 2 };
+
+// Energy ratio of Eq. 4 from the moments of Appendix B: per column k,
+// relaxed = (s2 - s1^2/s0)/2, forced = (xs^2 s0 - 2 xs s1 + s2)/2, ratio = forced / relaxed,
+// maximised over k. The paper divides by the relaxed energy, which vanishes for a node with a
+// single neighbour; a relaxed energy <= guard_eps * scale, scale = (|s2| + s1^2/|s0|)/2, counts
+// as zero, and the ratio is then 1 if the forced energy is also <= guard_eps * scale, else
+// infinite.
+static double energy_ratio(double s0, const double *s1, const double *s2, const double *xs,
+                           int K, double eps) {
+    double worst = 0.0;
+    for (int k = 0; k < K; k++) {
+        const double relaxed = 0.5 * (s2[k] - s1[k] * s1[k] / s0);
+        const double forced = 0.5 * (xs[k] * xs[k] * s0 - 2.0 * xs[k] * s1[k] + s2[k]);
+        const double scale = 0.5 * (std::fabs(s2[k]) + s1[k] * s1[k] / std::fabs(s0));
+        double r;
+        if (relaxed <= eps * scale) r = (forced <= eps * scale) ? 1.0 : INFINITY;
+        else r = forced / relaxed;
+        worst = std::max(worst, r);
+    }
+    return worst;
+}
+
+// Greedy guarded aggregation in ascending node order; candidates of an undecided node are its
+// strong (non-vetoed) neighbours that are seeds or undecided, admissible when the energy
+// ratio is <= Q; the node joins the admissible candidate of largest affinity (ties to the
+// lower id), which becomes a seed. Leftover undecided nodes are singleton seeds. Aggregates
+// are numbered by ascending seed.
+static void aggregate(HostLevel &L, const lamg_options &o, std::vector<int32_t> &status,
+                      std::vector<int32_t> &seed) {
+    const HostMat &A = L.A;
+    const int64_t n = A.n;
+    const int K = o.K;
+    std::vector<double> s0(n, 0.0), s1(n * K, 0.0), s2(n * K, 0.0);
+    for (int64_t u = 0; u < n; u++) {
+        for (int64_t e = A.rp[u]; e < A.rp[u + 1]; e++) {
+            const double w = -A.val[e];
+            const double *xv = &L.X[(int64_t)A.ci[e] * K];
+            s0[u] += w;
+            for (int k = 0; k < K; k++) {
+                s1[u * K + k] += w * xv[k];
+                s2[u * K + k] += w * xv[k] * xv[k];
+            }
+        }
+    }
+    status.assign(n, UNDECIDED);
+    seed.assign(n, -1);
+    for (int64_t u = 0; u < n; u++) {
+        if (status[u] != UNDECIDED) continue;
+        int32_t pick = -1;
+        double pick_aff = -1.0;
+        for (int64_t e = A.rp[u]; e < A.rp[u + 1]; e++) {
+            const int32_t s = A.ci[e];
+            if (!L.strong[e] || status[s] == ASSOCIATE) continue;
+            const double q = energy_ratio(s0[u], &s1[u * K], &s2[u * K], &L.X[(int64_t)s * K], K,
+                                          o.guard_eps);
+            if (!(q <= o.Q)) continue;
+            const double c = L.aff[e];
+            if (c > pick_aff || (c == pick_aff && s < pick)) { pick_aff = c; pick = s; }
+        }
+        if (pick < 0) continue;
+        if (status[pick] == UNDECIDED) { status[pick] = SEED; seed[pick] = pick; }
+        status[u] = ASSOCIATE;
+        seed[u] = pick;
+    }
+    for (int64_t u = 0; u < n; u++)
+        if (status[u] == UNDECIDED) { status[u] = SEED; seed[u] = (int32_t)u; }
+    std::vector<int32_t> id(n, -1);
+    int64_t nc = 0;
+    for (int64_t u = 0; u < n; u++)
+        if (status[u] == SEED) id[u] = (int32_t)nc++;
+    L.nc = nc;
+    L.agg.resize(n);
+    L.agg2.assign(n, -1);
+    L.wt.assign(n, 1.0);
+    for (int64_t u = 0; u < n; u++) L.agg[u] = id[seed[u]];
+}
+
+// Selective caliber-2 (Section 3.2, Eq. 13): a non-seed node whose strong edges reach exactly
+// one aggregate b besides its own a gets phi_u = w phi_a + (1-w) phi_b with the least-squares
+// weight over the test vectors taken at the two seeds, snapped to 0/1 within `snap`, kept
+// iff 0 <= w < 1.
+static void upgrade_caliber2(HostLevel &L, const lamg_options &o, const std::vector<int32_t> &status,
+                             const std::vector<int32_t> &seed) {
+    const HostMat &A = L.A;
+    const int K = o.K;
+    for (int64_t u = 0; u < A.n; u++) {
+        if (status[u] != ASSOCIATE) continue;
+        const int32_t a = L.agg[u];
+        int32_t b = -1, sb = -1;
+        bool more = false;
+        for (int64_t e = A.rp[u]; e < A.rp[u + 1] && !more; e++) {
+            if (!L.strong[e]) continue;
+            const int32_t v = A.ci[e];
+            const int32_t gv = L.agg[v];
+            if (gv == a) continue;
+            if (b < 0) { b = gv; sb = seed[v]; }
+            else if (gv != b) more = true;
+        }
+        if (more || b < 0) continue;
+        const double *xu = &L.X[u * K];
+        const double *xa = &L.X[(int64_t)seed[u] * K];
+        const double *xb = &L.X[(int64_t)sb * K];
+        double num = 0.0, den = 0.0;
+        for (int k = 0; k < K; k++) {
+            const double d = xa[k] - xb[k], e = xu[k] - xb[k];
+            num += d * e;
+            den += d * d;
+        }
+        if (!(den > 0.0)) continue;
+        double w = num / den;
+        if (std::fabs(w) <= o.snap) w = 0.0;
+        if (std::fabs(w - 1.0) <= o.snap) w = 1.0;
+        if (!(w >= 0.0 && w < 1.0)) continue;
+        L.agg2[u] = b;
+        L.wt[u] = w;
+    }
+}
+
+// Entries of P's row u.
+static inline int p_row(const HostLevel &L, int64_t u, int32_t *col, double *p) {
+    if (L.agg2[u] < 0) { col[0] = L.agg[u]; p[0] = 1.0; return 1; }
+    int k = 0;
+    if (L.wt[u] != 0.0) { col[k] = L.agg[u]; p[k] = L.wt[u]; k++; }
+    col[k] = L.agg2[u];
+    p[k] = 1.0 - L.wt[u];
+    return k + 1;
+}
+
+// Galerkin coarse operator P^T A P, one coarse row at a time over the fine rows that
+// interpolate from it (fine rows ascending).
+static void galerkin(const HostLevel &L, HostMat &Ac) {
+    const HostMat &A = L.A;
+    const int64_t n = A.n, nc = L.nc;
+    std::vector<int64_t> ptr(nc + 1, 0);
+    for (int64_t u = 0; u < n; u++) {
+        int32_t c[2]; double p[2];
+        int k = p_row(L, u, c, p);
+        for (int t = 0; t < k; t++) ptr[c[t] + 1]++;
+    }
+    for (int64_t a = 0; a < nc; a++) ptr[a + 1] += ptr[a];
+    std::vector<int32_t> rows(ptr[nc]);
+    std::vector<double> pw(ptr[nc]);
+    std::vector<int64_t> pos(ptr.begin(), ptr.end() - 1);
+    for (int64_t u = 0; u < n; u++) {
+        int32_t c[2]; double p[2];
+        int k = p_row(L, u, c, p);
+        for (int t = 0; t < k; t++) { rows[pos[c[t]]] = (int32_t)u; pw[pos[c[t]]] = p[t]; pos[c[t]]++; }
+    }
+    Ac.n = nc;
+    Ac.rp.assign(nc + 1, 0);
+    Ac.diag.assign(nc, 0.0);
+    Ac.ci.clear();
+    Ac.val.clear();
+    RowAcc acc(nc);
+    for (int64_t a = 0; a < nc; a++) {
+        acc.start(a);
+        for (int64_t t = ptr[a]; t < ptr[a + 1]; t++) {
+            const int64_t u = rows[t];
+            const double pa = pw[t];
+            int32_t c[2]; double p[2];
+            int k = p_row(L, u, c, p);
+            for (int s = 0; s < k; s++) acc.at(c[s]) += pa * A.diag[u] * p[s];
+            for (int64_t e = A.rp[u]; e < A.rp[u + 1]; e++) {
+                k = p_row(L, A.ci[e], c, p);
+                for (int s = 0; s < k; s++) acc.at(c[s]) += pa * A.val[e] * p[s];
+            }
+        }
+        std::sort(acc.cols.begin(), acc.cols.end());
+        double d = 0.0;
+        for (int32_t j : acc.cols) {
+            if (j == a) { d = acc.v[j]; continue; }
+            if (acc.v[j] == 0.0) continue;
+            Ac.ci.push_back(j);
+            Ac.val.push_back(acc.v[j]);
+        }
+        Ac.diag[a] = d;
+        Ac.rp[a + 1] = (int64_t)Ac.ci.size();
+    }
+}
+
+// ----------------------------------------------------------------------------------- coarsest
+
+// A^+ = (A + J/n)^{-1} - J/n for a connected Laplacian-like operator (null space span{1}),
+// through a Cholesky factorisation of A + J/n.
+int dense_pinv(const HostMat &A, std::vector<double> &pinv) {
+    const int64_t n = A.n;
+    std::vector<double> M(n * n, 1.0 / (double)n);
+    for (int64_t i = 0; i < n; i++) {
+        M[i * n + i] += A.diag[i];
+        for (int64_t e = A.rp[i]; e < A.rp[i + 1]; e++) M[i * n + A.ci[e]] += A.val[e];
+    }
+    // lower Cholesky factor G (row-major, in place): M = G G^T
+    for (int64_t j = 0; j < n; j++) {
+        double s = M[j * n + j];
+        for (int64_t k = 0; k < j; k++) s -= M[j * n + k] * M[j * n + k];
+        if (!(s > 0.0)) return LAMG_ERR_DISCONNECTED;
+        const double gjj = std::sqrt(s);
+        M[j * n + j] = gjj;
+        for (int64_t i = j + 1; i < n; i++) {
+            double t = M[i * n + j];
+            for (int64_t k = 0; k < j; k++) t -= M[i * n + k] * M[j * n + k];
+            M[i * n + j] = t / gjj;
+        }
+    }
+    // inverse of G (lower triangular), then M^{-1} = G^{-T} G^{-1}
+    std::vector<double> Gi(n * n, 0.0);
+    for (int64_t c = 0; c < n; c++) {
+        Gi[c * n + c] = 1.0 / M[c * n + c];
+        for (int64_t i = c + 1; i < n; i++) {
+            double t = 0.0;
+            for (int64_t k = c; k < i; k++) t -= M[i * n + k] * Gi[k * n + c];
+            Gi[i * n + c] = t / M[i * n + i];
+        }
+    }
+    pinv.assign(n * n, 0.0);
+    for (int64_t i = 0; i < n; i++) {
+        for (int64_t j = 0; j <= i; j++) {
+            double s = 0.0;
+            for (int64_t k = i; k < n; k++) s += Gi[k * n + i] * Gi[k * n + j];
+            pinv[i * n + j] = s - 1.0 / (double)n;
+            pinv[j * n + i] = pinv[i * n + j];
+        }
+    }
+    return LAMG_OK;
+}
+
+// Eq. 5 with the reading that gamma is clamped to [1, 2].
+double cycle_index(int64_t El, int64_t El1, int64_t E0) {
+    if ((double)El > 0.1 * (double)E0) return 1.5;
+    double g = 2.0;
+    if (El > 0 && El1 > 0) g = std::min(2.0, 0.7 / ((double)El1 / (double)El));
+    return std::max(1.0, g);
+}
+
+// ----------------------------------------------------------------------------------- driver
+
+int build_hierarchy(const lamg_graph *g, const lamg_options &o, std::vector<HostLevel> &levels) {
+    int rc = validate_graph(g);
+    if (rc) return rc;
+    if (o.K < 1 || o.K > 16 || o.nu_tv < 0 || o.coarsest_max < 1 || o.max_levels < 1)
+        return LAMG_ERR_INVALID;
+    levels.clear();
+    HostMat A;
+    laplacian(g, A);
+    const int64_t E0 = A.nnz() / 2;
+    for (int l = 0;; l++) {
+        levels.emplace_back();
+        HostLevel &L = levels.back();
+        L.A = std::move(A);
+        const int64_t n = L.A.n;
+        if (n <= o.coarsest_max || l + 1 >= o.max_levels) {
+            L.kind = KIND_COARSEST;
+            break;
+        }
+        std::vector<uint8_t> inF;
+        const int64_t nF = pick_F(L.A, o.dmax, inF);
+        HostMat Ac;
+        if (nF > 0 && (double)nF >= o.elim_min_frac * (double)n) {
+            L.kind = KIND_ELIM;
+            schur(L.A, inF, L, Ac);
+        } else {
+            L.kind = KIND_AGG;
+            L.ncol = greedy_colour(L.A, L.colour);
+            L.X.resize(n * o.K);
+            L.aff.resize(L.A.nnz());
+            L.strong.resize(L.A.nnz());
+            rc = gpu_tv_and_affinity(L.A, L.colour, l, o.seed, o.K, o.nu_tv, o.tau_soc, o.veto,
+                                     L.X.data(), L.aff.data(), L.strong.data());
+            if (rc) return rc;
+            std::vector<int32_t> status, seed;
+            aggregate(L, o, status, seed);
+            if (o.caliber2) upgrade_caliber2(L, o, status, seed);
+            if (L.nc >= n || ((double)L.nc > 0.9 * (double)n && n <= 4096)) {
+                // no useful coarsening: this level becomes the coarsest
+                L.kind = KIND_COARSEST;
+                L.agg.clear(); L.agg2.clear(); L.wt.clear();
+                break;
+            }
+            galerkin(L, Ac);
+        }
+        A = std::move(Ac);
+    }
+    HostLevel &last = levels.back();
+    if (last.A.n > 4096) return LAMG_ERR_SETUP;
+    if (dense_pinv(last.A, last.pinv)) return LAMG_ERR_SETUP;
+    for (size_t l = 0; l < levels.size(); l++) {
+        HostLevel &L = levels[l];
+        if (L.kind == KIND_ELIM) L.gamma = 1.0;
+        else if (L.kind == KIND_AGG)
+            L.gamma = o.gamma_fixed > 0 ? o.gamma_fixed
+                                        : cycle_index(L.A.nnz() / 2, levels[l + 1].A.nnz() / 2, E0);
+        else L.gamma = 0.0;
+    }
+    return LAMG_OK;
+}
+
+}  // namespace lamg

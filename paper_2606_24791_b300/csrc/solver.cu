@@ -1,0 +1,659 @@
+// Device hierarchy, static cycle schedule, CUDA-graph capture and the flexible-CG solve loop,
+// plus the C ABI entry points declared in lamg.h.
+//
+// The cycle of Section 2 is a fixed sequence of kernel launches once the hierarchy is known:
+// the visit counters that realise a fractional cycle index restart at every cycle, so every
+// cycle visits the levels in the same order. The sequence is generated once on the host and
+// captured into CUDA graphs, one for the preconditioner alone and one for the second half of a
+// CG iteration (cycle, projection, search-direction update); the first half (A p, the step,
+// the residual norm) is a third graph whose last node copies the residual norm to pinned host
+// memory for the stopping test.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <thread>
+
+#include "device.h"
+#include "internal.h"
+
+using namespace lamg;
+
+struct lamg_hier {
+    int device = 0;
+    lamg_options opt{};
+    std::vector<HostLevel> host;
+    std::vector<DevLevel> dev;
+    std::vector<Op> ops;
+    cudaStream_t stream = nullptr;
+    // outer CG vectors, device order of level 0
+    double *r = nullptr, *p = nullptr, *q = nullptr, *zold = nullptr, *xs = nullptr, *bkeep = nullptr;
+    double *nat_in = nullptr, *nat_out = nullptr;  // natural-order staging
+    int32_t *perm0 = nullptr;
+    Reduce red;
+    double *h_scal = nullptr;  // pinned
+    cudaGraphExec_t g_cycle = nullptr, g_tail = nullptr, g_head = nullptr;
+    cudaEvent_t ev_a = nullptr, ev_b = nullptr, ev_poll = nullptr;
+    std::vector<void *> allocs;
+    size_t dev_bytes = 0;
+    double wait_timeout_s = 120.0;
+
+    ~lamg_hier() {
+        if (g_cycle) cudaGraphExecDestroy(g_cycle);
+        if (g_tail) cudaGraphExecDestroy(g_tail);
+        if (g_head) cudaGraphExecDestroy(g_head);
+        if (ev_a) cudaEventDestroy(ev_a);
+        if (ev_b) cudaEventDestroy(ev_b);
+        if (ev_poll) cudaEventDestroy(ev_poll);
+        for (void *a : allocs) cudaFree(a);
+        if (h_scal) cudaFreeHost(h_scal);
+        if (stream) cudaStreamDestroy(stream);
+    }
+};
+
+namespace {
+
+#define CKR(x)                                     \
+    do {                                           \
+        cudaError_t e_ = (x);                      \
+        if (e_ != cudaSuccess) return cuda_status(e_); \
+    } while (0)
+
+template <typename T>
+int dalloc(lamg_hier *h, T **p, int64_t count) {
+    size_t bytes = (size_t)std::max<int64_t>(count, 1) * sizeof(T);
+    bytes = (bytes + 255) & ~(size_t)255;
+    void *q = nullptr;
+    cudaError_t e = cudaMalloc(&q, bytes);
+    if (e != cudaSuccess) return cuda_status(e);
+    h->allocs.push_back(q);
+    h->dev_bytes += bytes;
+    *p = (T *)q;
+    return LAMG_OK;
+}
+
+template <typename T>
+int dupload(lamg_hier *h, T **p, const std::vector<T> &v) {
+    int rc = dalloc(h, p, (int64_t)v.size());
+    if (rc) return rc;
+    if (!v.empty()) CKR(cudaMemcpy(*p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice));
+    return LAMG_OK;
+}
+
+// Device orders of all levels, from the coarsest up (see DevLevel).
+void build_orders(lamg_hier *h) {
+    const int L = (int)h->host.size();
+    h->dev.assign(L, DevLevel());
+    for (int l = L - 1; l >= 0; l--) {
+        const HostLevel &H = h->host[l];
+        DevLevel &D = h->dev[l];
+        const int64_t n = H.A.n;
+        D.kind = H.kind;
+        D.n = n;
+        D.nnz = H.A.nnz();
+        D.nc = H.nc;
+        D.perm.resize(n);
+        if (H.kind == KIND_COARSEST) {
+            for (int64_t i = 0; i < n; i++) D.perm[i] = (int32_t)i;
+        } else if (H.kind == KIND_AGG) {
+            int ncol = 0;
+            for (int32_t c : H.colour) ncol = std::max(ncol, c + 1);
+            D.ncol = ncol;
+            D.cptr.assign(ncol + 1, 0);
+            for (int32_t c : H.colour) D.cptr[c + 1]++;
+            for (int c = 0; c < ncol; c++) D.cptr[c + 1] += D.cptr[c];
+            std::vector<int64_t> fill(D.cptr.begin(), D.cptr.end() - 1);
+            for (int64_t u = 0; u < n; u++) D.perm[fill[H.colour[u]]++] = (int32_t)u;
+        } else {
+            std::vector<int32_t> cnode(H.nc);
+            for (int64_t u = 0; u < n; u++)
+                if (H.cidx[u] >= 0) cnode[H.cidx[u]] = (int32_t)u;
+            const std::vector<int32_t> &pc = h->dev[l + 1].perm;
+            for (int64_t i = 0; i < H.nc; i++) D.perm[i] = cnode[pc[i]];
+            int64_t t = H.nc;
+            for (int64_t u = 0; u < n; u++)
+                if (H.cidx[u] < 0) D.perm[t++] = (int32_t)u;
+            D.nF = n - H.nc;
+        }
+    }
+}
+
+int upload_level(lamg_hier *h, int l) {
+    const HostLevel &H = h->host[l];
+    DevLevel &D = h->dev[l];
+    const int64_t n = H.A.n;
+    int rc;
+    std::vector<int32_t> iperm(n);
+    for (int64_t i = 0; i < n; i++) iperm[D.perm[i]] = (int32_t)i;
+    if (H.A.nnz() >= (int64_t)INT32_MAX) return LAMG_ERR_INVALID;
+    // operator in device order, columns ascending
+    std::vector<int32_t> rp(n + 1, 0), ci(H.A.nnz());
+    std::vector<double> val(H.A.nnz()), diag(n);
+    std::vector<std::pair<int32_t, double>> row;
+    for (int64_t i = 0; i < n; i++) {
+        const int32_t u = D.perm[i];
+        row.clear();
+        for (int64_t e = H.A.rp[u]; e < H.A.rp[u + 1]; e++) row.emplace_back(iperm[H.A.ci[e]], H.A.val[e]);
+        std::sort(row.begin(), row.end(), [](auto &a, auto &b) { return a.first < b.first; });
+        for (size_t k = 0; k < row.size(); k++) { ci[rp[i] + k] = row[k].first; val[rp[i] + k] = row[k].second; }
+        rp[i + 1] = rp[i] + (int32_t)row.size();
+        diag[i] = H.A.diag[u];
+    }
+    if ((rc = dupload(h, &D.rp, rp)) || (rc = dupload(h, &D.ci, ci)) || (rc = dupload(h, &D.val, val)) ||
+        (rc = dupload(h, &D.diag, diag)))
+        return rc;
+    D.tpr = choose_tpr(n ? (double)H.A.nnz() / (double)n : 1.0);
+    if (H.kind == KIND_AGG) {
+        const std::vector<int32_t> &ip = h->dev[l + 1].perm;
+        std::vector<int32_t> ipc(H.nc);
+        for (int64_t i = 0; i < H.nc; i++) ipc[ip[i]] = (int32_t)i;
+        std::vector<int32_t> agg(n), agg2(n);
+        std::vector<double> wt(n);
+        std::vector<int64_t> cnt(H.nc + 1, 0);
+        for (int64_t i = 0; i < n; i++) {
+            const int32_t u = D.perm[i];
+            agg[i] = ipc[H.agg[u]];
+            agg2[i] = H.agg2[u] < 0 ? -1 : ipc[H.agg2[u]];
+            wt[i] = H.wt[u];
+            if (agg2[i] < 0) cnt[agg[i] + 1]++;
+            else {
+                if (wt[i] != 0.0) cnt[agg[i] + 1]++;
+                cnt[agg2[i] + 1]++;
+            }
+        }
+        for (int64_t a = 0; a < H.nc; a++) cnt[a + 1] += cnt[a];
+        std::vector<int32_t> ptr(cnt.begin(), cnt.end()), prow(cnt[H.nc]);
+        std::vector<double> pw(cnt[H.nc]);
+        std::vector<int64_t> fill(cnt.begin(), cnt.end() - 1);
+        for (int64_t i = 0; i < n; i++) {
+            if (agg2[i] < 0) { prow[fill[agg[i]]] = (int32_t)i; pw[fill[agg[i]]++] = 1.0; continue; }
+            if (wt[i] != 0.0) { prow[fill[agg[i]]] = (int32_t)i; pw[fill[agg[i]]++] = wt[i]; }
+            prow[fill[agg2[i]]] = (int32_t)i;
+            pw[fill[agg2[i]]++] = 1.0 - wt[i];
+        }
+        if ((rc = dupload(h, &D.agg, agg)) || (rc = dupload(h, &D.agg2, agg2)) || (rc = dupload(h, &D.wt, wt)) ||
+            (rc = dupload(h, &D.pt_ptr, ptr)) || (rc = dupload(h, &D.pt_row, prow)) || (rc = dupload(h, &D.pt_w, pw)))
+            return rc;
+        D.pt_tpr = choose_tpr(H.nc ? (double)cnt[H.nc] / (double)H.nc : 1.0);
+        if ((rc = dalloc(h, &D.r, n))) return rc;
+    } else if (H.kind == KIND_ELIM) {
+        const int64_t nc = H.nc, nF = n - nc;
+        std::vector<int32_t> pfc(4 * nF, -1);
+        std::vector<double> pfv(4 * nF, 0.0), dF(nF);
+        std::vector<std::vector<std::pair<int32_t, double>>> byc(nc);
+        for (int64_t t = 0; t < nF; t++) {
+            const int32_t u = D.perm[nc + t];
+            const int64_t deg = H.A.rp[u + 1] - H.A.rp[u];
+            if (deg > 4) return LAMG_ERR_INVALID;
+            for (int64_t e = H.A.rp[u], j = 0; e < H.A.rp[u + 1]; e++, j++) {
+                const int32_t c = iperm[H.A.ci[e]];
+                if (c >= nc) return LAMG_ERR_INVALID;  // F must be independent
+                const double pv = -H.A.val[e] / H.A.diag[u];
+                pfc[4 * t + j] = c;
+                pfv[4 * t + j] = pv;
+                byc[c].emplace_back((int32_t)t, pv);
+            }
+            dF[t] = H.A.diag[u];
+        }
+        std::vector<int32_t> ptr(nc + 1, 0), fidx;
+        std::vector<double> fval;
+        for (int64_t i = 0; i < nc; i++) {
+            for (auto &pr : byc[i]) { fidx.push_back(pr.first); fval.push_back(pr.second); }
+            ptr[i + 1] = (int32_t)fidx.size();
+        }
+        if ((rc = dupload(h, &D.pf_col, pfc)) || (rc = dupload(h, &D.pf_val, pfv)) || (rc = dupload(h, &D.dF, dF)) ||
+            (rc = dupload(h, &D.pft_ptr, ptr)) || (rc = dupload(h, &D.pft_f, fidx)) || (rc = dupload(h, &D.pft_val, fval)))
+            return rc;
+    } else {
+        std::vector<double> P(n * n);
+        for (int64_t i = 0; i < n; i++)
+            for (int64_t j = 0; j < n; j++) P[i * n + j] = H.pinv[(int64_t)D.perm[i] * n + D.perm[j]];
+        if ((rc = dupload(h, &D.pinv, P))) return rc;
+    }
+    return LAMG_OK;
+}
+
+// Simulate the recursion of one cycle (Section 2) and record its kernel sequence.
+void emit_visit(lamg_hier *h, std::vector<int64_t> &visits, int l, bool first) {
+    const DevLevel &D = h->dev[l];
+    if (D.kind == KIND_COARSEST) { h->ops.push_back({OP_COARSE, l, 0}); return; }
+    if (D.kind == KIND_ELIM) {
+        h->ops.push_back({OP_ELIM_RESTRICT, l, 0});
+        emit_visit(h, visits, l + 1, first);
+        h->ops.push_back({OP_ELIM_INTERP, l, 0});
+        return;
+    }
+    const int npre = h->opt.nu_pre, npost = h->opt.nu_post;
+    if (first && npre == 0) h->ops.push_back({OP_ZERO, l, 0});
+    for (int s = 0; s < npre; s++) {
+        int c0 = 0;
+        if (s == 0 && first) { h->ops.push_back({OP_GS_FIRST, l, 0}); c0 = 1; }
+        for (int c = c0; c < D.ncol; c++) h->ops.push_back({OP_GS, l, c});
+    }
+    h->ops.push_back({OP_RESID, l, 0});
+    h->ops.push_back({OP_RESTRICT, l, 0});
+    const double g = h->host[l].gamma;
+    const int64_t j = visits[l]++;
+    const int64_t nv = (int64_t)std::floor((double)(j + 1) * g) - (int64_t)std::floor((double)j * g);
+    for (int64_t i = 0; i < nv; i++) emit_visit(h, visits, l + 1, i == 0);
+    h->ops.push_back({OP_PROLONG, l, 0});
+    for (int s = 0; s < npost; s++)
+        for (int c = D.ncol - 1; c >= 0; c--) h->ops.push_back({OP_GS, l, c});
+}
+
+int capture(lamg_hier *h, cudaGraphExec_t *out, int which) {
+    cudaStream_t cs = h->stream;
+    cudaGraph_t g = nullptr;
+    CKR(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+    const DevLevel &F = h->dev[0];
+    const int64_t n = F.n;
+    if (which == 0 || which == 1) {
+        for (const Op &op : h->ops) launch_op(op, h->dev, h->red, cs);
+        launch_sum(n, F.x, h->red, cs);
+        if (which == 0) launch_sub_mean(n, F.x, h->red, cs);
+        else {
+            launch_proj_dots(n, F.x, h->zold, h->r, h->red, cs);
+            launch_update_p(n, F.x, h->p, h->zold, h->red, cs);
+        }
+    } else {
+        launch_spmv_dot(F, h->p, h->q, h->red, cs);
+        launch_update_xr(n, h->xs, h->r, h->p, h->q, h->red, cs);
+        cudaMemcpyAsync(h->h_scal, h->red.scal, S_COUNT * sizeof(double), cudaMemcpyDeviceToHost, cs);
+    }
+    cudaError_t e = cudaStreamEndCapture(cs, &g);
+    if (e != cudaSuccess) return cuda_status(e);
+    e = cudaGraphInstantiate(out, g, 0);
+    cudaGraphDestroy(g);
+    return cuda_status(e);
+}
+
+// Build device data, schedule and graphs for h->host.
+int finalize(lamg_hier *h) {
+    int rc;
+    CKR(cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking));
+    CKR(cudaEventCreate(&h->ev_a));
+    CKR(cudaEventCreate(&h->ev_b));
+    CKR(cudaEventCreateWithFlags(&h->ev_poll, cudaEventDisableTiming));
+    build_orders(h);
+    const int L = (int)h->host.size();
+    for (int l = 0; l < L; l++)
+        if ((rc = upload_level(h, l))) return rc;
+    // vectors: level 0's right-hand side is the CG residual; an elimination level's coarse
+    // iterate is the head of its own iterate
+    const int64_t n0 = h->host[0].A.n;
+    if ((rc = dalloc(h, &h->r, n0)) || (rc = dalloc(h, &h->p, n0)) || (rc = dalloc(h, &h->q, n0)) ||
+        (rc = dalloc(h, &h->zold, n0)) || (rc = dalloc(h, &h->xs, n0)) || (rc = dalloc(h, &h->bkeep, n0)) ||
+        (rc = dalloc(h, &h->nat_in, n0)) || (rc = dalloc(h, &h->nat_out, n0)))
+        return rc;
+    for (int l = 0; l < L; l++) {
+        DevLevel &D = h->dev[l];
+        if (l == 0) D.b = h->r;
+        else if ((rc = dalloc(h, &D.b, D.n))) return rc;
+        if (l == 0 || h->dev[l - 1].kind != KIND_ELIM) {
+            if ((rc = dalloc(h, &D.x, D.n))) return rc;
+        } else {
+            D.x = h->dev[l - 1].x;
+        }
+    }
+    if ((rc = dupload(h, &h->perm0, h->dev[0].perm))) return rc;
+    if ((rc = dalloc(h, &h->red.partials, RED_NV * RED_MAXG)) || (rc = dalloc(h, &h->red.ticket, 1)) ||
+        (rc = dalloc(h, &h->red.scal, S_COUNT)))
+        return rc;
+    CKR(cudaMemset(h->red.ticket, 0, sizeof(unsigned)));
+    CKR(cudaMemset(h->red.scal, 0, S_COUNT * sizeof(double)));
+    CKR(cudaHostAlloc(&h->h_scal, S_COUNT * sizeof(double), cudaHostAllocDefault));
+    std::vector<int64_t> visits(L, 0);
+    h->ops.clear();
+    emit_visit(h, visits, 0, true);
+    if ((rc = capture(h, &h->g_cycle, 0)) || (rc = capture(h, &h->g_tail, 1)) || (rc = capture(h, &h->g_head, 2)))
+        return rc;
+    CKR(cudaStreamSynchronize(h->stream));
+    return LAMG_OK;
+}
+
+int wait_event(lamg_hier *h, cudaEvent_t ev) {
+    auto t0 = std::chrono::steady_clock::now();
+    for (;;) {
+        cudaError_t e = cudaEventQuery(ev);
+        if (e == cudaSuccess) return LAMG_OK;
+        if (e != cudaErrorNotReady) return cuda_status(e);
+        double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        if (el > h->wait_timeout_s) return LAMG_ERR_TIMEOUT;
+    }
+}
+
+int set_device(int dev) {
+    int cnt = 0;
+    cudaError_t e = cudaGetDeviceCount(&cnt);
+    if (e != cudaSuccess || cnt == 0) return LAMG_ERR_NO_DEVICE;
+    if (dev < 0 || dev >= cnt) return LAMG_ERR_INVALID;
+    return cuda_status(cudaSetDevice(dev));
+}
+
+}  // namespace
+
+// =================================================================================== C ABI
+
+extern "C" {
+
+void lamg_options_default(lamg_options *o) {
+    std::memset(o, 0, sizeof(*o));
+    o->K = 4;
+    o->nu_tv = 3;
+    o->dmax = 4;
+    o->nu_pre = 1;
+    o->nu_post = 2;
+    o->coarsest_max = 1024;
+    o->max_levels = 100;
+    o->veto = 1;
+    o->caliber2 = 1;
+    o->precision = LAMG_FP64;
+    o->seed = 3;
+    o->Q = 2.5;
+    o->tau_soc = 0.05;
+    o->elim_min_frac = 0.01;
+    o->snap = 1e-3;
+    o->guard_eps = 1e-10;
+    o->gamma_fixed = 0.0;
+    o->device = 0;
+}
+
+const char *lamg_strerror(int c) {
+    switch (c) {
+        case LAMG_OK: return "ok";
+        case LAMG_ERR_INVALID: return "invalid argument or input graph";
+        case LAMG_ERR_DISCONNECTED: return "graph is not connected";
+        case LAMG_ERR_SETUP: return "coarsening stalled above the dense coarsest limit";
+        case LAMG_ERR_OOM: return "out of memory";
+        case LAMG_ERR_NOT_CONVERGED: return "not converged within maxit";
+        case LAMG_ERR_CUDA: return "CUDA runtime error";
+        case LAMG_ERR_TIMEOUT: return "bounded GPU wait ran out";
+        case LAMG_ERR_ADMISSION: return "request exceeds the memory budget";
+        case LAMG_ERR_NO_DEVICE: return "no CUDA device";
+        default: return "unknown error";
+    }
+}
+
+int lamg_setup(const lamg_graph *g, const lamg_options *opt, lamg_hier **out) {
+    if (!out) return LAMG_ERR_INVALID;
+    *out = nullptr;
+    lamg_options o;
+    if (opt) o = *opt; else lamg_options_default(&o);
+    int rc = set_device(o.device);
+    if (rc) return rc;
+    lamg_hier *h = new lamg_hier();
+    h->device = o.device;
+    h->opt = o;
+    rc = build_hierarchy(g, o, h->host);
+    if (!rc) rc = finalize(h);
+    if (rc) { delete h; return rc; }
+    *out = h;
+    return LAMG_OK;
+}
+
+int lamg_import(const lamg_level_desc *lv, int32_t nl, const lamg_options *opt, lamg_hier **out) {
+    if (!out || !lv || nl < 1) return LAMG_ERR_INVALID;
+    *out = nullptr;
+    lamg_options o;
+    if (opt) o = *opt; else lamg_options_default(&o);
+    int rc = set_device(o.device);
+    if (rc) return rc;
+    lamg_hier *h = new lamg_hier();
+    h->device = o.device;
+    h->opt = o;
+    h->host.resize(nl);
+    for (int l = 0; l < nl; l++) {
+        const lamg_level_desc &d = lv[l];
+        HostLevel &H = h->host[l];
+        const int64_t n = d.n;
+        if (n < 1 || !d.rp || !d.diag) { delete h; return LAMG_ERR_INVALID; }
+        const int64_t z = d.rp[n];
+        H.kind = d.kind;
+        H.A.n = n;
+        H.A.rp.assign(d.rp, d.rp + n + 1);
+        H.A.ci.assign(d.ci, d.ci + z);
+        H.A.val.assign(d.val, d.val + z);
+        H.A.diag.assign(d.diag, d.diag + n);
+        H.nc = d.nc;
+        H.gamma = d.gamma;
+        const bool last = (l == nl - 1);
+        if ((d.kind == KIND_COARSEST) != last) { delete h; return LAMG_ERR_INVALID; }
+        if (d.kind != KIND_COARSEST && lv[l + 1].n != d.nc) { delete h; return LAMG_ERR_INVALID; }
+        if (d.kind == KIND_AGG) {
+            if (!d.colour || !d.agg || !d.agg2 || !d.wt) { delete h; return LAMG_ERR_INVALID; }
+            H.colour.assign(d.colour, d.colour + n);
+            H.agg.assign(d.agg, d.agg + n);
+            H.agg2.assign(d.agg2, d.agg2 + n);
+            H.wt.assign(d.wt, d.wt + n);
+            for (int64_t u = 0; u < n; u++)
+                if (H.agg[u] < 0 || H.agg[u] >= d.nc || H.agg2[u] >= d.nc || H.colour[u] < 0) { delete h; return LAMG_ERR_INVALID; }
+            // colour classes must be independent sets
+            for (int64_t u = 0; u < n; u++)
+                for (int64_t e = H.A.rp[u]; e < H.A.rp[u + 1]; e++)
+                    if (H.colour[H.A.ci[e]] == H.colour[u]) { delete h; return LAMG_ERR_INVALID; }
+        } else if (d.kind == KIND_ELIM) {
+            if (!d.cidx) { delete h; return LAMG_ERR_INVALID; }
+            H.cidx.assign(d.cidx, d.cidx + n);
+        } else {
+            if (n > 4096) { delete h; return LAMG_ERR_INVALID; }
+            rc = dense_pinv(H.A, H.pinv);
+            if (rc) { delete h; return rc; }
+        }
+    }
+    rc = finalize(h);
+    if (rc) { delete h; return rc; }
+    *out = h;
+    return LAMG_OK;
+}
+
+void lamg_destroy(lamg_hier *h) {
+    if (!h) return;
+    cudaSetDevice(h->device);
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    delete h;
+}
+
+int lamg_solve(lamg_hier *h, const double *b, double *phi, const lamg_solve_opts *so, lamg_stats *st) {
+    if (!h || !b || !phi || !so || !(so->tol > 0) || so->maxit < 1) return LAMG_ERR_INVALID;
+    CKR(cudaSetDevice(h->device));
+    cudaStream_t s = so->stream ? (cudaStream_t)so->stream : h->stream;
+    const bool devp = so->flags & LAMG_DEVICE_PTRS;
+    const DevLevel &F = h->dev[0];
+    const int64_t n = F.n;
+    int rc = LAMG_OK;
+    CKR(cudaEventRecord(h->ev_a, s));
+    if (devp) CKR(cudaMemcpyAsync(h->nat_in, b, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    else CKR(cudaMemcpyAsync(h->nat_in, b, n * sizeof(double), cudaMemcpyHostToDevice, s));
+    launch_gather(n, h->perm0, h->nat_in, h->r, s);
+    launch_sum(n, h->r, h->red, s);
+    launch_init_b(n, h->r, h->bkeep, h->xs, h->p, h->zold, h->red, s);
+    CKR(cudaGetLastError());
+    CKR(cudaGraphLaunch(h->g_tail, s));
+    int it = 0;
+    double rel = 1.0, bn2 = 0.0;
+    if (st && st->hist) st->hist[0] = 1.0;
+    while (it < so->maxit) {
+        CKR(cudaGraphLaunch(h->g_head, s));
+        CKR(cudaEventRecord(h->ev_poll, s));
+        if ((rc = wait_event(h, h->ev_poll))) return rc;
+        it++;
+        bn2 = h->h_scal[S_BN2];
+        rel = bn2 > 0 ? std::sqrt(h->h_scal[S_RR] / bn2) : 0.0;
+        if (st && st->hist) st->hist[it] = rel;
+        if (!(rel > so->tol)) break;
+        CKR(cudaGraphLaunch(h->g_tail, s));
+    }
+    launch_true_resid(F, h->xs, h->bkeep, h->red, s);
+    launch_scatter(n, h->perm0, h->xs, h->nat_out, s);
+    if (devp) CKR(cudaMemcpyAsync(phi, h->nat_out, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    else CKR(cudaMemcpyAsync(phi, h->nat_out, n * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CKR(cudaMemcpyAsync(h->h_scal, h->red.scal, S_COUNT * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CKR(cudaEventRecord(h->ev_b, s));
+    if ((rc = wait_event(h, h->ev_b))) return rc;
+    CKR(cudaGetLastError());
+    if (st) {
+        st->iters = it;
+        st->nlevels = (int32_t)h->dev.size();
+        st->relres = rel;
+        st->relres_true = bn2 > 0 ? std::sqrt(h->h_scal[S_TRUE_RR] / bn2) : 0.0;
+        st->b_mean = h->h_scal[S_BMEAN];
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, h->ev_a, h->ev_b);
+        st->solve_ms = ms;
+    }
+    return rel <= so->tol ? LAMG_OK : LAMG_ERR_NOT_CONVERGED;
+}
+
+int lamg_cycle(lamg_hier *h, const double *r, double *z, uint32_t flags) {
+    if (!h || !r || !z) return LAMG_ERR_INVALID;
+    CKR(cudaSetDevice(h->device));
+    cudaStream_t s = h->stream;
+    const int64_t n = h->dev[0].n;
+    const bool devp = flags & LAMG_DEVICE_PTRS;
+    CKR(cudaMemcpyAsync(h->nat_in, r, n * sizeof(double), devp ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+    launch_gather(n, h->perm0, h->nat_in, h->r, s);
+    CKR(cudaGraphLaunch(h->g_cycle, s));
+    launch_scatter(n, h->perm0, h->dev[0].x, h->nat_out, s);
+    CKR(cudaMemcpyAsync(z, h->nat_out, n * sizeof(double), devp ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
+    CKR(cudaEventRecord(h->ev_b, s));
+    int rc = wait_event(h, h->ev_b);
+    if (rc) return rc;
+    CKR(cudaGetLastError());
+    return LAMG_OK;
+}
+
+int lamg_hier_info(const lamg_hier *h, int64_t *nlevels, int64_t *meta, double *gamma) {
+    if (!h || !nlevels) return LAMG_ERR_INVALID;
+    *nlevels = (int64_t)h->host.size();
+    for (size_t l = 0; l < h->host.size(); l++) {
+        const HostLevel &H = h->host[l];
+        if (meta) {
+            int64_t c2 = 0;
+            for (int32_t v : H.agg2) c2 += v >= 0;
+            meta[7 * l + 0] = H.kind;
+            meta[7 * l + 1] = H.A.n;
+            meta[7 * l + 2] = H.A.nnz();
+            meta[7 * l + 3] = h->dev.size() > l ? h->dev[l].ncol : 0;
+            meta[7 * l + 4] = H.nc;
+            meta[7 * l + 5] = c2;
+            meta[7 * l + 6] = h->dev.size() > l ? (int64_t)h->dev[l].bytes : 0;
+        }
+        if (gamma) gamma[l] = H.gamma;
+    }
+    return LAMG_OK;
+}
+
+int lamg_level_get(const lamg_hier *h, int32_t level, const char *name, void *dst, int64_t *count) {
+    if (!h || !name || level < 0 || level >= (int32_t)h->host.size()) return LAMG_ERR_INVALID;
+    const HostLevel &H = h->host[level];
+    const void *src = nullptr;
+    int64_t cnt = 0;
+    size_t es = 0;
+    std::string nm(name);
+    if (nm == "rp") { src = H.A.rp.data(); cnt = (int64_t)H.A.rp.size(); es = 8; }
+    else if (nm == "ci") { src = H.A.ci.data(); cnt = (int64_t)H.A.ci.size(); es = 4; }
+    else if (nm == "val") { src = H.A.val.data(); cnt = (int64_t)H.A.val.size(); es = 8; }
+    else if (nm == "diag") { src = H.A.diag.data(); cnt = (int64_t)H.A.diag.size(); es = 8; }
+    else if (nm == "colour") { src = H.colour.data(); cnt = (int64_t)H.colour.size(); es = 4; }
+    else if (nm == "cidx") { src = H.cidx.data(); cnt = (int64_t)H.cidx.size(); es = 4; }
+    else if (nm == "agg") { src = H.agg.data(); cnt = (int64_t)H.agg.size(); es = 4; }
+    else if (nm == "agg2") { src = H.agg2.data(); cnt = (int64_t)H.agg2.size(); es = 4; }
+    else if (nm == "wt") { src = H.wt.data(); cnt = (int64_t)H.wt.size(); es = 8; }
+    else if (nm == "X") { src = H.X.data(); cnt = (int64_t)H.X.size(); es = 8; }
+    else if (nm == "aff") { src = H.aff.data(); cnt = (int64_t)H.aff.size(); es = 8; }
+    else if (nm == "strong") { src = H.strong.data(); cnt = (int64_t)H.strong.size(); es = 1; }
+    else if (nm == "pinv") { src = H.pinv.data(); cnt = (int64_t)H.pinv.size(); es = 8; }
+    else return LAMG_ERR_INVALID;
+    if (count) *count = cnt;
+    if (dst && cnt) std::memcpy(dst, src, cnt * es);
+    return LAMG_OK;
+}
+
+int lamg_testvectors(int64_t n, const int64_t *rp, const int32_t *ci, const double *val, const double *diag,
+                     const int32_t *colour, int32_t level, uint64_t seed, int32_t K, int32_t nu, double *X) {
+    if (n < 1 || !rp || !diag || !colour || !X || K < 1 || nu < 0) return LAMG_ERR_INVALID;
+    int rc = set_device(0);
+    if (rc) return rc;
+    HostMat A;
+    A.n = n;
+    A.rp.assign(rp, rp + n + 1);
+    A.ci.assign(ci, ci + rp[n]);
+    A.val.assign(val, val + rp[n]);
+    A.diag.assign(diag, diag + n);
+    std::vector<int32_t> col(colour, colour + n);
+    return gpu_testvectors(A, col, level, seed, K, nu, X);
+}
+
+int lamg_affinity(int64_t n, const int64_t *rp, const int32_t *ci, const double *val, const double *X,
+                  int32_t K, double tau, double *aff, uint8_t *strong) {
+    if (n < 1 || !rp || !X || !aff || !strong || K < 1) return LAMG_ERR_INVALID;
+    int rc = set_device(0);
+    if (rc) return rc;
+    HostMat A;
+    A.n = n;
+    A.rp.assign(rp, rp + n + 1);
+    A.ci.assign(ci, ci + rp[n]);
+    A.val.assign(val, val + rp[n]);
+    A.diag.assign(n, 0.0);
+    return gpu_affinity(A, X, K, tau, aff, strong);
+}
+
+int lamg_time_kernel(lamg_hier *h, int32_t which, int32_t level, int32_t reps, double *out) {
+    if (!h || !out || reps < 1 || level < 0 || level >= (int32_t)h->dev.size()) return LAMG_ERR_INVALID;
+    CKR(cudaSetDevice(h->device));
+    DevLevel &D = h->dev[level];
+    const double n = (double)D.n, z = (double)D.nnz, nc = (double)D.nc;
+    if ((which == 0 || which == 1 || which == 3 || which == 4) && D.kind != KIND_AGG) return LAMG_ERR_INVALID;
+    if (which == 2 && level != 0) return LAMG_ERR_INVALID;
+    cudaStream_t s = h->stream;
+    // a buffer larger than the 126 MB L2, rewritten between repetitions so that every timed
+    // launch starts with a cold L2
+    const size_t flush_bytes = (size_t)256 << 20;
+    void *flush = nullptr;
+    CKR(cudaMalloc(&flush, flush_bytes));
+    double bytes = 0.0;
+    int launches = 1;
+    std::vector<Op> seq;
+    switch (which) {
+        case 0: seq.push_back({OP_RESID, level, 0}); bytes = 12 * z + 36 * n + 4; break;
+        case 1:
+            for (int c = 0; c < D.ncol; c++) seq.push_back({OP_GS, level, c});
+            bytes = 12 * z + 36 * n + 4 * D.ncol;
+            launches = D.ncol;
+            break;
+        case 2: bytes = 12 * z + 28 * n + 4; break;
+        case 3: {
+            int32_t ent = 0;
+            cudaMemcpy(&ent, D.pt_ptr + D.nc, sizeof(int32_t), cudaMemcpyDeviceToHost);
+            seq.push_back({OP_RESTRICT, level, 0});
+            bytes = 12.0 * ent + 4 * (nc + 1) + 8 * n + 8 * nc;
+            break;
+        }
+        case 4: seq.push_back({OP_PROLONG, level, 0}); bytes = 32 * n + 8 * nc; break;
+        default: cudaFree(flush); return LAMG_ERR_INVALID;
+    }
+    double total = 0.0;
+    int rc = LAMG_OK;
+    for (int r = 0; r < reps && !rc; r++) {
+        cudaMemsetAsync(flush, r & 0xff, flush_bytes, s);
+        cudaEventRecord(h->ev_a, s);
+        if (which == 2) launch_spmv_dot(h->dev[0], h->p, h->q, h->red, s);
+        else for (const Op &op : seq) launch_op(op, h->dev, h->red, s);
+        cudaEventRecord(h->ev_b, s);
+        rc = wait_event(h, h->ev_b);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, h->ev_a, h->ev_b);
+        total += ms;
+    }
+    cudaFree(flush);
+    if (rc) return rc;
+    CKR(cudaGetLastError());
+    out[0] = total / reps;
+    out[1] = bytes;
+    out[2] = launches;
+    return LAMG_OK;
+}
+
+}  // extern "C"
+
