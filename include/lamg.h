@@ -47,6 +47,10 @@ extern "C" {
 
 /* flags */
 #define LAMG_DEVICE_PTRS 1u       /* vectors are device pointers */
+#define LAMG_PERSISTENT 2u        /* run the whole solve as one persistent cooperative kernel
+                                     (grid barriers between steps) instead of the default CUDA
+                                     graphs of per-step kernels with programmatic dependent
+                                     launch; same arithmetic */
 
 /* cycle precision */
 #define LAMG_FP64 0
@@ -73,7 +77,9 @@ typedef struct lamg_options {
     double guard_eps;      /* relative size below which a nodal energy counts as zero: 1e-10 */
     double gamma_fixed;    /* > 0: this cycle index on every aggregation level instead of Eq. 5 */
     int32_t device;        /* CUDA device ordinal */
-    int32_t reserved[7];
+    int32_t tail_rows;     /* levels with at most this many rows run inside one CTA of the
+                              persistent solve kernel (no grid barrier per step): 8192 */
+    int32_t reserved[6];
 } lamg_options;
 
 typedef struct lamg_graph {
@@ -123,8 +129,11 @@ typedef struct lamg_stats {
     double relres;         /* recursive residual norm / ||b|| at exit */
     double relres_true;    /* ||b - L phi|| / ||b|| recomputed at exit (FP64) */
     double b_mean;         /* mean removed from b before solving */
-    double solve_ms;       /* device time of the solve (CUDA events) */
+    double solve_ms;       /* device time of the call, copies included (CUDA events) */
     double *hist;          /* optional caller buffer of maxit+1 doubles: relres per iteration */
+    double kernel_ms;      /* device time of the solve kernel(s) alone */
+    double alg_bytes;      /* algorithmic DRAM bytes of the solve (each array once per step) */
+    int64_t launches;      /* kernel launches of the solve */
 } lamg_stats;
 
 typedef struct lamg_hier lamg_hier;
@@ -203,6 +212,18 @@ int lamg_affinity(int64_t n, const int64_t *rp, const int32_t *ci, const double 
  * out[1] = algorithmic DRAM bytes of one launch (sweep), out[2] = kernels per launch.
  * The kernels run on the hierarchy's current vectors. Errors: INVALID, OOM, CUDA, TIMEOUT. */
 int lamg_time_kernel(lamg_hier *h, int32_t which, int32_t level, int32_t reps, double *out);
+
+/* Per-step timing of one cycle of the persistent solve kernel (r = 0): out receives up to cap
+ * pairs (next step index, nanoseconds since the previous pair), one per grid barrier, read
+ * from %globaltimer in CTA 0; *count = pairs written. Step indices refer to lamg_op_list.
+ * Errors: INVALID (no persistent kernel for this hierarchy), CUDA, TIMEOUT. */
+int lamg_profile_cycle(lamg_hier *h, int64_t *out, int64_t cap, int64_t *count);
+
+/* The static step list of one cycle: 3 int32 per step (kind, level, colour); kinds 0 first
+ * GS colour from zero, 1 GS colour class, 2 zero, 3 residual, 4 restriction, 5 prolongation,
+ * 6 elimination restriction, 7 elimination interpolation, 8 coarsest solve. out may be NULL
+ * to query *count. Errors: INVALID. */
+int lamg_op_list(const lamg_hier *h, int32_t *out, int64_t cap, int64_t *count);
 
 /* Name of an error code. */
 const char *lamg_strerror(int code);

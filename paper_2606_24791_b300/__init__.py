@@ -20,6 +20,7 @@ LAMG_OK = 0
 ERRORS = {1: "INVALID", 2: "DISCONNECTED", 3: "SETUP", 4: "OOM", 5: "NOT_CONVERGED", 6: "CUDA",
           7: "TIMEOUT", 8: "ADMISSION", 9: "NO_DEVICE"}
 DEVICE_PTRS = 1
+PERSISTENT = 2
 FP64, FP32 = 0, 1
 KINDS = {"elim": 0, "agg": 1, "coarsest": 2}
 KIND_NAMES = {v: k for k, v in KINDS.items()}
@@ -37,7 +38,8 @@ class Options(C.Structure):
                 ("veto", C.c_int32), ("caliber2", C.c_int32), ("precision", C.c_int32),
                 ("seed", C.c_uint64), ("Q", C.c_double), ("tau_soc", C.c_double),
                 ("elim_min_frac", C.c_double), ("snap", C.c_double), ("guard_eps", C.c_double),
-                ("gamma_fixed", C.c_double), ("device", C.c_int32), ("reserved", C.c_int32 * 7)]
+                ("gamma_fixed", C.c_double), ("device", C.c_int32), ("tail_rows", C.c_int32),
+                ("reserved", C.c_int32 * 6)]
 
 
 class Graph(C.Structure):
@@ -60,7 +62,8 @@ class SolveOpts(C.Structure):
 class Stats(C.Structure):
     _fields_ = [("iters", C.c_int32), ("nlevels", C.c_int32), ("relres", C.c_double),
                 ("relres_true", C.c_double), ("b_mean", C.c_double), ("solve_ms", C.c_double),
-                ("hist", C.c_void_p)]
+                ("hist", C.c_void_p), ("kernel_ms", C.c_double), ("alg_bytes", C.c_double),
+                ("launches", C.c_int64)]
 
 
 def lib_path() -> str:
@@ -90,6 +93,8 @@ def lib():
                                        C.c_int32, P]
         L.lamg_affinity.argtypes = [C.c_int64, P, P, P, P, C.c_int32, C.c_double, P, P]
         L.lamg_time_kernel.argtypes = [P, C.c_int32, C.c_int32, C.c_int32, P]
+        L.lamg_profile_cycle.argtypes = [P, P, C.c_int64, C.POINTER(C.c_int64)]
+        L.lamg_op_list.argtypes = [P, P, C.c_int64, C.POINTER(C.c_int64)]
         _lib = L
     return _lib
 
@@ -166,14 +171,15 @@ class Hierarchy:
             lib().lamg_level_get(self._h, level, name.encode(), _p(out), C.byref(cnt))
         return out
 
-    def solve(self, b, tol: float = 1e-8, maxit: int = 100, allow_unconverged: bool = False):
+    def solve(self, b, tol: float = 1e-8, maxit: int = 100, allow_unconverged: bool = False,
+              persistent: bool = False):
         """Host-pointer solve; returns (phi, stats dict with the residual history)."""
         b = _c(b, np.float64)
         if b.shape != (self.n,):
             raise ValueError("b has the wrong shape")
         phi = np.zeros(self.n)
         hist = np.zeros(maxit + 1)
-        so = SolveOpts(tol, maxit, 0, None)
+        so = SolveOpts(tol, maxit, PERSISTENT if persistent else 0, None)
         st = Stats()
         st.hist = hist.ctypes.data
         rc = lib().lamg_solve(self._h, _p(b), _p(phi), C.byref(so), C.byref(st))
@@ -181,9 +187,10 @@ class Hierarchy:
         return phi, _stats(st, hist)
 
     def solve_ptr(self, b_ptr: int, phi_ptr: int, tol: float = 1e-8, maxit: int = 100,
-                  stream: int = 0, device: bool = True, hist: bool = False):
+                  stream: int = 0, device: bool = True, hist: bool = False, persistent: bool = False):
         """Solve with raw pointers (device pointers when ``device``), e.g. torch ``data_ptr()``."""
-        so = SolveOpts(tol, maxit, DEVICE_PTRS if device else 0, C.c_void_p(stream) if stream else None)
+        flags = (DEVICE_PTRS if device else 0) | (PERSISTENT if persistent else 0)
+        so = SolveOpts(tol, maxit, flags, C.c_void_p(stream) if stream else None)
         st = Stats()
         h = np.zeros(maxit + 1) if hist else None
         if h is not None:
@@ -202,16 +209,35 @@ class Hierarchy:
         return dict(ms=float(out[0]), bytes=float(out[1]), launches=int(out[2]),
                     gbs=float(out[1]) / (float(out[0]) * 1e-3) / 1e9)
 
-    def cycle(self, r):
+    OP_KINDS = ["gs_first", "gs", "zero", "resid", "restrict", "prolong", "elim_restrict",
+                "elim_interp", "coarse"]
+
+    def op_list(self) -> list:
+        cnt = C.c_int64()
+        _check(lib().lamg_op_list(self._h, None, 0, C.byref(cnt)), "lamg_op_list")
+        out = np.zeros(3 * cnt.value, np.int32)
+        lib().lamg_op_list(self._h, _p(out), cnt.value, C.byref(cnt))
+        return [(self.OP_KINDS[k], int(l), int(c)) for k, l, c in out.reshape(-1, 3)]
+
+    def profile_cycle(self) -> list:
+        """[(first step index after the barrier, ns)] for one cycle of the persistent kernel."""
+        cap = len(self.op_list()) + 4
+        out = np.zeros(2 * cap, np.int64)
+        cnt = C.c_int64()
+        _check(lib().lamg_profile_cycle(self._h, _p(out), cap, C.byref(cnt)), "lamg_profile_cycle")
+        return [(int(a), int(b)) for a, b in out[: 2 * cnt.value].reshape(-1, 2)]
+
+    def cycle(self, r, persistent: bool = False):
         r = _c(r, np.float64)
         z = np.zeros(self.n)
-        _check(lib().lamg_cycle(self._h, _p(r), _p(z), 0), "lamg_cycle")
+        _check(lib().lamg_cycle(self._h, _p(r), _p(z), PERSISTENT if persistent else 0), "lamg_cycle")
         return z
 
 
 def _stats(st: Stats, hist) -> dict:
     d = dict(iters=st.iters, nlevels=st.nlevels, relres=st.relres, relres_true=st.relres_true,
-             b_mean=st.b_mean, solve_ms=st.solve_ms)
+             b_mean=st.b_mean, solve_ms=st.solve_ms, kernel_ms=st.kernel_ms,
+             alg_bytes=st.alg_bytes, launches=st.launches)
     if hist is not None:
         d["hist"] = hist[: st.iters + 1].copy()
     return d

@@ -1,45 +1,32 @@
 // sm_103a kernels of the LAMG+ solve phase: the cycle steps of Section 2 (colour-ordered
 // Gauss-Seidel, residual, restriction P^T, prolongation P with caliber-2 rows, elimination
-// transfers of Eq. 2, dense coarsest solve, mean-zero projection of Eq. 1) and the vector
-// kernels of the flexible CG outer iteration.
+// transfers of Eq. 2, dense coarsest solve with the mean-zero projection of Eq. 1) and the
+// vector kernels of the flexible CG outer iteration.
 //
-// All of these are memory-bound (no step is a dense contraction): CSR rows are handled by
-// groups of TPR lanes so that a group's loads of a row's column ids and values are
-// contiguous, group sums are combined with warp shuffles, and every reduction is
-// deterministic (fixed per-block partials, summed in a fixed order by the last block to
-// finish, which is found with an atomic ticket, not a spin-wait).
+// All of these are memory-bound (no step is a dense contraction) and the cycle is a long chain
+// of small dependent steps, so the kernels are built for latency:
+//  - Programmatic dependent launch: every kernel lets the next one launch as soon as it has
+//    started (griddepcontrol.launch_dependents), loads the operands that only setup writes
+//    (row pointers, column ids, values, diagonals, transfer weights) and only then waits for
+//    the previous kernel to finish (griddepcontrol.wait) before touching the vectors the
+//    solve writes. Launch latency and the first two links of each row's load chain overlap
+//    the previous step. Every thread reaches the wait, so a kernel never completes before its
+//    predecessor and completion order stays transitive along the chain.
+//  - CSR rows are handled by groups of TPR lanes (coalesced column/value loads), combined with
+//    warp shuffles.
+//  - Reductions are deterministic: fixed per-block partials, added in a fixed order by the
+//    last block to finish (found with an atomic ticket, not a spin-wait).
 #include <cuda_runtime.h>
 
 #include "device.h"
+#include "kernels_common.cuh"
 
 namespace lamg {
 
 constexpr int BS = 256;
 
-__device__ __forceinline__ double warp_sum(double v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
-}
-
-// Sum of NV values over the block; the totals are valid in thread 0.
-template <int NV>
-__device__ __forceinline__ void block_sum(double (&v)[NV]) {
-    __shared__ double sh[NV][32];
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-#pragma unroll
-    for (int k = 0; k < NV; k++) v[k] = warp_sum(v[k]);
-    if (lane == 0) {
-#pragma unroll
-        for (int k = 0; k < NV; k++) sh[k][w] = v[k];
-    }
-    __syncthreads();
-    if (w == 0) {
-#pragma unroll
-        for (int k = 0; k < NV; k++) v[k] = warp_sum(lane < nw ? sh[k][lane] : 0.0);
-    }
-    __syncthreads();
-}
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 
 // Grid-wide deterministic sum: every block publishes its partials, the last block to arrive
 // adds all partials in block order. Returns true in the last block, whose thread 0 holds the
@@ -70,12 +57,33 @@ __device__ bool grid_sum(double (&v)[NV], const Reduce red) {
     return true;
 }
 
-// Sum over a CSR row by a group of TPR lanes (all 32 lanes of the warp must call it).
+// A CSR row held by a group of TPR lanes: the first two entries of each lane are loaded before
+// the dependency wait, the rest (long rows only) after it.
+struct RowPre {
+    int e0, e1, c0, c1;
+    double v0, v1;
+};
+
 template <int TPR>
-__device__ __forceinline__ double row_sum(int e0, int e1, const int32_t *__restrict__ ci,
-                                          const double *__restrict__ val, const double *x) {
+__device__ __forceinline__ RowPre row_pre(bool ok, int row, int sub, const int32_t *__restrict__ rp,
+                                          const int32_t *__restrict__ ci, const double *__restrict__ val) {
+    RowPre p;
+    p.e0 = ok ? rp[row] + sub : 0;
+    p.e1 = ok ? rp[row + 1] : 0;
+    p.c0 = -1; p.c1 = -1; p.v0 = 0.0; p.v1 = 0.0;
+    if (p.e0 < p.e1) { p.c0 = ci[p.e0]; p.v0 = val[p.e0]; }
+    if (p.e0 + TPR < p.e1) { p.c1 = ci[p.e0 + TPR]; p.v1 = val[p.e0 + TPR]; }
+    return p;
+}
+
+// sum_e val[e] x[ci[e]] over the row (after the wait); group total on every lane of the group.
+template <int TPR>
+__device__ __forceinline__ double row_finish(const RowPre &p, const int32_t *__restrict__ ci,
+                                             const double *__restrict__ val, const double *x) {
     double s = 0.0;
-    for (int e = e0; e < e1; e += TPR) s += val[e] * x[ci[e]];
+    if (p.c0 >= 0) s += p.v0 * x[p.c0];
+    if (p.c1 >= 0) s += p.v1 * x[p.c1];
+    for (int e = p.e0 + 2 * TPR; e < p.e1; e += TPR) s += val[e] * x[ci[e]];
 #pragma unroll
     for (int o = TPR / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     return s;
@@ -90,24 +98,32 @@ __global__ void __launch_bounds__(BS) k_gs(int r0, int r1, const int32_t *__rest
                                            const double *__restrict__ val,
                                            const double *__restrict__ diag,
                                            const double *__restrict__ b, double *x) {
+    pdl_trigger();
     const int g = r0 + (int)((blockIdx.x * (unsigned)BS + threadIdx.x) / TPR);
     const int sub = threadIdx.x % TPR;
     const bool ok = g < r1;
-    const int e0 = ok ? rp[g] + sub : 0, e1 = ok ? rp[g + 1] : 0;
-    const double s = row_sum<TPR>(e0, e1, ci, val, x);
-    if (ok && sub == 0) x[g] = (b[g] - s) / diag[g];
+    const RowPre p = row_pre<TPR>(ok, g, sub, rp, ci, val);
+    const double d = ok ? diag[g] : 1.0;
+    pdl_wait();
+    const double s = row_finish<TPR>(p, ci, val, x);
+    if (ok && sub == 0) x[g] = (b[g] - s) / d;
 }
 
 // First sweep from x = 0: rows of colour 0 ([0, c1)) have no updated neighbours yet, so
 // x_u = b_u / A_uu there; every other row starts at 0.
 __global__ void k_gs_first(int n, int c1, const double *__restrict__ diag,
                            const double *__restrict__ b, double *x) {
+    pdl_trigger();
     const int i = blockIdx.x * BS + threadIdx.x;
+    const double d = (i < c1) ? diag[i] : 1.0;
+    pdl_wait();
     if (i >= n) return;
-    x[i] = i < c1 ? b[i] / diag[i] : 0.0;
+    x[i] = i < c1 ? b[i] / d : 0.0;
 }
 
 __global__ void k_zero(int n, double *x) {
+    pdl_trigger();
+    pdl_wait();
     const int i = blockIdx.x * BS + threadIdx.x;
     if (i < n) x[i] = 0.0;
 }
@@ -120,12 +136,15 @@ __global__ void __launch_bounds__(BS) k_resid(int n, const int32_t *__restrict__
                                               const double *__restrict__ diag,
                                               const double *__restrict__ x,
                                               const double *__restrict__ b, double *r) {
+    pdl_trigger();
     const int g = (int)((blockIdx.x * (unsigned)BS + threadIdx.x) / TPR);
     const int sub = threadIdx.x % TPR;
     const bool ok = g < n;
-    const int e0 = ok ? rp[g] + sub : 0, e1 = ok ? rp[g + 1] : 0;
-    const double s = row_sum<TPR>(e0, e1, ci, val, x);
-    if (ok && sub == 0) r[g] = b[g] - (diag[g] * x[g] + s);
+    const RowPre p = row_pre<TPR>(ok, g, sub, rp, ci, val);
+    const double d = ok ? diag[g] : 0.0;
+    pdl_wait();
+    const double s = row_finish<TPR>(p, ci, val, x);
+    if (ok && sub == 0) r[g] = b[g] - (d * x[g] + s);
 }
 
 // Restriction b^c = P^T r (Section 2): segmented sum over the fine rows of each aggregate,
@@ -135,11 +154,13 @@ __global__ void __launch_bounds__(BS) k_restrict(int nc, const int32_t *__restri
                                                  const int32_t *__restrict__ row,
                                                  const double *__restrict__ w,
                                                  const double *__restrict__ r, double *bc) {
+    pdl_trigger();
     const int a = (int)((blockIdx.x * (unsigned)BS + threadIdx.x) / TPR);
     const int sub = threadIdx.x % TPR;
     const bool ok = a < nc;
-    const int e0 = ok ? ptr[a] + sub : 0, e1 = ok ? ptr[a + 1] : 0;
-    const double s = row_sum<TPR>(e0, e1, row, w, r);
+    const RowPre p = row_pre<TPR>(ok, a, sub, ptr, row, w);
+    pdl_wait();
+    const double s = row_finish<TPR>(p, row, w, r);
     if (ok && sub == 0) bc[a] = s;
 }
 
@@ -147,16 +168,19 @@ __global__ void __launch_bounds__(BS) k_restrict(int nc, const int32_t *__restri
 // w x^c_a + (1 - w) x^c_b (Appendix A.2).
 __global__ void k_prolong(int n, const int32_t *__restrict__ agg, const int32_t *__restrict__ agg2,
                           const double *__restrict__ wt, const double *__restrict__ xc, double *x) {
+    pdl_trigger();
     const int u = blockIdx.x * BS + threadIdx.x;
-    if (u >= n) return;
-    const int b = agg2[u];
+    const bool ok = u < n;
+    const int a = ok ? agg[u] : 0, b = ok ? agg2[u] : -1;
+    const double w = (ok && b >= 0) ? wt[u] : 1.0;
+    pdl_wait();
+    if (!ok) return;
     double s;
     if (b < 0) {
-        s = xc[agg[u]];
+        s = xc[a];
     } else {
-        const double w = wt[u];
         s = (1.0 - w) * xc[b];
-        if (w != 0.0) s = w * xc[agg[u]] + s;
+        if (w != 0.0) s = w * xc[a] + s;
     }
     x[u] += s;
 }
@@ -164,11 +188,21 @@ __global__ void k_prolong(int n, const int32_t *__restrict__ agg, const int32_t 
 // Elimination restriction (Eq. 2): b^c_i = b_i + sum_f (P_F)_{f,i} b_f over the F neighbours.
 __global__ void k_elim_restrict(int nc, const int32_t *__restrict__ ptr, const int32_t *__restrict__ f,
                                 const double *__restrict__ pv, const double *__restrict__ b, double *bc) {
+    pdl_trigger();
     const int i = blockIdx.x * BS + threadIdx.x;
-    if (i >= nc) return;
+    const bool ok = i < nc;
+    const int e0 = ok ? ptr[i] : 0, e1 = ok ? ptr[i + 1] : 0;
+    int f0 = -1, f1 = -1;
+    double p0 = 0.0, p1 = 0.0;
+    if (e0 < e1) { f0 = f[e0]; p0 = pv[e0]; }
+    if (e0 + 1 < e1) { f1 = f[e0 + 1]; p1 = pv[e0 + 1]; }
+    pdl_wait();
+    if (!ok) return;
     const double *bF = b + nc;
     double s = b[i];
-    for (int e = ptr[i]; e < ptr[i + 1]; e++) s += pv[e] * bF[f[e]];
+    if (f0 >= 0) s += p0 * bF[f0];
+    if (f1 >= 0) s += p1 * bF[f1];
+    for (int e = e0 + 2; e < e1; e++) s += pv[e] * bF[f[e]];
     bc[i] = s;
 }
 
@@ -176,37 +210,40 @@ __global__ void k_elim_restrict(int nc, const int32_t *__restrict__ ptr, const i
 __global__ void k_elim_interp(int nc, int nF, const int32_t *__restrict__ col,
                               const double *__restrict__ pv, const double *__restrict__ dF,
                               const double *__restrict__ b, double *x) {
+    pdl_trigger();
     const int t = blockIdx.x * BS + threadIdx.x;
-    if (t >= nF) return;
-    double s = 0.0;
+    const bool ok = t < nF;
+    int c[4];
+    double p[4];
 #pragma unroll
     for (int j = 0; j < 4; j++) {
-        const int c = col[4 * t + j];
-        if (c >= 0) s += pv[4 * t + j] * x[c];
+        c[j] = ok ? col[4 * t + j] : -1;
+        p[j] = ok ? pv[4 * t + j] : 0.0;
     }
-    x[nc + t] = s + b[nc + t] / dF[t];
+    const double d = ok ? dF[t] : 1.0;
+    pdl_wait();
+    if (!ok) return;
+    double s = 0.0;
+#pragma unroll
+    for (int j = 0; j < 4; j++)
+        if (c[j] >= 0) s += p[j] * x[c[j]];
+    x[nc + t] = s + b[nc + t] / d;
 }
 
-// Coarsest level: x = A^+ b (one warp per row of the dense pseudo-inverse), then the mean-zero
-// projection done by the last block.
+// Coarsest level: x = Pi A^+ b with the mean-zero projection Pi = I - J/n folded into the stored
+// dense matrix (one warp per row).
 __global__ void __launch_bounds__(BS) k_coarse(int n, const double *__restrict__ pinv,
-                                               const double *__restrict__ b, double *x,
-                                               const Reduce red) {
+                                               const double *__restrict__ b, double *x) {
+    pdl_trigger();
+    pdl_wait();
     const int lane = threadIdx.x & 31;
     const int wg = (blockIdx.x * BS + threadIdx.x) >> 5, nwarps = (gridDim.x * BS) >> 5;
-    double part[1] = {0.0};
     for (int i = wg; i < n; i += nwarps) {
         const double *row = pinv + (int64_t)i * n;
         double s = 0.0;
         for (int j = lane; j < n; j += 32) s += row[j] * b[j];
         s = warp_sum(s);
-        if (lane == 0) { x[i] = s; part[0] += s; }
-    }
-    if (grid_sum<1>(part, red)) {
-        __shared__ double mean;
-        if (threadIdx.x == 0) mean = part[0] / (double)n;
-        __syncthreads();
-        for (int i = threadIdx.x; i < n; i += BS) x[i] = __ldcg(&x[i]) - mean;
+        if (lane == 0) x[i] = s;
     }
 }
 
@@ -214,24 +251,34 @@ __global__ void __launch_bounds__(BS) k_coarse(int n, const double *__restrict__
 
 __global__ void k_gather(int n, const int32_t *__restrict__ perm, const double *__restrict__ src,
                          double *dst) {
+    pdl_trigger();
     const int i = blockIdx.x * BS + threadIdx.x;
-    if (i < n) dst[i] = src[perm[i]];
+    const int j = i < n ? perm[i] : 0;
+    pdl_wait();
+    if (i < n) dst[i] = src[j];
 }
 
 __global__ void k_scatter(int n, const int32_t *__restrict__ perm, const double *__restrict__ src,
                           double *dst) {
+    pdl_trigger();
     const int i = blockIdx.x * BS + threadIdx.x;
-    if (i < n) dst[perm[i]] = src[i];
+    const int j = i < n ? perm[i] : 0;
+    pdl_wait();
+    if (i < n) dst[j] = src[i];
 }
 
 // S_MEAN = (sum v) / n
 __global__ void __launch_bounds__(BS) k_sum(int n, const double *__restrict__ v, const Reduce red) {
+    pdl_trigger();
+    pdl_wait();
     double s[1] = {0.0};
     for (int i = blockIdx.x * BS + threadIdx.x; i < n; i += gridDim.x * BS) s[0] += v[i];
     if (grid_sum<1>(s, red) && threadIdx.x == 0) red.scal[S_MEAN] = s[0] / (double)n;
 }
 
 __global__ void k_sub_mean(int n, double *v, const Reduce red) {
+    pdl_trigger();
+    pdl_wait();
     const int i = blockIdx.x * BS + threadIdx.x;
     if (i < n) v[i] -= red.scal[S_MEAN];
 }
@@ -239,6 +286,8 @@ __global__ void k_sub_mean(int n, double *v, const Reduce red) {
 // b <- b - mean(b) (kept in bkeep), S_BN2 = ||b||^2; x = p = zold = 0, S_RZ = 1.
 __global__ void __launch_bounds__(BS) k_init_b(int n, double *r, double *bkeep, double *x, double *p,
                                                double *zold, const Reduce red) {
+    pdl_trigger();
+    pdl_wait();
     const double m = red.scal[S_MEAN];
     double s[1] = {0.0};
     for (int i = blockIdx.x * BS + threadIdx.x; i < n; i += gridDim.x * BS) {
@@ -265,6 +314,8 @@ __global__ void __launch_bounds__(BS) k_spmv_dot(int n, const int32_t *__restric
                                                  const double *__restrict__ diag,
                                                  const double *__restrict__ p, double *q,
                                                  const Reduce red) {
+    pdl_trigger();
+    pdl_wait();
     const int groups = gridDim.x * (BS / TPR);
     const int sub = threadIdx.x % TPR;
     double pq[1] = {0.0};
@@ -287,6 +338,8 @@ __global__ void __launch_bounds__(BS) k_spmv_dot(int n, const int32_t *__restric
 // x += alpha p, r -= alpha q, S_RR = ||r||^2
 __global__ void __launch_bounds__(BS) k_update_xr(int n, double *x, double *r, const double *__restrict__ p,
                                                   const double *__restrict__ q, const Reduce red) {
+    pdl_trigger();
+    pdl_wait();
     const double a = red.scal[S_ALPHA];
     double s[1] = {0.0};
     for (int i = blockIdx.x * BS + threadIdx.x; i < n; i += gridDim.x * BS) {
@@ -301,6 +354,8 @@ __global__ void __launch_bounds__(BS) k_update_xr(int n, double *x, double *r, c
 // z -= mean(z); beta = r.(z - zold) / rz_old; rz = r.z (flexible CG, Polak-Ribiere form)
 __global__ void __launch_bounds__(BS) k_proj_dots(int n, double *z, const double *__restrict__ zold,
                                                   const double *__restrict__ r, const Reduce red) {
+    pdl_trigger();
+    pdl_wait();
     const double m = red.scal[S_MEAN];
     double s[2] = {0.0, 0.0};
     for (int i = blockIdx.x * BS + threadIdx.x; i < n; i += gridDim.x * BS) {
@@ -317,6 +372,8 @@ __global__ void __launch_bounds__(BS) k_proj_dots(int n, double *z, const double
 
 // p = z + beta p, zold = z
 __global__ void k_update_p(int n, const double *__restrict__ z, double *p, double *zold, const Reduce red) {
+    pdl_trigger();
+    pdl_wait();
     const int i = blockIdx.x * BS + threadIdx.x;
     if (i >= n) return;
     const double beta = red.scal[S_BETA];
@@ -333,6 +390,8 @@ __global__ void __launch_bounds__(BS) k_true_resid(int n, const int32_t *__restr
                                                    const double *__restrict__ diag,
                                                    const double *__restrict__ x,
                                                    const double *__restrict__ b, const Reduce red) {
+    pdl_trigger();
+    pdl_wait();
     const int groups = gridDim.x * (BS / TPR);
     const int sub = threadIdx.x % TPR;
     double acc[1] = {0.0};
@@ -352,6 +411,27 @@ __global__ void __launch_bounds__(BS) k_true_resid(int n, const int32_t *__restr
 
 // ------------------------------------------------------------------------------- launchers
 
+static bool g_pdl = true;
+
+void set_pdl(bool on) { g_pdl = on; }
+
+// Launch with programmatic stream serialisation, so the kernel may start while its
+// predecessor in the stream is still running (it waits for it at griddepcontrol.wait).
+template <typename... KArgs, typename... Args>
+static void launch(void (*kernel)(KArgs...), unsigned grid, cudaStream_t s, Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid < 1 ? 1 : grid);
+    cfg.blockDim = dim3(BS);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = g_pdl ? 1 : 0;
+    cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+
 static inline unsigned blocks(int64_t work) { return (unsigned)((work + BS - 1) / BS); }
 static inline unsigned red_blocks(int64_t work) {
     int64_t b = (work + BS - 1) / BS;
@@ -365,38 +445,42 @@ int choose_tpr(double avg_row) {
     return t;
 }
 
-#define TPR_DISPATCH(tpr, KERNEL, GRID, ...)                                  \
-    switch (tpr) {                                                            \
-        case 1: KERNEL<1><<<GRID(1), BS, 0, s>>>(__VA_ARGS__); break;         \
-        case 2: KERNEL<2><<<GRID(2), BS, 0, s>>>(__VA_ARGS__); break;         \
-        case 4: KERNEL<4><<<GRID(4), BS, 0, s>>>(__VA_ARGS__); break;         \
-        case 8: KERNEL<8><<<GRID(8), BS, 0, s>>>(__VA_ARGS__); break;         \
-        case 16: KERNEL<16><<<GRID(16), BS, 0, s>>>(__VA_ARGS__); break;      \
-        default: KERNEL<32><<<GRID(32), BS, 0, s>>>(__VA_ARGS__); break;      \
+#define TPR_DISPATCH(tpr, KERNEL, GRID, ...)                          \
+    switch (tpr) {                                                    \
+        case 1: launch(KERNEL<1>, GRID(1), s, __VA_ARGS__); break;    \
+        case 2: launch(KERNEL<2>, GRID(2), s, __VA_ARGS__); break;    \
+        case 4: launch(KERNEL<4>, GRID(4), s, __VA_ARGS__); break;    \
+        case 8: launch(KERNEL<8>, GRID(8), s, __VA_ARGS__); break;    \
+        case 16: launch(KERNEL<16>, GRID(16), s, __VA_ARGS__); break; \
+        default: launch(KERNEL<32>, GRID(32), s, __VA_ARGS__); break; \
     }
 
 void launch_op(const Op &op, std::vector<DevLevel> &lv, const Reduce &red, cudaStream_t s) {
+    (void)red;
     DevLevel &L = lv[op.level];
     const int n = (int)L.n;
     switch (op.kind) {
         case OP_GS_FIRST:
-            k_gs_first<<<blocks(n), BS, 0, s>>>(n, (int)L.cptr[1], L.diag, L.b, L.x);
+            launch(k_gs_first, blocks(n), s, n, (int)L.cptr[1], (const double *)L.diag, (const double *)L.b, L.x);
             break;
         case OP_ZERO:
-            k_zero<<<blocks(n), BS, 0, s>>>(n, L.x);
+            launch(k_zero, blocks(n), s, n, L.x);
             break;
         case OP_GS: {
             const int r0 = (int)L.cptr[op.colour], r1 = (int)L.cptr[op.colour + 1];
             const int64_t rows = r1 - r0;
             if (rows <= 0) break;
 #define GRID_GS(T) blocks(rows * (T))
-            TPR_DISPATCH(L.tpr, k_gs, GRID_GS, r0, r1, L.rp, L.ci, L.val, L.diag, L.b, L.x);
+            TPR_DISPATCH(L.tpr, k_gs, GRID_GS, r0, r1, (const int32_t *)L.rp, (const int32_t *)L.ci,
+                         (const double *)L.val, (const double *)L.diag, (const double *)L.b, L.x);
 #undef GRID_GS
             break;
         }
         case OP_RESID: {
 #define GRID_R(T) blocks((int64_t)n * (T))
-            TPR_DISPATCH(L.tpr, k_resid, GRID_R, n, L.rp, L.ci, L.val, L.diag, L.x, L.b, L.r);
+            TPR_DISPATCH(L.tpr, k_resid, GRID_R, n, (const int32_t *)L.rp, (const int32_t *)L.ci,
+                         (const double *)L.val, (const double *)L.diag, (const double *)L.x,
+                         (const double *)L.b, L.r);
 #undef GRID_R
             break;
         }
@@ -404,76 +488,81 @@ void launch_op(const Op &op, std::vector<DevLevel> &lv, const Reduce &red, cudaS
             DevLevel &Cl = lv[op.level + 1];
             const int nc = (int)L.nc;
 #define GRID_P(T) blocks((int64_t)nc * (T))
-            TPR_DISPATCH(L.pt_tpr, k_restrict, GRID_P, nc, L.pt_ptr, L.pt_row, L.pt_w, L.r, Cl.b);
+            TPR_DISPATCH(L.pt_tpr, k_restrict, GRID_P, nc, (const int32_t *)L.pt_ptr, (const int32_t *)L.pt_row,
+                         (const double *)L.pt_w, (const double *)L.r, Cl.b);
 #undef GRID_P
             break;
         }
         case OP_PROLONG:
-            k_prolong<<<blocks(n), BS, 0, s>>>(n, L.agg, L.agg2, L.wt, lv[op.level + 1].x, L.x);
+            launch(k_prolong, blocks(n), s, n, (const int32_t *)L.agg, (const int32_t *)L.agg2,
+                   (const double *)L.wt, (const double *)lv[op.level + 1].x, L.x);
             break;
         case OP_ELIM_RESTRICT:
-            k_elim_restrict<<<blocks(L.nc), BS, 0, s>>>((int)L.nc, L.pft_ptr, L.pft_f, L.pft_val, L.b,
-                                                        lv[op.level + 1].b);
+            launch(k_elim_restrict, blocks(L.nc), s, (int)L.nc, (const int32_t *)L.pft_ptr,
+                   (const int32_t *)L.pft_f, (const double *)L.pft_val, (const double *)L.b,
+                   lv[op.level + 1].b);
             break;
         case OP_ELIM_INTERP:
             if (L.nF > 0)
-                k_elim_interp<<<blocks(L.nF), BS, 0, s>>>((int)L.nc, (int)L.nF, L.pf_col, L.pf_val, L.dF,
-                                                          L.b, L.x);
+                launch(k_elim_interp, blocks(L.nF), s, (int)L.nc, (int)L.nF, (const int32_t *)L.pf_col,
+                       (const double *)L.pf_val, (const double *)L.dF, (const double *)L.b, L.x);
             break;
         case OP_COARSE:
-            k_coarse<<<red_blocks((int64_t)n * 32), BS, 0, s>>>(n, L.pinv, L.b, L.x, red);
+            launch(k_coarse, red_blocks((int64_t)n * 32), s, n, (const double *)L.pinv, (const double *)L.b, L.x);
             break;
     }
 }
 
 void launch_gather(int64_t n, const int32_t *perm, const double *src, double *dst, cudaStream_t s) {
-    k_gather<<<blocks(n), BS, 0, s>>>((int)n, perm, src, dst);
+    launch(k_gather, blocks(n), s, (int)n, perm, src, dst);
 }
 
 void launch_scatter(int64_t n, const int32_t *perm, const double *src, double *dst, cudaStream_t s) {
-    k_scatter<<<blocks(n), BS, 0, s>>>((int)n, perm, src, dst);
+    launch(k_scatter, blocks(n), s, (int)n, perm, src, dst);
 }
 
 void launch_sum(int64_t n, const double *v, const Reduce &red, cudaStream_t s) {
-    k_sum<<<red_blocks(n), BS, 0, s>>>((int)n, v, red);
+    launch(k_sum, red_blocks(n), s, (int)n, v, red);
 }
 
 void launch_sub_mean(int64_t n, double *v, const Reduce &red, cudaStream_t s) {
-    k_sub_mean<<<blocks(n), BS, 0, s>>>((int)n, v, red);
+    launch(k_sub_mean, blocks(n), s, (int)n, v, red);
 }
 
 void launch_init_b(int64_t n, double *r, double *bkeep, double *x, double *p, double *zold,
                    const Reduce &red, cudaStream_t s) {
-    k_init_b<<<red_blocks(n), BS, 0, s>>>((int)n, r, bkeep, x, p, zold, red);
+    launch(k_init_b, red_blocks(n), s, (int)n, r, bkeep, x, p, zold, red);
 }
 
 void launch_spmv_dot(const DevLevel &L, const double *p, double *q, const Reduce &red, cudaStream_t s) {
     const int n = (int)L.n;
 #define GRID_S(T) red_blocks((int64_t)n * (T))
-    TPR_DISPATCH(L.tpr, k_spmv_dot, GRID_S, n, L.rp, L.ci, L.val, L.diag, p, q, red);
+    TPR_DISPATCH(L.tpr, k_spmv_dot, GRID_S, n, (const int32_t *)L.rp, (const int32_t *)L.ci,
+                 (const double *)L.val, (const double *)L.diag, p, q, red);
 #undef GRID_S
 }
 
 void launch_update_xr(int64_t n, double *x, double *r, const double *p, const double *q,
                       const Reduce &red, cudaStream_t s) {
-    k_update_xr<<<red_blocks(n), BS, 0, s>>>((int)n, x, r, p, q, red);
+    launch(k_update_xr, red_blocks(n), s, (int)n, x, r, p, q, red);
 }
 
 void launch_proj_dots(int64_t n, double *z, const double *zold, const double *r, const Reduce &red,
                       cudaStream_t s) {
-    k_proj_dots<<<red_blocks(n), BS, 0, s>>>((int)n, z, zold, r, red);
+    launch(k_proj_dots, red_blocks(n), s, (int)n, z, zold, r, red);
 }
 
 void launch_update_p(int64_t n, const double *z, double *p, double *zold, const Reduce &red,
                      cudaStream_t s) {
-    k_update_p<<<blocks(n), BS, 0, s>>>((int)n, z, p, zold, red);
+    launch(k_update_p, blocks(n), s, (int)n, z, p, zold, red);
 }
 
 void launch_true_resid(const DevLevel &L, const double *x, const double *b, const Reduce &red,
                        cudaStream_t s) {
     const int n = (int)L.n;
 #define GRID_T(T) red_blocks((int64_t)n * (T))
-    TPR_DISPATCH(L.tpr, k_true_resid, GRID_T, n, L.rp, L.ci, L.val, L.diag, x, b, red);
+    TPR_DISPATCH(L.tpr, k_true_resid, GRID_T, n, (const int32_t *)L.rp, (const int32_t *)L.ci,
+                 (const double *)L.val, (const double *)L.diag, x, b, red);
 #undef GRID_T
 }
 

@@ -65,13 +65,55 @@ struct Op {
 // Reduction workspace: per-block partial sums, a completion ticket, device scalars.
 constexpr int RED_MAXG = 1184;   // 148 SMs x 8 blocks
 constexpr int RED_NV = 4;
-enum Scalar { S_RZ = 0, S_PQ, S_ALPHA, S_BETA, S_RR, S_BN2, S_MEAN, S_TRUE_RR, S_BMEAN, S_COUNT = 16 };
+enum Scalar { S_RZ = 0, S_PQ, S_ALPHA, S_BETA, S_RR, S_BN2, S_MEAN, S_TRUE_RR, S_BMEAN, S_ITERS, S_COUNT = 16 };
 
 struct Reduce {
     double *partials = nullptr;   // RED_NV x RED_MAXG
     unsigned *ticket = nullptr;
     double *scal = nullptr;       // S_COUNT
 };
+
+// Plain-data view of a level for the persistent kernel (device pointers only).
+struct PLevel {
+    int kind, n, nc, nF, ncol, tpr, pt_tpr, cptr_off;  // colour offsets at cptr_all + cptr_off
+    const int32_t *rp, *ci;
+    const double *val, *diag;
+    const int32_t *agg, *agg2;
+    const double *wt;
+    const int32_t *pt_ptr, *pt_row;
+    const double *pt_w;
+    const int32_t *pf_col;
+    const double *pf_val, *dF;
+    const int32_t *pft_ptr, *pft_f;
+    const double *pft_val;
+    const double *pinv;
+    double *x, *b, *r;
+};
+
+// Grid barrier state: arrival count, generation, failure flag.
+struct GridBar {
+    unsigned count, gen, err, pad;
+};
+
+struct PSolve {
+    int nlev, nops, n0, ncptr;
+    const PLevel *lv;
+    const Op *ops;
+    const int32_t *tail_end;      // per op: end of the single-CTA segment starting here, or -1
+    const int32_t *cptr_all;      // concatenated colour offsets of all levels
+    const int32_t *perm0;
+    double *r, *p, *q, *zold, *xs, *bkeep;
+    double *partials;             // 2 x RED_NV x grid
+    GridBar *bar;
+    double *scal;                 // S_COUNT outputs
+    double *hist;                 // relres per iteration
+};
+
+size_t persistent_smem(int nlev, int nops, int ncptr);
+int persistent_grid(int device, size_t smem);
+cudaError_t launch_persistent(const PSolve *P, int grid, size_t smem, int mode, int maxit, double tol,
+                              const double *b_in, double *phi_out, cudaStream_t s,
+                              unsigned long long *prof = nullptr);
 
 // launchers (cycle_kernels.cu)
 void launch_op(const Op &op, std::vector<DevLevel> &lv, const Reduce &red, cudaStream_t s);

@@ -34,12 +34,25 @@ struct lamg_hier {
     Reduce red;
     double *h_scal = nullptr;  // pinned
     cudaGraphExec_t g_cycle = nullptr, g_tail = nullptr, g_head = nullptr;
-    cudaEvent_t ev_a = nullptr, ev_b = nullptr, ev_poll = nullptr;
+    cudaEvent_t ev_a = nullptr, ev_b = nullptr, ev_poll = nullptr, ev_k0 = nullptr, ev_k1 = nullptr;
+    // persistent solve kernel
+    PSolve *psolve = nullptr;     // device copy
+    PSolve ph{};                  // host copy of the same pointers
+    GridBar *bar = nullptr;
+    double *hist = nullptr;
+    int hist_cap = 0;
+    int grid = 0;
+    size_t smem = 0;
+    bool persistent_ok = false;
+    double cycle_bytes = 0.0;     // algorithmic DRAM bytes of one cycle
+    int64_t cycle_launches = 0;   // kernels of one cycle in the graph path
     std::vector<void *> allocs;
     size_t dev_bytes = 0;
     double wait_timeout_s = 120.0;
 
     ~lamg_hier() {
+        if (ev_k0) cudaEventDestroy(ev_k0);
+        if (ev_k1) cudaEventDestroy(ev_k1);
         if (g_cycle) cudaGraphExecDestroy(g_cycle);
         if (g_tail) cudaGraphExecDestroy(g_tail);
         if (g_head) cudaGraphExecDestroy(g_head);
@@ -206,9 +219,15 @@ int upload_level(lamg_hier *h, int l) {
             (rc = dupload(h, &D.pft_ptr, ptr)) || (rc = dupload(h, &D.pft_f, fidx)) || (rc = dupload(h, &D.pft_val, fval)))
             return rc;
     } else {
-        std::vector<double> P(n * n);
+        // (I - J/n) A^+: the coarsest solve and its mean-zero projection as one matrix
+        std::vector<double> P(n * n), colmean(n, 0.0);
         for (int64_t i = 0; i < n; i++)
             for (int64_t j = 0; j < n; j++) P[i * n + j] = H.pinv[(int64_t)D.perm[i] * n + D.perm[j]];
+        for (int64_t i = 0; i < n; i++)
+            for (int64_t j = 0; j < n; j++) colmean[j] += P[i * n + j];
+        for (int64_t j = 0; j < n; j++) colmean[j] /= (double)n;
+        for (int64_t i = 0; i < n; i++)
+            for (int64_t j = 0; j < n; j++) P[i * n + j] -= colmean[j];
         if ((rc = dupload(h, &D.pinv, P))) return rc;
     }
     return LAMG_OK;
@@ -268,6 +287,112 @@ int capture(lamg_hier *h, cudaGraphExec_t *out, int which) {
     return cuda_status(e);
 }
 
+// Algorithmic DRAM bytes of one step of the persistent schedule (FP64 values, int32 indices;
+// each array read or written once, gathered vectors counted once).
+double op_bytes(const lamg_hier *h, const Op &op) {
+    const HostLevel &H = h->host[op.level];
+    const DevLevel &D = h->dev[op.level];
+    const double n = (double)D.n, z = (double)D.nnz, nc = (double)D.nc, nF = (double)D.nF;
+    switch (op.kind) {
+        case OP_GS_FIRST: return 16.0 * (double)D.cptr[1] + 8 * n;
+        case OP_ZERO: return 8 * n;
+        case OP_GS: {
+            const int64_t r0 = D.cptr[op.colour], r1 = D.cptr[op.colour + 1];
+            double zc = 0;
+            for (int64_t i = r0; i < r1; i++) {
+                const int32_t u = D.perm[i];
+                zc += (double)(H.A.rp[u + 1] - H.A.rp[u]);
+            }
+            const double R = (double)(r1 - r0);
+            return 12 * zc + 28 * R + 4 + 8 * std::min(zc, n);
+        }
+        case OP_RESID: return 0.0;  // fused into the restriction
+        case OP_RESTRICT: {
+            double E = 0;
+            for (int64_t u = 0; u < D.n; u++) E += H.agg2[u] < 0 ? 1 : (H.wt[u] != 0.0 ? 2 : 1);
+            return 12 * z + 28 * n + 12 * E + 12 * nc + 4;
+        }
+        case OP_PROLONG: return 32 * n + 8 * nc;
+        case OP_ELIM_RESTRICT: {
+            double E = 0;
+            for (int64_t u = 0; u < D.n; u++)
+                if (H.cidx[u] < 0) E += (double)(H.A.rp[u + 1] - H.A.rp[u]);
+            return 20 * nc + 12 * E + 8 * nF + 4;
+        }
+        case OP_ELIM_INTERP: return 72 * nF + 8 * nc;
+        case OP_COARSE: return 8 * n * n + 16 * n;
+    }
+    return 0.0;
+}
+
+// Device tables of the persistent solve kernel.
+int setup_persistent(lamg_hier *h) {
+    int rc;
+    const int L = (int)h->dev.size();
+    const int64_t tail_rows = h->opt.tail_rows > 0 ? h->opt.tail_rows : 8192;
+    std::vector<PLevel> pl(L);
+    std::vector<int32_t> cptr_all;
+    for (int l = 0; l < L; l++) {
+        DevLevel &D = h->dev[l];
+        PLevel &P = pl[l];
+        std::memset(&P, 0, sizeof(P));
+        P.kind = D.kind; P.n = (int)D.n; P.nc = (int)D.nc; P.nF = (int)D.nF; P.ncol = D.ncol;
+        P.tpr = D.tpr; P.pt_tpr = D.pt_tpr;
+        P.cptr_off = (int)cptr_all.size();
+        for (int64_t c : D.cptr) cptr_all.push_back((int32_t)c);
+        P.rp = D.rp; P.ci = D.ci; P.val = D.val; P.diag = D.diag;
+        P.agg = D.agg; P.agg2 = D.agg2; P.wt = D.wt;
+        P.pt_ptr = D.pt_ptr; P.pt_row = D.pt_row; P.pt_w = D.pt_w;
+        P.pf_col = D.pf_col; P.pf_val = D.pf_val; P.dF = D.dF;
+        P.pft_ptr = D.pft_ptr; P.pft_f = D.pft_f; P.pft_val = D.pft_val;
+        P.pinv = D.pinv;
+        P.x = D.x; P.b = D.b; P.r = D.r;
+    }
+    if (cptr_all.empty()) cptr_all.push_back(0);
+    // single-CTA segments: maximal runs of steps on levels with at most tail_rows rows (the
+    // dense coarsest only while its matrix is at most 512 x 512)
+    const int nops = (int)h->ops.size();
+    std::vector<uint8_t> small(nops, 0);
+    for (int i = 0; i < nops; i++) {
+        const DevLevel &D = h->dev[h->ops[i].level];
+        small[i] = D.kind == KIND_COARSEST ? (D.n <= 512 && D.n <= tail_rows) : (D.n <= tail_rows);
+    }
+    std::vector<int32_t> tail_end(nops, -1);
+    for (int i = 0; i < nops;) {
+        if (!small[i]) { i++; continue; }
+        int j = i;
+        while (j < nops && small[j]) j++;
+        tail_end[i] = j;
+        i = j;
+    }
+    h->smem = persistent_smem(L, nops, (int)cptr_all.size());
+    if (h->smem > 200 * 1024) return LAMG_OK;  // tables do not fit: graph path only
+    h->grid = persistent_grid(h->device, h->smem);
+    if (h->grid < 1) return LAMG_OK;
+    PLevel *dlv = nullptr;
+    Op *dops = nullptr;
+    int32_t *dtail = nullptr, *dcptr = nullptr;
+    if ((rc = dupload(h, &dlv, pl)) || (rc = dupload(h, &dops, h->ops)) || (rc = dupload(h, &dtail, tail_end)) ||
+        (rc = dupload(h, &dcptr, cptr_all)))
+        return rc;
+    PSolve &S = h->ph;
+    std::memset(&S, 0, sizeof(S));
+    S.nlev = L; S.nops = nops; S.n0 = (int)h->dev[0].n; S.ncptr = (int)cptr_all.size();
+    S.lv = dlv; S.ops = dops; S.tail_end = dtail; S.cptr_all = dcptr; S.perm0 = h->perm0;
+    S.r = h->r; S.p = h->p; S.q = h->q; S.zold = h->zold; S.xs = h->xs; S.bkeep = h->bkeep;
+    if ((rc = dalloc(h, &S.partials, 2 * RED_NV * h->grid)) || (rc = dalloc(h, &h->bar, 1))) return rc;
+    S.bar = h->bar;
+    S.scal = h->red.scal;
+    h->hist_cap = 1024;
+    if ((rc = dalloc(h, &h->hist, h->hist_cap))) return rc;
+    S.hist = h->hist;
+    if ((rc = dalloc(h, &h->psolve, 1))) return rc;
+    CKR(cudaMemcpy(h->psolve, &S, sizeof(S), cudaMemcpyHostToDevice));
+    CKR(cudaMemset(h->bar, 0, sizeof(GridBar)));
+    h->persistent_ok = true;
+    return LAMG_OK;
+}
+
 // Build device data, schedule and graphs for h->host.
 int finalize(lamg_hier *h) {
     int rc;
@@ -308,6 +433,16 @@ int finalize(lamg_hier *h) {
     emit_visit(h, visits, 0, true);
     if ((rc = capture(h, &h->g_cycle, 0)) || (rc = capture(h, &h->g_tail, 1)) || (rc = capture(h, &h->g_head, 2)))
         return rc;
+    CKR(cudaEventCreate(&h->ev_k0));
+    CKR(cudaEventCreate(&h->ev_k1));
+    h->cycle_bytes = 0.0;
+    for (const Op &op : h->ops) h->cycle_bytes += op_bytes(h, op);
+    h->cycle_launches = 0;
+    for (const Op &op : h->ops)
+        if (!(op.kind == OP_ELIM_INTERP && h->dev[op.level].nF == 0) &&
+            !(op.kind == OP_GS && h->dev[op.level].cptr[op.colour + 1] == h->dev[op.level].cptr[op.colour]))
+            h->cycle_launches++;
+    if ((rc = setup_persistent(h))) return rc;
     CKR(cudaStreamSynchronize(h->stream));
     return LAMG_OK;
 }
@@ -357,6 +492,7 @@ void lamg_options_default(lamg_options *o) {
     o->guard_eps = 1e-10;
     o->gamma_fixed = 0.0;
     o->device = 0;
+    o->tail_rows = 8192;
 }
 
 const char *lamg_strerror(int c) {
@@ -454,9 +590,7 @@ void lamg_destroy(lamg_hier *h) {
     delete h;
 }
 
-int lamg_solve(lamg_hier *h, const double *b, double *phi, const lamg_solve_opts *so, lamg_stats *st) {
-    if (!h || !b || !phi || !so || !(so->tol > 0) || so->maxit < 1) return LAMG_ERR_INVALID;
-    CKR(cudaSetDevice(h->device));
+static int solve_graph(lamg_hier *h, const double *b, double *phi, const lamg_solve_opts *so, lamg_stats *st) {
     cudaStream_t s = so->stream ? (cudaStream_t)so->stream : h->stream;
     const bool devp = so->flags & LAMG_DEVICE_PTRS;
     const DevLevel &F = h->dev[0];
@@ -501,8 +635,84 @@ int lamg_solve(lamg_hier *h, const double *b, double *phi, const lamg_solve_opts
         float ms = 0.f;
         cudaEventElapsedTime(&ms, h->ev_a, h->ev_b);
         st->solve_ms = ms;
+        st->kernel_ms = ms;
+        const double z0 = (double)h->dev[0].nnz, n0 = (double)n;
+        st->alg_bytes = (double)it * (h->cycle_bytes + 12 * z0 + 148 * n0) + h->cycle_bytes + 72 * n0 +
+                        (12 * z0 + 36 * n0) + 16 * n0;
+        // gather, sum, init; per cycle the schedule + mean, projection/dots, p update (one
+        // cycle per iteration that did not stop, plus the first); per iteration SpMV-dot and
+        // x/r update; true residual and scatter
+        const int64_t cycles = rel <= so->tol ? it : it + 1;
+        st->launches = 3 + 2 * (int64_t)it + cycles * (h->cycle_launches + 3) + 2;
     }
     return rel <= so->tol ? LAMG_OK : LAMG_ERR_NOT_CONVERGED;
+}
+
+// The whole solve as one cooperative launch of the persistent kernel.
+static int solve_persistent(lamg_hier *h, const double *b, double *phi, const lamg_solve_opts *so,
+                            lamg_stats *st) {
+    cudaStream_t s = so->stream ? (cudaStream_t)so->stream : h->stream;
+    const bool devp = so->flags & LAMG_DEVICE_PTRS;
+    const int64_t n = h->dev[0].n;
+    int rc = LAMG_OK;
+    if (so->maxit + 1 > h->hist_cap) {
+        double *nh = nullptr;
+        if ((rc = dalloc(h, &nh, so->maxit + 1))) return rc;
+        h->hist = nh;
+        h->hist_cap = so->maxit + 1;
+        h->ph.hist = nh;
+        CKR(cudaMemcpyAsync(h->psolve, &h->ph, sizeof(PSolve), cudaMemcpyHostToDevice, s));
+    }
+    CKR(cudaEventRecord(h->ev_a, s));
+    const double *b_in = b;
+    double *phi_out = phi;
+    if (!devp) {
+        CKR(cudaMemcpyAsync(h->nat_in, b, n * sizeof(double), cudaMemcpyHostToDevice, s));
+        b_in = h->nat_in;
+        phi_out = h->nat_out;
+    }
+    CKR(cudaMemsetAsync(h->bar, 0, sizeof(GridBar), s));
+    CKR(cudaEventRecord(h->ev_k0, s));
+    CKR(launch_persistent(h->psolve, h->grid, h->smem, 0, so->maxit, so->tol, b_in, phi_out, s));
+    CKR(cudaEventRecord(h->ev_k1, s));
+    if (!devp) CKR(cudaMemcpyAsync(phi, h->nat_out, n * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CKR(cudaMemcpyAsync(h->h_scal, h->red.scal, S_COUNT * sizeof(double), cudaMemcpyDeviceToHost, s));
+    GridBar hb{};
+    CKR(cudaMemcpyAsync(&hb, h->bar, sizeof(GridBar), cudaMemcpyDeviceToHost, s));
+    CKR(cudaEventRecord(h->ev_b, s));
+    if ((rc = wait_event(h, h->ev_b))) return rc;
+    CKR(cudaGetLastError());
+    if (hb.err) return LAMG_ERR_TIMEOUT;
+    const int it = (int)h->h_scal[S_ITERS];
+    const double bn2 = h->h_scal[S_BN2];
+    const double rel = bn2 > 0 ? std::sqrt(h->h_scal[S_RR] / bn2) : 0.0;
+    if (st) {
+        if (st->hist) CKR(cudaMemcpy(st->hist, h->hist, (it + 1) * sizeof(double), cudaMemcpyDeviceToHost));
+        st->iters = it;
+        st->nlevels = (int32_t)h->dev.size();
+        st->relres = rel;
+        st->relres_true = bn2 > 0 ? std::sqrt(h->h_scal[S_TRUE_RR] / bn2) : 0.0;
+        st->b_mean = h->h_scal[S_BMEAN];
+        float ms = 0.f, kms = 0.f;
+        cudaEventElapsedTime(&ms, h->ev_a, h->ev_b);
+        cudaEventElapsedTime(&kms, h->ev_k0, h->ev_k1);
+        st->solve_ms = ms;
+        st->kernel_ms = kms;
+        // per iteration: cycle + CG vectors (SpMV with dot 12z+28n, x/r update 48n, mean 8n,
+        // projection with dots 32n, p update 32n); once: gather/projection of b, true residual
+        const double z0 = (double)h->dev[0].nnz, n0 = (double)n;
+        st->alg_bytes = (double)it * (h->cycle_bytes + 12 * z0 + 148 * n0) + h->cycle_bytes + 72 * n0 +
+                        (12 * z0 + 36 * n0) + 16 * n0;
+        st->launches = 1;
+    }
+    return rel <= so->tol ? LAMG_OK : LAMG_ERR_NOT_CONVERGED;
+}
+
+int lamg_solve(lamg_hier *h, const double *b, double *phi, const lamg_solve_opts *so, lamg_stats *st) {
+    if (!h || !b || !phi || !so || !(so->tol > 0) || so->maxit < 1) return LAMG_ERR_INVALID;
+    CKR(cudaSetDevice(h->device));
+    if (!(so->flags & LAMG_PERSISTENT) || !h->persistent_ok) return solve_graph(h, b, phi, so, st);
+    return solve_persistent(h, b, phi, so, st);
 }
 
 int lamg_cycle(lamg_hier *h, const double *r, double *z, uint32_t flags) {
@@ -512,14 +722,62 @@ int lamg_cycle(lamg_hier *h, const double *r, double *z, uint32_t flags) {
     const int64_t n = h->dev[0].n;
     const bool devp = flags & LAMG_DEVICE_PTRS;
     CKR(cudaMemcpyAsync(h->nat_in, r, n * sizeof(double), devp ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
-    launch_gather(n, h->perm0, h->nat_in, h->r, s);
-    CKR(cudaGraphLaunch(h->g_cycle, s));
-    launch_scatter(n, h->perm0, h->dev[0].x, h->nat_out, s);
+    if (!(flags & LAMG_PERSISTENT) || !h->persistent_ok) {
+        launch_gather(n, h->perm0, h->nat_in, h->r, s);
+        CKR(cudaGraphLaunch(h->g_cycle, s));
+        launch_scatter(n, h->perm0, h->dev[0].x, h->nat_out, s);
+    } else {
+        CKR(cudaMemsetAsync(h->bar, 0, sizeof(GridBar), s));
+        CKR(launch_persistent(h->psolve, h->grid, h->smem, 1, 0, 0.0, h->nat_in, h->nat_out, s));
+    }
     CKR(cudaMemcpyAsync(z, h->nat_out, n * sizeof(double), devp ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
+    GridBar hb{};
+    CKR(cudaMemcpyAsync(&hb, h->bar, sizeof(GridBar), cudaMemcpyDeviceToHost, s));
     CKR(cudaEventRecord(h->ev_b, s));
     int rc = wait_event(h, h->ev_b);
     if (rc) return rc;
     CKR(cudaGetLastError());
+    if (hb.err) return LAMG_ERR_TIMEOUT;
+    return LAMG_OK;
+}
+
+int lamg_profile_cycle(lamg_hier *h, int64_t *out, int64_t cap, int64_t *count) {
+    if (!h || !out || !count || cap < 1) return LAMG_ERR_INVALID;
+    if (!h->persistent_ok) return LAMG_ERR_INVALID;
+    CKR(cudaSetDevice(h->device));
+    cudaStream_t s = h->stream;
+    const int64_t n = h->dev[0].n;
+    const int64_t slots = 2 * ((int64_t)h->ops.size() + 2);
+    unsigned long long *dprof = nullptr;
+    CKR(cudaMalloc(&dprof, slots * sizeof(unsigned long long)));
+    std::vector<unsigned long long> hp(slots, 0);
+    CKR(cudaMemsetAsync(h->nat_in, 0, n * sizeof(double), s));
+    CKR(cudaMemsetAsync(h->bar, 0, sizeof(GridBar), s));
+    cudaError_t e = launch_persistent(h->psolve, h->grid, h->smem, 1, 0, 0.0, h->nat_in, h->nat_out, s, dprof);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hp.data(), dprof, slots * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaEventRecord(h->ev_b, s);
+    int rc = e == cudaSuccess ? wait_event(h, h->ev_b) : cuda_status(e);
+    cudaFree(dprof);
+    if (rc) return rc;
+    const int64_t nrec = (int64_t)hp[0];
+    int64_t k = 0;
+    for (int64_t r = 1; r <= nrec && k < cap; r++, k++) {
+        out[2 * k] = (int64_t)hp[2 * r];
+        out[2 * k + 1] = (int64_t)(hp[2 * r + 1] - hp[2 * r - 1 == 1 ? 1 : 2 * r - 1]);
+    }
+    *count = k;
+    return LAMG_OK;
+}
+
+int lamg_op_list(const lamg_hier *h, int32_t *out, int64_t cap, int64_t *count) {
+    if (!h || !count) return LAMG_ERR_INVALID;
+    *count = (int64_t)h->ops.size();
+    if (out)
+        for (int64_t i = 0; i < (int64_t)h->ops.size() && i < cap; i++) {
+            out[3 * i] = h->ops[i].kind;
+            out[3 * i + 1] = h->ops[i].level;
+            out[3 * i + 2] = h->ops[i].colour;
+        }
     return LAMG_OK;
 }
 

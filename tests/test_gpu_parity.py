@@ -102,38 +102,44 @@ def test_setup_matches_oracle(case):
 
 # ------------------------------------------------------------------------ cycle and CG
 
-def test_cycle_parity(case):
+PATHS = {"graph": False, "persistent": True}
+
+
+@pytest.mark.parametrize("path", sorted(PATHS))
+def test_cycle_parity(case, path):
     name, g, cm, H = case
     P = lamg.import_levels(oracle_levels(H))
     rng = np.random.default_rng(7)
     for _ in range(2):
         r = rng.standard_normal(g.n)
         r -= r.mean()
-        z_gpu = P.cycle(r)
+        z_gpu = P.cycle(r, persistent=PATHS[path])
         z_ref = H.cycle(r)
         assert rel(z_gpu, z_ref) <= RTOL, name
         assert abs(z_gpu.sum()) <= 1e-12 * np.abs(z_gpu).sum()
     P.close()
 
 
-def test_fcg_iterates_parity(case):
+@pytest.mark.parametrize("path", sorted(PATHS))
+def test_fcg_iterates_parity(case, path):
     name, g, cm, H = case
     P = lamg.import_levels(oracle_levels(H))
     b = gg.rhs(g, 2)
     ref = H.fcg(b, tol=1e-300, maxit=6, record=True)
     for k in range(1, ref["iters"] + 1):
-        x, st = P.solve(b, tol=1e-300, maxit=k, allow_unconverged=True)
+        x, st = P.solve(b, tol=1e-300, maxit=k, allow_unconverged=True, persistent=PATHS[path])
         xr = ref["iterates"][k - 1]
         assert rel(x, xr) <= RTOL, (name, k, rel(x, xr))
         assert st["hist"][k] == pytest.approx(ref["hist"][k], rel=1e-8, abs=1e-15)
     P.close()
 
 
-def test_solve_to_tolerance(case):
+@pytest.mark.parametrize("path", sorted(PATHS))
+def test_solve_to_tolerance(case, path):
     name, g, cm, H = case
     P = lamg.setup(g, coarsest_max=cm)
     b = gg.rhs(g, 2)
-    x, st = P.solve(b, tol=1e-8, maxit=200)
+    x, st = P.solve(b, tol=1e-8, maxit=200, persistent=PATHS[path])
     assert st["relres"] <= 1e-8 and st["relres_true"] <= 2e-8, (name, st)
     ref = H.fcg(b, tol=1e-8, maxit=200)
     assert st["iters"] == ref["iters"], name
@@ -227,6 +233,20 @@ def test_rerun_is_bitwise_identical():
     x1, _ = P.solve(b, 1e-10, 100)
     x2, _ = P.solve(b, 1e-10, 100)
     assert np.array_equal(x1, x2)
+    x3, _ = P.solve(b, 1e-10, 100, persistent=True)
+    x4, _ = P.solve(b, 1e-10, 100, persistent=True)
+    assert np.array_equal(x3, x4)
+    assert rel(x1, x3) <= 1e-12
+
+
+def test_persistent_path_is_one_launch_and_counts_bytes():
+    g = gg.grid2d(256, 256, 1.0, 1e-3)
+    P = lamg.setup(g)
+    b = gg.rhs(g, 2)
+    x, st = P.solve(b, 1e-8, 100, persistent=True)
+    assert st["launches"] == 1 and st["kernel_ms"] > 0
+    # the algorithmic byte count covers at least one pass over L per iteration
+    assert st["alg_bytes"] > st["iters"] * 12 * g.nnz_off
 
 
 def test_device_pointer_path_matches_host_path():
