@@ -213,6 +213,22 @@ int lamg_affinity(int64_t n, const int64_t *rp, const int32_t *ci, const double 
  * The kernels run on the hierarchy's current vectors. Errors: INVALID, OOM, CUDA, TIMEOUT. */
 int lamg_time_kernel(lamg_hier *h, int32_t which, int32_t level, int32_t reps, double *out);
 
+/* Allocation-free variant of lamg_testvectors for callers that cannot allocate device memory
+ * (no counterpart in the paper: it is a deployment form of the same setup kernel). All
+ * pointers are DEVICE pointers owned by the caller: rp[n+1] (int64), ci, val, diag, colour[n]
+ * (values 0..ncol-1; rows of one colour pairwise non-adjacent) and the output X (n x K,
+ * row-major). The work is queued on `stream` (a cudaStream_t, 0 for the default stream) and
+ * the call returns without waiting. X is bit-identical to lamg_testvectors on the same input.
+ * Scratch (rows grouped by colour) lives in a fixed 8 MiB __device__ array held by every GPU
+ * that loads the library until exit: n <= 2^21 and ncol <= 1024, else LAMG_ERR_INVALID. The
+ * first call on a device looks up the array's device address and should come before any
+ * stream capture on that device. Calls share the array; calls that overlap on the GPU race
+ * and must be serialised by the caller. No device memory is allocated.
+ * Errors: INVALID, CUDA. */
+int lamg_testvectors_noalloc(int64_t n, const int64_t *rp, const int32_t *ci, const double *val,
+                             const double *diag, const int32_t *colour, int32_t ncol, int32_t level,
+                             uint64_t seed, int32_t K, int32_t nu, double *X, void *stream);
+
 /* Per-step timing of one cycle of the persistent solve kernel (r = 0): out receives up to cap
  * pairs (next step index, nanoseconds since the previous pair), one per grid barrier, read
  * from %globaltimer in CTA 0; *count = pairs written. Step indices refer to lamg_op_list.

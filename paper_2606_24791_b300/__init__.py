@@ -94,6 +94,8 @@ def lib():
         L.lamg_affinity.argtypes = [C.c_int64, P, P, P, P, C.c_int32, C.c_double, P, P]
         L.lamg_time_kernel.argtypes = [P, C.c_int32, C.c_int32, C.c_int32, P]
         L.lamg_profile_cycle.argtypes = [P, P, C.c_int64, C.POINTER(C.c_int64)]
+        L.lamg_testvectors_noalloc.argtypes = [C.c_int64, P, P, P, P, P, C.c_int32, C.c_int32, C.c_uint64,
+                                               C.c_int32, C.c_int32, P, P]
         L.lamg_op_list.argtypes = [P, P, C.c_int64, C.POINTER(C.c_int64)]
         _lib = L
     return _lib
@@ -288,6 +290,16 @@ def testvectors(rp, ci, val, diag, colour, level: int, seed: int, K: int = 4, nu
     _check(lib().lamg_testvectors(n, _p(rp), _p(ci), _p(val), _p(diag), _p(colour), level, seed, K,
                                   nu, _p(X)), "lamg_testvectors")
     return X
+
+
+def testvectors_noalloc(n: int, rp_ptr: int, ci_ptr: int, val_ptr: int, diag_ptr: int, colour_ptr: int,
+                        ncol: int, level: int, seed: int, K: int, nu: int, X_ptr: int, stream: int = 0):
+    """lamg_testvectors_noalloc on caller-owned device memory (raw device pointers); queued on
+    `stream`, returns without waiting. For callers that cannot allocate device memory."""
+    _check(lib().lamg_testvectors_noalloc(n, C.c_void_p(rp_ptr), C.c_void_p(ci_ptr), C.c_void_p(val_ptr),
+                                          C.c_void_p(diag_ptr), C.c_void_p(colour_ptr), ncol, level, seed,
+                                          K, nu, C.c_void_p(X_ptr), C.c_void_p(stream) if stream else None),
+           "lamg_testvectors_noalloc")
 
 
 def affinity(rp, ci, val, X, tau: float = 0.05):
