@@ -44,8 +44,22 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--tail-rows", type=int, default=8192,
-                    help="levels with at most this many rows run inside one CTA")
+                    help="levels with at most this many rows run inside one CTA (persistent path)")
+    ap.add_argument("--profile-sweep", type=int, default=-1, metavar="LEVEL",
+                    help="set up the workload, run one cold-L2 Gauss-Seidel sweep at LEVEL, exit "
+                         "(a target for ncu)")
     return ap.parse_args()
+
+
+def profile_sweep(level: int):
+    import paper_2606_24791_b300 as lamg
+    g, b = workload()
+    P = lamg.setup(g)
+    # fill the level vectors with a real cycle iterate through the persistent kernel, so that
+    # the only k_gs launches of this process are the profiled sweep
+    P.cycle(b - b.mean(), persistent=True)
+    r = P.time_kernel("gs_sweep", level, reps=1)
+    print(json.dumps({"level": level, "info": P.info[level], "sweep": r}))
 
 
 def dist_env():
@@ -383,6 +397,9 @@ def run_reference(args, ws, rank):
 def main():
     args = parse()
     ws, rank, local = dist_env()
+    if args.profile_sweep >= 0:
+        profile_sweep(args.profile_sweep)
+        return
     if args.impl == "reference":
         out = run_reference(args, ws, rank)
         if out is not None:
