@@ -201,6 +201,31 @@ class Hierarchy:
         _check(rc, "lamg_solve", (LAMG_OK, 5))
         return _stats(st, h)
 
+    def solve_batch(self, B, tol: float = 1e-8, maxit: int = 100, allow_unconverged: bool = False):
+        """k right-hand sides (B: n x k) in one SpMM-form solve; returns (PHI, [stats per column])."""
+        B = _c(B, np.float64)
+        if B.ndim != 2 or B.shape[0] != self.n:
+            raise ValueError("B must be n x k")
+        k = B.shape[1]
+        PHI = np.zeros_like(B)
+        hists = [np.zeros(maxit + 1) for _ in range(k)]
+        st = (Stats * k)()
+        for j in range(k):
+            st[j].hist = hists[j].ctypes.data
+        so = SolveOpts(tol, maxit, 0, None)
+        rc = lib().lamg_solve_batch(self._h, k, _p(B), _p(PHI), C.byref(so), st)
+        _check(rc, "lamg_solve_batch", (LAMG_OK, 5) if allow_unconverged else (LAMG_OK,))
+        return PHI, [_stats(st[j], hists[j]) for j in range(k)]
+
+    def solve_batch_ptr(self, k: int, B_ptr: int, PHI_ptr: int, tol: float = 1e-8, maxit: int = 100,
+                        stream: int = 0, device: bool = True):
+        """Batched solve on raw (device) pointers to n x k row-major blocks."""
+        so = SolveOpts(tol, maxit, DEVICE_PTRS if device else 0, C.c_void_p(stream) if stream else None)
+        st = (Stats * k)()
+        rc = lib().lamg_solve_batch(self._h, k, C.c_void_p(B_ptr), C.c_void_p(PHI_ptr), C.byref(so), st)
+        _check(rc, "lamg_solve_batch", (LAMG_OK, 5))
+        return [_stats(st[j], None) for j in range(k)]
+
     KERNELS = {"resid": 0, "gs_sweep": 1, "spmv_dot": 2, "restrict": 3, "prolong": 4}
 
     def time_kernel(self, which: str, level: int, reps: int = 20) -> dict:

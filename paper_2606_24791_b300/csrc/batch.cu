@@ -1,0 +1,915 @@
+// Multi-RHS solves in SpMM form and the FP32 cycle (lamg_solve_batch; lamg_solve with
+// precision LAMG_FP32).
+//
+// k right-hand sides are stored row-major (entry (u, j) at u*k + j), so one step of the cycle
+// reads each matrix row once for all k columns and the gathered neighbour values of a row are
+// k contiguous numbers. A row is handled by a group of KL x TPR lanes: KL lanes, one per column
+// (KL = k rounded up to a power of two, lanes j >= k idle), times TPR lanes splitting the row's
+// entries. Every column runs its own flexible CG (own alpha, beta, r.z, stopping test); a column
+// that has converged keeps x and r fixed (its step length is forced to 0) while the others
+// continue, so its result equals a solve of that column alone.
+//
+// The cycle runs in the value type T: double (FP64 cycle) or float (FP32 cycle with FP32 copies
+// of the level operators and transfer weights). The outer CG (residual, dot products, step
+// lengths, projection) is always FP64; with the FP32 cycle the residual is rounded to FP32 before
+// the cycle and the correction widened back to FP64 after it, and the coarsest-level solve
+// accumulates in FP64 against the FP64 pseudo-inverse.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#include "hier.h"
+#include "kernels_common.cuh"
+
+namespace lamg {
+
+constexpr int BBS = 256;
+constexpr int KMAX = 32;
+
+__device__ __forceinline__ void b_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void b_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+enum BScalar { B_RZ = 0, B_ALPHA, B_BETA, B_RR, B_BN2, B_MEAN, B_TRUE_RR, B_BMEAN, B_ITERS, B_TOL2, B_COUNT = 12 };
+
+struct BRed {
+    double *part;      // 2 x KMAX x RED_MAXG
+    unsigned *ticket;
+    double *sk;        // B_COUNT x KMAX
+    int *done;         // KMAX
+    int *itc;          // iteration counter
+};
+
+// ------------------------------------------------------------------ per-column reductions
+
+// Each thread contributes to column threadIdx.x % KL. Deterministic: per-block column sums in a
+// fixed order, then the last block to finish adds the blocks in a fixed order. Returns true in
+// the last block, where threads j < KL hold column j's totals.
+template <int KL, int NV>
+__device__ bool col_sum(double (&v)[NV], const BRed R) {
+    __shared__ double sh[NV][BBS];
+    __shared__ bool last;
+    __threadfence();
+#pragma unroll
+    for (int q = 0; q < NV; q++) sh[q][threadIdx.x] = v[q];
+    __syncthreads();
+    if (threadIdx.x < KL) {
+#pragma unroll
+        for (int q = 0; q < NV; q++) {
+            double s = 0.0;
+            for (int m = threadIdx.x; m < BBS; m += KL) s += sh[q][m];
+            R.part[(q * KMAX + threadIdx.x) * RED_MAXG + blockIdx.x] = s;
+        }
+        __threadfence();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) last = (atomicAdd(R.ticket, 1u) == gridDim.x - 1);
+    __syncthreads();
+    if (!last) return false;
+    __threadfence();
+    // threads t = j + KL * m sum blocks m, m + BBS/KL, ... of column j; then fixed-order combine
+    constexpr int PER = BBS / KL;
+    const int j = threadIdx.x % KL, m = threadIdx.x / KL;
+#pragma unroll
+    for (int q = 0; q < NV; q++) {
+        double s = 0.0;
+        for (int b = m; b < (int)gridDim.x; b += PER) s += __ldcg(&R.part[(q * KMAX + j) * RED_MAXG + b]);
+        sh[q][threadIdx.x] = s;
+    }
+    __syncthreads();
+    if (threadIdx.x < KL) {
+#pragma unroll
+        for (int q = 0; q < NV; q++) {
+            double s = 0.0;
+            for (int mm = 0; mm < PER; mm++) s += sh[q][threadIdx.x + KL * mm];
+            v[q] = s;
+        }
+    }
+    if (threadIdx.x == 0) *R.ticket = 0u;
+    return true;
+}
+
+// ------------------------------------------------------------------ cycle steps in SpMM form
+
+template <int KL, int TPR>
+struct Lanes {
+    static constexpr int G = KL * TPR;
+    int row_in_grid, sub, j;
+    __device__ Lanes() {
+        const int t = blockIdx.x * BBS + threadIdx.x;
+        row_in_grid = t / G;
+        const int lig = t % G;
+        j = lig % KL;
+        sub = lig / KL;
+    }
+};
+
+template <typename T, int KL, int TPR>
+__device__ __forceinline__ T rowsum_k(int e0, int e1, int k, int j, const int32_t *__restrict__ ci,
+                                      const T *__restrict__ val, const T *x) {
+    T s = T(0);
+    if (j < k)
+        for (int e = e0; e < e1; e += TPR) s += val[e] * x[(size_t)ci[e] * k + j];
+#pragma unroll
+    for (int o = KL; o < KL * TPR; o <<= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    return s;
+}
+
+// Gauss-Seidel on one colour class [r0, r1), all k columns (Section 2).
+template <typename T, int KL, int TPR>
+__global__ void __launch_bounds__(BBS) bk_gs(int r0, int r1, int k, const int32_t *__restrict__ rp,
+                                             const int32_t *__restrict__ ci, const T *__restrict__ val,
+                                             const T *__restrict__ diag, const T *__restrict__ b, T *x) {
+    b_trigger();
+    const Lanes<KL, TPR> L;
+    const int row = r0 + L.row_in_grid;
+    const bool ok = row < r1;
+    const int e0 = ok ? rp[row] + L.sub : 0, e1 = ok ? rp[row + 1] : 0;
+    const T d = ok ? diag[row] : T(1);
+    b_wait();
+    const T s = rowsum_k<T, KL, TPR>(e0, e1, k, L.j, ci, val, x);
+    if (ok && L.sub == 0 && L.j < k) x[(size_t)row * k + L.j] = (b[(size_t)row * k + L.j] - s) / d;
+}
+
+template <typename T, int KL, int TPR>
+__global__ void __launch_bounds__(BBS) bk_resid(int n, int k, const int32_t *__restrict__ rp,
+                                                const int32_t *__restrict__ ci, const T *__restrict__ val,
+                                                const T *__restrict__ diag, const T *__restrict__ x,
+                                                const T *__restrict__ b, T *r) {
+    b_trigger();
+    const Lanes<KL, TPR> L;
+    const int row = L.row_in_grid;
+    const bool ok = row < n;
+    const int e0 = ok ? rp[row] + L.sub : 0, e1 = ok ? rp[row + 1] : 0;
+    const T d = ok ? diag[row] : T(0);
+    b_wait();
+    const T s = rowsum_k<T, KL, TPR>(e0, e1, k, L.j, ci, val, x);
+    if (ok && L.sub == 0 && L.j < k) {
+        const size_t i = (size_t)row * k + L.j;
+        r[i] = b[i] - (d * x[i] + s);
+    }
+}
+
+// b^c = P^T r
+template <typename T, int KL, int TPR>
+__global__ void __launch_bounds__(BBS) bk_restrict(int nc, int k, const int32_t *__restrict__ ptr,
+                                                   const int32_t *__restrict__ row, const T *__restrict__ w,
+                                                   const T *__restrict__ r, T *bc) {
+    b_trigger();
+    const Lanes<KL, TPR> L;
+    const int a = L.row_in_grid;
+    const bool ok = a < nc;
+    const int e0 = ok ? ptr[a] + L.sub : 0, e1 = ok ? ptr[a + 1] : 0;
+    b_wait();
+    const T s = rowsum_k<T, KL, TPR>(e0, e1, k, L.j, row, w, r);
+    if (ok && L.sub == 0 && L.j < k) bc[(size_t)a * k + L.j] = s;
+}
+
+// Element-wise steps: thread -> (row i, column j = threadIdx.x % KL).
+template <int KL>
+__device__ __forceinline__ void elem_pos(int &i, int &j) {
+    const int t = blockIdx.x * BBS + threadIdx.x;
+    i = t / KL;
+    j = t % KL;
+}
+
+template <typename T, int KL>
+__global__ void bk_gs_first(int n, int c1, int k, const T *__restrict__ diag, const T *__restrict__ b, T *x) {
+    b_trigger();
+    int i, j;
+    elem_pos<KL>(i, j);
+    const T d = (i < c1) ? diag[i] : T(1);
+    b_wait();
+    if (i >= n || j >= k) return;
+    const size_t e = (size_t)i * k + j;
+    x[e] = i < c1 ? b[e] / d : T(0);
+}
+
+template <typename T>
+__global__ void bk_zero(int64_t cnt, T *x) {
+    b_trigger();
+    b_wait();
+    const int64_t t = (int64_t)blockIdx.x * BBS + threadIdx.x;
+    if (t < cnt) x[t] = T(0);
+}
+
+template <typename T, int KL>
+__global__ void bk_prolong(int n, int k, const int32_t *__restrict__ agg, const int32_t *__restrict__ agg2,
+                           const T *__restrict__ wt, const T *__restrict__ xc, T *x) {
+    b_trigger();
+    int u, j;
+    elem_pos<KL>(u, j);
+    const bool ok = u < n;
+    const int a = ok ? agg[u] : 0, bb = ok ? agg2[u] : -1;
+    const T w = (ok && bb >= 0) ? wt[u] : T(1);
+    b_wait();
+    if (!ok || j >= k) return;
+    T s;
+    if (bb < 0) {
+        s = xc[(size_t)a * k + j];
+    } else {
+        s = (T(1) - w) * xc[(size_t)bb * k + j];
+        if (w != T(0)) s = w * xc[(size_t)a * k + j] + s;
+    }
+    x[(size_t)u * k + j] += s;
+}
+
+template <typename T, int KL>
+__global__ void bk_elim_restrict(int nc, int k, const int32_t *__restrict__ ptr, const int32_t *__restrict__ f,
+                                 const T *__restrict__ pv, const T *__restrict__ b, T *bc) {
+    b_trigger();
+    int i, j;
+    elem_pos<KL>(i, j);
+    const bool ok = i < nc;
+    const int e0 = ok ? ptr[i] : 0, e1 = ok ? ptr[i + 1] : 0;
+    b_wait();
+    if (!ok || j >= k) return;
+    const T *bF = b + (size_t)nc * k;
+    T s = b[(size_t)i * k + j];
+    for (int e = e0; e < e1; e++) s += pv[e] * bF[(size_t)f[e] * k + j];
+    bc[(size_t)i * k + j] = s;
+}
+
+template <typename T, int KL>
+__global__ void bk_elim_interp(int nc, int nF, int k, const int32_t *__restrict__ col, const T *__restrict__ pv,
+                               const T *__restrict__ dF, const T *__restrict__ b, T *x) {
+    b_trigger();
+    int t, j;
+    elem_pos<KL>(t, j);
+    const bool ok = t < nF;
+    int c[4];
+    T p[4];
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+        c[q] = ok ? col[4 * t + q] : -1;
+        p[q] = ok ? pv[4 * t + q] : T(0);
+    }
+    const T d = ok ? dF[t] : T(1);
+    b_wait();
+    if (!ok || j >= k) return;
+    T s = T(0);
+#pragma unroll
+    for (int q = 0; q < 4; q++)
+        if (c[q] >= 0) s += p[q] * x[(size_t)c[q] * k + j];
+    const size_t e = (size_t)(nc + t) * k + j;
+    x[e] = s + b[e] / d;
+}
+
+// Coarsest level (FP64 accumulation against the FP64 projected pseudo-inverse): one warp per
+// row, KL lanes per column times 32/KL lanes splitting the row.
+template <typename T, int KL>
+__global__ void __launch_bounds__(BBS) bk_coarse(int n, int k, const double *__restrict__ pinv,
+                                                 const T *__restrict__ b, T *x) {
+    b_trigger();
+    b_wait();
+    constexpr int TPR = 32 / KL;
+    const int lane = threadIdx.x & 31;
+    const int j = lane % KL, sub = lane / KL;
+    const int wg = (blockIdx.x * BBS + threadIdx.x) >> 5, nwarps = (gridDim.x * BBS) >> 5;
+    for (int i = wg; i < n; i += nwarps) {
+        const double *row = pinv + (size_t)i * n;
+        double s = 0.0;
+        if (j < k)
+            for (int m = sub; m < n; m += TPR) s += row[m] * (double)b[(size_t)m * k + j];
+#pragma unroll
+        for (int o = KL; o < 32; o <<= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (sub == 0 && j < k) x[(size_t)i * k + j] = (T)s;
+    }
+}
+
+// ------------------------------------------------------------------ outer CG, k columns (FP64)
+
+template <typename Tin, typename Tout>
+__global__ void bk_cast(int64_t cnt, const Tin *__restrict__ src, Tout *dst) {
+    b_trigger();
+    b_wait();
+    const int64_t t = (int64_t)blockIdx.x * BBS + threadIdx.x;
+    if (t < cnt) dst[t] = (Tout)src[t];
+}
+
+template <int KL>
+__global__ void bk_gather_rows(int n, int k, const int32_t *__restrict__ perm, const double *__restrict__ src,
+                               double *dst) {
+    b_trigger();
+    int i, j;
+    elem_pos<KL>(i, j);
+    const int pi = i < n ? perm[i] : 0;
+    b_wait();
+    if (i < n && j < k) dst[(size_t)i * k + j] = src[(size_t)pi * k + j];
+}
+
+template <int KL>
+__global__ void bk_scatter_rows(int n, int k, const int32_t *__restrict__ perm, const double *__restrict__ src,
+                                double *dst) {
+    b_trigger();
+    int i, j;
+    elem_pos<KL>(i, j);
+    const int pi = i < n ? perm[i] : 0;
+    b_wait();
+    if (i < n && j < k) dst[(size_t)pi * k + j] = src[(size_t)i * k + j];
+}
+
+// Grid-stride loop over rows for element-wise CG kernels: thread column j = threadIdx.x % KL.
+#define FOR_ELEM(n, k)                                                                   \
+    const int j = threadIdx.x % KL;                                                      \
+    const int rows_per_pass = (gridDim.x * BBS) / KL;                                    \
+    for (int i = (blockIdx.x * BBS + threadIdx.x) / KL; i < (n); i += rows_per_pass)     \
+        if (j < (k))
+
+// mean_j = sum_i v(i, j) / n
+template <int KL>
+__global__ void __launch_bounds__(BBS) bk_sum(int n, int k, const double *__restrict__ v, const BRed R) {
+    b_trigger();
+    b_wait();
+    double s[1] = {0.0};
+    FOR_ELEM(n, k) s[0] += v[(size_t)i * k + j];
+    if (col_sum<KL, 1>(s, R) && threadIdx.x < k) R.sk[B_MEAN * KMAX + threadIdx.x] = s[0] / (double)n;
+}
+
+template <int KL>
+__global__ void __launch_bounds__(BBS) bk_init_b(int n, int k, double *r, double *bkeep, double *x, double *p,
+                                                 double *zold, const BRed R) {
+    b_trigger();
+    b_wait();
+    double s[1] = {0.0};
+    {
+        const double m = R.sk[B_MEAN * KMAX + (threadIdx.x % KL)];
+        FOR_ELEM(n, k) {
+            const size_t e = (size_t)i * k + j;
+            const double v = r[e] - m;
+            r[e] = v;
+            bkeep[e] = v;
+            x[e] = 0.0;
+            p[e] = 0.0;
+            zold[e] = 0.0;
+            s[0] += v * v;
+        }
+    }
+    if (col_sum<KL, 1>(s, R)) {
+        const int c = threadIdx.x;
+        if (c < k) {
+            R.sk[B_BN2 * KMAX + c] = s[0];
+            R.sk[B_RZ * KMAX + c] = 1.0;
+            R.sk[B_BMEAN * KMAX + c] = R.sk[B_MEAN * KMAX + c];
+            R.sk[B_ITERS * KMAX + c] = 0.0;
+            R.done[c] = 0;
+        }
+        if (c == 0) *R.itc = 0;
+    }
+}
+
+template <int KL, int TPR>
+__global__ void __launch_bounds__(BBS) bk_spmv_dot(int n, int k, const int32_t *__restrict__ rp,
+                                                   const int32_t *__restrict__ ci, const double *__restrict__ val,
+                                                   const double *__restrict__ diag, const double *__restrict__ p,
+                                                   double *q, const BRed R) {
+    b_trigger();
+    b_wait();
+    constexpr int G = KL * TPR;
+    const int t = blockIdx.x * BBS + threadIdx.x;
+    const int lig = t % G, j = lig % KL, sub = lig / KL;
+    const int groups = gridDim.x * (BBS / G);
+    const int rounds = (n + groups - 1) / groups;
+    double pq[1] = {0.0};
+    int row = t / G;
+    for (int it = 0; it < rounds; it++, row += groups) {
+        const bool ok = row < n;
+        const int e0 = ok ? rp[row] + sub : 0, e1 = ok ? rp[row + 1] : 0;
+        const double s = rowsum_k<double, KL, TPR>(e0, e1, k, j, ci, val, p);
+        if (ok && sub == 0 && j < k) {
+            const size_t e = (size_t)row * k + j;
+            const double qi = diag[row] * p[e] + s;
+            q[e] = qi;
+            pq[0] += p[e] * qi;
+        }
+    }
+    if (col_sum<KL, 1>(pq, R) && threadIdx.x < k) {
+        const int c = threadIdx.x;
+        const double rz = R.sk[B_RZ * KMAX + c];
+        R.sk[B_ALPHA * KMAX + c] = (R.done[c] || pq[0] == 0.0) ? 0.0 : rz / pq[0];
+    }
+}
+
+template <int KL>
+__global__ void __launch_bounds__(BBS) bk_update_xr(int n, int k, double *x, double *r, const double *__restrict__ p,
+                                                    const double *__restrict__ q, const BRed R) {
+    b_trigger();
+    b_wait();
+    double s[1] = {0.0};
+    {
+        const double a = R.sk[B_ALPHA * KMAX + (threadIdx.x % KL)];
+        FOR_ELEM(n, k) {
+            const size_t e = (size_t)i * k + j;
+            x[e] += a * p[e];
+            const double ri = r[e] - a * q[e];
+            r[e] = ri;
+            s[0] += ri * ri;
+        }
+    }
+    if (col_sum<KL, 1>(s, R)) {
+        __shared__ int it;
+        if (threadIdx.x == 0) it = ++(*R.itc);
+        __syncthreads();
+        const int c = threadIdx.x;
+        if (c < k) {
+            R.sk[B_RR * KMAX + c] = s[0];
+            const double tol2 = R.sk[B_TOL2 * KMAX];
+            if (!R.done[c] && s[0] <= tol2 * R.sk[B_BN2 * KMAX + c]) {
+                R.done[c] = 1;
+                R.sk[B_ITERS * KMAX + c] = (double)it;
+            }
+        }
+    }
+}
+
+template <int KL>
+__global__ void __launch_bounds__(BBS) bk_proj_dots(int n, int k, double *z, const double *__restrict__ zold,
+                                                    const double *__restrict__ r, const BRed R) {
+    b_trigger();
+    b_wait();
+    double s[2] = {0.0, 0.0};
+    {
+        const double m = R.sk[B_MEAN * KMAX + (threadIdx.x % KL)];
+        FOR_ELEM(n, k) {
+            const size_t e = (size_t)i * k + j;
+            const double zi = z[e] - m;
+            z[e] = zi;
+            s[0] += r[e] * (zi - zold[e]);
+            s[1] += r[e] * zi;
+        }
+    }
+    if (col_sum<KL, 2>(s, R) && threadIdx.x < k) {
+        const int c = threadIdx.x;
+        const double rz = R.sk[B_RZ * KMAX + c];
+        R.sk[B_BETA * KMAX + c] = rz != 0.0 ? s[0] / rz : 0.0;
+        R.sk[B_RZ * KMAX + c] = s[1];
+    }
+}
+
+template <int KL>
+__global__ void bk_update_p(int n, int k, const double *__restrict__ z, double *p, double *zold, const BRed R) {
+    b_trigger();
+    b_wait();
+    int i, j;
+    elem_pos<KL>(i, j);
+    if (i >= n || j >= k) return;
+    const double beta = R.sk[B_BETA * KMAX + j];
+    const size_t e = (size_t)i * k + j;
+    const double zi = z[e];
+    p[e] = zi + beta * p[e];
+    zold[e] = zi;
+}
+
+template <int KL, int TPR>
+__global__ void __launch_bounds__(BBS) bk_true_resid(int n, int k, const int32_t *__restrict__ rp,
+                                                     const int32_t *__restrict__ ci, const double *__restrict__ val,
+                                                     const double *__restrict__ diag, const double *__restrict__ x,
+                                                     const double *__restrict__ b, const BRed R) {
+    b_trigger();
+    b_wait();
+    constexpr int G = KL * TPR;
+    const int t = blockIdx.x * BBS + threadIdx.x;
+    const int lig = t % G, j = lig % KL, sub = lig / KL;
+    const int groups = gridDim.x * (BBS / G);
+    const int rounds = (n + groups - 1) / groups;
+    double acc[1] = {0.0};
+    int row = t / G;
+    for (int it = 0; it < rounds; it++, row += groups) {
+        const bool ok = row < n;
+        const int e0 = ok ? rp[row] + sub : 0, e1 = ok ? rp[row + 1] : 0;
+        const double s = rowsum_k<double, KL, TPR>(e0, e1, k, j, ci, val, x);
+        if (ok && sub == 0 && j < k) {
+            const size_t e = (size_t)row * k + j;
+            const double ri = b[e] - (diag[row] * x[e] + s);
+            acc[0] += ri * ri;
+        }
+    }
+    if (col_sum<KL, 1>(acc, R) && threadIdx.x < k) R.sk[B_TRUE_RR * KMAX + threadIdx.x] = acc[0];
+}
+
+// ------------------------------------------------------------------ launch helpers
+
+template <typename... KArgs, typename... Args>
+static void blaunch(void (*kernel)(KArgs...), int64_t grid, cudaStream_t s, Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(grid < 1 ? 1 : grid));
+    cfg.blockDim = dim3(BBS);
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+
+static inline int64_t nblocks(int64_t threads) { return (threads + BBS - 1) / BBS; }
+static inline int64_t rblocks(int64_t threads) {
+    int64_t b = (threads + BBS - 1) / BBS;
+    return std::max<int64_t>(1, std::min<int64_t>(b, RED_MAXG));
+}
+
+static int pow2_at_least(int k) {
+    int p = 1;
+    while (p < k) p <<= 1;
+    return p;
+}
+
+// (KL, TPR) pairs instantiated: KL = 1 with TPR 1..32, KL >= 2 with TPR 1, 2, 4 (KL*TPR <= 32)
+#define KT_CODE(KL, TPR) ((KL) * 64 + (TPR))
+#define KT_CASES(X, ...)              \
+    X(1, 1, __VA_ARGS__)              \
+    X(1, 2, __VA_ARGS__)              \
+    X(1, 4, __VA_ARGS__)              \
+    X(1, 8, __VA_ARGS__)              \
+    X(1, 16, __VA_ARGS__)             \
+    X(1, 32, __VA_ARGS__)             \
+    X(2, 1, __VA_ARGS__)              \
+    X(2, 2, __VA_ARGS__)              \
+    X(2, 4, __VA_ARGS__)              \
+    X(4, 1, __VA_ARGS__)              \
+    X(4, 2, __VA_ARGS__)              \
+    X(4, 4, __VA_ARGS__)              \
+    X(8, 1, __VA_ARGS__)              \
+    X(8, 2, __VA_ARGS__)              \
+    X(8, 4, __VA_ARGS__)              \
+    X(16, 1, __VA_ARGS__)             \
+    X(16, 2, __VA_ARGS__)             \
+    X(32, 1, __VA_ARGS__)
+
+static int row_tpr(int KL, int level_tpr) {
+    if (KL == 1) return level_tpr;
+    return std::max(1, std::min(level_tpr, std::min(4, 32 / KL)));
+}
+
+#define K_CASES(X, ...) X(1, __VA_ARGS__) X(2, __VA_ARGS__) X(4, __VA_ARGS__) X(8, __VA_ARGS__) X(16, __VA_ARGS__) X(32, __VA_ARGS__)
+
+// ------------------------------------------------------------------ workspace
+
+struct BLev {
+    int kind = 0, ncol = 0, tpr = 1, pt_tpr = 1;
+    int64_t n = 0, nc = 0, nF = 0;
+    std::vector<int64_t> cptr;
+    const int32_t *rp = nullptr, *ci = nullptr, *agg = nullptr, *agg2 = nullptr, *pt_ptr = nullptr,
+                  *pt_row = nullptr, *pf_col = nullptr, *pft_ptr = nullptr, *pft_f = nullptr;
+    const void *val = nullptr, *diag = nullptr, *wt = nullptr, *pt_w = nullptr, *pf_val = nullptr,
+               *dF = nullptr, *pft_val = nullptr;
+    const double *pinv = nullptr;
+    void *x = nullptr, *b = nullptr, *r = nullptr;
+};
+
+struct BatchCtx {
+    int k = 0, prec = 0, KL = 1;
+    std::vector<BLev> lv;
+    double *r = nullptr, *p = nullptr, *q = nullptr, *zold = nullptr, *xs = nullptr, *bkeep = nullptr;
+    double *nat_in = nullptr, *nat_out = nullptr, *z64 = nullptr;
+    void *b0 = nullptr;  // FP32 copy of the residual fed to the cycle
+    BRed red{};
+    double *h_sk = nullptr;  // pinned: B_COUNT x KMAX scalars + KMAX done flags
+    cudaGraphExec_t g_tail = nullptr, g_head = nullptr;
+};
+
+void batch_free(BatchCtx *b) {
+    if (!b) return;
+    if (b->g_tail) cudaGraphExecDestroy(b->g_tail);
+    if (b->g_head) cudaGraphExecDestroy(b->g_head);
+    if (b->h_sk) cudaFreeHost(b->h_sk);
+    delete b;
+}
+
+template <typename T>
+static int typed_copy(lamg_hier *h, const double *src, int64_t cnt, const void **out) {
+    if (!src || cnt <= 0) { *out = nullptr; return LAMG_OK; }
+    if (sizeof(T) == sizeof(double)) { *out = src; return LAMG_OK; }
+    std::vector<double> tmp(cnt);
+    CKR(cudaMemcpy(tmp.data(), src, cnt * sizeof(double), cudaMemcpyDeviceToHost));
+    std::vector<T> f(tmp.begin(), tmp.end());
+    T *d = nullptr;
+    int rc = dupload(h, &d, f);
+    *out = d;
+    return rc;
+}
+
+template <typename T>
+static int build_ctx(lamg_hier *h, BatchCtx *c) {
+    int rc;
+    const int L = (int)h->dev.size();
+    const int64_t k = c->k;
+    c->lv.resize(L);
+    for (int l = 0; l < L; l++) {
+        const DevLevel &D = h->dev[l];
+        BLev &B = c->lv[l];
+        B.kind = D.kind; B.ncol = D.ncol; B.tpr = D.tpr; B.pt_tpr = D.pt_tpr;
+        B.n = D.n; B.nc = D.nc; B.nF = D.nF; B.cptr = D.cptr;
+        B.rp = D.rp; B.ci = D.ci; B.agg = D.agg; B.agg2 = D.agg2; B.pt_ptr = D.pt_ptr; B.pt_row = D.pt_row;
+        B.pf_col = D.pf_col; B.pft_ptr = D.pft_ptr; B.pft_f = D.pft_f; B.pinv = D.pinv;
+        const int64_t pte = (D.kind == KIND_AGG) ? (int64_t)h->host[l].A.n * 2 : 0;
+        int32_t ent = 0;
+        if (D.kind == KIND_AGG) CKR(cudaMemcpy(&ent, D.pt_ptr + D.nc, sizeof(int32_t), cudaMemcpyDeviceToHost));
+        (void)pte;
+        int32_t fent = 0;
+        if (D.kind == KIND_ELIM) CKR(cudaMemcpy(&fent, D.pft_ptr + D.nc, sizeof(int32_t), cudaMemcpyDeviceToHost));
+        if ((rc = typed_copy<T>(h, D.val, D.nnz, &B.val)) || (rc = typed_copy<T>(h, D.diag, D.n, &B.diag)) ||
+            (rc = typed_copy<T>(h, D.wt, D.kind == KIND_AGG ? D.n : 0, &B.wt)) ||
+            (rc = typed_copy<T>(h, D.pt_w, ent, &B.pt_w)) ||
+            (rc = typed_copy<T>(h, D.pf_val, D.kind == KIND_ELIM ? 4 * D.nF : 0, &B.pf_val)) ||
+            (rc = typed_copy<T>(h, D.dF, D.kind == KIND_ELIM ? D.nF : 0, &B.dF)) ||
+            (rc = typed_copy<T>(h, D.pft_val, fent, &B.pft_val)))
+            return rc;
+    }
+    const int64_t n0 = h->dev[0].n;
+    if ((rc = dalloc(h, &c->r, n0 * k)) || (rc = dalloc(h, &c->p, n0 * k)) || (rc = dalloc(h, &c->q, n0 * k)) ||
+        (rc = dalloc(h, &c->zold, n0 * k)) || (rc = dalloc(h, &c->xs, n0 * k)) ||
+        (rc = dalloc(h, &c->bkeep, n0 * k)) || (rc = dalloc(h, &c->nat_in, n0 * k)) ||
+        (rc = dalloc(h, &c->nat_out, n0 * k)))
+        return rc;
+    // cycle vectors in T; level 0's right-hand side is the residual (FP64 cycle) or its FP32 copy
+    for (int l = 0; l < L; l++) {
+        BLev &B = c->lv[l];
+        T *x = nullptr, *b = nullptr, *r = nullptr;
+        if (l == 0) {
+            if (c->prec == LAMG_FP32) {
+                if ((rc = dalloc(h, &b, B.n * k))) return rc;
+                c->b0 = b;
+            } else {
+                b = (T *)c->r;
+            }
+        } else if ((rc = dalloc(h, &b, B.n * k))) {
+            return rc;
+        }
+        if (l == 0 || c->lv[l - 1].kind != KIND_ELIM) {
+            if ((rc = dalloc(h, &x, B.n * k))) return rc;
+        } else {
+            x = (T *)c->lv[l - 1].x;
+        }
+        if (B.kind == KIND_AGG && (rc = dalloc(h, &r, B.n * k))) return rc;
+        B.x = x; B.b = b; B.r = r;
+    }
+    if (c->prec == LAMG_FP32) {
+        if ((rc = dalloc(h, &c->z64, n0 * k))) return rc;
+    } else {
+        c->z64 = (double *)c->lv[0].x;
+    }
+    if ((rc = dalloc(h, &c->red.part, 2 * KMAX * RED_MAXG)) || (rc = dalloc(h, &c->red.ticket, 1)) ||
+        (rc = dalloc(h, &c->red.sk, B_COUNT * KMAX)) || (rc = dalloc(h, &c->red.done, KMAX)) ||
+        (rc = dalloc(h, &c->red.itc, 1)))
+        return rc;
+    CKR(cudaMemset(c->red.ticket, 0, sizeof(unsigned)));
+    CKR(cudaMemset(c->red.sk, 0, B_COUNT * KMAX * sizeof(double)));
+    CKR(cudaMemset(c->red.done, 0, KMAX * sizeof(int)));
+    CKR(cudaHostAlloc(&c->h_sk, (B_COUNT * KMAX + KMAX) * sizeof(double), cudaHostAllocDefault));
+    return LAMG_OK;
+}
+
+// One step of the cycle schedule for k columns in type T.
+template <typename T>
+static void bop(const Op &op, BatchCtx *c, cudaStream_t s) {
+    BLev &L = c->lv[op.level];
+    const int n = (int)L.n, k = c->k, KL = c->KL;
+    const T *val = (const T *)L.val, *diag = (const T *)L.diag;
+    T *x = (T *)L.x, *b = (T *)L.b, *r = (T *)L.r;
+    switch (op.kind) {
+        case OP_GS_FIRST:
+#define C1(KLv, ...) case KLv: blaunch(bk_gs_first<T, KLv>, nblocks((int64_t)n * KLv), s, n, (int)L.cptr[1], k, diag, (const T *)b, x); break;
+            switch (KL) { K_CASES(C1) }
+#undef C1
+            break;
+        case OP_ZERO:
+            blaunch(bk_zero<T>, nblocks((int64_t)n * k), s, (int64_t)n * k, x);
+            break;
+        case OP_GS: {
+            const int r0 = (int)L.cptr[op.colour], r1 = (int)L.cptr[op.colour + 1];
+            if (r1 <= r0) break;
+            const int tpr = row_tpr(KL, L.tpr);
+#define C2(KLv, TPRv, ...) case KT_CODE(KLv, TPRv): blaunch(bk_gs<T, KLv, TPRv>, nblocks((int64_t)(r1 - r0) * KLv * TPRv), s, r0, r1, k, L.rp, L.ci, val, diag, (const T *)b, x); break;
+            switch (KT_CODE(KL, tpr)) { KT_CASES(C2) }
+#undef C2
+            break;
+        }
+        case OP_RESID: {
+            const int tpr = row_tpr(KL, L.tpr);
+#define C3(KLv, TPRv, ...) case KT_CODE(KLv, TPRv): blaunch(bk_resid<T, KLv, TPRv>, nblocks((int64_t)n * KLv * TPRv), s, n, k, L.rp, L.ci, val, diag, (const T *)x, (const T *)b, r); break;
+            switch (KT_CODE(KL, tpr)) { KT_CASES(C3) }
+#undef C3
+            break;
+        }
+        case OP_RESTRICT: {
+            const int nc = (int)L.nc;
+            const int tpr = row_tpr(KL, L.pt_tpr);
+            T *bc = (T *)c->lv[op.level + 1].b;
+#define C4(KLv, TPRv, ...) case KT_CODE(KLv, TPRv): blaunch(bk_restrict<T, KLv, TPRv>, nblocks((int64_t)nc * KLv * TPRv), s, nc, k, L.pt_ptr, L.pt_row, (const T *)L.pt_w, (const T *)r, bc); break;
+            switch (KT_CODE(KL, tpr)) { KT_CASES(C4) }
+#undef C4
+            break;
+        }
+        case OP_PROLONG: {
+            const T *xc = (const T *)c->lv[op.level + 1].x;
+#define C5(KLv, ...) case KLv: blaunch(bk_prolong<T, KLv>, nblocks((int64_t)n * KLv), s, n, k, L.agg, L.agg2, (const T *)L.wt, xc, x); break;
+            switch (KL) { K_CASES(C5) }
+#undef C5
+            break;
+        }
+        case OP_ELIM_RESTRICT: {
+            T *bc = (T *)c->lv[op.level + 1].b;
+            const int nc = (int)L.nc;
+#define C6(KLv, ...) case KLv: blaunch(bk_elim_restrict<T, KLv>, nblocks((int64_t)nc * KLv), s, nc, k, L.pft_ptr, L.pft_f, (const T *)L.pft_val, (const T *)b, bc); break;
+            switch (KL) { K_CASES(C6) }
+#undef C6
+            break;
+        }
+        case OP_ELIM_INTERP: {
+            if (L.nF <= 0) break;
+            const int nF = (int)L.nF;
+#define C7(KLv, ...) case KLv: blaunch(bk_elim_interp<T, KLv>, nblocks((int64_t)nF * KLv), s, (int)L.nc, nF, k, L.pf_col, (const T *)L.pf_val, (const T *)L.dF, (const T *)b, x); break;
+            switch (KL) { K_CASES(C7) }
+#undef C7
+            break;
+        }
+        case OP_COARSE:
+#define C8(KLv, ...) case KLv: blaunch(bk_coarse<T, KLv>, rblocks((int64_t)n * 32), s, n, k, L.pinv, (const T *)b, x); break;
+            switch (KL) { K_CASES(C8) }
+#undef C8
+            break;
+    }
+}
+
+#define KL_SWITCH(KL, CALL) \
+    switch (KL) {           \
+        case 1: { constexpr int KLc = 1; CALL; } break;   \
+        case 2: { constexpr int KLc = 2; CALL; } break;   \
+        case 4: { constexpr int KLc = 4; CALL; } break;   \
+        case 8: { constexpr int KLc = 8; CALL; } break;   \
+        case 16: { constexpr int KLc = 16; CALL; } break; \
+        default: { constexpr int KLc = 32; CALL; } break; \
+    }
+
+static void cg_spmv_dot(lamg_hier *h, BatchCtx *c, cudaStream_t s) {
+    const DevLevel &F = h->dev[0];
+    const int n = (int)F.n, k = c->k;
+    const int tpr = row_tpr(c->KL, F.tpr);
+#define C9(KLv, TPRv, ...) case KT_CODE(KLv, TPRv): blaunch(bk_spmv_dot<KLv, TPRv>, rblocks((int64_t)n * KLv * TPRv), s, n, k, F.rp, F.ci, (const double *)F.val, (const double *)F.diag, (const double *)c->p, c->q, c->red); break;
+    switch (KT_CODE(c->KL, tpr)) { KT_CASES(C9) }
+#undef C9
+}
+
+static void cg_true_resid(lamg_hier *h, BatchCtx *c, cudaStream_t s) {
+    const DevLevel &F = h->dev[0];
+    const int n = (int)F.n, k = c->k;
+    const int tpr = row_tpr(c->KL, F.tpr);
+#define C10(KLv, TPRv, ...) case KT_CODE(KLv, TPRv): blaunch(bk_true_resid<KLv, TPRv>, rblocks((int64_t)n * KLv * TPRv), s, n, k, F.rp, F.ci, (const double *)F.val, (const double *)F.diag, (const double *)c->xs, (const double *)c->bkeep, c->red); break;
+    switch (KT_CODE(c->KL, tpr)) { KT_CASES(C10) }
+#undef C10
+}
+
+// Second half of a CG iteration: cycle on the residual, projection, dots, new direction.
+template <typename T>
+static void cg_tail(lamg_hier *h, BatchCtx *c, cudaStream_t s) {
+    const int n = (int)h->dev[0].n, k = c->k;
+    const int64_t cnt = (int64_t)n * k;
+    if (c->prec == LAMG_FP32) blaunch(bk_cast<double, float>, nblocks(cnt), s, cnt, (const double *)c->r, (float *)c->b0);
+    for (const Op &op : h->ops) bop<T>(op, c, s);
+    if (c->prec == LAMG_FP32) blaunch(bk_cast<float, double>, nblocks(cnt), s, cnt, (const float *)c->lv[0].x, c->z64);
+    KL_SWITCH(c->KL, blaunch(bk_sum<KLc>, rblocks((int64_t)n * KLc), s, n, k, (const double *)c->z64, c->red));
+    KL_SWITCH(c->KL, blaunch(bk_proj_dots<KLc>, rblocks((int64_t)n * KLc), s, n, k, c->z64, (const double *)c->zold,
+                             (const double *)c->r, c->red));
+    KL_SWITCH(c->KL, blaunch(bk_update_p<KLc>, nblocks((int64_t)n * KLc), s, n, k, (const double *)c->z64, c->p,
+                             c->zold, c->red));
+}
+
+static void cg_head(lamg_hier *h, BatchCtx *c, cudaStream_t s) {
+    const int n = (int)h->dev[0].n, k = c->k;
+    cg_spmv_dot(h, c, s);
+    KL_SWITCH(c->KL, blaunch(bk_update_xr<KLc>, rblocks((int64_t)n * KLc), s, n, k, c->xs, c->r, (const double *)c->p,
+                             (const double *)c->q, c->red));
+    cudaMemcpyAsync(c->h_sk, c->red.sk, B_COUNT * KMAX * sizeof(double), cudaMemcpyDeviceToHost, s);
+    cudaMemcpyAsync(c->h_sk + B_COUNT * KMAX, c->red.done, KMAX * sizeof(int), cudaMemcpyDeviceToHost, s);
+}
+
+static int capture_ctx(lamg_hier *h, BatchCtx *c) {
+    cudaStream_t cs = h->stream;
+    for (int which = 0; which < 2; which++) {
+        cudaGraph_t g = nullptr;
+        CKR(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+        if (which == 0) {
+            if (c->prec == LAMG_FP32) cg_tail<float>(h, c, cs);
+            else cg_tail<double>(h, c, cs);
+        } else {
+            cg_head(h, c, cs);
+        }
+        cudaError_t e = cudaStreamEndCapture(cs, &g);
+        if (e != cudaSuccess) return cuda_status(e);
+        e = cudaGraphInstantiate(which == 0 ? &c->g_tail : &c->g_head, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) return cuda_status(e);
+    }
+    return LAMG_OK;
+}
+
+static int get_ctx(lamg_hier *h, int k, int prec, BatchCtx **out) {
+    for (BatchCtx *b : h->batch)
+        if (b->k == k && b->prec == prec) { *out = b; return LAMG_OK; }
+    BatchCtx *c = new BatchCtx();
+    c->k = k;
+    c->prec = prec;
+    c->KL = pow2_at_least(k);
+    int rc = prec == LAMG_FP32 ? build_ctx<float>(h, c) : build_ctx<double>(h, c);
+    if (!rc) rc = capture_ctx(h, c);
+    if (rc) { batch_free(c); return rc; }
+    h->batch.push_back(c);
+    *out = c;
+    return LAMG_OK;
+}
+
+// The k-column flexible-CG solve (FP64 outer iteration, cycle in the context's precision).
+int solve_batch_impl(lamg_hier *h, int k, const double *B, double *PHI, const lamg_solve_opts *so,
+                     lamg_stats *st, int prec) {
+    if (k < 1 || k > KMAX || !B || !PHI || !so || !(so->tol > 0) || so->maxit < 1) return LAMG_ERR_INVALID;
+    BatchCtx *c = nullptr;
+    int rc = get_ctx(h, k, prec, &c);
+    if (rc) return rc;
+    cudaStream_t s = so->stream ? (cudaStream_t)so->stream : h->stream;
+    const bool devp = so->flags & LAMG_DEVICE_PTRS;
+    const int n = (int)h->dev[0].n;
+    const int64_t cnt = (int64_t)n * k;
+    CKR(cudaEventRecord(h->ev_a, s));
+    CKR(cudaMemcpyAsync(c->nat_in, B, cnt * sizeof(double), devp ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+    c->h_sk[B_TOL2 * KMAX] = so->tol * so->tol;
+    CKR(cudaMemcpyAsync(c->red.sk + B_TOL2 * KMAX, c->h_sk + B_TOL2 * KMAX, sizeof(double), cudaMemcpyHostToDevice, s));
+    KL_SWITCH(c->KL, blaunch(bk_gather_rows<KLc>, nblocks((int64_t)n * KLc), s, n, k, (const int32_t *)h->perm0,
+                             (const double *)c->nat_in, c->r));
+    KL_SWITCH(c->KL, blaunch(bk_sum<KLc>, rblocks((int64_t)n * KLc), s, n, k, (const double *)c->r, c->red));
+    KL_SWITCH(c->KL, blaunch(bk_init_b<KLc>, rblocks((int64_t)n * KLc), s, n, k, c->r, c->bkeep, c->xs, c->p, c->zold,
+                             c->red));
+    CKR(cudaGetLastError());
+    CKR(cudaEventRecord(h->ev_k0, s));
+    CKR(cudaGraphLaunch(c->g_tail, s));
+    int it = 0, cycles = 1;
+    bool all_done = false;
+    std::vector<double> rel(k, 1.0);
+    if (st)
+        for (int j = 0; j < k; j++)
+            if (st[j].hist) st[j].hist[0] = 1.0;
+    const int *hdone = (const int *)(c->h_sk + B_COUNT * KMAX);
+    while (it < so->maxit) {
+        CKR(cudaGraphLaunch(c->g_head, s));
+        CKR(cudaEventRecord(h->ev_poll, s));
+        if ((rc = wait_event(h, h->ev_poll))) return rc;
+        it++;
+        all_done = true;
+        for (int j = 0; j < k; j++) {
+            const double bn2 = c->h_sk[B_BN2 * KMAX + j];
+            rel[j] = bn2 > 0 ? std::sqrt(c->h_sk[B_RR * KMAX + j] / bn2) : 0.0;
+            if (st && st[j].hist && (hdone[j] == 0 || (int)c->h_sk[B_ITERS * KMAX + j] == it)) st[j].hist[it] = rel[j];
+            all_done = all_done && hdone[j];
+        }
+        if (all_done) break;
+        CKR(cudaGraphLaunch(c->g_tail, s));
+        cycles++;
+    }
+    CKR(cudaEventRecord(h->ev_k1, s));
+    cg_true_resid(h, c, s);
+    KL_SWITCH(c->KL, blaunch(bk_scatter_rows<KLc>, nblocks((int64_t)n * KLc), s, n, k, (const int32_t *)h->perm0,
+                             (const double *)c->xs, c->nat_out));
+    CKR(cudaMemcpyAsync(PHI, c->nat_out, cnt * sizeof(double), devp ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
+    CKR(cudaMemcpyAsync(c->h_sk, c->red.sk, B_COUNT * KMAX * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CKR(cudaMemcpyAsync(c->h_sk + B_COUNT * KMAX, c->red.done, KMAX * sizeof(int), cudaMemcpyDeviceToHost, s));
+    CKR(cudaEventRecord(h->ev_b, s));
+    if ((rc = wait_event(h, h->ev_b))) return rc;
+    CKR(cudaGetLastError());
+    if (st) {
+        float ms = 0.f, kms = 0.f;
+        cudaEventElapsedTime(&ms, h->ev_a, h->ev_b);
+        cudaEventElapsedTime(&kms, h->ev_k0, h->ev_k1);
+        const double z0 = (double)h->dev[0].nnz, n0 = (double)n;
+        const int pi = prec == LAMG_FP32 ? 1 : 0;
+        // per cycle: operator bytes once, vector bytes per column (+ the FP32 casts of r and z);
+        // per CG iteration: SpMV operator once, 136 bytes per row and column of CG vectors
+        const double cyc = h->cycle_mat[pi] + (double)k * (h->cycle_vec[pi] + (pi ? 24 * n0 : 0.0));
+        const double per_it = 12 * z0 + 12 * n0 + 136 * n0 * k;
+        const double once = 12 * z0 + 12 * n0 + 24 * n0 * k + 80 * n0 * k;
+        for (int j = 0; j < k; j++) {
+            const double bn2 = c->h_sk[B_BN2 * KMAX + j];
+            st[j].iters = hdone[j] ? (int)c->h_sk[B_ITERS * KMAX + j] : it;
+            st[j].nlevels = (int32_t)h->dev.size();
+            st[j].relres = bn2 > 0 ? std::sqrt(c->h_sk[B_RR * KMAX + j] / bn2) : 0.0;
+            st[j].relres_true = bn2 > 0 ? std::sqrt(c->h_sk[B_TRUE_RR * KMAX + j] / bn2) : 0.0;
+            st[j].b_mean = c->h_sk[B_BMEAN * KMAX + j];
+            st[j].solve_ms = ms;
+            st[j].kernel_ms = kms;
+            st[j].alg_bytes = ((double)cycles * cyc + (double)it * per_it + once) / k;  // this column's share
+            st[j].launches = 0;
+        }
+    }
+    return all_done ? LAMG_OK : LAMG_ERR_NOT_CONVERGED;
+}
+
+}  // namespace lamg
+
+extern "C" int lamg_solve_batch(lamg_hier *h, int32_t k, const double *B, double *PHI, const lamg_solve_opts *so,
+                                lamg_stats *st) {
+    using namespace lamg;
+    if (!h) return LAMG_ERR_INVALID;
+    CKR(cudaSetDevice(h->device));
+    return lamg::solve_batch_impl(h, k, B, PHI, so, st, h->opt.precision == LAMG_FP32 ? LAMG_FP32 : LAMG_FP64);
+}

@@ -1,0 +1,114 @@
+// The hierarchy handle (lamg_hier) and the device-memory helpers shared by the solver files.
+#pragma once
+
+#include <chrono>
+#include <cstring>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "device.h"
+#include "internal.h"
+
+namespace lamg {
+struct BatchCtx;                  // multi-RHS / FP32-cycle workspace (batch.cu)
+void batch_free(BatchCtx *b);
+}  // namespace lamg
+
+struct lamg_hier {
+    int device = 0;
+    lamg_options opt{};
+    std::vector<lamg::HostLevel> host;
+    std::vector<lamg::DevLevel> dev;
+    std::vector<lamg::Op> ops;
+    cudaStream_t stream = nullptr;
+    // outer CG vectors, device order of level 0
+    double *r = nullptr, *p = nullptr, *q = nullptr, *zold = nullptr, *xs = nullptr, *bkeep = nullptr;
+    double *nat_in = nullptr, *nat_out = nullptr;  // natural-order staging
+    int32_t *perm0 = nullptr;
+    lamg::Reduce red;
+    double *h_scal = nullptr;  // pinned
+    cudaGraphExec_t g_cycle = nullptr, g_tail = nullptr, g_head = nullptr;
+    cudaEvent_t ev_a = nullptr, ev_b = nullptr, ev_poll = nullptr, ev_k0 = nullptr, ev_k1 = nullptr;
+    // persistent solve kernel
+    lamg::PSolve *psolve = nullptr;   // device copy
+    lamg::PSolve ph{};                // host copy of the same pointers
+    lamg::GridBar *bar = nullptr;
+    double *hist = nullptr;
+    int hist_cap = 0;
+    int grid = 0;
+    size_t smem = 0;
+    bool persistent_ok = false;
+    double cycle_bytes = 0.0;     // algorithmic DRAM bytes of one cycle (FP64, one RHS)
+    double cycle_mat[2] = {0, 0}; // per cycle, read once whatever k: [FP64 cycle, FP32 cycle]
+    double cycle_vec[2] = {0, 0}; // per cycle and right-hand side
+    int64_t cycle_launches = 0;   // kernels of one cycle in the graph path
+    // multi-RHS / FP32 workspaces, one per (k, precision) used so far
+    std::vector<lamg::BatchCtx *> batch;
+    std::vector<void *> allocs;
+    size_t dev_bytes = 0;
+    double wait_timeout_s = 120.0;
+
+    ~lamg_hier() {
+        for (lamg::BatchCtx *b : batch) lamg::batch_free(b);
+        if (ev_k0) cudaEventDestroy(ev_k0);
+        if (ev_k1) cudaEventDestroy(ev_k1);
+        if (g_cycle) cudaGraphExecDestroy(g_cycle);
+        if (g_tail) cudaGraphExecDestroy(g_tail);
+        if (g_head) cudaGraphExecDestroy(g_head);
+        if (ev_a) cudaEventDestroy(ev_a);
+        if (ev_b) cudaEventDestroy(ev_b);
+        if (ev_poll) cudaEventDestroy(ev_poll);
+        for (void *a : allocs) cudaFree(a);
+        if (h_scal) cudaFreeHost(h_scal);
+        if (stream) cudaStreamDestroy(stream);
+    }
+};
+
+namespace lamg {
+
+#define CKR(x)                                         \
+    do {                                               \
+        cudaError_t e_ = (x);                          \
+        if (e_ != cudaSuccess) return cuda_status(e_); \
+    } while (0)
+
+// Device allocation owned by the hierarchy (freed by lamg_destroy), 256-byte granularity.
+template <typename T>
+inline int dalloc(lamg_hier *h, T **p, int64_t count) {
+    size_t bytes = (size_t)(count > 1 ? count : 1) * sizeof(T);
+    bytes = (bytes + 255) & ~(size_t)255;
+    void *q = nullptr;
+    cudaError_t e = cudaMalloc(&q, bytes);
+    if (e != cudaSuccess) return cuda_status(e);
+    h->allocs.push_back(q);
+    h->dev_bytes += bytes;
+    *p = (T *)q;
+    return LAMG_OK;
+}
+
+template <typename T>
+inline int dupload(lamg_hier *h, T **p, const std::vector<T> &v) {
+    int rc = dalloc(h, p, (int64_t)v.size());
+    if (rc) return rc;
+    if (!v.empty()) CKR(cudaMemcpy(*p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice));
+    return LAMG_OK;
+}
+
+// Bounded wait for an event recorded on one of the hierarchy's streams.
+inline int wait_event(lamg_hier *h, cudaEvent_t ev) {
+    auto t0 = std::chrono::steady_clock::now();
+    for (;;) {
+        cudaError_t e = cudaEventQuery(ev);
+        if (e == cudaSuccess) return LAMG_OK;
+        if (e != cudaErrorNotReady) return cuda_status(e);
+        double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        if (el > h->wait_timeout_s) return LAMG_ERR_TIMEOUT;
+    }
+}
+
+void op_bytes(const lamg_hier *h, const Op &op, double s, double *mat, double *vec);
+int solve_batch_impl(lamg_hier *h, int k, const double *B, double *PHI, const lamg_solve_opts *so,
+                     lamg_stats *st, int prec);
+
+}  // namespace lamg

@@ -3,10 +3,6 @@
 
 extern "C" {
 
-int lamg_solve_batch(lamg_hier *, int32_t, const double *, double *, const lamg_solve_opts *, lamg_stats *) {
-    return LAMG_ERR_INVALID;
-}
-
 int lamg_server_create(const lamg_server_opts *, const lamg_options *, lamg_server **out) {
     if (out) *out = nullptr;
     return LAMG_ERR_INVALID;

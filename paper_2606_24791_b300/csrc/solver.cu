@@ -15,84 +15,11 @@
 #include <cstring>
 #include <thread>
 
-#include "device.h"
-#include "internal.h"
+#include "hier.h"
 
 using namespace lamg;
 
-struct lamg_hier {
-    int device = 0;
-    lamg_options opt{};
-    std::vector<HostLevel> host;
-    std::vector<DevLevel> dev;
-    std::vector<Op> ops;
-    cudaStream_t stream = nullptr;
-    // outer CG vectors, device order of level 0
-    double *r = nullptr, *p = nullptr, *q = nullptr, *zold = nullptr, *xs = nullptr, *bkeep = nullptr;
-    double *nat_in = nullptr, *nat_out = nullptr;  // natural-order staging
-    int32_t *perm0 = nullptr;
-    Reduce red;
-    double *h_scal = nullptr;  // pinned
-    cudaGraphExec_t g_cycle = nullptr, g_tail = nullptr, g_head = nullptr;
-    cudaEvent_t ev_a = nullptr, ev_b = nullptr, ev_poll = nullptr, ev_k0 = nullptr, ev_k1 = nullptr;
-    // persistent solve kernel
-    PSolve *psolve = nullptr;     // device copy
-    PSolve ph{};                  // host copy of the same pointers
-    GridBar *bar = nullptr;
-    double *hist = nullptr;
-    int hist_cap = 0;
-    int grid = 0;
-    size_t smem = 0;
-    bool persistent_ok = false;
-    double cycle_bytes = 0.0;     // algorithmic DRAM bytes of one cycle
-    int64_t cycle_launches = 0;   // kernels of one cycle in the graph path
-    std::vector<void *> allocs;
-    size_t dev_bytes = 0;
-    double wait_timeout_s = 120.0;
-
-    ~lamg_hier() {
-        if (ev_k0) cudaEventDestroy(ev_k0);
-        if (ev_k1) cudaEventDestroy(ev_k1);
-        if (g_cycle) cudaGraphExecDestroy(g_cycle);
-        if (g_tail) cudaGraphExecDestroy(g_tail);
-        if (g_head) cudaGraphExecDestroy(g_head);
-        if (ev_a) cudaEventDestroy(ev_a);
-        if (ev_b) cudaEventDestroy(ev_b);
-        if (ev_poll) cudaEventDestroy(ev_poll);
-        for (void *a : allocs) cudaFree(a);
-        if (h_scal) cudaFreeHost(h_scal);
-        if (stream) cudaStreamDestroy(stream);
-    }
-};
-
 namespace {
-
-#define CKR(x)                                     \
-    do {                                           \
-        cudaError_t e_ = (x);                      \
-        if (e_ != cudaSuccess) return cuda_status(e_); \
-    } while (0)
-
-template <typename T>
-int dalloc(lamg_hier *h, T **p, int64_t count) {
-    size_t bytes = (size_t)std::max<int64_t>(count, 1) * sizeof(T);
-    bytes = (bytes + 255) & ~(size_t)255;
-    void *q = nullptr;
-    cudaError_t e = cudaMalloc(&q, bytes);
-    if (e != cudaSuccess) return cuda_status(e);
-    h->allocs.push_back(q);
-    h->dev_bytes += bytes;
-    *p = (T *)q;
-    return LAMG_OK;
-}
-
-template <typename T>
-int dupload(lamg_hier *h, T **p, const std::vector<T> &v) {
-    int rc = dalloc(h, p, (int64_t)v.size());
-    if (rc) return rc;
-    if (!v.empty()) CKR(cudaMemcpy(*p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice));
-    return LAMG_OK;
-}
 
 // Device orders of all levels, from the coarsest up (see DevLevel).
 void build_orders(lamg_hier *h) {
@@ -289,13 +216,22 @@ int capture(lamg_hier *h, cudaGraphExec_t *out, int which) {
 
 // Algorithmic DRAM bytes of one step of the persistent schedule (FP64 values, int32 indices;
 // each array read or written once, gathered vectors counted once).
-double op_bytes(const lamg_hier *h, const Op &op) {
+}  // namespace
+
+// Algorithmic DRAM bytes of one step of the cycle, split into the bytes read once per step
+// whatever the number of right-hand sides (operator values and indices, transfer weights) and
+// the bytes moved per right-hand side (vectors). s = bytes per value (8 FP64, 4 FP32 cycle);
+// indices are 4 bytes, the dense coarsest matrix is always FP64; each array is counted once per
+// step and a gathered vector at most once. The residual is counted as fused into the
+// restriction (r is never written), which is the algorithmic minimum.
+void lamg::op_bytes(const lamg_hier *h, const Op &op, double s, double *mat, double *vec) {
     const HostLevel &H = h->host[op.level];
     const DevLevel &D = h->dev[op.level];
     const double n = (double)D.n, z = (double)D.nnz, nc = (double)D.nc, nF = (double)D.nF;
+    double m = 0.0, v = 0.0;
     switch (op.kind) {
-        case OP_GS_FIRST: return 16.0 * (double)D.cptr[1] + 8 * n;
-        case OP_ZERO: return 8 * n;
+        case OP_GS_FIRST: m = s * (double)D.cptr[1]; v = s * (double)D.cptr[1] + s * n; break;
+        case OP_ZERO: v = s * n; break;
         case OP_GS: {
             const int64_t r0 = D.cptr[op.colour], r1 = D.cptr[op.colour + 1];
             double zc = 0;
@@ -304,26 +240,35 @@ double op_bytes(const lamg_hier *h, const Op &op) {
                 zc += (double)(H.A.rp[u + 1] - H.A.rp[u]);
             }
             const double R = (double)(r1 - r0);
-            return 12 * zc + 28 * R + 4 + 8 * std::min(zc, n);
+            m = (4 + s) * zc + 4 * (R + 1) + s * R;
+            v = 2 * s * R + s * std::min(zc, n);
+            break;
         }
-        case OP_RESID: return 0.0;  // fused into the restriction
+        case OP_RESID: break;
         case OP_RESTRICT: {
             double E = 0;
             for (int64_t u = 0; u < D.n; u++) E += H.agg2[u] < 0 ? 1 : (H.wt[u] != 0.0 ? 2 : 1);
-            return 12 * z + 28 * n + 12 * E + 12 * nc + 4;
+            m = (4 + s) * z + 4 * (n + 1) + s * n + (4 + s) * E + 4 * (nc + 1);
+            v = 2 * s * n + s * nc;
+            break;
         }
-        case OP_PROLONG: return 32 * n + 8 * nc;
+        case OP_PROLONG: m = 8 * n + s * n; v = 2 * s * n + s * nc; break;
         case OP_ELIM_RESTRICT: {
             double E = 0;
             for (int64_t u = 0; u < D.n; u++)
                 if (H.cidx[u] < 0) E += (double)(H.A.rp[u + 1] - H.A.rp[u]);
-            return 20 * nc + 12 * E + 8 * nF + 4;
+            m = 4 * (nc + 1) + (4 + s) * E;
+            v = 2 * s * nc + s * nF;
+            break;
         }
-        case OP_ELIM_INTERP: return 72 * nF + 8 * nc;
-        case OP_COARSE: return 8 * n * n + 16 * n;
+        case OP_ELIM_INTERP: m = 16 * nF + 5 * s * nF; v = s * nc + 2 * s * nF; break;
+        case OP_COARSE: m = 8 * n * n; v = 2 * s * n; break;
     }
-    return 0.0;
+    *mat = m;
+    *vec = v;
 }
+
+namespace {
 
 // Device tables of the persistent solve kernel.
 int setup_persistent(lamg_hier *h) {
@@ -435,8 +380,16 @@ int finalize(lamg_hier *h) {
         return rc;
     CKR(cudaEventCreate(&h->ev_k0));
     CKR(cudaEventCreate(&h->ev_k1));
-    h->cycle_bytes = 0.0;
-    for (const Op &op : h->ops) h->cycle_bytes += op_bytes(h, op);
+    for (int p = 0; p < 2; p++) {
+        h->cycle_mat[p] = h->cycle_vec[p] = 0.0;
+        for (const Op &op : h->ops) {
+            double m, v;
+            op_bytes(h, op, p == 0 ? 8.0 : 4.0, &m, &v);
+            h->cycle_mat[p] += m;
+            h->cycle_vec[p] += v;
+        }
+    }
+    h->cycle_bytes = h->cycle_mat[0] + h->cycle_vec[0];
     h->cycle_launches = 0;
     for (const Op &op : h->ops)
         if (!(op.kind == OP_ELIM_INTERP && h->dev[op.level].nF == 0) &&
@@ -445,17 +398,6 @@ int finalize(lamg_hier *h) {
     if ((rc = setup_persistent(h))) return rc;
     CKR(cudaStreamSynchronize(h->stream));
     return LAMG_OK;
-}
-
-int wait_event(lamg_hier *h, cudaEvent_t ev) {
-    auto t0 = std::chrono::steady_clock::now();
-    for (;;) {
-        cudaError_t e = cudaEventQuery(ev);
-        if (e == cudaSuccess) return LAMG_OK;
-        if (e != cudaErrorNotReady) return cuda_status(e);
-        double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
-        if (el > h->wait_timeout_s) return LAMG_ERR_TIMEOUT;
-    }
 }
 
 int set_device(int dev) {
@@ -711,6 +653,7 @@ static int solve_persistent(lamg_hier *h, const double *b, double *phi, const la
 int lamg_solve(lamg_hier *h, const double *b, double *phi, const lamg_solve_opts *so, lamg_stats *st) {
     if (!h || !b || !phi || !so || !(so->tol > 0) || so->maxit < 1) return LAMG_ERR_INVALID;
     CKR(cudaSetDevice(h->device));
+    if (h->opt.precision == LAMG_FP32) return solve_batch_impl(h, 1, b, phi, so, st, LAMG_FP32);
     if (!(so->flags & LAMG_PERSISTENT) || !h->persistent_ok) return solve_graph(h, b, phi, so, st);
     return solve_persistent(h, b, phi, so, st);
 }
