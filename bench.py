@@ -45,10 +45,82 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--tail-rows", type=int, default=8192,
                     help="levels with at most this many rows run inside one CTA (persistent path)")
+    ap.add_argument("--serve", action="store_true", help="run the serving workload instead")
+    ap.add_argument("--serve-requests", type=int, default=200)
+    ap.add_argument("--serve-max-n", type=int, default=200000)
+    ap.add_argument("--serve-threads", type=int, default=8)
     ap.add_argument("--profile-sweep", type=int, default=-1, metavar="LEVEL",
                     help="set up the workload, run one cold-L2 Gauss-Seidel sweep at LEVEL, exit "
                          "(a target for ncu)")
     return ap.parse_args()
+
+
+def serve_bench(args):
+    """Serving workload: Poisson arrivals of single-RHS requests whose graphs are drawn uniformly
+    from three families (2D grids with sides log-uniform in [32, 512], random geometric graphs
+    and Barabasi-Albert graphs with n log-uniform up to args.serve_max_n), weights U(0.5, 1.5],
+    one mean-zero Gaussian RHS each, tol 1e-8, device memory budget 120 GB. The graphs come from
+    a pre-generated pool of 24 family members (input generation is outside the timed region);
+    every request is set up and solved independently. The arrival rate is 0.8 x the server's
+    measured closed-loop throughput on the same pool."""
+    import graphgen as gg
+    import paper_2606_24791_b300 as lamg
+    rng = np.random.default_rng(1)
+    pool = []
+    top = math.log10(args.serve_max_n)
+    for i in range(24):
+        fam = i % 3
+        if fam == 0:
+            side = int(round(10 ** rng.uniform(math.log10(32), math.log10(min(512, math.sqrt(args.serve_max_n))))))
+            g = gg.grid2d_random(side, side, seed=100 + i)
+        elif fam == 1:
+            g = gg.rgg(int(10 ** rng.uniform(4, max(4.0, top))), 10, seed=100 + i)
+        else:
+            g = gg.barabasi_albert(int(10 ** rng.uniform(3, top)), 4, seed=100 + i)
+        pool.append((g, gg.rhs(g, seed=200 + i)))
+    S = lamg.Server(budget_bytes=120e9, max_inflight=64, setup_threads=args.serve_threads, tol=TOL, maxit=200)
+    # closed-loop capacity on the pool
+    t0 = time.perf_counter()
+    tk = [S.submit(g, b) for g, b in pool]
+    S.drain(3600)
+    cap = len(pool) / (time.perf_counter() - t0)
+    # open loop: Poisson arrivals at 0.8 x capacity
+    lam = 0.8 * cap
+    nreq = args.serve_requests
+    picks = rng.integers(0, len(pool), nreq)
+    gaps = rng.exponential(1.0 / lam, nreq)
+    tickets = []
+    t_start = time.perf_counter()
+    t_next = t_start
+    for i in range(nreq):
+        t_next += gaps[i]
+        dt = t_next - time.perf_counter()
+        if dt > 0:
+            time.sleep(dt)
+        g, b = pool[picks[i]]
+        tickets.append(S.submit(g, b))
+    S.drain(3600)
+    infos = [S.poll(t) for t in tickets]
+    S.close()
+    lat = np.array([i["t_done_ms"] - i["t_submit_ms"] for i in infos])
+    setup = np.array([i["t_ready_ms"] - i["t_admit_ms"] for i in infos])
+    wait = np.array([i["t_admit_ms"] - i["t_submit_ms"] for i in infos])
+    solve = np.array([i["t_done_ms"] - i["t_ready_ms"] for i in infos])
+    span = (max(i["t_done_ms"] for i in infos) - min(i["t_submit_ms"] for i in infos)) / 1e3
+    ok = sum(1 for i in infos if i["status"] == 0 and i["relres_true"] <= 2e-8)
+    sizes = [pool[p][0].n for p in picks]
+    print(json.dumps({
+        "metric": "served solves/s + p50/p99", "value": round(nreq / span, 3), "unit": "solves/s",
+        "p50_ms": round(float(np.percentile(lat, 50)), 2), "p99_ms": round(float(np.percentile(lat, 99)), 2),
+        "requests": nreq, "converged_1e-8": ok, "arrival_rate_per_s": round(lam, 3),
+        "closed_loop_capacity_per_s": round(cap, 3),
+        "latency_parts_p50_ms": {"admission_wait": round(float(np.median(wait)), 2),
+                                 "setup": round(float(np.median(setup)), 2),
+                                 "device_solve": round(float(np.median(solve)), 2)},
+        "n_range": [int(min(sizes)), int(max(sizes))], "setup_threads": args.serve_threads,
+        "config": {"workload": "serving: Poisson arrivals, grids/RGG/BA pool (24 graphs), "
+                               f"n <= {args.serve_max_n}, weights U(0.5,1.5], tol 1e-8, budget 120 GB"},
+    }), flush=True)
 
 
 def profile_sweep(level: int):
@@ -192,6 +264,18 @@ def schedule_counts(P, iters: int) -> dict:
     return visits
 
 
+def combine_ranks(total_ms: float, units: float, device="cpu"):
+    """Whole-job figures of independent replicas: the slowest rank's time and the units of all
+    ranks (timing metadata only; the solves exchange no data)."""
+    import torch
+    import torch.distributed as td
+    tmax = torch.tensor([total_ms], dtype=torch.float64, device=device)
+    tsum = torch.tensor([units], dtype=torch.float64, device=device)
+    td.all_reduce(tmax, op=td.ReduceOp.MAX)
+    td.all_reduce(tsum, op=td.ReduceOp.SUM)
+    return float(tmax[0]), float(tsum[0])
+
+
 def run_ours(args, ws, rank, local):
     import torch
     import paper_2606_24791_b300 as lamg
@@ -303,13 +387,44 @@ def run_ours(args, ws, rank, local):
     kernels["persistent_path_ms_per_solve"] = round(float(np.median(graph_ms)), 3)
     kernels["graph_path_launches_per_solve"] = 3 + (nops + 3) * iters[0] + 2 * iters[0] + 2
 
+    # other forms of the same solve on the same workload (same metric, per right-hand side):
+    # FP32 cycle inside FP64 CG, and 16 right-hand sides per SpMM-form solve (FP64 / FP32 cycle)
+    variants = {}
+    x64 = xt.cpu().numpy()
+    P32 = lamg.setup(g, device=local, precision=lamg.FP32)
+    for name, PP, k in (("fp32_cycle", P32, 1), ("batch16_fp64", P, 16), ("batch16_fp32_cycle", P32, 16)):
+        import graphgen as gg
+        # k independent mean-zero Gaussian right-hand sides b = L x (seed 2); k = 1 is the main b
+        Bk = torch.from_numpy(gg.rhs(g, seed=2, k=k) if k > 1 else b).to(dev)
+        Xk = torch.zeros_like(Bk)
+        ms, unit_sum, its, rts = [], 0.0, [], []
+        for rep in range(2 + 3):
+            flush.fill_(rep & 0xff)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            if k == 1:
+                sts = [PP.solve_ptr(Bk.data_ptr(), Xk.data_ptr(), TOL, 200, stream=stream.cuda_stream)]
+            else:
+                sts = PP.solve_batch_ptr(k, Bk.data_ptr(), Xk.data_ptr(), TOL, 200, stream=stream.cuda_stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            if rep >= 2:
+                ms.append(e0.elapsed_time(e1))
+                unit_sum += sum(g.nnz_L * digits(s["relres_true"]) for s in sts)
+                its.append(max(s["iters"] for s in sts))
+                rts.append(max(s["relres_true"] for s in sts))
+        v = {"value": round(float(np.sum(ms)) * 1e6 / unit_sum, 5), "unit": UNIT + " (per right-hand side)",
+             "rhs": k, "ms_per_solve": round(float(np.mean(ms)), 3), "iterations": its[-1],
+             "relres_true_max": max(rts),
+             "achieved_gbs": round(float(np.mean([s["alg_bytes"] for s in sts])) * k / (np.mean(ms) * 1e-3) / 1e9, 1)}
+        if k == 1:
+            v["rel_err_vs_fp64_solution"] = float(np.linalg.norm(Xk.cpu().numpy() - x64) / np.linalg.norm(x64))
+        variants[name] = v
+    P32.close()
+
     # whole-job value across ranks: max time over ranks / sum of units
     if ws > 1:
-        import torch.distributed as td
-        t = torch.tensor([total_ms, units], dtype=torch.float64, device=dev)
-        tmax = t.clone(); td.all_reduce(tmax[:1], op=td.ReduceOp.MAX)
-        tsum = t.clone(); td.all_reduce(tsum[1:], op=td.ReduceOp.SUM)
-        total_ms, units_all = float(tmax[0]), float(tsum[1])
+        total_ms, units_all = combine_ranks(total_ms, units, dev)
     else:
         units_all = units
     value = total_ms * 1e6 / units_all
@@ -327,6 +442,7 @@ def run_ours(args, ws, rank, local):
         "gpu_launches": launches,
         "roofline": roofline,
         "solve_roofline": solve_roofline,
+        "variants": variants,
         "kernels": kernels,
         "clocks": clocks,
         "wall_s_timed": round(wall, 3),
@@ -399,6 +515,10 @@ def main():
     ws, rank, local = dist_env()
     if args.profile_sweep >= 0:
         profile_sweep(args.profile_sweep)
+        return
+    if args.serve:
+        if rank == 0:
+            serve_bench(args)
         return
     if args.impl == "reference":
         out = run_reference(args, ws, rank)

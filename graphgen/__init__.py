@@ -112,6 +112,18 @@ def aniso_patch(N: int, patch: int, eps: float) -> Graph:
                       np.concatenate([np.ones(ux.size), wy]), f"patch{N}_{patch}_{eps:g}")
 
 
+def grid2d_random(nx: int, ny: int, seed: int, wlo: float = 0.5, whi: float = 1.5) -> Graph:
+    """5-point grid with i.i.d. weights U(wlo, whi]."""
+    g = grid2d(nx, ny)
+    rng = np.random.default_rng(seed)
+    rows = np.repeat(np.arange(g.n), np.diff(g.rp))
+    lo = np.minimum(rows, g.ci)
+    hi = np.maximum(rows, g.ci)
+    keep = rows < g.ci
+    w = whi - (whi - wlo) * rng.random(int(keep.sum()))
+    return from_edges(g.n, lo[keep], hi[keep], w, f"grid2d_{nx}x{ny}_rand")
+
+
 def path(n: int, w=None) -> Graph:
     u = np.arange(n - 1); v = u + 1
     w = np.ones(n - 1) if w is None else np.asarray(w, dtype=np.float64)

@@ -266,14 +266,30 @@ typedef struct lamg_ticket_info {
     int32_t status;        /* LAMG_OK or an error code once done */
     int32_t iters;
     int32_t pad;
-    double relres;
-    double t_submit_ms, t_admit_ms, t_done_ms;  /* server clock */
+    double relres;         /* recursive residual at exit */
+    double relres_true;    /* ||b - L phi|| / ||b|| recomputed at exit */
+    double t_submit_ms, t_admit_ms, t_ready_ms, t_done_ms;  /* server clock: submitted,
+                              admitted (setup starts), hierarchy ready, result ready */
 } lamg_ticket_info;
 
+/* Create a server on device so->device with the given setup options (NULL: defaults), one
+ * executor thread and so->setup_threads setup threads. Errors: INVALID, NO_DEVICE. */
 int lamg_server_create(const lamg_server_opts *so, const lamg_options *opt, lamg_server **out);
+/* Submit one request (graph + right-hand side, copied; same conventions as lamg_setup and
+ * lamg_solve); returns at once with a ticket. A request whose estimated device memory alone
+ * exceeds the budget is refused with LAMG_ERR_ADMISSION; an invalid graph is accepted and its
+ * ticket finishes with the setup's error code. */
 int lamg_serve(lamg_server *s, const lamg_graph *g, const double *b, int64_t *ticket);
+/* State of a ticket; when done and phi != NULL, the n-value solution is copied to phi.
+ * Errors: INVALID (unknown ticket). */
 int lamg_serve_poll(lamg_server *s, int64_t ticket, lamg_ticket_info *info, double *phi);
+/* Wait (at most timeout_s seconds) until every submitted request has finished.
+ * Errors: TIMEOUT. */
 int lamg_server_drain(lamg_server *s, double timeout_s);
+/* out[0] device bytes held by in-flight requests, out[1] requests in flight, out[2] requests
+ * waiting for admission, out[3] requests not yet finished. */
+int lamg_server_stats(lamg_server *s, int64_t *out);
+/* Stop the threads and release everything; unfinished requests are dropped. */
 void lamg_server_destroy(lamg_server *s);
 
 #ifdef __cplusplus

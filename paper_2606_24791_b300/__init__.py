@@ -66,6 +66,17 @@ class Stats(C.Structure):
                 ("launches", C.c_int64)]
 
 
+class ServerOpts(C.Structure):
+    _fields_ = [("budget_bytes", C.c_double), ("max_inflight", C.c_int32), ("setup_threads", C.c_int32),
+                ("tol", C.c_double), ("maxit", C.c_int32), ("device", C.c_int32)]
+
+
+class TicketInfo(C.Structure):
+    _fields_ = [("done", C.c_int32), ("status", C.c_int32), ("iters", C.c_int32), ("pad", C.c_int32),
+                ("relres", C.c_double), ("relres_true", C.c_double), ("t_submit_ms", C.c_double),
+                ("t_admit_ms", C.c_double), ("t_ready_ms", C.c_double), ("t_done_ms", C.c_double)]
+
+
 def lib_path() -> str:
     return _build.SO
 
@@ -96,6 +107,13 @@ def lib():
         L.lamg_profile_cycle.argtypes = [P, P, C.c_int64, C.POINTER(C.c_int64)]
         L.lamg_testvectors_noalloc.argtypes = [C.c_int64, P, P, P, P, P, C.c_int32, C.c_int32, C.c_uint64,
                                                C.c_int32, C.c_int32, P, P]
+        L.lamg_server_create.argtypes = [C.POINTER(ServerOpts), C.POINTER(Options), C.POINTER(P)]
+        L.lamg_serve.argtypes = [P, C.POINTER(Graph), P, C.POINTER(C.c_int64)]
+        L.lamg_serve_poll.argtypes = [P, C.c_int64, C.POINTER(TicketInfo), P]
+        L.lamg_server_drain.argtypes = [P, C.c_double]
+        L.lamg_server_stats.argtypes = [P, P]
+        L.lamg_server_destroy.argtypes = [P]
+        L.lamg_server_destroy.restype = None
         L.lamg_op_list.argtypes = [P, P, C.c_int64, C.POINTER(C.c_int64)]
         _lib = L
     return _lib
@@ -268,6 +286,55 @@ def _stats(st: Stats, hist) -> dict:
     if hist is not None:
         d["hist"] = hist[: st.iters + 1].copy()
     return d
+
+
+class Server:
+    """Continuous-batching solve server (lamg_server_*): submit (graph, b) requests, poll tickets."""
+
+    def __init__(self, budget_bytes: float, max_inflight: int = 64, setup_threads: int = 4,
+                 tol: float = 1e-8, maxit: int = 200, device: int = 0, **opts):
+        so = ServerOpts(float(budget_bytes), max_inflight, setup_threads, tol, maxit, device)
+        o = options(**opts)
+        h = C.c_void_p()
+        _check(lib().lamg_server_create(C.byref(so), C.byref(o), C.byref(h)), "lamg_server_create")
+        self._s = h
+
+    def submit(self, g, b) -> int:
+        rp, ci, w = _c(g.rp, np.int64), _c(g.ci, np.int32), _c(g.w, np.float64)
+        b = _c(b, np.float64)
+        G = Graph(g.n, rp.ctypes.data, ci.ctypes.data, w.ctypes.data)
+        t = C.c_int64()
+        _check(lib().lamg_serve(self._s, C.byref(G), _p(b), C.byref(t)), "lamg_serve")
+        return int(t.value)
+
+    def poll(self, ticket: int, n: int = 0) -> dict:
+        info = TicketInfo()
+        phi = np.zeros(n) if n else None
+        _check(lib().lamg_serve_poll(self._s, ticket, C.byref(info), _p(phi)), "lamg_serve_poll")
+        d = {f: getattr(info, f) for f, _ in TicketInfo._fields_ if f != "pad"}
+        if phi is not None and info.done:
+            d["phi"] = phi
+        return d
+
+    def drain(self, timeout_s: float = 600.0):
+        _check(lib().lamg_server_drain(self._s, timeout_s), "lamg_server_drain")
+
+    def stats(self) -> dict:
+        out = np.zeros(4, np.int64)
+        lib().lamg_server_stats(self._s, _p(out))
+        return dict(bytes_in_flight=int(out[0]), inflight=int(out[1]), waiting=int(out[2]),
+                    unfinished=int(out[3]))
+
+    def close(self):
+        if getattr(self, "_s", None):
+            lib().lamg_server_destroy(self._s)
+            self._s = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:  # noqa: BLE001 - interpreter shutdown
+            pass
 
 
 def setup(g, **opts) -> Hierarchy:

@@ -583,7 +583,8 @@ static int typed_copy(lamg_hier *h, const double *src, int64_t cnt, const void *
     if (!src || cnt <= 0) { *out = nullptr; return LAMG_OK; }
     if (sizeof(T) == sizeof(double)) { *out = src; return LAMG_OK; }
     std::vector<double> tmp(cnt);
-    CKR(cudaMemcpy(tmp.data(), src, cnt * sizeof(double), cudaMemcpyDeviceToHost));
+    CKR(cudaMemcpyAsync(tmp.data(), src, cnt * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    CKR(cudaStreamSynchronize(h->stream));
     std::vector<T> f(tmp.begin(), tmp.end());
     T *d = nullptr;
     int rc = dupload(h, &d, f);
@@ -606,10 +607,16 @@ static int build_ctx(lamg_hier *h, BatchCtx *c) {
         B.pf_col = D.pf_col; B.pft_ptr = D.pft_ptr; B.pft_f = D.pft_f; B.pinv = D.pinv;
         const int64_t pte = (D.kind == KIND_AGG) ? (int64_t)h->host[l].A.n * 2 : 0;
         int32_t ent = 0;
-        if (D.kind == KIND_AGG) CKR(cudaMemcpy(&ent, D.pt_ptr + D.nc, sizeof(int32_t), cudaMemcpyDeviceToHost));
+        if (D.kind == KIND_AGG) {
+            CKR(cudaMemcpyAsync(&ent, D.pt_ptr + D.nc, sizeof(int32_t), cudaMemcpyDeviceToHost, h->stream));
+            CKR(cudaStreamSynchronize(h->stream));
+        }
         (void)pte;
         int32_t fent = 0;
-        if (D.kind == KIND_ELIM) CKR(cudaMemcpy(&fent, D.pft_ptr + D.nc, sizeof(int32_t), cudaMemcpyDeviceToHost));
+        if (D.kind == KIND_ELIM) {
+            CKR(cudaMemcpyAsync(&fent, D.pft_ptr + D.nc, sizeof(int32_t), cudaMemcpyDeviceToHost, h->stream));
+            CKR(cudaStreamSynchronize(h->stream));
+        }
         if ((rc = typed_copy<T>(h, D.val, D.nnz, &B.val)) || (rc = typed_copy<T>(h, D.diag, D.n, &B.diag)) ||
             (rc = typed_copy<T>(h, D.wt, D.kind == KIND_AGG ? D.n : 0, &B.wt)) ||
             (rc = typed_copy<T>(h, D.pt_w, ent, &B.pt_w)) ||
@@ -655,9 +662,10 @@ static int build_ctx(lamg_hier *h, BatchCtx *c) {
         (rc = dalloc(h, &c->red.sk, B_COUNT * KMAX)) || (rc = dalloc(h, &c->red.done, KMAX)) ||
         (rc = dalloc(h, &c->red.itc, 1)))
         return rc;
-    CKR(cudaMemset(c->red.ticket, 0, sizeof(unsigned)));
-    CKR(cudaMemset(c->red.sk, 0, B_COUNT * KMAX * sizeof(double)));
-    CKR(cudaMemset(c->red.done, 0, KMAX * sizeof(int)));
+    CKR(cudaMemsetAsync(c->red.ticket, 0, sizeof(unsigned), h->stream));
+    CKR(cudaMemsetAsync(c->red.sk, 0, B_COUNT * KMAX * sizeof(double), h->stream));
+    CKR(cudaMemsetAsync(c->red.done, 0, KMAX * sizeof(int), h->stream));
+    CKR(cudaStreamSynchronize(h->stream));
     CKR(cudaHostAlloc(&c->h_sk, (B_COUNT * KMAX + KMAX) * sizeof(double), cudaHostAllocDefault));
     return LAMG_OK;
 }

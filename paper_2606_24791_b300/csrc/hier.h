@@ -13,6 +13,10 @@
 namespace lamg {
 struct BatchCtx;                  // multi-RHS / FP32-cycle workspace (batch.cu)
 void batch_free(BatchCtx *b);
+// 16-double slots of pinned host memory carved from process-lifetime slabs, so that creating
+// and destroying hierarchies never calls cudaFreeHost (which can synchronise the device).
+double *pinned_slot();
+void pinned_release(double *p);
 }  // namespace lamg
 
 struct lamg_hier {
@@ -59,8 +63,9 @@ struct lamg_hier {
         if (ev_a) cudaEventDestroy(ev_a);
         if (ev_b) cudaEventDestroy(ev_b);
         if (ev_poll) cudaEventDestroy(ev_poll);
-        for (void *a : allocs) cudaFree(a);
-        if (h_scal) cudaFreeHost(h_scal);
+        // stream-ordered frees: releasing one hierarchy never waits for other streams' work
+        for (void *a : allocs) cudaFreeAsync(a, stream);
+        if (h_scal) lamg::pinned_release(h_scal);
         if (stream) cudaStreamDestroy(stream);
     }
 };
@@ -73,13 +78,16 @@ namespace lamg {
         if (e_ != cudaSuccess) return cuda_status(e_); \
     } while (0)
 
-// Device allocation owned by the hierarchy (freed by lamg_destroy), 256-byte granularity.
+// Device allocation owned by the hierarchy (freed by lamg_destroy), 256-byte granularity,
+// stream-ordered on the hierarchy's stream (which exists before the first allocation) and
+// ready for any stream when this returns.
 template <typename T>
 inline int dalloc(lamg_hier *h, T **p, int64_t count) {
     size_t bytes = (size_t)(count > 1 ? count : 1) * sizeof(T);
     bytes = (bytes + 255) & ~(size_t)255;
     void *q = nullptr;
-    cudaError_t e = cudaMalloc(&q, bytes);
+    cudaError_t e = cudaMallocAsync(&q, bytes, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) return cuda_status(e);
     h->allocs.push_back(q);
     h->dev_bytes += bytes;
@@ -91,7 +99,10 @@ template <typename T>
 inline int dupload(lamg_hier *h, T **p, const std::vector<T> &v) {
     int rc = dalloc(h, p, (int64_t)v.size());
     if (rc) return rc;
-    if (!v.empty()) CKR(cudaMemcpy(*p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice));
+    if (!v.empty()) {
+        CKR(cudaMemcpyAsync(*p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, h->stream));
+        CKR(cudaStreamSynchronize(h->stream));
+    }
     return LAMG_OK;
 }
 

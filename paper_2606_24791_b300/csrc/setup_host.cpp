@@ -11,6 +11,7 @@
 #include <cmath>
 #include <cstring>
 #include <numeric>
+#include <thread>
 
 #include "internal.h"
 
@@ -382,25 +383,45 @@ int dense_pinv(const HostMat &A, std::vector<double> &pinv) {
             M[i * n + j] = t / gjj;
         }
     }
-    // inverse of G (lower triangular), then M^{-1} = G^{-T} G^{-1}
-    std::vector<double> Gi(n * n, 0.0);
-    for (int64_t c = 0; c < n; c++) {
-        Gi[c * n + c] = 1.0 / M[c * n + c];
+    // M^{-1} = G^{-T} G^{-1}. Row c of H = G^{-T} (stored row-major) is column c of G^{-1}, the
+    // forward substitution G y = e_c (y_i = 0 for i < c); then (M^{-1})_{ij} = H_i . H_j over
+    // k >= max(i, j). All inner loops run over contiguous memory; rows are split over threads.
+    std::vector<double> H(n * n, 0.0);
+    const int nthr = (int)std::max<unsigned>(1u, std::min<unsigned>(16u, std::thread::hardware_concurrency()));
+    auto parallel_rows = [&](auto &&fn) {
+        if (n < 128 || nthr == 1) {
+            for (int64_t r = 0; r < n; r++) fn(r);
+            return;
+        }
+        std::vector<std::thread> th;
+        for (int t = 0; t < nthr; t++)
+            th.emplace_back([&, t] {
+                for (int64_t r = t; r < n; r += nthr) fn(r);
+            });
+        for (auto &x : th) x.join();
+    };
+    parallel_rows([&](int64_t c) {
+        double *y = &H[c * n];
+        y[c] = 1.0 / M[c * n + c];
         for (int64_t i = c + 1; i < n; i++) {
+            const double *gi = &M[i * n];
             double t = 0.0;
-            for (int64_t k = c; k < i; k++) t -= M[i * n + k] * Gi[k * n + c];
-            Gi[i * n + c] = t / M[i * n + i];
+            for (int64_t k = c; k < i; k++) t -= gi[k] * y[k];
+            y[i] = t / gi[i];
         }
-    }
+    });
     pinv.assign(n * n, 0.0);
-    for (int64_t i = 0; i < n; i++) {
+    parallel_rows([&](int64_t i) {
+        const double *hi = &H[i * n];
         for (int64_t j = 0; j <= i; j++) {
+            const double *hj = &H[j * n];
             double s = 0.0;
-            for (int64_t k = i; k < n; k++) s += Gi[k * n + i] * Gi[k * n + j];
+            for (int64_t k = i; k < n; k++) s += hi[k] * hj[k];
             pinv[i * n + j] = s - 1.0 / (double)n;
-            pinv[j * n + i] = pinv[i * n + j];
         }
-    }
+    });
+    for (int64_t i = 0; i < n; i++)
+        for (int64_t j = 0; j < i; j++) pinv[j * n + i] = pinv[i * n + j];
     return LAMG_OK;
 }
 

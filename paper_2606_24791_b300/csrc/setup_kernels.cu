@@ -114,7 +114,9 @@ __global__ void k_affinity(int64_t n, int K, double tau, int veto, const int64_t
 
 static inline unsigned nblk(int64_t work, int bs) { return (unsigned)((work + bs - 1) / bs); }
 
-// Upload a level operator (natural order) and run K9 (and K10 when aff != nullptr).
+// Upload a level operator (natural order) and run K9 (and K10 when aff != nullptr). Everything is
+// ordered on a private stream with stream-ordered allocations, so a setup running on a host
+// thread never synchronises the whole device (solves of other hierarchies keep running).
 static int run_setup_kernels(const HostMat &A, const std::vector<int32_t> *colour, int level,
                              uint64_t seed, int K, int nu, double tau, int veto, double *X,
                              const double *Xin, double *aff, uint8_t *strong) {
@@ -125,55 +127,64 @@ static int run_setup_kernels(const HostMat &A, const std::vector<int32_t> *colou
     double *d_val = nullptr, *d_diag = nullptr, *d_X = nullptr, *d_aff = nullptr;
     uint8_t *d_strong = nullptr;
     const int bs = 128;
-    CK(cudaMalloc(&d_rp, (n + 1) * sizeof(int64_t)));
-    CK(cudaMalloc(&d_ci, (z ? z : 1) * sizeof(int32_t)));
-    CK(cudaMalloc(&d_val, (z ? z : 1) * sizeof(double)));
-    CK(cudaMalloc(&d_diag, n * sizeof(double)));
-    CK(cudaMalloc(&d_X, n * K * sizeof(double)));
-    CK(cudaMemcpy(d_rp, A.rp.data(), (n + 1) * sizeof(int64_t), cudaMemcpyHostToDevice));
-    if (z) CK(cudaMemcpy(d_ci, A.ci.data(), z * sizeof(int32_t), cudaMemcpyHostToDevice));
-    if (z) CK(cudaMemcpy(d_val, A.val.data(), z * sizeof(double), cudaMemcpyHostToDevice));
-    CK(cudaMemcpy(d_diag, A.diag.data(), n * sizeof(double), cudaMemcpyHostToDevice));
+    cudaStream_t st = nullptr;
+    std::vector<int32_t> rows;
+    std::vector<int64_t> cptr;
+    int ncol = 0;
+    CK(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+    CK(cudaMallocAsync((void **)&d_rp, (n + 1) * sizeof(int64_t), st));
+    CK(cudaMallocAsync((void **)&d_ci, (z ? z : 1) * sizeof(int32_t), st));
+    CK(cudaMallocAsync((void **)&d_val, (z ? z : 1) * sizeof(double), st));
+    CK(cudaMallocAsync((void **)&d_diag, n * sizeof(double), st));
+    CK(cudaMallocAsync((void **)&d_X, n * K * sizeof(double), st));
+    CK(cudaMemcpyAsync(d_rp, A.rp.data(), (n + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, st));
+    if (z) CK(cudaMemcpyAsync(d_ci, A.ci.data(), z * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    if (z) CK(cudaMemcpyAsync(d_val, A.val.data(), z * sizeof(double), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(d_diag, A.diag.data(), n * sizeof(double), cudaMemcpyHostToDevice, st));
     if (colour) {
         // rows grouped by colour, ascending within a colour
-        int ncol = 0;
         for (int32_t c : *colour) ncol = std::max(ncol, c + 1);
-        std::vector<int64_t> cptr(ncol + 1, 0);
+        cptr.assign(ncol + 1, 0);
         for (int32_t c : *colour) cptr[c + 1]++;
         for (int c = 0; c < ncol; c++) cptr[c + 1] += cptr[c];
-        std::vector<int32_t> rows(n);
+        rows.resize(n);
         std::vector<int64_t> fill(cptr.begin(), cptr.end() - 1);
         for (int64_t u = 0; u < n; u++) rows[fill[(*colour)[u]]++] = (int32_t)u;
-        CK(cudaMalloc(&d_rows, n * sizeof(int32_t)));
-        CK(cudaMemcpy(d_rows, rows.data(), n * sizeof(int32_t), cudaMemcpyHostToDevice));
-        k_tv_start<<<nblk(n * K, bs), bs>>>(n, K, seed, level, d_X);
+        CK(cudaMallocAsync((void **)&d_rows, n * sizeof(int32_t), st));
+        CK(cudaMemcpyAsync(d_rows, rows.data(), n * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+        k_tv_start<<<nblk(n * K, bs), bs, 0, st>>>(n, K, seed, level, d_X);
         for (int s = 0; s < nu; s++) {
             for (int c = 0; c < ncol; c++) {
                 const int64_t cnt = cptr[c + 1] - cptr[c];
                 if (!cnt) continue;
                 if (K == 4)
-                    k_tv_colour<4><<<nblk(cnt, bs), bs>>>(cnt, d_rows + cptr[c], d_rp, d_ci, d_val, d_diag, d_X);
+                    k_tv_colour<4><<<nblk(cnt, bs), bs, 0, st>>>(cnt, d_rows + cptr[c], d_rp, d_ci, d_val, d_diag, d_X);
                 else
-                    k_tv_colour_any<<<nblk(cnt, bs), bs>>>(K, cnt, d_rows + cptr[c], d_rp, d_ci, d_val, d_diag, d_X);
+                    k_tv_colour_any<<<nblk(cnt, bs), bs, 0, st>>>(K, cnt, d_rows + cptr[c], d_rp, d_ci, d_val, d_diag, d_X);
             }
         }
         CK(cudaGetLastError());
-        if (X) CK(cudaMemcpy(X, d_X, n * K * sizeof(double), cudaMemcpyDeviceToHost));
+        if (X) CK(cudaMemcpyAsync(X, d_X, n * K * sizeof(double), cudaMemcpyDeviceToHost, st));
     } else {
-        CK(cudaMemcpy(d_X, Xin, n * K * sizeof(double), cudaMemcpyHostToDevice));
+        CK(cudaMemcpyAsync(d_X, Xin, n * K * sizeof(double), cudaMemcpyHostToDevice, st));
     }
     if (aff) {
-        CK(cudaMalloc(&d_aff, (z ? z : 1) * sizeof(double)));
-        CK(cudaMalloc(&d_strong, (z ? z : 1)));
-        k_affinity<<<nblk(n, bs), bs>>>(n, K, tau, veto, d_rp, d_ci, d_val, d_X, d_aff, d_strong);
+        CK(cudaMallocAsync((void **)&d_aff, (z ? z : 1) * sizeof(double), st));
+        CK(cudaMallocAsync((void **)&d_strong, (z ? z : 1), st));
+        k_affinity<<<nblk(n, bs), bs, 0, st>>>(n, K, tau, veto, d_rp, d_ci, d_val, d_X, d_aff, d_strong);
         CK(cudaGetLastError());
-        if (z) CK(cudaMemcpy(aff, d_aff, z * sizeof(double), cudaMemcpyDeviceToHost));
-        if (z) CK(cudaMemcpy(strong, d_strong, z, cudaMemcpyDeviceToHost));
+        if (z) CK(cudaMemcpyAsync(aff, d_aff, z * sizeof(double), cudaMemcpyDeviceToHost, st));
+        if (z) CK(cudaMemcpyAsync(strong, d_strong, z, cudaMemcpyDeviceToHost, st));
     }
-    CK(cudaDeviceSynchronize());
+    CK(cudaStreamSynchronize(st));
 out:
-    cudaFree(d_rp); cudaFree(d_ci); cudaFree(d_val); cudaFree(d_diag); cudaFree(d_X);
-    cudaFree(d_rows); cudaFree(d_aff); cudaFree(d_strong);
+    if (st) {
+        void *ptrs[] = {d_rp, d_ci, d_val, d_diag, d_X, d_rows, d_aff, d_strong};
+        for (void *q : ptrs)
+            if (q) cudaFreeAsync(q, st);
+        cudaStreamSynchronize(st);
+        cudaStreamDestroy(st);
+    }
     return rc;
 }
 

@@ -332,8 +332,9 @@ int setup_persistent(lamg_hier *h) {
     if ((rc = dalloc(h, &h->hist, h->hist_cap))) return rc;
     S.hist = h->hist;
     if ((rc = dalloc(h, &h->psolve, 1))) return rc;
-    CKR(cudaMemcpy(h->psolve, &S, sizeof(S), cudaMemcpyHostToDevice));
-    CKR(cudaMemset(h->bar, 0, sizeof(GridBar)));
+    CKR(cudaMemcpyAsync(h->psolve, &S, sizeof(S), cudaMemcpyHostToDevice, h->stream));
+    CKR(cudaMemsetAsync(h->bar, 0, sizeof(GridBar), h->stream));
+    CKR(cudaStreamSynchronize(h->stream));
     h->persistent_ok = true;
     return LAMG_OK;
 }
@@ -370,9 +371,10 @@ int finalize(lamg_hier *h) {
     if ((rc = dalloc(h, &h->red.partials, RED_NV * RED_MAXG)) || (rc = dalloc(h, &h->red.ticket, 1)) ||
         (rc = dalloc(h, &h->red.scal, S_COUNT)))
         return rc;
-    CKR(cudaMemset(h->red.ticket, 0, sizeof(unsigned)));
-    CKR(cudaMemset(h->red.scal, 0, S_COUNT * sizeof(double)));
-    CKR(cudaHostAlloc(&h->h_scal, S_COUNT * sizeof(double), cudaHostAllocDefault));
+    CKR(cudaMemsetAsync(h->red.ticket, 0, sizeof(unsigned), h->stream));
+    CKR(cudaMemsetAsync(h->red.scal, 0, S_COUNT * sizeof(double), h->stream));
+    h->h_scal = pinned_slot();
+    if (!h->h_scal) return LAMG_ERR_OOM;
     std::vector<int64_t> visits(L, 0);
     h->ops.clear();
     emit_visit(h, visits, 0, true);
@@ -629,7 +631,10 @@ static int solve_persistent(lamg_hier *h, const double *b, double *phi, const la
     const double bn2 = h->h_scal[S_BN2];
     const double rel = bn2 > 0 ? std::sqrt(h->h_scal[S_RR] / bn2) : 0.0;
     if (st) {
-        if (st->hist) CKR(cudaMemcpy(st->hist, h->hist, (it + 1) * sizeof(double), cudaMemcpyDeviceToHost));
+        if (st->hist) {
+            CKR(cudaMemcpyAsync(st->hist, h->hist, (it + 1) * sizeof(double), cudaMemcpyDeviceToHost, s));
+            CKR(cudaStreamSynchronize(s));
+        }
         st->iters = it;
         st->nlevels = (int32_t)h->dev.size();
         st->relres = rel;
@@ -826,7 +831,8 @@ int lamg_time_kernel(lamg_hier *h, int32_t which, int32_t level, int32_t reps, d
         case 2: bytes = 12 * z + 28 * n + 4; break;
         case 3: {
             int32_t ent = 0;
-            cudaMemcpy(&ent, D.pt_ptr + D.nc, sizeof(int32_t), cudaMemcpyDeviceToHost);
+            cudaMemcpyAsync(&ent, D.pt_ptr + D.nc, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+            cudaStreamSynchronize(s);
             seq.push_back({OP_RESTRICT, level, 0});
             bytes = 12.0 * ent + 4 * (nc + 1) + 8 * n + 8 * nc;
             break;

@@ -1,0 +1,71 @@
+"""Serving: continuous batching of mixed requests under a memory budget (B300).
+
+A served solve runs the same kernels on the same hierarchy as lamg_solve, so each result must
+equal the solve of that request run alone; the stated tolerance is 1e-12 relative (bit-equal is
+expected: every reduction is deterministic).
+"""
+import numpy as np
+import pytest
+
+import graphgen as gg
+import paper_2606_24791_b300 as lamg
+
+pytestmark = pytest.mark.gpu
+
+
+def mix():
+    gs = [gg.grid2d(32, 32), gg.grid2d(96, 80, 1.0, 1e-3), gg.rgg(3000, 10, seed=3),
+          gg.barabasi_albert(4000, 4, seed=4), gg.grid2d(64, 64, 0.7, 1.3), gg.rgg(12000, 10, seed=5),
+          gg.barabasi_albert(1500, 4, seed=6), gg.grid3d(12, 12, 12, "loguniform", seed=7),
+          gg.chung_lu(6000, 2.1, 16, seed=8), gg.grid2d(128, 40, 1.0, 0.05),
+          gg.grid2d(256, 256, 1.0, 1e-3), gg.grid2d(300, 200, 1.0, 1e-3), gg.rgg(60000, 10, seed=9),
+          gg.grid3d(40, 40, 40, "loguniform", seed=10)]
+    return [(g, gg.rhs(g, seed=20 + i)) for i, g in enumerate(gs)]
+
+
+def rel(a, b):
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+def test_served_results_equal_solo_results_and_requests_overlap():
+    reqs = mix()
+    alone = []
+    for g, b in reqs:
+        P = lamg.setup(g)
+        x, st = P.solve(b, 1e-8, 200)
+        alone.append((x, st["iters"]))
+        P.close()
+    # a budget that holds only a few hierarchies at once forces queueing and admission
+    S = lamg.Server(budget_bytes=400e6, max_inflight=6, setup_threads=4, tol=1e-8, maxit=200)
+    tickets = [S.submit(g, b) for g, b in reqs]
+    S.drain(300)
+    infos = [S.poll(t, g.n) for t, (g, _) in zip(tickets, reqs)]
+    for (x, iters), info in zip(alone, infos):
+        assert info["done"] and info["status"] == 0
+        assert info["relres_true"] <= 2e-8
+        assert info["iters"] == iters
+        assert rel(info["phi"], x) <= 1e-12
+    # at least two requests were on the device at the same time
+    spans = [(i["t_ready_ms"], i["t_done_ms"]) for i in infos]
+    overlap = max(sum(1 for a, b in spans if a <= t < b) for t, _ in spans)
+    assert overlap >= 2, spans
+    assert S.stats()["unfinished"] == 0 and S.stats()["bytes_in_flight"] == 0
+    S.close()
+
+
+def test_admission_refuses_oversized_and_reports_invalid_graphs():
+    S = lamg.Server(budget_bytes=20e6, max_inflight=2, setup_threads=1)
+    big = gg.grid2d(300, 300)
+    with pytest.raises(lamg.LamgError) as e:
+        S.submit(big, gg.rhs(big, 1))
+    assert e.value.code == 8
+    g = gg.grid2d(20, 20)
+    bad = gg.Graph(g.n, g.rp.copy(), g.ci.copy(), g.w.copy())
+    bad.w[0] *= 3.0
+    t_bad = S.submit(bad, gg.rhs(g, 1))
+    t_ok = S.submit(g, gg.rhs(g, 2))
+    S.drain(60)
+    assert S.poll(t_bad)["status"] == 1
+    ok = S.poll(t_ok, g.n)
+    assert ok["status"] == 0 and ok["relres_true"] <= 2e-8
+    S.close()
