@@ -166,84 +166,27 @@ double oracle_random_start(uint64_t seed, int level, int64_t u, int k) {
 
 /* ------------------------------------------------------------------ colouring */
 
-/* Smallest-last order (Matula and Beck): repeatedly remove a node of minimum remaining degree,
- * the lowest id among ties; the order is the reverse of the removals. Plain O(n^2)-worst
- * selection by scanning degree buckets kept as per-degree lists in id order. */
-static void smallest_last_order(const Mat *A, int32_t *order) {
-    int64_t n = A->n;
-    int64_t *deg = xcalloc(n, sizeof(int64_t));
-    uint8_t *gone = xcalloc(n, 1);
-    int64_t maxd = 0;
-    for (int64_t u = 0; u < n; u++) {
-        deg[u] = A->rp[u + 1] - A->rp[u];
-        if (deg[u] > maxd) maxd = deg[u];
-    }
-    /* min-heap of (degree, id) with lazy deletion */
-    int64_t cap = n + A->nnz + 1, sz = 0;
-    int64_t *hk = xcalloc(cap, sizeof(int64_t)), *hv = xcalloc(cap, sizeof(int64_t));
-#define HLESS(i, j) (hk[i] < hk[j] || (hk[i] == hk[j] && hv[i] < hv[j]))
-#define HSWAP(i, j) do { int64_t t_ = hk[i]; hk[i] = hk[j]; hk[j] = t_; t_ = hv[i]; hv[i] = hv[j]; hv[j] = t_; } while (0)
-    for (int64_t u = 0; u < n; u++) {
-        int64_t i = sz++;
-        hk[i] = deg[u]; hv[i] = u;
-        while (i > 0 && HLESS(i, (i - 1) / 2)) { HSWAP(i, (i - 1) / 2); i = (i - 1) / 2; }
-    }
-    int64_t removed = 0;
-    while (removed < n) {
-        int64_t d = hk[0], u = hv[0];
-        /* pop */
-        sz--; hk[0] = hk[sz]; hv[0] = hv[sz];
-        for (int64_t i = 0;;) {
-            int64_t l = 2 * i + 1, r = l + 1, m = i;
-            if (l < sz && HLESS(l, m)) m = l;
-            if (r < sz && HLESS(r, m)) m = r;
-            if (m == i) break;
-            HSWAP(i, m); i = m;
-        }
-        if (gone[u] || d != deg[u]) continue;  /* stale entry */
-        gone[u] = 1;
-        order[n - 1 - removed] = (int32_t)u;
-        removed++;
-        for (int64_t e = A->rp[u]; e < A->rp[u + 1]; e++) {
-            int32_t v = A->ci[e];
-            if (gone[v]) continue;
-            deg[v]--;
-            int64_t i = sz++;
-            hk[i] = deg[v]; hv[i] = v;
-            while (i > 0 && HLESS(i, (i - 1) / 2)) { HSWAP(i, (i - 1) / 2); i = (i - 1) / 2; }
-        }
-    }
-#undef HLESS
-#undef HSWAP
-    free(deg); free(gone); free(hk); free(hv);
-}
-
-/* Greedy colouring in smallest-last order: each node takes the smallest colour unused by its
- * already-coloured neighbours (at most degeneracy + 1 colours). Rows of one colour are
- * pairwise non-adjacent, so a Gauss-Seidel sweep over one colour is the same whatever order its
- * rows are visited in. */
+/* Greedy colouring in ascending node order, smallest colour unused by coloured neighbours.
+ * Rows of one colour are pairwise non-adjacent, so a Gauss-Seidel sweep over one colour is
+ * the same whatever order its rows are visited in. */
 static void colour_level(Level *L) {
     const Mat *A = &L->A;
     int64_t n = A->n;
     L->colour = xcalloc(n, sizeof(int32_t));
     int maxc = 0;
     int32_t *mark = xcalloc(n + 2, sizeof(int32_t));
-    int32_t *order = xcalloc(n, sizeof(int32_t));
-    smallest_last_order(A, order);
     for (int64_t u = 0; u < n; u++) L->colour[u] = -1;
-    for (int64_t t = 0; t < n; t++) {
-        int64_t u = order[t];
+    for (int64_t u = 0; u < n; u++) {
         for (int64_t e = A->rp[u]; e < A->rp[u + 1]; e++) {
             int32_t c = L->colour[A->ci[e]];
-            if (c >= 0) mark[c] = (int32_t)(t + 1);
+            if (c >= 0) mark[c] = (int32_t)(u + 1);
         }
         int c = 0;
-        while (mark[c] == (int32_t)(t + 1)) c++;
+        while (mark[c] == (int32_t)(u + 1)) c++;
         L->colour[u] = c;
         if (c + 1 > maxc) maxc = c + 1;
     }
     free(mark);
-    free(order);
     L->ncol = maxc;
     L->cptr = xcalloc(maxc + 1, sizeof(int64_t));
     for (int64_t u = 0; u < n; u++) L->cptr[L->colour[u] + 1]++;
@@ -1134,7 +1077,7 @@ int oracle_laplacian(int64_t n, const int64_t *rp, const int32_t *ci, const doub
 /* Greedy colouring; returns the number of colours. */
 int oracle_colour(int64_t n, const int64_t *rp, const int32_t *ci, int32_t *colour) {
     Level L; memset(&L, 0, sizeof(L));
-    L.A.n = n; L.A.nnz = rp[n]; L.A.rp = (int64_t *)rp; L.A.ci = (int32_t *)ci;
+    L.A.n = n; L.A.rp = (int64_t *)rp; L.A.ci = (int32_t *)ci;
     colour_level(&L);
     memcpy(colour, L.colour, n * sizeof(int32_t));
     int nc = L.ncol;

@@ -61,42 +61,19 @@ def test_laplacian_definition():
     assert math.isclose(x @ D @ x, energy, rel_tol=1e-12)
 
 
-def smallest_last(g):
-    """Brute force: repeatedly remove the lowest-id node of minimum remaining degree; the
-    colouring order is the reverse of the removals. Also returns the degeneracy."""
-    alive = set(range(g.n))
-    deg = {u: int(g.rp[u + 1] - g.rp[u]) for u in range(g.n)}
-    removal, degen = [], 0
-    while alive:
-        u = min(alive, key=lambda v: (deg[v], v))
-        degen = max(degen, deg[u])
-        removal.append(u)
-        alive.remove(u)
-        for v in g.ci[g.rp[u]:g.rp[u + 1]]:
-            if int(v) in alive:
-                deg[int(v)] -= 1
-    return removal[::-1], degen
-
-
-@pytest.mark.parametrize("make", [lambda: gg.random_connected(80, 200, seed=5),
-                                  lambda: gg.barabasi_albert(150, 4, seed=2),
-                                  lambda: gg.grid2d(9, 7)])
-def test_colouring_is_smallest_last_greedy_and_proper(make):
-    g = make()
+def test_colouring_is_greedy_and_proper():
+    g = gg.random_connected(80, 200, seed=5)
     A = oracle.laplacian(g)
     col, nc = oracle.colour(A)
-    order, degen = smallest_last(g)
-    pos = np.empty(g.n, int)
-    pos[order] = np.arange(g.n)
     for u in range(g.n):
         nb = g.ci[g.rp[u]:g.rp[u + 1]]
         assert np.all(col[nb] != col[u])
-        earlier = set(col[nb[pos[nb] < pos[u]]].tolist())
+        lower = set(col[nb[nb < u]].tolist())
         c = 0
-        while c in earlier:
+        while c in lower:
             c += 1
         assert col[u] == c
-    assert nc == col.max() + 1 <= degen + 1
+    assert nc == col.max() + 1
 
 
 @pytest.mark.parametrize("order", ["forward", "reverse", "lex"])
@@ -285,7 +262,7 @@ def test_caliber2_gate_is_self_targeting():
     La = next(l for l in an.levels if l["kind"] == "agg")
     assert Li["n_caliber2"] / Li["n"] < 0.03
     assoc = np.sum(La["seed_of"] != np.arange(La["n"]))
-    assert La["n_caliber2"] / assoc > 0.85      # measured 0.897 on this grid
+    assert La["n_caliber2"] / assoc > 0.9
 
 
 def test_veto_is_inert_on_uniform_weights():
