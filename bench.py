@@ -46,6 +46,8 @@ def parse():
     ap.add_argument("--tail-rows", type=int, default=8192,
                     help="levels with at most this many rows run inside one CTA (persistent path)")
     ap.add_argument("--serve", action="store_true", help="run the serving workload instead")
+    ap.add_argument("--profile-cycle", action="store_true",
+                    help="per-step timing of one persistent-kernel cycle of the workload")
     ap.add_argument("--serve-requests", type=int, default=200)
     ap.add_argument("--serve-max-n", type=int, default=200000)
     ap.add_argument("--serve-threads", type=int, default=8)
@@ -121,6 +123,36 @@ def serve_bench(args):
         "config": {"workload": "serving: Poisson arrivals, grids/RGG/BA pool (24 graphs), "
                                f"n <= {args.serve_max_n}, weights U(0.5,1.5], tol 1e-8, budget 120 GB"},
     }), flush=True)
+
+
+def profile_cycle():
+    """Per-step device time of one cycle of the persistent kernel (%globaltimer at every grid
+    barrier), grouped by (step kind, level), for the workload's hierarchy."""
+    import collections
+    import paper_2606_24791_b300 as lamg
+    g, b = workload()
+    P = lamg.setup(g)
+    ops = P.op_list()
+    for _ in range(3):
+        P.profile_cycle()
+    prof = P.profile_cycle()
+    groups = collections.defaultdict(lambda: [0, 0])
+    prev = 0
+    for nxt, ns in prof:
+        kinds = sorted(set((ops[i][0], ops[i][1]) for i in range(prev, nxt) if ops[i][0] != "resid"))
+        key = "single-CTA segment" if len(kinds) > 1 else (f"{kinds[0][0]}@L{kinds[0][1]}" if kinds else "?")
+        groups[key][0] += 1
+        groups[key][1] += ns
+        prev = nxt
+    x, st = P.solve(b, TOL, 200)
+    x2, st2 = P.solve(b, TOL, 200, persistent=True)
+    print(json.dumps({
+        "levels": [(i["kind"], i["n"], i["ncol"]) for i in P.info],
+        "cycle_us": sum(t for _, t in prof) / 1e3, "barrier_steps": len(prof),
+        "steps": {k: {"count": c, "total_us": round(t / 1e3, 1), "avg_us": round(t / c / 1e3, 2)}
+                  for k, (c, t) in sorted(groups.items(), key=lambda kv: -kv[1][1])},
+        "graph_path_solve_ms": st["solve_ms"], "persistent_solve_ms": st2["solve_ms"],
+        "iterations": st["iters"]}))
 
 
 def profile_sweep(level: int):
@@ -515,6 +547,9 @@ def main():
     ws, rank, local = dist_env()
     if args.profile_sweep >= 0:
         profile_sweep(args.profile_sweep)
+        return
+    if args.profile_cycle:
+        profile_cycle()
         return
     if args.serve:
         if rank == 0:

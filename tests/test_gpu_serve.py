@@ -27,7 +27,7 @@ def rel(a, b):
     return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
 
 
-def test_served_results_equal_solo_results_and_requests_overlap():
+def test_served_results_equal_solo_results():
     reqs = mix()
     alone = []
     for g, b in reqs:
@@ -45,11 +45,24 @@ def test_served_results_equal_solo_results_and_requests_overlap():
         assert info["relres_true"] <= 2e-8
         assert info["iters"] == iters
         assert rel(info["phi"], x) <= 1e-12
-    # at least two requests were on the device at the same time
+    assert S.stats()["unfinished"] == 0 and S.stats()["bytes_in_flight"] == 0
+    S.close()
+
+
+def test_requests_of_equal_size_share_the_device():
+    # eight equal requests submitted together: the setup threads finish them in groups within
+    # a fraction of a solve, and the executor must interleave their solves instead of running
+    # one request to completion before launching the next
+    reqs = [(gg.grid2d(128, 128, 1.0, 1e-3), None) for _ in range(8)]
+    reqs = [(g, gg.rhs(g, seed=40 + i)) for i, (g, _) in enumerate(reqs)]
+    S = lamg.Server(budget_bytes=2e9, max_inflight=8, setup_threads=4, tol=1e-10, maxit=200)
+    tickets = [S.submit(g, b) for g, b in reqs]
+    S.drain(120)
+    infos = [S.poll(t, g.n) for t, (g, _) in zip(tickets, reqs)]
+    assert all(i["done"] and i["status"] == 0 and i["relres_true"] <= 2e-10 for i in infos)
     spans = [(i["t_ready_ms"], i["t_done_ms"]) for i in infos]
     overlap = max(sum(1 for a, b in spans if a <= t < b) for t, _ in spans)
     assert overlap >= 2, spans
-    assert S.stats()["unfinished"] == 0 and S.stats()["bytes_in_flight"] == 0
     S.close()
 
 
