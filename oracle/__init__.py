@@ -22,11 +22,11 @@ _lock = threading.Lock()
 _lib = None
 
 DEFAULTS = dict(K=4, nu_tv=3, dmax=4, nu_pre=1, nu_post=2, coarsest_max=1024, max_levels=100,
-                veto=1, caliber2=1, tv_lex=0, symmetric=0, seed=3,
+                veto=1, caliber2=1, tv_lex=0, symmetric=0, seed=3, dense_rows=4096,
                 Q=2.5, tau_soc=0.05, elim_min_frac=0.01, snap=1e-3, guard_eps=1e-10,
                 gamma_fixed=0.0)
 _IKEYS = ["K", "nu_tv", "dmax", "nu_pre", "nu_post", "coarsest_max", "max_levels", "veto",
-          "caliber2", "tv_lex", "symmetric", "seed"]
+          "caliber2", "tv_lex", "symmetric", "seed", "dense_rows"]
 _DKEYS = ["Q", "tau_soc", "elim_min_frac", "snap", "guard_eps", "gamma_fixed"]
 
 KIND = {0: "elim", 1: "agg", 2: "coarsest"}

@@ -45,6 +45,8 @@ typedef struct {
     int dmax;           /* low-degree elimination bound, Eq. 2: d_max = 4 */
     int nu_pre, nu_post;/* (1,2) cycle, Appendix A Table 4 */
     int coarsest_max;   /* dense coarsest level when n <= this */
+    int dense_rows;     /* dense coarsest level also when n <= this and the level has at least
+                           n^2 / 8 off-diagonal entries (0: off) */
     int max_levels;
     int veto;           /* strength-of-connection veto on/off (Eq. 9) */
     int caliber2;       /* selective caliber-2 on/off (Section 3.2) */
@@ -633,6 +635,7 @@ static void fill_opts(Opts *o, const int64_t *iopt, const double *dopt) {
     o->nu_pre = (int)iopt[3]; o->nu_post = (int)iopt[4]; o->coarsest_max = (int)iopt[5];
     o->max_levels = (int)iopt[6]; o->veto = (int)iopt[7]; o->caliber2 = (int)iopt[8];
     o->tv_lex = (int)iopt[9]; o->symmetric = (int)iopt[10]; o->seed = (uint64_t)iopt[11];
+    o->dense_rows = (int)iopt[12];
     o->Q = dopt[0]; o->tau_soc = dopt[1]; o->elim_min_frac = dopt[2]; o->snap = dopt[3];
     o->guard_eps = dopt[4]; o->gamma_fixed = dopt[5];
 }
@@ -739,8 +742,11 @@ void oracle_free(Hier *H) {
 /* Build the hierarchy (Section 2): alternate low-degree elimination (kept while it removes
  * at least elim_min_frac of the nodes) and guarded aggregation, until the level has at most
  * coarsest_max nodes. Readings: a level whose aggregation removes fewer than 10% of its
- * nodes and has at most 4096 nodes becomes the coarsest; otherwise coarsening continues
- * while it makes progress; at most max_levels levels. */
+ * nodes and has at most 4096 nodes becomes the coarsest; so does a level with at most
+ * dense_rows nodes and at least n^2/8 off-diagonal entries (the paper leaves the size of the
+ * directly solved level open: a dense level costs one dense solve instead of a sweep per
+ * colour class); otherwise coarsening continues while it makes progress; at most max_levels
+ * levels. */
 int oracle_setup(int64_t n, const int64_t *rp, const int32_t *ci, const double *w,
                  const int64_t *iopt, const double *dopt, Hier **out) {
     *out = NULL;
@@ -759,7 +765,8 @@ int oracle_setup(int64_t n, const int64_t *rp, const int32_t *ci, const double *
         L->A = A;
         alloc_vectors(L);
         H->nlev = l + 1;
-        if (A.n <= o->coarsest_max || l + 1 >= o->max_levels) {
+        const int dense = A.n <= o->dense_rows && (double)A.nnz >= (double)A.n * (double)A.n / 8.0;
+        if (A.n <= o->coarsest_max || dense || l + 1 >= o->max_levels) {
             L->kind = LV_COARSEST;
             if (A.n > 4096) { oracle_free(H); return ERR_SETUP; }
             rc = coarsest_pinv(L);

@@ -335,6 +335,29 @@ def test_star_graph_leaves_eliminated():
     assert np.linalg.norm(out["x"] - ref) <= 1e-12 * np.linalg.norm(ref)
 
 
+def test_dense_level_becomes_the_coarsest():
+    # a level with at most dense_rows nodes and >= n^2/8 off-diagonal entries is solved
+    # directly: a dense random graph (density ~0.3) stops at level 0 and one preconditioned
+    # step is the exact pseudo-inverse solution; with the rule off it is coarsened further
+    rng = np.random.default_rng(11)
+    n = 400
+    iu = np.triu_indices(n, 1)
+    keep = rng.random(len(iu[0])) < 0.3
+    g = gg.largest_cc(gg.from_edges(n, iu[0][keep], iu[1][keep], rng.uniform(0.5, 1.5, keep.sum())))
+    assert 2 * g.m >= g.n * g.n / 8
+    H = oracle.Hierarchy(g, coarsest_max=16)
+    assert H.nlevels == 1 and H.levels[0]["kind"] == "coarsest"
+    b = gg.rhs(g, 4)
+    out = H.fcg(b, tol=1e-13, maxit=5)
+    ref = np.linalg.pinv(dense_L(g), rcond=1e-10, hermitian=True) @ b
+    assert out["iters"] == 1
+    assert np.linalg.norm(out["x"] - ref) <= 1e-11 * np.linalg.norm(ref)
+    off = oracle.Hierarchy(g, coarsest_max=16, dense_rows=0)
+    assert off.nlevels > 1
+    # a size bound below n switches the rule off for this level
+    assert oracle.Hierarchy(g, coarsest_max=16, dense_rows=g.n - 1).nlevels > 1
+
+
 @pytest.mark.parametrize("gamma", [1.0, 2.0])
 def test_symmetric_cycle_is_symmetric(gamma):
     # With nu_pre = nu_post, forward pre- and reverse post-smoothing, P^T restriction and exact
