@@ -371,7 +371,6 @@ def run_ours(args, ws, rank, local):
         e1.record(stream)
         torch.cuda.synchronize()
         graph_ms.append(e0.elapsed_time(e1))
-    nops = P_ops(P)
 
     # e2e: the same solve through the C ABI with host buffers (H2D of b, D2H of phi inside)
     e2e_t, e2e_units = 0.0, 0.0
@@ -417,7 +416,21 @@ def run_ours(args, ws, rank, local):
     kernels = {name + " (per-step kernel, cold L2, alone)": {"gbs": round(rr["gbs"], 1), "ms": round(rr["ms"], 4)}
                for _, name, rr in cand}
     kernels["persistent_path_ms_per_solve"] = round(float(np.median(graph_ms)), 3)
-    kernels["graph_path_launches_per_solve"] = 3 + (nops + 3) * iters[0] + 2 * iters[0] + 2
+    kernels["graph_path_launches_per_solve"] = launches // max(args.steps, 1)
+    kernels["schedule"] = P.schedule()
+    # the same solve with every cycle step its own kernel (no cluster sub-cycle)
+    Pq = lamg.setup(g, device=local, cluster_rows=-1)
+    qms = []
+    for _ in range(3):
+        flush.fill_(9)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        Pq.solve_ptr(bt.data_ptr(), xt.data_ptr(), TOL, 200, stream=stream.cuda_stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        qms.append(e0.elapsed_time(e1))
+    kernels["per_step_schedule_ms_per_solve"] = round(float(np.median(qms)), 3)
+    Pq.close()
 
     # other forms of the same solve on the same workload (same metric, per right-hand side):
     # FP32 cycle inside FP64 CG, and 16 right-hand sides per SpMM-form solve (FP64 / FP32 cycle)
@@ -483,31 +496,6 @@ def run_ours(args, ws, rank, local):
         out["cpu_baseline"] = cpu_baseline(g, b)
     P.close()
     return out
-
-
-def P_ops(P) -> int:
-    """Kernels in one cycle of the static schedule (as the library generates it)."""
-    import math as m
-    lv = P.info
-    cnt = [0]
-    jv = {}
-
-    def visit(l, first):
-        L = lv[l]
-        if L["kind"] == "coarsest":
-            cnt[0] += 1
-            return
-        if L["kind"] == "elim":
-            cnt[0] += 2
-            visit(l + 1, first)
-            return
-        cnt[0] += L["ncol"] * 3 + 3   # pre sweep (first colour fused), resid, restrict, prolong, post
-        j = jv.get(l, 0); jv[l] = j + 1
-        nv = m.floor((j + 1) * L["gamma"]) - m.floor(j * L["gamma"])
-        for i in range(nv):
-            visit(l + 1, i == 0)
-    visit(0, True)
-    return cnt[0]
 
 
 def run_reference(args, ws, rank):

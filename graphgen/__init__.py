@@ -124,6 +124,30 @@ def grid2d_random(nx: int, ny: int, seed: int, wlo: float = 0.5, whi: float = 1.
     return from_edges(g.n, lo[keep], hi[keep], w, f"grid2d_{nx}x{ny}_rand")
 
 
+def grid_with_hubs(nx: int, ny: int, hubs: int, deg: int, seed: int = 1) -> Graph:
+    """A 2D 5-point grid (weights U(0.5, 1.5]) plus `hubs` extra nodes, each joined to `deg`
+    distinct random grid nodes (weights U(0.5, 1.5]) and to the previous hub: a mesh with a
+    few rows far longer than the rest, as power-law graphs have."""
+    rng = np.random.default_rng(seed)
+    g0 = grid2d_random(nx, ny, seed)
+    ng = nx * ny
+    n = ng + hubs
+    r = np.repeat(np.arange(ng), np.diff(g0.rp))
+    m = r < g0.ci
+    us, vs, ws = [r[m]], [g0.ci[m].astype(np.int64)], [g0.w[m]]
+    for h in range(hubs):
+        nb = rng.choice(ng, size=deg, replace=False)
+        us.append(np.full(deg, ng + h))
+        vs.append(nb)
+        ws.append(rng.uniform(0.5, 1.5, deg))
+        if h:
+            us.append(np.array([ng + h]))
+            vs.append(np.array([ng + h - 1]))
+            ws.append(np.array([1.0]))
+    return from_edges(n, np.concatenate(us), np.concatenate(vs), np.concatenate(ws),
+                      f"grid_hubs{nx}x{ny}_{hubs}x{deg}")
+
+
 def path(n: int, w=None) -> Graph:
     u = np.arange(n - 1); v = u + 1
     w = np.ones(n - 1) if w is None else np.asarray(w, dtype=np.float64)

@@ -79,7 +79,24 @@ typedef struct lamg_options {
     int32_t device;        /* CUDA device ordinal */
     int32_t tail_rows;     /* levels with at most this many rows run inside one CTA of the
                               persistent solve kernel (no grid barrier per step): 8192 */
-    int32_t reserved[6];
+    int32_t cluster_rows;  /* graph path: a visit of the first level from which on every level
+                              has at most this many rows, with all its sub-visits, runs as one
+                              launch of a thread-block cluster. 0 (default): chosen at setup by
+                              timing one cycle of each candidate and of the per-step schedule;
+                              < 0: every step is its own kernel. Results are bit-identical
+                              whatever the choice. */
+    int32_t row_tpr;       /* lanes per CSR row in the operator kernels: 0 (default) picks per
+                              level from the mean row length; 1, 2, 4, ..., 32 forces it */
+    int32_t sell;          /* operator kernels: 0 (default) one thread per row on a sliced
+                              ELLPACK copy (32-row slices) where rows have at most 64 entries and
+                              padding adds at most 30%, else lane groups on CSR; 1 sliced ELLPACK
+                              wherever rows have at most 64 entries; -1 CSR only */
+    int32_t autotune;      /* 1 (default): setup times the kernel form of each level's sweep
+                              and residual (lanes per row, or one thread per row) and, with
+                              cluster_rows = 0, the cluster schedule; 0: rules only */
+    int32_t dense_rows;    /* a level with at most this many nodes (<= 4096) and at least n^2/8
+                              off-diagonal entries is the coarsest, solved densely: 4096; 0 off */
+    int32_t reserved[1];
 } lamg_options;
 
 typedef struct lamg_graph {
@@ -241,6 +258,25 @@ int lamg_profile_cycle(lamg_hier *h, int64_t *out, int64_t cap, int64_t *count);
  * to query *count. Errors: INVALID. */
 int lamg_op_list(const lamg_hier *h, int32_t *out, int64_t cap, int64_t *count);
 
+/* The launch schedule of the graph path (no counterpart in the paper: it records how the
+ * cycle of Section 2 is mapped onto kernel launches). out[0] = first level of the cluster
+ * sub-cycle (-1: none), out[1] = CTAs per cluster (0: cluster launch unavailable), out[2] =
+ * kernel launches of one cycle, out[3] = steps of one cycle, out[4] = levels L, then per
+ * level the kernel form of the sweep and of the residual-type passes (0: one thread per row
+ * on the sliced copy, t > 0: t lanes per CSR row), then for each schedule timed by the
+ * automatic choice a pair (first cluster level or -1, nanoseconds per cycle). cap >= 5 + 2 L
+ * int64 entries; *count = entries written. Errors: INVALID. */
+int lamg_schedule_info(const lamg_hier *h, int64_t *out, int64_t cap, int64_t *count);
+
+/* Per-step device time of one cycle (r = 0) with the steps on levels >= from_level run as
+ * cluster launches (from_level < 0: none), outside any graph: out receives 3 int64 per step
+ * (step index, 1 if the step ran inside a cluster launch, nanoseconds). A step inside a
+ * cluster is timed by %globaltimer in its first CTA, from before the step to after the
+ * barrier that ends it; any other step by CUDA events around its own launch (no overlap with
+ * its neighbours). cap >= 3 x steps. No counterpart in the paper. Errors: INVALID (cap, or
+ * no cluster launch on this device), CUDA, TIMEOUT. */
+int lamg_profile_schedule(lamg_hier *h, int32_t from_level, int64_t *out, int64_t cap, int64_t *count);
+
 /* Name of an error code. */
 const char *lamg_strerror(int code);
 
@@ -273,7 +309,8 @@ typedef struct lamg_ticket_info {
 } lamg_ticket_info;
 
 /* Create a server on device so->device with the given setup options (NULL: defaults), one
- * executor thread and so->setup_threads setup threads. Errors: INVALID, NO_DEVICE. */
+ * executor thread and so->setup_threads setup threads. A served setup runs no timing trials:
+ * autotune is taken as 0 and cluster_rows = 0 as -1. Errors: INVALID, NO_DEVICE. */
 int lamg_server_create(const lamg_server_opts *so, const lamg_options *opt, lamg_server **out);
 /* Submit one request (graph + right-hand side, copied; same conventions as lamg_setup and
  * lamg_solve); returns at once with a ticket. A request whose estimated device memory alone

@@ -39,7 +39,7 @@ class Options(C.Structure):
                 ("seed", C.c_uint64), ("Q", C.c_double), ("tau_soc", C.c_double),
                 ("elim_min_frac", C.c_double), ("snap", C.c_double), ("guard_eps", C.c_double),
                 ("gamma_fixed", C.c_double), ("device", C.c_int32), ("tail_rows", C.c_int32),
-                ("reserved", C.c_int32 * 6)]
+                ("cluster_rows", C.c_int32), ("row_tpr", C.c_int32), ("sell", C.c_int32), ("autotune", C.c_int32), ("dense_rows", C.c_int32), ("reserved", C.c_int32 * 1)]
 
 
 class Graph(C.Structure):
@@ -115,6 +115,8 @@ def lib():
         L.lamg_server_destroy.argtypes = [P]
         L.lamg_server_destroy.restype = None
         L.lamg_op_list.argtypes = [P, P, C.c_int64, C.POINTER(C.c_int64)]
+        L.lamg_schedule_info.argtypes = [P, P, C.c_int64, C.POINTER(C.c_int64)]
+        L.lamg_profile_schedule.argtypes = [P, C.c_int32, P, C.c_int64, C.POINTER(C.c_int64)]
         _lib = L
     return _lib
 
@@ -263,6 +265,30 @@ class Hierarchy:
         out = np.zeros(3 * cnt.value, np.int32)
         lib().lamg_op_list(self._h, _p(out), cnt.value, C.byref(cnt))
         return [(self.OP_KINDS[k], int(l), int(c)) for k, l, c in out.reshape(-1, 3)]
+
+    def schedule(self) -> dict:
+        """Launch schedule of the graph path: first level of the cluster sub-cycle (-1: none),
+        CTAs per cluster, kernels and steps per cycle, and the cycle times of the schedules
+        the automatic choice compared."""
+        out = np.zeros(5 + 2 * 128 + 2 * 16, np.int64)
+        cnt = C.c_int64()
+        _check(lib().lamg_schedule_info(self._h, _p(out), out.size, C.byref(cnt)), "lamg_schedule_info")
+        nl = int(out[4])
+        forms = [(int(out[5 + 2 * l]), int(out[6 + 2 * l])) for l in range(nl)]
+        k0 = 5 + 2 * nl
+        tuned = [(int(out[k]), out[k + 1] / 1e6) for k in range(k0, cnt.value, 2)]
+        return {"cluster_from": int(out[0]), "cluster_ctas": int(out[1]), "launches_per_cycle": int(out[2]),
+                "steps_per_cycle": int(out[3]), "forms": forms, "tuned_ms": tuned}
+
+    def profile_schedule(self, from_level: int) -> list:
+        """[(step, in_cluster, ns)] for one cycle with the steps on levels >= from_level run
+        as cluster launches (from_level < 0: one kernel per step)."""
+        cnt = C.c_int64()
+        nops = len(self.op_list())
+        out = np.zeros(3 * nops, np.int64)
+        _check(lib().lamg_profile_schedule(self._h, from_level, _p(out), out.size, C.byref(cnt)),
+               "lamg_profile_schedule")
+        return [(int(a), bool(b), int(c)) for a, b, c in out.reshape(-1, 3)]
 
     def profile_cycle(self) -> list:
         """[(first step index after the barrier, ns)] for one cycle of the persistent kernel."""

@@ -116,37 +116,91 @@ __device__ __forceinline__ T rowsum_k(int e0, int e1, int k, int j, const int32_
     return s;
 }
 
-// Gauss-Seidel on one colour class [r0, r1), all k columns (Section 2).
-template <typename T, int KL, int TPR>
-__global__ void __launch_bounds__(BBS) bk_gs(int r0, int r1, int k, const int32_t *__restrict__ rp,
-                                             const int32_t *__restrict__ ci, const T *__restrict__ val,
-                                             const T *__restrict__ diag, const T *__restrict__ b, T *x) {
-    b_trigger();
-    const Lanes<KL, TPR> L;
-    const int row = r0 + L.row_in_grid;
-    const bool ok = row < r1;
-    const int e0 = ok ? rp[row] + L.sub : 0, e1 = ok ? rp[row + 1] : 0;
-    const T d = ok ? diag[row] : T(1);
-    b_wait();
-    const T s = rowsum_k<T, KL, TPR>(e0, e1, k, L.j, ci, val, x);
-    if (ok && L.sub == 0 && L.j < k) x[(size_t)row * k + L.j] = (b[(size_t)row * k + L.j] - s) / d;
+// A row longer than LONG_ROW entries, all k columns, summed by the whole block: column
+// j = threadIdx.x % KL, entry lane m = threadIdx.x / KL taking entries e0 + m, e0 + m + BBS/KL,
+// ...; the lanes of one column are combined by a shuffle tree inside each warp, then the warps
+// in order. Column j's total is returned in thread j (j < KL).
+template <typename T, int KL>
+__device__ __forceinline__ T block_row_k(int e0, int e1, int k, const int32_t *__restrict__ ci,
+                                         const T *__restrict__ val, const T *x) {
+    __shared__ T sh[BBS / 32][32];
+    constexpr int M = BBS / KL;
+    const int j = threadIdx.x % KL, m = threadIdx.x / KL;
+    T s = T(0);
+    if (j < k)
+        for (int e = e0 + m; e < e1; e += M) s += val[e] * x[(size_t)ci[e] * k + j];
+#pragma unroll
+    for (int o = KL; o < 32; o <<= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane < KL) sh[w][lane] = s;
+    __syncthreads();
+    T t = T(0);
+    if (threadIdx.x < KL)
+        for (int q = 0; q < BBS / 32; q++) t += sh[q][threadIdx.x];
+    __syncthreads();
+    return t;
 }
 
+// Gauss-Seidel on one colour class [r0, r1), all k columns (Section 2). The class's first nl
+// rows are long (rows are sorted longest first inside a class): block b < nl takes row r0 + b.
+template <typename T, int KL, int TPR>
+__global__ void __launch_bounds__(BBS) bk_gs(int r0, int r1, int nl, int k, const int32_t *__restrict__ rp,
+                                             const int32_t *__restrict__ ci, const T *__restrict__ val,
+                                             const T *__restrict__ idiag, const T *__restrict__ b, T *x) {
+    b_trigger();
+    if ((int)blockIdx.x < nl) {
+        const int row = r0 + (int)blockIdx.x;
+        const int e0 = rp[row], e1 = rp[row + 1];
+        const T id = idiag[row];
+        b_wait();
+        const T s = block_row_k<T, KL>(e0, e1, k, ci, val, x);
+        if ((int)threadIdx.x < k) x[(size_t)row * k + threadIdx.x] = (b[(size_t)row * k + threadIdx.x] - s) * id;
+        return;
+    }
+    const int t = (blockIdx.x - nl) * BBS + threadIdx.x;
+    constexpr int G = KL * TPR;
+    const int lig = t % G, j = lig % KL, sub = lig / KL;
+    const int row = r0 + nl + t / G;
+    const bool ok = row < r1;
+    const int e0 = ok ? rp[row] + sub : 0, e1 = ok ? rp[row + 1] : 0;
+    const T id = ok ? idiag[row] : T(1);
+    b_wait();
+    const T s = rowsum_k<T, KL, TPR>(e0, e1, k, j, ci, val, x);
+    if (ok && sub == 0 && j < k) x[(size_t)row * k + j] = (b[(size_t)row * k + j] - s) * id;
+}
+
+// r = b - A x, all k columns; blocks b < nl take the long rows lr[b], the lane groups skip them.
 template <typename T, int KL, int TPR>
 __global__ void __launch_bounds__(BBS) bk_resid(int n, int k, const int32_t *__restrict__ rp,
                                                 const int32_t *__restrict__ ci, const T *__restrict__ val,
                                                 const T *__restrict__ diag, const T *__restrict__ x,
-                                                const T *__restrict__ b, T *r) {
+                                                const T *__restrict__ b, T *r, const int32_t *__restrict__ lr,
+                                                int nl) {
     b_trigger();
-    const Lanes<KL, TPR> L;
-    const int row = L.row_in_grid;
-    const bool ok = row < n;
-    const int e0 = ok ? rp[row] + L.sub : 0, e1 = ok ? rp[row + 1] : 0;
+    if ((int)blockIdx.x < nl) {
+        const int row = lr[blockIdx.x];
+        const int e0 = rp[row], e1 = rp[row + 1];
+        const T d = diag[row];
+        b_wait();
+        const T s = block_row_k<T, KL>(e0, e1, k, ci, val, x);
+        if ((int)threadIdx.x < k) {
+            const size_t i = (size_t)row * k + threadIdx.x;
+            r[i] = b[i] - (d * x[i] + s);
+        }
+        return;
+    }
+    const int t = (blockIdx.x - nl) * BBS + threadIdx.x;
+    constexpr int G = KL * TPR;
+    const int lig = t % G, j = lig % KL, sub = lig / KL;
+    const int row = t / G;
+    bool ok = row < n;
+    int e0 = ok ? rp[row] + sub : 0, e1 = ok ? rp[row + 1] : 0;
+    if (ok && e1 - (e0 - sub) > LONG_ROW) { ok = false; e0 = e1; }
     const T d = ok ? diag[row] : T(0);
     b_wait();
-    const T s = rowsum_k<T, KL, TPR>(e0, e1, k, L.j, ci, val, x);
-    if (ok && L.sub == 0 && L.j < k) {
-        const size_t i = (size_t)row * k + L.j;
+    const T s = rowsum_k<T, KL, TPR>(e0, e1, k, j, ci, val, x);
+    if (ok && sub == 0 && j < k) {
+        const size_t i = (size_t)row * k + j;
         r[i] = b[i] - (d * x[i] + s);
     }
 }
@@ -175,15 +229,15 @@ __device__ __forceinline__ void elem_pos(int &i, int &j) {
 }
 
 template <typename T, int KL>
-__global__ void bk_gs_first(int n, int c1, int k, const T *__restrict__ diag, const T *__restrict__ b, T *x) {
+__global__ void bk_gs_first(int n, int c1, int k, const T *__restrict__ idiag, const T *__restrict__ b, T *x) {
     b_trigger();
     int i, j;
     elem_pos<KL>(i, j);
-    const T d = (i < c1) ? diag[i] : T(1);
+    const T id = (i < c1) ? idiag[i] : T(1);
     b_wait();
     if (i >= n || j >= k) return;
     const size_t e = (size_t)i * k + j;
-    x[e] = i < c1 ? b[e] / d : T(0);
+    x[e] = i < c1 ? b[e] * id : T(0);
 }
 
 template <typename T>
@@ -363,7 +417,7 @@ template <int KL, int TPR>
 __global__ void __launch_bounds__(BBS) bk_spmv_dot(int n, int k, const int32_t *__restrict__ rp,
                                                    const int32_t *__restrict__ ci, const double *__restrict__ val,
                                                    const double *__restrict__ diag, const double *__restrict__ p,
-                                                   double *q, const BRed R) {
+                                                   double *q, const BRed R, const int32_t *__restrict__ lr, int nl) {
     b_trigger();
     b_wait();
     constexpr int G = KL * TPR;
@@ -372,10 +426,21 @@ __global__ void __launch_bounds__(BBS) bk_spmv_dot(int n, int k, const int32_t *
     const int groups = gridDim.x * (BBS / G);
     const int rounds = (n + groups - 1) / groups;
     double pq[1] = {0.0};
+    for (int lt = blockIdx.x; lt < nl; lt += gridDim.x) {
+        const int row = lr[lt];
+        const double s = block_row_k<double, KL>(rp[row], rp[row + 1], k, ci, val, p);
+        if ((int)threadIdx.x < k) {
+            const size_t e = (size_t)row * k + threadIdx.x;
+            const double qi = diag[row] * p[e] + s;
+            q[e] = qi;
+            pq[0] += p[e] * qi;
+        }
+    }
     int row = t / G;
     for (int it = 0; it < rounds; it++, row += groups) {
-        const bool ok = row < n;
-        const int e0 = ok ? rp[row] + sub : 0, e1 = ok ? rp[row + 1] : 0;
+        bool ok = row < n;
+        int e0 = ok ? rp[row] + sub : 0, e1 = ok ? rp[row + 1] : 0;
+        if (ok && e1 - (e0 - sub) > LONG_ROW) { ok = false; e0 = e1; }
         const double s = rowsum_k<double, KL, TPR>(e0, e1, k, j, ci, val, p);
         if (ok && sub == 0 && j < k) {
             const size_t e = (size_t)row * k + j;
@@ -465,7 +530,8 @@ template <int KL, int TPR>
 __global__ void __launch_bounds__(BBS) bk_true_resid(int n, int k, const int32_t *__restrict__ rp,
                                                      const int32_t *__restrict__ ci, const double *__restrict__ val,
                                                      const double *__restrict__ diag, const double *__restrict__ x,
-                                                     const double *__restrict__ b, const BRed R) {
+                                                     const double *__restrict__ b, const BRed R,
+                                                     const int32_t *__restrict__ lr, int nl) {
     b_trigger();
     b_wait();
     constexpr int G = KL * TPR;
@@ -474,10 +540,20 @@ __global__ void __launch_bounds__(BBS) bk_true_resid(int n, int k, const int32_t
     const int groups = gridDim.x * (BBS / G);
     const int rounds = (n + groups - 1) / groups;
     double acc[1] = {0.0};
+    for (int lt = blockIdx.x; lt < nl; lt += gridDim.x) {
+        const int row = lr[lt];
+        const double s = block_row_k<double, KL>(rp[row], rp[row + 1], k, ci, val, x);
+        if ((int)threadIdx.x < k) {
+            const size_t e = (size_t)row * k + threadIdx.x;
+            const double ri = b[e] - (diag[row] * x[e] + s);
+            acc[0] += ri * ri;
+        }
+    }
     int row = t / G;
     for (int it = 0; it < rounds; it++, row += groups) {
-        const bool ok = row < n;
-        const int e0 = ok ? rp[row] + sub : 0, e1 = ok ? rp[row + 1] : 0;
+        bool ok = row < n;
+        int e0 = ok ? rp[row] + sub : 0, e1 = ok ? rp[row + 1] : 0;
+        if (ok && e1 - (e0 - sub) > LONG_ROW) { ok = false; e0 = e1; }
         const double s = rowsum_k<double, KL, TPR>(e0, e1, k, j, ci, val, x);
         if (ok && sub == 0 && j < k) {
             const size_t e = (size_t)row * k + j;
@@ -549,8 +625,10 @@ static int row_tpr(int KL, int level_tpr) {
 
 struct BLev {
     int kind = 0, ncol = 0, tpr = 1, pt_tpr = 1;
-    int64_t n = 0, nc = 0, nF = 0;
-    std::vector<int64_t> cptr;
+    int64_t n = 0, nc = 0, nF = 0, nlong = 0;
+    std::vector<int64_t> cptr, lptr;
+    const int32_t *lrows = nullptr;
+    const void *idiag = nullptr;
     const int32_t *rp = nullptr, *ci = nullptr, *agg = nullptr, *agg2 = nullptr, *pt_ptr = nullptr,
                   *pt_row = nullptr, *pf_col = nullptr, *pft_ptr = nullptr, *pft_f = nullptr;
     const void *val = nullptr, *diag = nullptr, *wt = nullptr, *pt_w = nullptr, *pf_val = nullptr,
@@ -603,6 +681,7 @@ static int build_ctx(lamg_hier *h, BatchCtx *c) {
         BLev &B = c->lv[l];
         B.kind = D.kind; B.ncol = D.ncol; B.tpr = D.tpr; B.pt_tpr = D.pt_tpr;
         B.n = D.n; B.nc = D.nc; B.nF = D.nF; B.cptr = D.cptr;
+        B.nlong = D.nlong; B.lptr = D.lptr; B.lrows = D.lrows;
         B.rp = D.rp; B.ci = D.ci; B.agg = D.agg; B.agg2 = D.agg2; B.pt_ptr = D.pt_ptr; B.pt_row = D.pt_row;
         B.pf_col = D.pf_col; B.pft_ptr = D.pft_ptr; B.pft_f = D.pft_f; B.pinv = D.pinv;
         const int64_t pte = (D.kind == KIND_AGG) ? (int64_t)h->host[l].A.n * 2 : 0;
@@ -618,6 +697,7 @@ static int build_ctx(lamg_hier *h, BatchCtx *c) {
             CKR(cudaStreamSynchronize(h->stream));
         }
         if ((rc = typed_copy<T>(h, D.val, D.nnz, &B.val)) || (rc = typed_copy<T>(h, D.diag, D.n, &B.diag)) ||
+            (rc = typed_copy<T>(h, D.idiag, D.n, &B.idiag)) ||
             (rc = typed_copy<T>(h, D.wt, D.kind == KIND_AGG ? D.n : 0, &B.wt)) ||
             (rc = typed_copy<T>(h, D.pt_w, ent, &B.pt_w)) ||
             (rc = typed_copy<T>(h, D.pf_val, D.kind == KIND_ELIM ? 4 * D.nF : 0, &B.pf_val)) ||
@@ -675,11 +755,11 @@ template <typename T>
 static void bop(const Op &op, BatchCtx *c, cudaStream_t s) {
     BLev &L = c->lv[op.level];
     const int n = (int)L.n, k = c->k, KL = c->KL;
-    const T *val = (const T *)L.val, *diag = (const T *)L.diag;
+    const T *val = (const T *)L.val, *diag = (const T *)L.diag, *idiag = (const T *)L.idiag;
     T *x = (T *)L.x, *b = (T *)L.b, *r = (T *)L.r;
     switch (op.kind) {
         case OP_GS_FIRST:
-#define C1(KLv, ...) case KLv: blaunch(bk_gs_first<T, KLv>, nblocks((int64_t)n * KLv), s, n, (int)L.cptr[1], k, diag, (const T *)b, x); break;
+#define C1(KLv, ...) case KLv: blaunch(bk_gs_first<T, KLv>, nblocks((int64_t)n * KLv), s, n, (int)L.cptr[1], k, idiag, (const T *)b, x); break;
             switch (KL) { K_CASES(C1) }
 #undef C1
             break;
@@ -690,14 +770,15 @@ static void bop(const Op &op, BatchCtx *c, cudaStream_t s) {
             const int r0 = (int)L.cptr[op.colour], r1 = (int)L.cptr[op.colour + 1];
             if (r1 <= r0) break;
             const int tpr = row_tpr(KL, L.tpr);
-#define C2(KLv, TPRv, ...) case KT_CODE(KLv, TPRv): blaunch(bk_gs<T, KLv, TPRv>, nblocks((int64_t)(r1 - r0) * KLv * TPRv), s, r0, r1, k, L.rp, L.ci, val, diag, (const T *)b, x); break;
+            const int nl = L.nlong ? (int)(L.lptr[op.colour + 1] - L.lptr[op.colour]) : 0;
+#define C2(KLv, TPRv, ...) case KT_CODE(KLv, TPRv): blaunch(bk_gs<T, KLv, TPRv>, nl + nblocks((int64_t)(r1 - r0 - nl) * KLv * TPRv), s, r0, r1, nl, k, L.rp, L.ci, val, idiag, (const T *)b, x); break;
             switch (KT_CODE(KL, tpr)) { KT_CASES(C2) }
 #undef C2
             break;
         }
         case OP_RESID: {
             const int tpr = row_tpr(KL, L.tpr);
-#define C3(KLv, TPRv, ...) case KT_CODE(KLv, TPRv): blaunch(bk_resid<T, KLv, TPRv>, nblocks((int64_t)n * KLv * TPRv), s, n, k, L.rp, L.ci, val, diag, (const T *)x, (const T *)b, r); break;
+#define C3(KLv, TPRv, ...) case KT_CODE(KLv, TPRv): blaunch(bk_resid<T, KLv, TPRv>, L.nlong + nblocks((int64_t)n * KLv * TPRv), s, n, k, L.rp, L.ci, val, diag, (const T *)x, (const T *)b, r, L.lrows, (int)L.nlong); break;
             switch (KT_CODE(KL, tpr)) { KT_CASES(C3) }
 #undef C3
             break;
@@ -756,7 +837,7 @@ static void cg_spmv_dot(lamg_hier *h, BatchCtx *c, cudaStream_t s) {
     const DevLevel &F = h->dev[0];
     const int n = (int)F.n, k = c->k;
     const int tpr = row_tpr(c->KL, F.tpr);
-#define C9(KLv, TPRv, ...) case KT_CODE(KLv, TPRv): blaunch(bk_spmv_dot<KLv, TPRv>, rblocks((int64_t)n * KLv * TPRv), s, n, k, F.rp, F.ci, (const double *)F.val, (const double *)F.diag, (const double *)c->p, c->q, c->red); break;
+#define C9(KLv, TPRv, ...) case KT_CODE(KLv, TPRv): blaunch(bk_spmv_dot<KLv, TPRv>, rblocks((int64_t)n * KLv * TPRv), s, n, k, F.rp, F.ci, (const double *)F.val, (const double *)F.diag, (const double *)c->p, c->q, c->red, (const int32_t *)F.lrows, (int)F.nlong); break;
     switch (KT_CODE(c->KL, tpr)) { KT_CASES(C9) }
 #undef C9
 }
@@ -765,7 +846,7 @@ static void cg_true_resid(lamg_hier *h, BatchCtx *c, cudaStream_t s) {
     const DevLevel &F = h->dev[0];
     const int n = (int)F.n, k = c->k;
     const int tpr = row_tpr(c->KL, F.tpr);
-#define C10(KLv, TPRv, ...) case KT_CODE(KLv, TPRv): blaunch(bk_true_resid<KLv, TPRv>, rblocks((int64_t)n * KLv * TPRv), s, n, k, F.rp, F.ci, (const double *)F.val, (const double *)F.diag, (const double *)c->xs, (const double *)c->bkeep, c->red); break;
+#define C10(KLv, TPRv, ...) case KT_CODE(KLv, TPRv): blaunch(bk_true_resid<KLv, TPRv>, rblocks((int64_t)n * KLv * TPRv), s, n, k, F.rp, F.ci, (const double *)F.val, (const double *)F.diag, (const double *)c->xs, (const double *)c->bkeep, c->red, (const int32_t *)F.lrows, (int)F.nlong); break;
     switch (KT_CODE(c->KL, tpr)) { KT_CASES(C10) }
 #undef C10
 }

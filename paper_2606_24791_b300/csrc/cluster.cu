@@ -1,0 +1,337 @@
+// Cluster sub-cycle kernel: every step of one visit of a small level, and of all the levels
+// below it (the recursion of Section 2 with its gamma visits, elimination transfers of Eq. 2
+// and the dense coarsest solve), in one launch of a single thread-block cluster.
+//
+// On the coarse levels a cycle step moves kilobytes, so run as separate kernels each step
+// costs a launch and a chain of dependent loads whatever its size. Here the steps are
+// separated by the cluster's hardware barrier (barrier.cluster with release/acquire
+// semantics) instead of kernel boundaries: up to 16 CTAs of 1024 threads, one row per lane
+// group, walk the step list held in shared memory.
+//
+// Results are bit-identical to the per-step kernels: every row, aggregate and dense row is
+// summed by the same number of lanes in the same order, with the same shuffle tree.
+// Vectors written during the launch (iterates, right-hand sides, residuals) are read through
+// L2 (ld.global.cg), so no CTA reads a stale line from its own L1 after another CTA wrote it.
+// The barrier is a hardware barrier reached by every thread the same number of times (the
+// step loop is uniform), so there is no software spin-wait to bound.
+#include <cuda_runtime.h>
+
+#include "device.h"
+#include "kernels_common.cuh"
+
+namespace lamg {
+
+constexpr int CBS = 1024;
+
+__device__ __forceinline__ void cl_sync() {
+    asm volatile(
+        "barrier.cluster.arrive.release.aligned;\n\t"
+        "barrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ unsigned cl_rank() {
+    unsigned r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+
+__device__ __forceinline__ unsigned cl_size() {
+    unsigned r;
+    asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(r));
+    return r;
+}
+
+struct CPos {
+    int tid, nthreads, lane, warp, nwarps;
+};
+
+// Sum over a CSR row by TPR lanes (entries e0, e0 + TPR, ...), x read through L2.
+template <int TPR>
+__device__ __forceinline__ double cl_row(int e0, int e1, const int32_t *__restrict__ ci,
+                                         const double *__restrict__ val, const double *x) {
+    double s = 0.0;
+    for (int e = e0; e < e1; e += TPR) s += __ldg(&val[e]) * __ldcg(&x[__ldg(&ci[e])]);
+#pragma unroll
+    for (int o = TPR / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    return s;
+}
+
+// One colour class of Gauss-Seidel: x_u = (b_u - sum_v A_uv x_v) / A_uu, u in [r0, r1).
+template <int TPR>
+__device__ __forceinline__ void cl_gs(const PLevel &L, int r0, int r1, const CPos &p) {
+    const int groups = p.nthreads / TPR, sub = p.tid % TPR;
+    const int rounds = (r1 - r0 + groups - 1) / groups;
+    int row = r0 + p.tid / TPR;
+    for (int it = 0; it < rounds; it++, row += groups) {
+        const bool ok = row < r1;
+        const int e0 = ok ? __ldg(&L.rp[row]) + sub : 0, e1 = ok ? __ldg(&L.rp[row + 1]) : 0;
+        const double s = cl_row<TPR>(e0, e1, L.ci, L.val, L.x);
+        if (ok && sub == 0) L.x[row] = (__ldcg(&L.b[row]) - s) * __ldg(&L.idiag[row]);
+    }
+}
+
+// Sliced-ELLPACK row sum, entries in order (as the per-step kernels sum them).
+__device__ __forceinline__ double cl_sell_row(const PLevel &L, int row, const double *x) {
+    const int s = row >> 5;
+    const int a = __ldg(&L.sl_ptr[s]), w = (__ldg(&L.sl_ptr[s + 1]) - a) >> 5;
+    const int e = a + (row & 31);
+    double acc = 0.0;
+    for (int j = 0; j < w; j++) acc += __ldg(&L.sl_val[e + 32 * j]) * __ldcg(&x[__ldg(&L.sl_col[e + 32 * j])]);
+    return acc;
+}
+
+// Slices are dealt to the cluster's warps round-robin over the CTAs, so a small class spreads
+// over all of the cluster's SMs (their few FP64 units are the limit, not the loads).
+__device__ __forceinline__ int cl_slice_warp(const CPos &p) {
+    return (int)((threadIdx.x >> 5) * cl_size() + cl_rank());
+}
+
+__device__ __forceinline__ void cl_gs_sell(const PLevel &L, int r0, int r1, const CPos &p) {
+    const int s0 = r0 >> 5, s1 = (r1 + 31) >> 5;
+    for (int sl = s0 + cl_slice_warp(p); sl < s1; sl += p.nwarps) {
+        const int row = 32 * sl + p.lane;
+        if (row < r0 || row >= r1) continue;
+        const double s = cl_sell_row(L, row, L.x);
+        L.x[row] = (__ldcg(&L.b[row]) - s) * __ldg(&L.idiag[row]);
+    }
+}
+
+__device__ __forceinline__ void cl_resid_sell(const PLevel &L, const CPos &p) {
+    const int ns = (L.n + 31) >> 5;
+    for (int sl = cl_slice_warp(p); sl < ns; sl += p.nwarps) {
+        const int row = 32 * sl + p.lane;
+        if (row >= L.n) continue;
+        const double s = cl_sell_row(L, row, L.x);
+        L.r[row] = __ldcg(&L.b[row]) - (__ldg(&L.diag[row]) * __ldcg(&L.x[row]) + s);
+    }
+}
+
+// r = b - A x
+template <int TPR>
+__device__ __forceinline__ void cl_resid(const PLevel &L, const CPos &p) {
+    const int groups = p.nthreads / TPR, sub = p.tid % TPR;
+    const int rounds = (L.n + groups - 1) / groups;
+    int row = p.tid / TPR;
+    for (int it = 0; it < rounds; it++, row += groups) {
+        const bool ok = row < L.n;
+        const int e0 = ok ? __ldg(&L.rp[row]) + sub : 0, e1 = ok ? __ldg(&L.rp[row + 1]) : 0;
+        const double s = cl_row<TPR>(e0, e1, L.ci, L.val, L.x);
+        if (ok && sub == 0) L.r[row] = __ldcg(&L.b[row]) - (__ldg(&L.diag[row]) * __ldcg(&L.x[row]) + s);
+    }
+}
+
+// b^c = P^T r: one P^T row (aggregate) per TPR lanes.
+template <int TPR>
+__device__ __forceinline__ void cl_restrict(const PLevel &L, double *bc, const CPos &p) {
+    const int groups = p.nthreads / TPR, sub = p.tid % TPR;
+    const int rounds = (L.nc + groups - 1) / groups;
+    int a = p.tid / TPR;
+    for (int it = 0; it < rounds; it++, a += groups) {
+        const bool ok = a < L.nc;
+        const int e0 = ok ? __ldg(&L.pt_ptr[a]) + sub : 0, e1 = ok ? __ldg(&L.pt_ptr[a + 1]) : 0;
+        const double s = cl_row<TPR>(e0, e1, L.pt_row, L.pt_w, L.r);
+        if (ok && sub == 0) bc[a] = s;
+    }
+}
+
+#define CL_TPR(tpr, FN, ...)                 \
+    switch (tpr) {                           \
+        case 1: FN<1>(__VA_ARGS__); break;   \
+        case 2: FN<2>(__VA_ARGS__); break;   \
+        case 4: FN<4>(__VA_ARGS__); break;   \
+        case 8: FN<8>(__VA_ARGS__); break;   \
+        case 16: FN<16>(__VA_ARGS__); break; \
+        default: FN<32>(__VA_ARGS__); break; \
+    }
+
+__device__ __forceinline__ void cl_op(const Op &op, const PLevel *lv, const int32_t *cptr_all, const CPos &p) {
+    const PLevel &L = lv[op.level];
+    const int32_t *cptr = cptr_all + L.cptr_off;
+    switch (op.kind) {
+        case OP_GS_FIRST: {
+            const int c1 = cptr[1];
+            for (int i = p.tid; i < L.n; i += p.nthreads)
+                L.x[i] = i < c1 ? __ldcg(&L.b[i]) * __ldg(&L.idiag[i]) : 0.0;
+            break;
+        }
+        case OP_ZERO:
+            for (int i = p.tid; i < L.n; i += p.nthreads) L.x[i] = 0.0;
+            break;
+        case OP_GS:
+            if (L.gs_tpr == 0) cl_gs_sell(L, cptr[op.colour], cptr[op.colour + 1], p);
+            else CL_TPR(L.gs_tpr, cl_gs, L, cptr[op.colour], cptr[op.colour + 1], p);
+            break;
+        case OP_RESID:
+            if (L.rs_tpr == 0) cl_resid_sell(L, p);
+            else CL_TPR(L.rs_tpr, cl_resid, L, p);
+            break;
+        case OP_RESTRICT:
+            CL_TPR(L.pt_tpr, cl_restrict, L, lv[op.level + 1].b, p);
+            break;
+        case OP_PROLONG: {
+            const double *xc = lv[op.level + 1].x;
+            for (int u = p.tid; u < L.n; u += p.nthreads) {
+                const int a = __ldg(&L.agg[u]), bb = __ldg(&L.agg2[u]);
+                double s;
+                if (bb < 0) {
+                    s = __ldcg(&xc[a]);
+                } else {
+                    const double w = __ldg(&L.wt[u]);
+                    s = (1.0 - w) * __ldcg(&xc[bb]);
+                    if (w != 0.0) s = w * __ldcg(&xc[a]) + s;
+                }
+                L.x[u] = __ldcg(&L.x[u]) + s;
+            }
+            break;
+        }
+        case OP_ELIM_RESTRICT: {
+            double *bc = lv[op.level + 1].b;
+            const double *bF = L.b + L.nc;
+            for (int i = p.tid; i < L.nc; i += p.nthreads) {
+                const int e0 = __ldg(&L.pft_ptr[i]), e1 = __ldg(&L.pft_ptr[i + 1]);
+                double s = __ldcg(&L.b[i]);
+                for (int e = e0; e < e1; e++) s += __ldg(&L.pft_val[e]) * __ldcg(&bF[__ldg(&L.pft_f[e])]);
+                bc[i] = s;
+            }
+            break;
+        }
+        case OP_ELIM_INTERP:
+            for (int t = p.tid; t < L.nF; t += p.nthreads) {
+                double s = 0.0;
+#pragma unroll
+                for (int j = 0; j < 4; j++) {
+                    const int c = __ldg(&L.pf_col[4 * t + j]);
+                    if (c >= 0) s += __ldg(&L.pf_val[4 * t + j]) * __ldcg(&L.x[c]);
+                }
+                L.x[L.nc + t] = s + __ldcg(&L.b[L.nc + t]) / __ldg(&L.dF[t]);
+            }
+            break;
+        case OP_COARSE:
+            // same summation order as the per-step kernel (lane j, j + 32, ...); eight loads
+            // per lane are issued before they are used, so one warp keeps 2 KB in flight
+            for (int i = p.warp; i < L.n; i += p.nwarps) {
+                const double *row = L.pinv + (size_t)i * L.n;
+                double s = 0.0;
+                for (int j0 = p.lane; j0 < L.n; j0 += 32 * 8) {
+                    double a[8], v[8];
+#pragma unroll
+                    for (int k = 0; k < 8; k++) {
+                        const int j = j0 + 32 * k;
+                        a[k] = j < L.n ? __ldg(&row[j]) : 0.0;
+                        v[k] = j < L.n ? __ldcg(&L.b[j]) : 0.0;
+                    }
+#pragma unroll
+                    for (int k = 0; k < 8; k++)
+                        if (j0 + 32 * k < L.n) s += a[k] * v[k];
+                }
+                s = warp_sum(s);
+                if (p.lane == 0) L.x[i] = s;
+            }
+            break;
+    }
+}
+
+// Steps ops[0 .. nops) on the levels of lv (device tables), run by one cluster.
+// prof (optional): CTA 0 records %globaltimer before step i (prof[2i]) and after its barrier
+// (prof[2i + 1]).
+__device__ __forceinline__ unsigned long long cl_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__global__ void __launch_bounds__(CBS, 1) k_cluster(const PLevel *__restrict__ lv_g, int nlev,
+                                                    const int32_t *__restrict__ cptr_g, int ncptr,
+                                                    const Op *__restrict__ ops_g, int nops,
+                                                    unsigned long long *prof) {
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    extern __shared__ __align__(16) unsigned char smem[];
+    PLevel *s_lv = reinterpret_cast<PLevel *>(smem);
+    int32_t *s_cptr = reinterpret_cast<int32_t *>(s_lv + nlev);
+    Op *s_ops = reinterpret_cast<Op *>(s_cptr + ((ncptr + 3) & ~3));
+    const bool ops_in_smem = nops <= CL_OPS_SMEM;
+    {
+        const long long *src = reinterpret_cast<const long long *>(lv_g);
+        long long *dst = reinterpret_cast<long long *>(s_lv);
+        const int nw = (int)(nlev * sizeof(PLevel) / sizeof(long long));
+        for (int i = threadIdx.x; i < nw; i += blockDim.x) dst[i] = src[i];
+        for (int i = threadIdx.x; i < ncptr; i += blockDim.x) s_cptr[i] = cptr_g[i];
+        if (ops_in_smem)
+            for (int i = threadIdx.x; i < nops; i += blockDim.x) s_ops[i] = ops_g[i];
+    }
+    __syncthreads();
+    const Op *ops = ops_in_smem ? s_ops : ops_g;
+    CPos p;
+    p.tid = (int)(cl_rank() * blockDim.x + threadIdx.x);
+    p.nthreads = (int)(cl_size() * blockDim.x);
+    p.lane = threadIdx.x & 31;
+    p.warp = p.tid >> 5;
+    p.nwarps = p.nthreads >> 5;
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    for (int i = 0; i < nops; i++) {
+        const Op op = ops[i];
+        if (prof && p.tid == 0) prof[2 * i] = cl_ns();
+        cl_op(op, s_lv, s_cptr, p);
+        cl_sync();
+        if (prof && p.tid == 0) prof[2 * i + 1] = cl_ns();
+    }
+}
+
+size_t cluster_smem(int nlev, int ncptr, int nops) {
+    return (size_t)nlev * sizeof(PLevel) + (size_t)((ncptr + 3) & ~3) * sizeof(int32_t) +
+           (size_t)(nops <= CL_OPS_SMEM ? nops : 0) * sizeof(Op);
+}
+
+// Largest cluster (16, 8 or 4 CTAs of 1024 threads) of which one can be resident with smem
+// bytes of dynamic shared memory per CTA; 0 if none. The kernel's dynamic shared-memory limit
+// is a per-function setting shared by every hierarchy, so it is always set to CL_SMEM_MAX.
+int cluster_dim(int device, size_t smem) {
+    int ok = 0;
+    if (smem > CL_SMEM_MAX) return 0;
+    if (cudaDeviceGetAttribute(&ok, cudaDevAttrClusterLaunch, device) != cudaSuccess || !ok) return 0;
+    if (cudaFuncSetAttribute(k_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CL_SMEM_MAX) !=
+        cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    if (cudaFuncSetAttribute(k_cluster, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess)
+        cudaGetLastError();
+    for (int cl : {16, 8, 4}) {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(cl);
+        cfg.blockDim = dim3(CBS);
+        cfg.dynamicSmemBytes = smem;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = cl;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        int n = 0;
+        if (cudaOccupancyMaxActiveClusters(&n, k_cluster, &cfg) == cudaSuccess && n >= 1) return cl;
+        cudaGetLastError();
+    }
+    return 0;
+}
+
+void launch_cluster(const PLevel *lv, int nlev, const int32_t *cptr, int ncptr, const Op *ops, int nops,
+                    int cl, bool pdl, cudaStream_t s, unsigned long long *prof) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(cl);
+    cfg.blockDim = dim3(CBS);
+    cfg.dynamicSmemBytes = cluster_smem(nlev, ncptr, nops);
+    cfg.stream = s;
+    cudaLaunchAttribute attr[2];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = cl;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[1].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = pdl ? 2 : 1;
+    cudaLaunchKernelEx(&cfg, k_cluster, lv, nlev, cptr, ncptr, ops, nops, prof);
+}
+
+}  // namespace lamg

@@ -89,36 +89,157 @@ __device__ __forceinline__ double row_finish(const RowPre &p, const int32_t *__r
     return s;
 }
 
+// A row longer than LONG_ROW entries summed by the whole block: thread t takes entries
+// e0 + t, e0 + t + BS, ..., then a fixed-order block reduction; the total is valid in thread 0.
+__device__ __forceinline__ double block_row(int e0, int e1, const int32_t *__restrict__ ci,
+                                            const double *__restrict__ val, const double *x) {
+    double v[1] = {0.0};
+    for (int e = e0 + (int)threadIdx.x; e < e1; e += BS) v[0] += val[e] * x[ci[e]];
+    block_sum<1>(v);
+    return v[0];
+}
+
+// Lane-group rows of a pass over all rows skip the long rows (a block takes each of those).
+__device__ __forceinline__ void drop_long(RowPre &p, bool &ok, int sub) {
+    if (ok && p.e1 - (p.e0 - sub) > LONG_ROW) {
+        ok = false;
+        p.e0 = p.e1;
+        p.c0 = -1;
+        p.c1 = -1;
+    }
+}
+
 // ------------------------------------------------------------------------------- cycle steps
 
 // One colour class [r0, r1) of Gauss-Seidel (Section 2): x_u = (b_u - sum_v A_uv x_v) / A_uu.
+// (b_u - sum) times the stored reciprocal of A_uu: one FP64 multiply instead of a division,
+// whose Newton iteration costs about ten FP64 instructions on a part with few FP64 units.
+// The class's first nl rows are long (rows are sorted longest first inside a class): block b
+// < nl takes row r0 + b, the other blocks the rows from r0 + nl on.
 template <int TPR>
-__global__ void __launch_bounds__(BS) k_gs(int r0, int r1, const int32_t *__restrict__ rp,
+__global__ void __launch_bounds__(BS) k_gs(int r0, int r1, int nl, const int32_t *__restrict__ rp,
                                            const int32_t *__restrict__ ci,
                                            const double *__restrict__ val,
-                                           const double *__restrict__ diag,
+                                           const double *__restrict__ idiag,
                                            const double *__restrict__ b, double *x) {
     pdl_trigger();
-    const int g = r0 + (int)((blockIdx.x * (unsigned)BS + threadIdx.x) / TPR);
+    if ((int)blockIdx.x < nl) {
+        const int row = r0 + (int)blockIdx.x;
+        const int e0 = rp[row], e1 = rp[row + 1];
+        const double id = idiag[row];
+        pdl_wait();
+        const double s = block_row(e0, e1, ci, val, x);
+        if (threadIdx.x == 0) x[row] = (b[row] - s) * id;
+        return;
+    }
+    const int g = r0 + nl + (int)(((blockIdx.x - nl) * (unsigned)BS + threadIdx.x) / TPR);
     const int sub = threadIdx.x % TPR;
     const bool ok = g < r1;
     const RowPre p = row_pre<TPR>(ok, g, sub, rp, ci, val);
-    const double d = ok ? diag[g] : 1.0;
+    const double id = ok ? idiag[g] : 1.0;
     pdl_wait();
     const double s = row_finish<TPR>(p, ci, val, x);
-    if (ok && sub == 0) x[g] = (b[g] - s) / d;
+    if (ok && sub == 0) x[g] = (b[g] - s) * id;
+}
+
+// --------------------------------------------------- sliced ELLPACK, one thread per row
+//
+// Rows in 32-row slices; entry j of row 32 s + l sits at sl_ptr[s] + 32 j + l, so the loads
+// of a warp (one slice) are contiguous. Every row is summed by one thread in entry order,
+// without a shuffle tree: on a part with few FP64 units the FP64 instruction count per row is
+// what bounds these kernels. Padding entries hold value 0 at a valid column. The slice
+// bounds and the first SELL_PRE entries are loaded before the dependency wait.
+constexpr int SELL_PRE = 4;
+
+struct SellPre {
+    int e, w;
+    int c[SELL_PRE];
+    double v[SELL_PRE];
+};
+
+__device__ __forceinline__ SellPre sell_pre(bool ok, int row, const int32_t *__restrict__ sp,
+                                            const int32_t *__restrict__ sc, const double *__restrict__ sv) {
+    SellPre p;
+    const int s = row >> 5;
+    const int a = ok ? sp[s] : 0, bnd = ok ? sp[s + 1] : 0;
+    p.e = a + (row & 31);
+    p.w = (bnd - a) >> 5;
+#pragma unroll
+    for (int k = 0; k < SELL_PRE; k++) {
+        const bool h = k < p.w;
+        p.c[k] = h ? sc[p.e + 32 * k] : 0;
+        p.v[k] = h ? sv[p.e + 32 * k] : 0.0;
+    }
+    return p;
+}
+
+__device__ __forceinline__ double sell_finish(const SellPre &p, const int32_t *__restrict__ sc,
+                                              const double *__restrict__ sv, const double *x) {
+    double s = 0.0;
+#pragma unroll
+    for (int k = 0; k < SELL_PRE; k++)
+        if (k < p.w) s += p.v[k] * x[p.c[k]];
+    for (int j = SELL_PRE; j < p.w; j += 4) {
+        int c[4];
+        double v[4], xv[4];
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+            const bool h = j + k < p.w;
+            c[k] = h ? sc[p.e + 32 * (j + k)] : 0;
+            v[k] = h ? sv[p.e + 32 * (j + k)] : 0.0;
+        }
+#pragma unroll
+        for (int k = 0; k < 4; k++) xv[k] = j + k < p.w ? x[c[k]] : 0.0;
+#pragma unroll
+        for (int k = 0; k < 4; k++)
+            if (j + k < p.w) s += v[k] * xv[k];
+    }
+    return s;
+}
+
+// One colour class [r0, r1) of Gauss-Seidel; thread t of the launch takes row 32 s0 + t
+// (s0 = first slice touching the class).
+__global__ void __launch_bounds__(64) k_gs_sell(int r0, int r1, int s0, const int32_t *__restrict__ sp,
+                                                const int32_t *__restrict__ sc, const double *__restrict__ sv,
+                                                const double *__restrict__ idiag,
+                                                const double *__restrict__ b, double *x) {
+    pdl_trigger();
+    const int row = 32 * s0 + (int)(blockIdx.x * blockDim.x + threadIdx.x);
+    const bool ok = row >= r0 && row < r1;
+    const SellPre p = sell_pre(ok, row, sp, sc, sv);
+    const double id = ok ? idiag[row] : 1.0;
+    pdl_wait();
+    if (!ok) return;
+    const double s = sell_finish(p, sc, sv, x);
+    x[row] = (b[row] - s) * id;
+}
+
+// r = b - A x
+__global__ void __launch_bounds__(BS) k_resid_sell(int n, const int32_t *__restrict__ sp,
+                                                   const int32_t *__restrict__ sc, const double *__restrict__ sv,
+                                                   const double *__restrict__ diag, const double *__restrict__ x,
+                                                   const double *__restrict__ b, double *r) {
+    pdl_trigger();
+    const int row = (int)(blockIdx.x * blockDim.x + threadIdx.x);
+    const bool ok = row < n;
+    const SellPre p = sell_pre(ok, row, sp, sc, sv);
+    const double d = ok ? diag[row] : 0.0;
+    pdl_wait();
+    if (!ok) return;
+    const double s = sell_finish(p, sc, sv, x);
+    r[row] = b[row] - (d * x[row] + s);
 }
 
 // First sweep from x = 0: rows of colour 0 ([0, c1)) have no updated neighbours yet, so
 // x_u = b_u / A_uu there; every other row starts at 0.
-__global__ void k_gs_first(int n, int c1, const double *__restrict__ diag,
+__global__ void k_gs_first(int n, int c1, const double *__restrict__ idiag,
                            const double *__restrict__ b, double *x) {
     pdl_trigger();
     const int i = blockIdx.x * BS + threadIdx.x;
-    const double d = (i < c1) ? diag[i] : 1.0;
+    const double id = (i < c1) ? idiag[i] : 1.0;
     pdl_wait();
     if (i >= n) return;
-    x[i] = i < c1 ? b[i] / d : 0.0;
+    x[i] = i < c1 ? b[i] * id : 0.0;
 }
 
 __global__ void k_zero(int n, double *x) {
@@ -128,19 +249,30 @@ __global__ void k_zero(int n, double *x) {
     if (i < n) x[i] = 0.0;
 }
 
-// r = b - A x
+// r = b - A x; blocks b < nl take the long rows lr[b]
 template <int TPR>
 __global__ void __launch_bounds__(BS) k_resid(int n, const int32_t *__restrict__ rp,
                                               const int32_t *__restrict__ ci,
                                               const double *__restrict__ val,
                                               const double *__restrict__ diag,
                                               const double *__restrict__ x,
-                                              const double *__restrict__ b, double *r) {
+                                              const double *__restrict__ b, double *r,
+                                              const int32_t *__restrict__ lr, int nl) {
     pdl_trigger();
-    const int g = (int)((blockIdx.x * (unsigned)BS + threadIdx.x) / TPR);
+    if ((int)blockIdx.x < nl) {
+        const int row = lr[blockIdx.x];
+        const int e0 = rp[row], e1 = rp[row + 1];
+        const double d = diag[row];
+        pdl_wait();
+        const double s = block_row(e0, e1, ci, val, x);
+        if (threadIdx.x == 0) r[row] = b[row] - (d * x[row] + s);
+        return;
+    }
+    const int g = (int)(((blockIdx.x - nl) * (unsigned)BS + threadIdx.x) / TPR);
     const int sub = threadIdx.x % TPR;
-    const bool ok = g < n;
-    const RowPre p = row_pre<TPR>(ok, g, sub, rp, ci, val);
+    bool ok = g < n;
+    RowPre p = row_pre<TPR>(ok, g, sub, rp, ci, val);
+    drop_long(p, ok, sub);
     const double d = ok ? diag[g] : 0.0;
     pdl_wait();
     const double s = row_finish<TPR>(p, ci, val, x);
@@ -306,24 +438,34 @@ __global__ void __launch_bounds__(BS) k_init_b(int n, double *r, double *bkeep, 
     }
 }
 
-// q = A p, S_ALPHA = S_RZ / (p . q)
+// q = A p, S_ALPHA = S_RZ / (p . q); block b takes the long rows lr[b], lr[b + grid], ...
 template <int TPR>
 __global__ void __launch_bounds__(BS) k_spmv_dot(int n, const int32_t *__restrict__ rp,
                                                  const int32_t *__restrict__ ci,
                                                  const double *__restrict__ val,
                                                  const double *__restrict__ diag,
                                                  const double *__restrict__ p, double *q,
-                                                 const Reduce red) {
+                                                 const Reduce red, const int32_t *__restrict__ lr, int nl) {
     pdl_trigger();
     pdl_wait();
     const int groups = gridDim.x * (BS / TPR);
     const int sub = threadIdx.x % TPR;
     double pq[1] = {0.0};
+    for (int t = blockIdx.x; t < nl; t += gridDim.x) {
+        const int row = lr[t];
+        const double s = block_row(rp[row], rp[row + 1], ci, val, p);
+        if (threadIdx.x == 0) {
+            const double qi = diag[row] * p[row] + s;
+            q[row] = qi;
+            pq[0] += p[row] * qi;
+        }
+    }
     const int rounds = (n + groups - 1) / groups;
     int g = (int)((blockIdx.x * (unsigned)BS + threadIdx.x) / TPR);
     for (int it = 0; it < rounds; it++, g += groups) {
-        const bool ok = g < n;
-        const int e0 = ok ? rp[g] + sub : 0, e1 = ok ? rp[g + 1] : 0;
+        bool ok = g < n;
+        int e0 = ok ? rp[g] + sub : 0, e1 = ok ? rp[g + 1] : 0;
+        if (ok && e1 - (e0 - sub) > LONG_ROW) { ok = false; e0 = e1; }
         const double s = row_sum<TPR>(e0, e1, ci, val, p);
         if (ok && sub == 0) {
             const double qi = diag[g] * p[g] + s;
@@ -333,6 +475,27 @@ __global__ void __launch_bounds__(BS) k_spmv_dot(int n, const int32_t *__restric
     }
     if (grid_sum<1>(pq, red) && threadIdx.x == 0)
         red.scal[S_ALPHA] = pq[0] != 0.0 ? red.scal[S_RZ] / pq[0] : 0.0;  // b = 0: nothing to do
+}
+
+// q = A p, S_ALPHA = S_RZ / (p . q), one thread per row (sliced ELLPACK)
+__global__ void __launch_bounds__(BS) k_spmv_dot_sell(int n, const int32_t *__restrict__ sp,
+                                                      const int32_t *__restrict__ sc,
+                                                      const double *__restrict__ sv,
+                                                      const double *__restrict__ diag,
+                                                      const double *__restrict__ p, double *q,
+                                                      const Reduce red) {
+    pdl_trigger();
+    pdl_wait();
+    double pq[1] = {0.0};
+    for (int row = blockIdx.x * BS + threadIdx.x; row < n; row += gridDim.x * BS) {
+        const SellPre pre = sell_pre(true, row, sp, sc, sv);
+        const double s = sell_finish(pre, sc, sv, p);
+        const double qi = diag[row] * p[row] + s;
+        q[row] = qi;
+        pq[0] += p[row] * qi;
+    }
+    if (grid_sum<1>(pq, red) && threadIdx.x == 0)
+        red.scal[S_ALPHA] = pq[0] != 0.0 ? red.scal[S_RZ] / pq[0] : 0.0;
 }
 
 // x += alpha p, r -= alpha q, S_RR = ||r||^2
@@ -382,24 +545,34 @@ __global__ void k_update_p(int n, const double *__restrict__ z, double *p, doubl
     zold[i] = zi;
 }
 
-// S_TRUE_RR = ||b - A x||^2
+// S_TRUE_RR = ||b - A x||^2; long rows as in k_spmv_dot
 template <int TPR>
 __global__ void __launch_bounds__(BS) k_true_resid(int n, const int32_t *__restrict__ rp,
                                                    const int32_t *__restrict__ ci,
                                                    const double *__restrict__ val,
                                                    const double *__restrict__ diag,
                                                    const double *__restrict__ x,
-                                                   const double *__restrict__ b, const Reduce red) {
+                                                   const double *__restrict__ b, const Reduce red,
+                                                   const int32_t *__restrict__ lr, int nl) {
     pdl_trigger();
     pdl_wait();
     const int groups = gridDim.x * (BS / TPR);
     const int sub = threadIdx.x % TPR;
     double acc[1] = {0.0};
+    for (int t = blockIdx.x; t < nl; t += gridDim.x) {
+        const int row = lr[t];
+        const double s = block_row(rp[row], rp[row + 1], ci, val, x);
+        if (threadIdx.x == 0) {
+            const double ri = b[row] - (diag[row] * x[row] + s);
+            acc[0] += ri * ri;
+        }
+    }
     const int rounds = (n + groups - 1) / groups;
     int g = (int)((blockIdx.x * (unsigned)BS + threadIdx.x) / TPR);
     for (int it = 0; it < rounds; it++, g += groups) {
-        const bool ok = g < n;
-        const int e0 = ok ? rp[g] + sub : 0, e1 = ok ? rp[g + 1] : 0;
+        bool ok = g < n;
+        int e0 = ok ? rp[g] + sub : 0, e1 = ok ? rp[g + 1] : 0;
+        if (ok && e1 - (e0 - sub) > LONG_ROW) { ok = false; e0 = e1; }
         const double s = row_sum<TPR>(e0, e1, ci, val, x);
         if (ok && sub == 0) {
             const double ri = b[g] - (diag[g] * x[g] + s);
@@ -409,11 +582,31 @@ __global__ void __launch_bounds__(BS) k_true_resid(int n, const int32_t *__restr
     if (grid_sum<1>(acc, red) && threadIdx.x == 0) red.scal[S_TRUE_RR] = acc[0];
 }
 
+// S_TRUE_RR = ||b - A x||^2, one thread per row (sliced ELLPACK)
+__global__ void __launch_bounds__(BS) k_true_resid_sell(int n, const int32_t *__restrict__ sp,
+                                                        const int32_t *__restrict__ sc,
+                                                        const double *__restrict__ sv,
+                                                        const double *__restrict__ diag,
+                                                        const double *__restrict__ x,
+                                                        const double *__restrict__ b, const Reduce red) {
+    pdl_trigger();
+    pdl_wait();
+    double acc[1] = {0.0};
+    for (int row = blockIdx.x * BS + threadIdx.x; row < n; row += gridDim.x * BS) {
+        const SellPre pre = sell_pre(true, row, sp, sc, sv);
+        const double s = sell_finish(pre, sc, sv, x);
+        const double ri = b[row] - (diag[row] * x[row] + s);
+        acc[0] += ri * ri;
+    }
+    if (grid_sum<1>(acc, red) && threadIdx.x == 0) red.scal[S_TRUE_RR] = acc[0];
+}
+
 // ------------------------------------------------------------------------------- launchers
 
 static bool g_pdl = true;
 
 void set_pdl(bool on) { g_pdl = on; }
+bool pdl_enabled() { return g_pdl; }
 
 // Launch with programmatic stream serialisation, so the kernel may start while its
 // predecessor in the stream is still running (it waits for it at griddepcontrol.wait).
@@ -422,6 +615,21 @@ static void launch(void (*kernel)(KArgs...), unsigned grid, cudaStream_t s, Args
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid < 1 ? 1 : grid);
     cfg.blockDim = dim3(BS);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = g_pdl ? 1 : 0;
+    cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+
+template <typename... KArgs, typename... Args>
+static void launch_bs(void (*kernel)(KArgs...), unsigned grid, unsigned bs, cudaStream_t s, Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid < 1 ? 1 : grid);
+    cfg.blockDim = dim3(bs);
     cfg.dynamicSmemBytes = 0;
     cfg.stream = s;
     cudaLaunchAttribute attr[1];
@@ -461,7 +669,7 @@ void launch_op(const Op &op, std::vector<DevLevel> &lv, const Reduce &red, cudaS
     const int n = (int)L.n;
     switch (op.kind) {
         case OP_GS_FIRST:
-            launch(k_gs_first, blocks(n), s, n, (int)L.cptr[1], (const double *)L.diag, (const double *)L.b, L.x);
+            launch(k_gs_first, blocks(n), s, n, (int)L.cptr[1], (const double *)L.idiag, (const double *)L.b, L.x);
             break;
         case OP_ZERO:
             launch(k_zero, blocks(n), s, n, L.x);
@@ -470,17 +678,31 @@ void launch_op(const Op &op, std::vector<DevLevel> &lv, const Reduce &red, cudaS
             const int r0 = (int)L.cptr[op.colour], r1 = (int)L.cptr[op.colour + 1];
             const int64_t rows = r1 - r0;
             if (rows <= 0) break;
-#define GRID_GS(T) blocks(rows * (T))
-            TPR_DISPATCH(L.tpr, k_gs, GRID_GS, r0, r1, (const int32_t *)L.rp, (const int32_t *)L.ci,
-                         (const double *)L.val, (const double *)L.diag, (const double *)L.b, L.x);
+            if (L.gs_tpr == 0) {
+                const int s0 = r0 / 32, s1 = (r1 + 31) / 32;
+                launch_bs(k_gs_sell, (unsigned)((32 * (s1 - s0) + 63) / 64), 64, s, r0, r1, s0,
+                          (const int32_t *)L.sl_ptr, (const int32_t *)L.sl_col, (const double *)L.sl_val,
+                          (const double *)L.idiag, (const double *)L.b, L.x);
+                break;
+            }
+            const int nl = L.nlong ? (int)(L.lptr[op.colour + 1] - L.lptr[op.colour]) : 0;
+#define GRID_GS(T) (unsigned)nl + blocks((rows - nl) * (T))
+            TPR_DISPATCH(L.gs_tpr, k_gs, GRID_GS, r0, r1, nl, (const int32_t *)L.rp, (const int32_t *)L.ci,
+                         (const double *)L.val, (const double *)L.idiag, (const double *)L.b, L.x);
 #undef GRID_GS
             break;
         }
         case OP_RESID: {
-#define GRID_R(T) blocks((int64_t)n * (T))
-            TPR_DISPATCH(L.tpr, k_resid, GRID_R, n, (const int32_t *)L.rp, (const int32_t *)L.ci,
+            if (L.rs_tpr == 0) {
+                launch(k_resid_sell, blocks(n), s, n, (const int32_t *)L.sl_ptr, (const int32_t *)L.sl_col,
+                       (const double *)L.sl_val, (const double *)L.diag, (const double *)L.x,
+                       (const double *)L.b, L.r);
+                break;
+            }
+#define GRID_R(T) (unsigned)L.nlong + blocks((int64_t)n * (T))
+            TPR_DISPATCH(L.rs_tpr, k_resid, GRID_R, n, (const int32_t *)L.rp, (const int32_t *)L.ci,
                          (const double *)L.val, (const double *)L.diag, (const double *)L.x,
-                         (const double *)L.b, L.r);
+                         (const double *)L.b, L.r, (const int32_t *)L.lrows, (int)L.nlong);
 #undef GRID_R
             break;
         }
@@ -536,9 +758,15 @@ void launch_init_b(int64_t n, double *r, double *bkeep, double *x, double *p, do
 
 void launch_spmv_dot(const DevLevel &L, const double *p, double *q, const Reduce &red, cudaStream_t s) {
     const int n = (int)L.n;
+    if (L.rs_tpr == 0) {
+        launch(k_spmv_dot_sell, red_blocks(n), s, n, (const int32_t *)L.sl_ptr, (const int32_t *)L.sl_col,
+               (const double *)L.sl_val, (const double *)L.diag, p, q, red);
+        return;
+    }
 #define GRID_S(T) red_blocks((int64_t)n * (T))
-    TPR_DISPATCH(L.tpr, k_spmv_dot, GRID_S, n, (const int32_t *)L.rp, (const int32_t *)L.ci,
-                 (const double *)L.val, (const double *)L.diag, p, q, red);
+    TPR_DISPATCH(L.rs_tpr, k_spmv_dot, GRID_S, n, (const int32_t *)L.rp, (const int32_t *)L.ci,
+                 (const double *)L.val, (const double *)L.diag, p, q, red, (const int32_t *)L.lrows,
+                 (int)L.nlong);
 #undef GRID_S
 }
 
@@ -560,9 +788,15 @@ void launch_update_p(int64_t n, const double *z, double *p, double *zold, const 
 void launch_true_resid(const DevLevel &L, const double *x, const double *b, const Reduce &red,
                        cudaStream_t s) {
     const int n = (int)L.n;
+    if (L.rs_tpr == 0) {
+        launch(k_true_resid_sell, red_blocks(n), s, n, (const int32_t *)L.sl_ptr, (const int32_t *)L.sl_col,
+               (const double *)L.sl_val, (const double *)L.diag, x, b, red);
+        return;
+    }
 #define GRID_T(T) red_blocks((int64_t)n * (T))
-    TPR_DISPATCH(L.tpr, k_true_resid, GRID_T, n, (const int32_t *)L.rp, (const int32_t *)L.ci,
-                 (const double *)L.val, (const double *)L.diag, x, b, red);
+    TPR_DISPATCH(L.rs_tpr, k_true_resid, GRID_T, n, (const int32_t *)L.rp, (const int32_t *)L.ci,
+                 (const double *)L.val, (const double *)L.diag, x, b, red, (const int32_t *)L.lrows,
+                 (int)L.nlong);
 #undef GRID_T
 }
 

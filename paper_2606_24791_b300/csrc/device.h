@@ -23,9 +23,26 @@ struct DevLevel {
     std::vector<int64_t> cptr;    // colour class row ranges (aggregation)
     std::vector<int32_t> perm;    // device index -> natural id
 
-    // operator: off-diagonal CSR + diagonal (FP64), int32 row pointers
+    // operator: off-diagonal CSR + diagonal and its reciprocal (FP64), int32 row pointers
     int32_t *rp = nullptr, *ci = nullptr;
-    double *val = nullptr, *diag = nullptr;
+    double *val = nullptr, *diag = nullptr, *idiag = nullptr;
+    // the same off-diagonal entries as sliced ELLPACK (sell = 1): 32-row slices, entry j of
+    // row 32 s + l at sl_ptr[s] + 32 j + l, padding (value 0, the row's own column) up to the
+    // slice's longest row
+    int sell = 0;
+    int64_t sell_nnz = 0;
+    // rows with more than LONG_ROW off-diagonal entries, summed by a whole thread block: their
+    // device indices (ascending) and, per colour class, the offsets into that list (an
+    // aggregation level's long rows are the first rows of their class)
+    int32_t *lrows = nullptr;
+    int64_t nlong = 0;
+    std::vector<int64_t> lptr;
+    // kernel form of the colour-class sweep (gs_tpr) and of the residual-type passes (rs_tpr:
+    // residual, A p with its dot product, true residual): 0 one thread per row on the sliced
+    // copy, else that many lanes per CSR row; set by rule and refined by timing at setup
+    int gs_tpr = 1, rs_tpr = 1;
+    int32_t *sl_ptr = nullptr, *sl_col = nullptr;
+    double *sl_val = nullptr;
     // aggregation: P rows (coarse device ids) and P^T as CSR over coarse rows
     int32_t *agg = nullptr, *agg2 = nullptr;
     double *wt = nullptr;
@@ -73,11 +90,17 @@ struct Reduce {
     double *scal = nullptr;       // S_COUNT
 };
 
-// Plain-data view of a level for the persistent kernel (device pointers only).
+constexpr int SELL_MAX_ROW = 64;   // longer rows keep the level on the lane-group CSR kernels
+constexpr int LONG_ROW = 256;      // longer rows are summed by a whole thread block
+
+// Plain-data view of a level for the persistent and cluster kernels (device pointers only).
 struct PLevel {
     int kind, n, nc, nF, ncol, tpr, pt_tpr, cptr_off;  // colour offsets at cptr_all + cptr_off
+    int gs_tpr, rs_tpr;                                 // as in DevLevel (0: sliced ELLPACK)
     const int32_t *rp, *ci;
-    const double *val, *diag;
+    const double *val, *diag, *idiag;
+    const int32_t *sl_ptr, *sl_col;
+    const double *sl_val;
     const int32_t *agg, *agg2;
     const double *wt;
     const int32_t *pt_ptr, *pt_row;
@@ -114,6 +137,15 @@ int persistent_grid(int device, size_t smem);
 cudaError_t launch_persistent(const PSolve *P, int grid, size_t smem, int mode, int maxit, double tol,
                               const double *b_in, double *phi_out, cudaStream_t s,
                               unsigned long long *prof = nullptr);
+
+// cluster sub-cycle kernel (cluster.cu)
+constexpr int CL_OPS_SMEM = 4096;               // longer step lists are read from global memory
+constexpr size_t CL_SMEM_MAX = 160 * 1024;      // dynamic shared memory limit of the kernel
+int cluster_dim(int device, size_t smem);   // CTAs per cluster that fit (16, 8, 4) or 0
+size_t cluster_smem(int nlev, int ncptr, int nops);
+void launch_cluster(const PLevel *lv, int nlev, const int32_t *cptr, int ncptr, const Op *ops, int nops,
+                    int cl, bool pdl, cudaStream_t s, unsigned long long *prof = nullptr);
+bool pdl_enabled();
 
 // launchers (cycle_kernels.cu)
 void launch_op(const Op &op, std::vector<DevLevel> &lv, const Reduce &red, cudaStream_t s);

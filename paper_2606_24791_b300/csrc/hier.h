@@ -47,6 +47,17 @@ struct lamg_hier {
     double cycle_mat[2] = {0, 0}; // per cycle, read once whatever k: [FP64 cycle, FP32 cycle]
     double cycle_vec[2] = {0, 0}; // per cycle and right-hand side
     int64_t cycle_launches = 0;   // kernels of one cycle in the graph path
+    // device copies of the level table, colour offsets and step list (persistent and cluster
+    // kernels)
+    lamg::PLevel *d_lv = nullptr;
+    int32_t *d_cptr = nullptr;
+    lamg::Op *d_ops = nullptr;
+    int ncptr = 0;
+    // cluster sub-cycle: steps on levels >= cluster_from run as one cluster launch per visit
+    int cl_dim = 0;               // CTAs per cluster (0: cluster launch unavailable)
+    int cluster_from = -1;        // -1: every step is its own kernel
+    std::vector<double> tune_ms;  // cycle time of each candidate tried by the automatic choice
+    std::vector<int> tune_from;
     // multi-RHS / FP32 workspaces, one per (k, precision) used so far
     std::vector<lamg::BatchCtx *> batch;
     std::vector<void *> allocs;

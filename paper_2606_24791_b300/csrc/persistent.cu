@@ -165,7 +165,7 @@ __device__ __forceinline__ void p_gs(const PLevel &L, int r0, int r1, const Grid
         for (int u = 0; u < U; u++) {
 #pragma unroll
             for (int o = TPR / 2; o > 0; o >>= 1) s[u] += __shfl_xor_sync(0xffffffffu, s[u], o);
-            if (row[u] < r1 && sub == 0) L.x[row[u]] = (L.b[row[u]] - s[u]) / L.diag[row[u]];
+            if (row[u] < r1 && sub == 0) L.x[row[u]] = (L.b[row[u]] - s[u]) * L.idiag[row[u]];
         }
     }
 }
@@ -211,7 +211,7 @@ __device__ __forceinline__ void p_op(const Op &op, const Tables &T, const GridPo
     switch (op.kind) {
         case OP_GS_FIRST: {
             const int c1 = cptr[1];
-            for (int i = g.tid; i < L.n; i += g.nthreads) L.x[i] = i < c1 ? L.b[i] / L.diag[i] : 0.0;
+            for (int i = g.tid; i < L.n; i += g.nthreads) L.x[i] = i < c1 ? L.b[i] * L.idiag[i] : 0.0;
             break;
         }
         case OP_ZERO:
@@ -406,9 +406,9 @@ __global__ void __launch_bounds__(PBS, 2) k_persistent(const PSolve *__restrict_
     int32_t *s_tail = reinterpret_cast<int32_t *>(s_ops + P.nops);
     int32_t *s_cptr = s_tail + P.nops;
     {
-        const int4 *src = reinterpret_cast<const int4 *>(P.lv);
-        int4 *dst = reinterpret_cast<int4 *>(s_lv);
-        const int nw = (int)(P.nlev * sizeof(PLevel) / sizeof(int4));
+        const long long *src = reinterpret_cast<const long long *>(P.lv);
+        long long *dst = reinterpret_cast<long long *>(s_lv);
+        const int nw = (int)(P.nlev * sizeof(PLevel) / sizeof(long long));
         for (int i = threadIdx.x; i < nw; i += blockDim.x) dst[i] = src[i];
         for (int i = threadIdx.x; i < P.nops; i += blockDim.x) {
             s_ops[i] = P.ops[i];

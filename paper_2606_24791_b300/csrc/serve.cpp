@@ -302,6 +302,10 @@ int lamg_server_create(const lamg_server_opts *so, const lamg_options *opt, lamg
     if (opt) s->opt = *opt;
     else lamg_options_default(&s->opt);
     s->opt.device = so->device;
+    // a served setup runs no timing trials (kernel forms, launch schedule): they would queue
+    // behind other requests' solves and lengthen every setup
+    s->opt.autotune = 0;
+    if (s->opt.cluster_rows == 0) s->opt.cluster_rows = -1;
     const int nw = std::max(1, so->setup_threads);
     for (int i = 0; i < nw; i++) s->workers.emplace_back([s] { s->setup_worker(); });
     s->exec = std::thread([s] { s->executor(); });

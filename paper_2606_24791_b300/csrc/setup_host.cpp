@@ -11,6 +11,8 @@
 #include <cmath>
 #include <cstring>
 #include <numeric>
+#include <condition_variable>
+#include <mutex>
 #include <thread>
 
 #include "internal.h"
@@ -370,24 +372,69 @@ int dense_pinv(const HostMat &A, std::vector<double> &pinv) {
         M[i * n + i] += A.diag[i];
         for (int64_t e = A.rp[i]; e < A.rp[i + 1]; e++) M[i * n + A.ci[e]] += A.val[e];
     }
-    // lower Cholesky factor G (row-major, in place): M = G G^T
-    for (int64_t j = 0; j < n; j++) {
-        double s = M[j * n + j];
-        for (int64_t k = 0; k < j; k++) s -= M[j * n + k] * M[j * n + k];
-        if (!(s > 0.0)) return LAMG_ERR_DISCONNECTED;
-        const double gjj = std::sqrt(s);
-        M[j * n + j] = gjj;
-        for (int64_t i = j + 1; i < n; i++) {
-            double t = M[i * n + j];
-            for (int64_t k = 0; k < j; k++) t -= M[i * n + k] * M[j * n + k];
-            M[i * n + j] = t / gjj;
+    const int nthr = (int)std::max<unsigned>(1u, std::min<unsigned>(16u, std::thread::hardware_concurrency()));
+    // lower Cholesky factor G (row-major, in place): M = G G^T, column by column. Rows below
+    // the diagonal of one column are independent; for large n they are split over threads that
+    // meet at a barrier after each column.
+    bool spd = true;
+    if (n < 512 || nthr == 1) {
+        for (int64_t j = 0; j < n && spd; j++) {
+            double s = M[j * n + j];
+            for (int64_t k = 0; k < j; k++) s -= M[j * n + k] * M[j * n + k];
+            if (!(s > 0.0)) { spd = false; break; }
+            const double gjj = std::sqrt(s);
+            M[j * n + j] = gjj;
+            for (int64_t i = j + 1; i < n; i++) {
+                double t = M[i * n + j];
+                for (int64_t k = 0; k < j; k++) t -= M[i * n + k] * M[j * n + k];
+                M[i * n + j] = t / gjj;
+            }
         }
+    } else {
+        std::mutex mu;
+        std::condition_variable cv;
+        int arrived = 0;
+        int64_t phase = 0;
+        auto barrier = [&]() {
+            std::unique_lock<std::mutex> lk(mu);
+            const int64_t my = phase;
+            if (++arrived == nthr) {
+                arrived = 0;
+                phase++;
+                cv.notify_all();
+            } else {
+                cv.wait(lk, [&] { return phase != my; });
+            }
+        };
+        std::vector<std::thread> th;
+        for (int t = 0; t < nthr; t++)
+            th.emplace_back([&, t] {
+                for (int64_t j = 0; j < n; j++) {
+                    if (t == 0) {
+                        double s = M[j * n + j];
+                        for (int64_t k = 0; k < j; k++) s -= M[j * n + k] * M[j * n + k];
+                        if (!(s > 0.0)) spd = false;
+                        M[j * n + j] = spd ? std::sqrt(s) : 1.0;
+                    }
+                    barrier();
+                    const double gjj = M[j * n + j];
+                    const double *gj = &M[j * n];
+                    for (int64_t i = j + 1 + t; i < n; i += nthr) {
+                        double *gi = &M[i * n];
+                        double v = gi[j];
+                        for (int64_t k = 0; k < j; k++) v -= gi[k] * gj[k];
+                        gi[j] = v / gjj;
+                    }
+                    barrier();
+                }
+            });
+        for (auto &x : th) x.join();
     }
+    if (!spd) return LAMG_ERR_DISCONNECTED;
     // M^{-1} = G^{-T} G^{-1}. Row c of H = G^{-T} (stored row-major) is column c of G^{-1}, the
     // forward substitution G y = e_c (y_i = 0 for i < c); then (M^{-1})_{ij} = H_i . H_j over
     // k >= max(i, j). All inner loops run over contiguous memory; rows are split over threads.
     std::vector<double> H(n * n, 0.0);
-    const int nthr = (int)std::max<unsigned>(1u, std::min<unsigned>(16u, std::thread::hardware_concurrency()));
     auto parallel_rows = [&](auto &&fn) {
         if (n < 128 || nthr == 1) {
             for (int64_t r = 0; r < n; r++) fn(r);
@@ -438,7 +485,8 @@ double cycle_index(int64_t El, int64_t El1, int64_t E0) {
 int build_hierarchy(const lamg_graph *g, const lamg_options &o, std::vector<HostLevel> &levels) {
     int rc = validate_graph(g);
     if (rc) return rc;
-    if (o.K < 1 || o.K > 16 || o.nu_tv < 0 || o.coarsest_max < 1 || o.max_levels < 1)
+    if (o.K < 1 || o.K > 16 || o.nu_tv < 0 || o.coarsest_max < 1 || o.max_levels < 1 || o.dense_rows < 0 ||
+        o.dense_rows > 4096)
         return LAMG_ERR_INVALID;
     levels.clear();
     HostMat A;
@@ -449,7 +497,9 @@ int build_hierarchy(const lamg_graph *g, const lamg_options &o, std::vector<Host
         HostLevel &L = levels.back();
         L.A = std::move(A);
         const int64_t n = L.A.n;
-        if (n <= o.coarsest_max || l + 1 >= o.max_levels) {
+        // a small level with at least n^2/8 off-diagonal entries is solved directly
+        const bool dense = n <= o.dense_rows && (double)L.A.nnz() >= (double)n * (double)n / 8.0;
+        if (n <= o.coarsest_max || dense || l + 1 >= o.max_levels) {
             L.kind = KIND_COARSEST;
             break;
         }

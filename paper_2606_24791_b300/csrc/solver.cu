@@ -45,6 +45,13 @@ void build_orders(lamg_hier *h) {
             for (int c = 0; c < ncol; c++) D.cptr[c + 1] += D.cptr[c];
             std::vector<int64_t> fill(D.cptr.begin(), D.cptr.end() - 1);
             for (int64_t u = 0; u < n; u++) D.perm[fill[H.colour[u]]++] = (int32_t)u;
+            // inside a colour class, longer rows first (ties in ascending id): the 32-row
+            // slices of the sliced-ELLPACK operator then hold rows of similar length
+            for (int c = 0; c < ncol; c++)
+                std::stable_sort(D.perm.begin() + D.cptr[c], D.perm.begin() + D.cptr[c + 1],
+                                 [&H](int32_t a, int32_t b) {
+                                     return H.A.rp[a + 1] - H.A.rp[a] > H.A.rp[b + 1] - H.A.rp[b];
+                                 });
         } else {
             std::vector<int32_t> cnode(H.nc);
             for (int64_t u = 0; u < n; u++)
@@ -80,10 +87,73 @@ int upload_level(lamg_hier *h, int l) {
         rp[i + 1] = rp[i] + (int32_t)row.size();
         diag[i] = H.A.diag[u];
     }
+    std::vector<double> idiag(n);
+    for (int64_t i = 0; i < n; i++) idiag[i] = 1.0 / diag[i];
     if ((rc = dupload(h, &D.rp, rp)) || (rc = dupload(h, &D.ci, ci)) || (rc = dupload(h, &D.val, val)) ||
-        (rc = dupload(h, &D.diag, diag)))
+        (rc = dupload(h, &D.diag, diag)) || (rc = dupload(h, &D.idiag, idiag)))
         return rc;
-    D.tpr = choose_tpr(n ? (double)H.A.nnz() / (double)n : 1.0);
+    D.tpr = h->opt.row_tpr > 0 ? h->opt.row_tpr : choose_tpr(n ? (double)H.A.nnz() / (double)n : 1.0);
+    // sliced ELLPACK copy of the operator (32-row slices, entry j of row 32 s + l at
+    // sl_ptr[s] + 32 j + l, padded with value 0 at the row's own column), used by the
+    // one-thread-per-row kernels when rows are short and padding is small
+    {
+        const int64_t ns = (n + 31) / 32;
+        std::vector<int32_t> sp(ns + 1, 0);
+        int64_t tot = 0, maxlen = 0;
+        for (int64_t sl = 0; sl < ns; sl++) {
+            int64_t w = 0;
+            for (int64_t i = 32 * sl; i < std::min(n, 32 * sl + 32); i++) w = std::max<int64_t>(w, rp[i + 1] - rp[i]);
+            maxlen = std::max(maxlen, w);
+            sp[sl] = (int32_t)tot;
+            tot += 32 * w;
+        }
+        sp[ns] = (int32_t)tot;
+        const int64_t z = H.A.nnz();
+        const bool use = h->opt.sell >= 0 && tot < (int64_t)INT32_MAX && maxlen <= SELL_MAX_ROW &&
+                         (h->opt.sell > 0 || (double)tot <= 1.5 * (double)z + 64.0);
+        if (use) {
+            std::vector<int32_t> sc(tot);
+            std::vector<double> sv(tot, 0.0);
+            for (int64_t sl = 0; sl < ns; sl++) {
+                const int64_t w = (sp[sl + 1] - sp[sl]) / 32;
+                for (int64_t l = 0; l < 32; l++) {
+                    const int64_t i = 32 * sl + l;
+                    for (int64_t j = 0; j < w; j++) {
+                        const int64_t e = sp[sl] + 32 * j + l;
+                        if (i < n && j < rp[i + 1] - rp[i]) { sc[e] = ci[rp[i] + j]; sv[e] = val[rp[i] + j]; }
+                        else sc[e] = (int32_t)std::min<int64_t>(i, n - 1);
+                    }
+                }
+            }
+            if ((rc = dupload(h, &D.sl_ptr, sp)) || (rc = dupload(h, &D.sl_col, sc)) || (rc = dupload(h, &D.sl_val, sv)))
+                return rc;
+            D.sell = 1;
+            D.sell_nnz = tot;
+        }
+    }
+    // long rows
+    {
+        std::vector<int32_t> lr;
+        for (int64_t i = 0; i < n; i++)
+            if (rp[i + 1] - rp[i] > LONG_ROW) lr.push_back((int32_t)i);
+        D.nlong = (int64_t)lr.size();
+        if (D.nlong && (rc = dupload(h, &D.lrows, lr))) return rc;
+        if (H.kind == KIND_AGG) {
+            D.lptr.assign(D.ncol + 1, 0);
+            for (int c = 0; c < D.ncol; c++) {
+                int64_t cnt = 0;
+                for (int64_t i = D.cptr[c]; i < D.cptr[c + 1] && rp[i + 1] - rp[i] > LONG_ROW; i++) cnt++;
+                D.lptr[c + 1] = D.lptr[c] + cnt;
+            }
+            if (D.lptr[D.ncol] != D.nlong) return LAMG_ERR_INVALID;  // classes sorted longest first
+        }
+    }
+    // rule (refined by timing when the options ask for it): sweeps on lane groups, whose
+    // short per-lane chains suit the latency-bound colour classes; residual-type passes of
+    // large levels one thread per row, which issues the fewest FP64 instructions per entry
+    D.gs_tpr = D.tpr;
+    D.rs_tpr = (D.sell && (h->opt.sell > 0 || n >= 65536)) ? 0 : D.tpr;
+    if (D.sell && h->opt.sell > 0) D.gs_tpr = 0;
     if (H.kind == KIND_AGG) {
         const std::vector<int32_t> &ip = h->dev[l + 1].perm;
         std::vector<int32_t> ipc(H.nc);
@@ -195,7 +265,18 @@ int capture(lamg_hier *h, cudaGraphExec_t *out, int which) {
     const DevLevel &F = h->dev[0];
     const int64_t n = F.n;
     if (which == 0 || which == 1) {
-        for (const Op &op : h->ops) launch_op(op, h->dev, h->red, cs);
+        const int nops = (int)h->ops.size(), nlev = (int)h->dev.size();
+        for (int i = 0; i < nops;) {
+            if (h->cluster_from >= 0 && h->ops[i].level >= h->cluster_from) {
+                int j = i;
+                while (j < nops && h->ops[j].level >= h->cluster_from) j++;
+                launch_cluster(h->d_lv, nlev, h->d_cptr, h->ncptr, h->d_ops + i, j - i, h->cl_dim,
+                               pdl_enabled(), cs);
+                i = j;
+            } else {
+                launch_op(h->ops[i++], h->dev, h->red, cs);
+            }
+        }
         launch_sum(n, F.x, h->red, cs);
         if (which == 0) launch_sub_mean(n, F.x, h->red, cs);
         else {
@@ -270,11 +351,10 @@ void lamg::op_bytes(const lamg_hier *h, const Op &op, double s, double *mat, dou
 
 namespace {
 
-// Device tables of the persistent solve kernel.
-int setup_persistent(lamg_hier *h) {
+// Device copies of the level table, the colour offsets of all levels and the step list.
+int upload_tables(lamg_hier *h) {
     int rc;
     const int L = (int)h->dev.size();
-    const int64_t tail_rows = h->opt.tail_rows > 0 ? h->opt.tail_rows : 8192;
     std::vector<PLevel> pl(L);
     std::vector<int32_t> cptr_all;
     for (int l = 0; l < L; l++) {
@@ -285,7 +365,8 @@ int setup_persistent(lamg_hier *h) {
         P.tpr = D.tpr; P.pt_tpr = D.pt_tpr;
         P.cptr_off = (int)cptr_all.size();
         for (int64_t c : D.cptr) cptr_all.push_back((int32_t)c);
-        P.rp = D.rp; P.ci = D.ci; P.val = D.val; P.diag = D.diag;
+        P.rp = D.rp; P.ci = D.ci; P.val = D.val; P.diag = D.diag; P.idiag = D.idiag;
+        P.gs_tpr = D.gs_tpr; P.rs_tpr = D.rs_tpr; P.sl_ptr = D.sl_ptr; P.sl_col = D.sl_col; P.sl_val = D.sl_val;
         P.agg = D.agg; P.agg2 = D.agg2; P.wt = D.wt;
         P.pt_ptr = D.pt_ptr; P.pt_row = D.pt_row; P.pt_w = D.pt_w;
         P.pf_col = D.pf_col; P.pf_val = D.pf_val; P.dF = D.dF;
@@ -294,6 +375,17 @@ int setup_persistent(lamg_hier *h) {
         P.x = D.x; P.b = D.b; P.r = D.r;
     }
     if (cptr_all.empty()) cptr_all.push_back(0);
+    h->ncptr = (int)cptr_all.size();
+    if ((rc = dupload(h, &h->d_lv, pl)) || (rc = dupload(h, &h->d_ops, h->ops)) || (rc = dupload(h, &h->d_cptr, cptr_all)))
+        return rc;
+    return LAMG_OK;
+}
+
+// Device tables of the persistent solve kernel.
+int setup_persistent(lamg_hier *h) {
+    int rc;
+    const int L = (int)h->dev.size();
+    const int64_t tail_rows = h->opt.tail_rows > 0 ? h->opt.tail_rows : 8192;
     // single-CTA segments: maximal runs of steps on levels with at most tail_rows rows (the
     // dense coarsest only while its matrix is at most 512 x 512)
     const int nops = (int)h->ops.size();
@@ -310,20 +402,16 @@ int setup_persistent(lamg_hier *h) {
         tail_end[i] = j;
         i = j;
     }
-    h->smem = persistent_smem(L, nops, (int)cptr_all.size());
+    h->smem = persistent_smem(L, nops, h->ncptr);
     if (h->smem > 200 * 1024) return LAMG_OK;  // tables do not fit: graph path only
     h->grid = persistent_grid(h->device, h->smem);
     if (h->grid < 1) return LAMG_OK;
-    PLevel *dlv = nullptr;
-    Op *dops = nullptr;
-    int32_t *dtail = nullptr, *dcptr = nullptr;
-    if ((rc = dupload(h, &dlv, pl)) || (rc = dupload(h, &dops, h->ops)) || (rc = dupload(h, &dtail, tail_end)) ||
-        (rc = dupload(h, &dcptr, cptr_all)))
-        return rc;
+    int32_t *dtail = nullptr;
+    if ((rc = dupload(h, &dtail, tail_end))) return rc;
     PSolve &S = h->ph;
     std::memset(&S, 0, sizeof(S));
-    S.nlev = L; S.nops = nops; S.n0 = (int)h->dev[0].n; S.ncptr = (int)cptr_all.size();
-    S.lv = dlv; S.ops = dops; S.tail_end = dtail; S.cptr_all = dcptr; S.perm0 = h->perm0;
+    S.nlev = L; S.nops = nops; S.n0 = (int)h->dev[0].n; S.ncptr = h->ncptr;
+    S.lv = h->d_lv; S.ops = h->d_ops; S.tail_end = dtail; S.cptr_all = h->d_cptr; S.perm0 = h->perm0;
     S.r = h->r; S.p = h->p; S.q = h->q; S.zold = h->zold; S.xs = h->xs; S.bkeep = h->bkeep;
     if ((rc = dalloc(h, &S.partials, 2 * RED_NV * h->grid)) || (rc = dalloc(h, &h->bar, 1))) return rc;
     S.bar = h->bar;
@@ -336,6 +424,172 @@ int setup_persistent(lamg_hier *h) {
     CKR(cudaMemsetAsync(h->bar, 0, sizeof(GridBar), h->stream));
     CKR(cudaStreamSynchronize(h->stream));
     h->persistent_ok = true;
+    return LAMG_OK;
+}
+
+// Mean time of reps launches of seq (after one untimed pass), or -1 on error.
+double time_ops(lamg_hier *h, const std::vector<Op> &seq, bool spmv, int reps) {
+    cudaStream_t s = h->stream;
+    auto pass = [&]() {
+        if (spmv) launch_spmv_dot(h->dev[0], h->p, h->q, h->red, s);
+        else for (const Op &op : seq) launch_op(op, h->dev, h->red, s);
+    };
+    pass();
+    cudaEventRecord(h->ev_a, s);
+    for (int r = 0; r < reps; r++) pass();
+    cudaEventRecord(h->ev_b, s);
+    if (wait_event(h, h->ev_b) != LAMG_OK || cudaGetLastError() != cudaSuccess) return -1.0;
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, h->ev_a, h->ev_b);
+    return ms / reps;
+}
+
+// Kernel form per level, chosen by timing: for the colour-class sweep (one forward sweep of
+// every class) and for the residual-type pass (the residual; A p with its dot product on the
+// finest level), every lanes-per-row count from a quarter to twice the rule's, and one thread
+// per row on the sliced copy where it exists. Vectors are zero while timing. Every form
+// computes the same sums in a form-specific order, so the choice changes rounding only.
+int tune_kernels(lamg_hier *h) {
+    if (!h->opt.autotune) return LAMG_OK;
+    cudaStream_t s = h->stream;
+    const int L = (int)h->dev.size();
+    for (int l = 0; l < L; l++) {
+        DevLevel &D = h->dev[l];
+        if (D.x) CKR(cudaMemsetAsync(D.x, 0, D.n * sizeof(double), s));
+        if (D.b) CKR(cudaMemsetAsync(D.b, 0, D.n * sizeof(double), s));
+        if (D.r) CKR(cudaMemsetAsync(D.r, 0, D.n * sizeof(double), s));
+    }
+    CKR(cudaMemsetAsync(h->p, 0, h->dev[0].n * sizeof(double), s));
+    const int reps = 3;
+    for (int l = 0; l < L; l++) {
+        DevLevel &D = h->dev[l];
+        if (D.kind == KIND_COARSEST) continue;
+        std::vector<int> cand;
+        if (D.sell) cand.push_back(0);
+        for (int t = 1; t <= 32; t *= 2)
+            if (4 * t >= D.tpr && t <= 2 * D.tpr) cand.push_back(t);
+        if (D.kind == KIND_AGG) {
+            std::vector<Op> sweep;
+            for (int c = 0; c < D.ncol; c++) sweep.push_back({OP_GS, l, c});
+            double best = -1.0;
+            int pick = D.gs_tpr;
+            for (int t : cand) {
+                D.gs_tpr = t;
+                const double ms = time_ops(h, sweep, false, reps);
+                if (ms > 0 && (best < 0 || ms < best)) { best = ms; pick = t; }
+            }
+            D.gs_tpr = pick;
+        }
+        if (D.kind == KIND_AGG || l == 0) {
+            const std::vector<Op> res{{OP_RESID, l, 0}};
+            double best = -1.0;
+            int pick = D.rs_tpr;
+            for (int t : cand) {
+                D.rs_tpr = t;
+                const double ms = l == 0 ? time_ops(h, res, true, reps)
+                                         : (D.kind == KIND_AGG ? time_ops(h, res, false, reps) : -1.0);
+                if (ms > 0 && (best < 0 || ms < best)) { best = ms; pick = t; }
+            }
+            D.rs_tpr = pick;
+        }
+    }
+    CKR(cudaMemsetAsync(h->red.ticket, 0, sizeof(unsigned), s));
+    CKR(cudaStreamSynchronize(s));
+    return LAMG_OK;
+}
+
+// Kernels of one cycle in the graph path (steps with no rows launch nothing; a cluster
+// segment is one launch).
+int64_t count_cycle_launches(const lamg_hier *h) {
+    int64_t k = 0;
+    const int nops = (int)h->ops.size();
+    for (int i = 0; i < nops;) {
+        const Op &op = h->ops[i];
+        if (h->cluster_from >= 0 && op.level >= h->cluster_from) {
+            while (i < nops && h->ops[i].level >= h->cluster_from) i++;
+            k++;
+            continue;
+        }
+        i++;
+        if (op.kind == OP_ELIM_INTERP && h->dev[op.level].nF == 0) continue;
+        if (op.kind == OP_GS && h->dev[op.level].cptr[op.colour + 1] == h->dev[op.level].cptr[op.colour]) continue;
+        k++;
+    }
+    return k;
+}
+
+// Mean device time of one preconditioner cycle under the current schedule; -1 if the
+// schedule cannot be captured.
+double time_cycle(lamg_hier *h) {
+    cudaGraphExec_t g = nullptr;
+    if (capture(h, &g, 0) != LAMG_OK) {
+        cudaGetLastError();
+        return -1.0;
+    }
+    cudaStream_t s = h->stream;
+    const int warm = 3, reps = 10;
+    for (int r = 0; r < warm; r++) cudaGraphLaunch(g, s);
+    cudaEventRecord(h->ev_a, s);
+    for (int r = 0; r < reps; r++) cudaGraphLaunch(g, s);
+    cudaEventRecord(h->ev_b, s);
+    double ms = -1.0;
+    if (wait_event(h, h->ev_b) == LAMG_OK && cudaGetLastError() == cudaSuccess) {
+        float t = 0.f;
+        cudaEventElapsedTime(&t, h->ev_a, h->ev_b);
+        ms = t / reps;
+    }
+    cudaGraphExecDestroy(g);
+    return ms;
+}
+
+// Which levels run as one cluster launch per visit. Candidates are the levels from which on
+// every level has at most cluster_rows rows (2^18 when automatic). cluster_rows > 0 takes the
+// largest candidate; 0 times one cycle of the per-step schedule and of up to eight candidates
+// (largest first) and keeps the fastest; < 0 keeps every step its own kernel. Every schedule
+// computes bit-identical iterates, so the choice changes time only.
+int choose_cluster(lamg_hier *h) {
+    h->cluster_from = -1;
+    h->cl_dim = 0;
+    h->tune_ms.clear();
+    h->tune_from.clear();
+    const int L = (int)h->dev.size();
+    const int64_t rows = h->opt.cluster_rows == 0 && !h->opt.autotune ? -1 : h->opt.cluster_rows;
+    // largest table size of any segment: the step list is staged when it has at most
+    // CL_OPS_SMEM steps
+    const size_t smem = cluster_smem(L, h->ncptr, std::min((int)h->ops.size(), CL_OPS_SMEM));
+    if (smem > CL_SMEM_MAX) return LAMG_OK;
+    h->cl_dim = cluster_dim(h->device, smem);
+    if (!h->cl_dim || rows < 0) return LAMG_OK;
+    const int64_t limit = rows > 0 ? rows : ((int64_t)1 << 18);
+    // levels with block-per-row long rows stay on the per-step kernels (the cluster kernel
+    // sums every row with lane groups)
+    std::vector<int64_t> smax(L + 1, 0), lng(L + 1, 0);
+    for (int l = L - 1; l >= 0; l--) {
+        smax[l] = std::max(smax[l + 1], h->dev[l].n);
+        lng[l] = lng[l + 1] + h->dev[l].nlong;
+    }
+    std::vector<int> cand;
+    for (int l = 0; l < L; l++)
+        if (smax[l] <= limit && lng[l] == 0) cand.push_back(l);
+    if (cand.empty()) return LAMG_OK;
+    if (rows > 0) {
+        h->cluster_from = cand[0];
+        return LAMG_OK;
+    }
+    // timed on a zero right-hand side, which keeps every vector finite
+    CKR(cudaMemsetAsync(h->r, 0, h->dev[0].n * sizeof(double), h->stream));
+    int best = -1;
+    double best_ms = time_cycle(h);
+    h->tune_from.push_back(-1);
+    h->tune_ms.push_back(best_ms);
+    for (size_t k = 0; k < cand.size() && k < 8; k++) {
+        h->cluster_from = cand[k];
+        const double ms = time_cycle(h);
+        h->tune_from.push_back(cand[k]);
+        h->tune_ms.push_back(ms);
+        if (ms > 0 && (best_ms < 0 || ms < best_ms)) { best_ms = ms; best = cand[k]; }
+    }
+    h->cluster_from = best;
     return LAMG_OK;
 }
 
@@ -375,9 +629,11 @@ int finalize(lamg_hier *h) {
     CKR(cudaMemsetAsync(h->red.scal, 0, S_COUNT * sizeof(double), h->stream));
     h->h_scal = pinned_slot();
     if (!h->h_scal) return LAMG_ERR_OOM;
+    if ((rc = tune_kernels(h))) return rc;
     std::vector<int64_t> visits(L, 0);
     h->ops.clear();
     emit_visit(h, visits, 0, true);
+    if ((rc = upload_tables(h)) || (rc = choose_cluster(h))) return rc;
     if ((rc = capture(h, &h->g_cycle, 0)) || (rc = capture(h, &h->g_tail, 1)) || (rc = capture(h, &h->g_head, 2)))
         return rc;
     CKR(cudaEventCreate(&h->ev_k0));
@@ -392,11 +648,7 @@ int finalize(lamg_hier *h) {
         }
     }
     h->cycle_bytes = h->cycle_mat[0] + h->cycle_vec[0];
-    h->cycle_launches = 0;
-    for (const Op &op : h->ops)
-        if (!(op.kind == OP_ELIM_INTERP && h->dev[op.level].nF == 0) &&
-            !(op.kind == OP_GS && h->dev[op.level].cptr[op.colour + 1] == h->dev[op.level].cptr[op.colour]))
-            h->cycle_launches++;
+    h->cycle_launches = count_cycle_launches(h);
     if ((rc = setup_persistent(h))) return rc;
     CKR(cudaStreamSynchronize(h->stream));
     return LAMG_OK;
@@ -437,6 +689,9 @@ void lamg_options_default(lamg_options *o) {
     o->gamma_fixed = 0.0;
     o->device = 0;
     o->tail_rows = 8192;
+    o->cluster_rows = 0;
+    o->autotune = 1;
+    o->dense_rows = 4096;
 }
 
 const char *lamg_strerror(int c) {
@@ -460,6 +715,7 @@ int lamg_setup(const lamg_graph *g, const lamg_options *opt, lamg_hier **out) {
     *out = nullptr;
     lamg_options o;
     if (opt) o = *opt; else lamg_options_default(&o);
+    if (o.row_tpr < 0 || o.row_tpr > 32 || (o.row_tpr & (o.row_tpr - 1))) return LAMG_ERR_INVALID;
     int rc = set_device(o.device);
     if (rc) return rc;
     lamg_hier *h = new lamg_hier();
@@ -477,6 +733,7 @@ int lamg_import(const lamg_level_desc *lv, int32_t nl, const lamg_options *opt, 
     *out = nullptr;
     lamg_options o;
     if (opt) o = *opt; else lamg_options_default(&o);
+    if (o.row_tpr < 0 || o.row_tpr > 32 || (o.row_tpr & (o.row_tpr - 1))) return LAMG_ERR_INVALID;
     int rc = set_device(o.device);
     if (rc) return rc;
     lamg_hier *h = new lamg_hier();
@@ -712,6 +969,81 @@ int lamg_profile_cycle(lamg_hier *h, int64_t *out, int64_t cap, int64_t *count) 
     for (int64_t r = 1; r <= nrec && k < cap; r++, k++) {
         out[2 * k] = (int64_t)hp[2 * r];
         out[2 * k + 1] = (int64_t)(hp[2 * r + 1] - hp[2 * r - 1 == 1 ? 1 : 2 * r - 1]);
+    }
+    *count = k;
+    return LAMG_OK;
+}
+
+int lamg_profile_schedule(lamg_hier *h, int32_t from_level, int64_t *out, int64_t cap, int64_t *count) {
+    if (!h || !out || !count) return LAMG_ERR_INVALID;
+    CKR(cudaSetDevice(h->device));
+    const int nops = (int)h->ops.size(), nlev = (int)h->dev.size();
+    if (cap < 3 * (int64_t)nops) return LAMG_ERR_INVALID;
+    if (from_level >= 0 && !h->cl_dim) return LAMG_ERR_INVALID;
+    cudaStream_t s = h->stream;
+    unsigned long long *dprof = nullptr;
+    CKR(cudaMalloc(&dprof, 2 * (size_t)nops * sizeof(unsigned long long)));
+    std::vector<unsigned long long> hp(2 * (size_t)nops, 0);
+    std::vector<cudaEvent_t> ev(2 * (size_t)nops, nullptr);
+    std::vector<uint8_t> in_cl(nops, 0);
+    cudaError_t e = cudaMemsetAsync(h->r, 0, h->dev[0].n * sizeof(double), s);
+    for (int i = 0; i < nops && e == cudaSuccess;) {
+        if (from_level >= 0 && h->ops[i].level >= from_level) {
+            int j = i;
+            while (j < nops && h->ops[j].level >= from_level) in_cl[j++] = 1;
+            launch_cluster(h->d_lv, nlev, h->d_cptr, h->ncptr, h->d_ops + i, j - i, h->cl_dim, false, s,
+                           dprof + 2 * (size_t)i);
+            i = j;
+        } else {
+            cudaEventCreate(&ev[2 * i]);
+            cudaEventCreate(&ev[2 * i + 1]);
+            cudaEventRecord(ev[2 * i], s);
+            launch_op(h->ops[i], h->dev, h->red, s);
+            e = cudaEventRecord(ev[2 * i + 1], s);
+            i++;
+        }
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hp.data(), dprof, hp.size() * sizeof(unsigned long long),
+                                              cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaEventRecord(h->ev_b, s);
+    int rc = e == cudaSuccess ? wait_event(h, h->ev_b) : cuda_status(e);
+    if (!rc && cudaGetLastError() != cudaSuccess) rc = LAMG_ERR_CUDA;
+    for (int i = 0; i < nops; i++) {
+        out[3 * i] = i;
+        out[3 * i + 1] = in_cl[i];
+        out[3 * i + 2] = 0;
+        if (rc) continue;
+        if (in_cl[i]) {
+            out[3 * i + 2] = (int64_t)(hp[2 * i + 1] - hp[2 * i]);
+        } else if (ev[2 * i]) {
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, ev[2 * i], ev[2 * i + 1]);
+            out[3 * i + 2] = (int64_t)std::llround(ms * 1e6);
+        }
+    }
+    for (cudaEvent_t x : ev)
+        if (x) cudaEventDestroy(x);
+    cudaFree(dprof);
+    *count = 3 * (int64_t)nops;
+    return rc;
+}
+
+int lamg_schedule_info(const lamg_hier *h, int64_t *out, int64_t cap, int64_t *count) {
+    if (!h || !out || !count || cap < 5 + 2 * (int64_t)h->dev.size()) return LAMG_ERR_INVALID;
+    out[0] = h->cluster_from;
+    out[1] = h->cl_dim;
+    out[2] = h->cycle_launches;
+    out[3] = (int64_t)h->ops.size();
+    int64_t k = 4;
+    out[k++] = (int64_t)h->dev.size();
+    for (const DevLevel &D : h->dev) {
+        if (k + 2 > cap) break;
+        out[k++] = D.gs_tpr;
+        out[k++] = D.rs_tpr;
+    }
+    for (size_t i = 0; i < h->tune_ms.size() && k + 2 <= cap; i++) {
+        out[k++] = h->tune_from[i];
+        out[k++] = (int64_t)std::llround(h->tune_ms[i] * 1e6);  // nanoseconds
     }
     *count = k;
     return LAMG_OK;

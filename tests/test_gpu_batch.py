@@ -27,6 +27,7 @@ GRAPHS = {
     "grid3d_hetero": (lambda: gg.grid3d(14, 14, 14, "loguniform", seed=1), 16),
     "chunglu5000": (lambda: gg.chung_lu(5000, 2.1, 16, seed=1), 24),
     "grid_ragged": (lambda: gg.grid2d(37, 23, 1.0, 0.3), 8),
+    "grid_hubs": (lambda: gg.grid_with_hubs(48, 48, 6, 600, seed=2), 16),
 }
 
 
@@ -50,7 +51,9 @@ def test_batch_columns_equal_single_solves_and_oracle(gcase, k):
         assert sts[j]["iters"] == ref["iters"]
         assert rel(X[:, j], ref["x"]) <= 1e-9
         assert sts[j]["relres_true"] <= 2e-8
-        assert np.allclose(sts[j]["hist"], ref["hist"], rtol=1e-7, atol=1e-15)
+        h, hr = np.asarray(sts[j]["hist"]), np.asarray(ref["hist"])
+        big = hr > 1e-11          # below: rounding noise of the summation order
+        assert np.allclose(h[big], hr[big], rtol=1e-7) and np.all(h[~big] <= 1e-11)
 
 
 def test_batch_32_columns_with_a_zero_and_a_repeated_column():

@@ -45,6 +45,8 @@ CASES = {
     "path1000": (lambda: gg.path(1000, np.random.default_rng(0).uniform(0.5, 1.5, 999)), 4),
     "star300": (lambda: gg.star(300), 1),
     "grid_ragged": (lambda: gg.grid2d(37, 23, 1.0, 0.3), 8),
+    # six hubs of degree 600: rows longer than one block's stride on aggregation levels
+    "grid_hubs": (lambda: gg.grid_with_hubs(48, 48, 6, 600, seed=2), 16),
 }
 
 
@@ -102,13 +104,16 @@ def test_setup_matches_oracle(case):
 
 # ------------------------------------------------------------------------ cycle and CG
 
-PATHS = {"graph": False, "persistent": True}
+# graph: every cycle step its own kernel; cluster: the whole cycle as one launch of a
+# thread-block cluster (every level of these graphs fits); persistent: one cooperative kernel
+PATHS = {"graph": False, "cluster": False, "persistent": True}
+SCHED = {"graph": -1, "cluster": 10 ** 9, "persistent": -1}
 
 
 @pytest.mark.parametrize("path", sorted(PATHS))
 def test_cycle_parity(case, path):
     name, g, cm, H = case
-    P = lamg.import_levels(oracle_levels(H))
+    P = lamg.import_levels(oracle_levels(H), cluster_rows=SCHED[path])
     rng = np.random.default_rng(7)
     for _ in range(2):
         r = rng.standard_normal(g.n)
@@ -123,21 +128,26 @@ def test_cycle_parity(case, path):
 @pytest.mark.parametrize("path", sorted(PATHS))
 def test_fcg_iterates_parity(case, path):
     name, g, cm, H = case
-    P = lamg.import_levels(oracle_levels(H))
+    P = lamg.import_levels(oracle_levels(H), cluster_rows=SCHED[path])
     b = gg.rhs(g, 2)
     ref = H.fcg(b, tol=1e-300, maxit=6, record=True)
     for k in range(1, ref["iters"] + 1):
         x, st = P.solve(b, tol=1e-300, maxit=k, allow_unconverged=True, persistent=PATHS[path])
         xr = ref["iterates"][k - 1]
         assert rel(x, xr) <= RTOL, (name, k, rel(x, xr))
-        assert st["hist"][k] == pytest.approx(ref["hist"][k], rel=1e-8, abs=1e-15)
+        # below 1e-11 the recursive residual is rounding noise whose size depends on the
+        # summation order of the kernel form (a graph solved exactly by one cycle, say)
+        if ref["hist"][k] > 1e-11:
+            assert st["hist"][k] == pytest.approx(ref["hist"][k], rel=1e-8)
+        else:
+            assert st["hist"][k] <= 1e-11
     P.close()
 
 
 @pytest.mark.parametrize("path", sorted(PATHS))
 def test_solve_to_tolerance(case, path):
     name, g, cm, H = case
-    P = lamg.setup(g, coarsest_max=cm)
+    P = lamg.setup(g, coarsest_max=cm, cluster_rows=SCHED[path])
     b = gg.rhs(g, 2)
     x, st = P.solve(b, tol=1e-8, maxit=200, persistent=PATHS[path])
     assert st["relres"] <= 1e-8 and st["relres_true"] <= 2e-8, (name, st)
@@ -146,6 +156,56 @@ def test_solve_to_tolerance(case, path):
     assert rel(x, ref["x"]) <= 1e-9, name
     r = gg.laplacian_apply(g, x) - (b - b.mean())
     assert np.linalg.norm(r) <= 2e-8 * np.linalg.norm(b - b.mean())
+    P.close()
+
+
+def test_cluster_schedules_are_bitwise_identical(case):
+    # the cluster sub-cycle sums every row in the same order as the per-step kernels, so any
+    # split of the cycle between the two gives the same bits
+    name, g, cm, H = case
+    b = gg.rhs(g, 2)
+    # kernel forms by rule (autotune=0), so that every hierarchy uses the same forms
+    base = lamg.setup(g, coarsest_max=cm, cluster_rows=-1, autotune=0)
+    assert base.schedule()["cluster_from"] == -1
+    x0, st0 = base.solve(b, 1e-10, 200)
+    sizes = sorted({i["n"] for i in base.info}, reverse=True)
+    for rows in sizes[:4] + [10 ** 9]:
+        P = lamg.setup(g, coarsest_max=cm, cluster_rows=rows, autotune=0)
+        sch = P.schedule()
+        if rows > 0:
+            assert sch["cluster_from"] >= 0 and sch["cluster_ctas"] >= 4, (name, rows, sch)
+            assert all(i["n"] <= rows for i in P.info[sch["cluster_from"]:])
+        x, st = P.solve(b, 1e-10, 200)
+        assert st["iters"] == st0["iters"], (name, rows)
+        assert np.array_equal(x, x0), (name, rows, rel(x, x0))
+        P.close()
+    base.close()
+
+
+FORMS = {"csr_rule": dict(sell=-1, autotune=0), "sell_all": dict(sell=1, autotune=0),
+         "csr_1lane": dict(sell=-1, row_tpr=1, autotune=0), "csr_32lanes": dict(sell=-1, row_tpr=32, autotune=0),
+         "timed": dict(autotune=1)}
+
+
+@pytest.mark.parametrize("form", sorted(FORMS))
+def test_kernel_forms_match_oracle(case, form):
+    # lane groups of any width or one thread per row on the sliced copy: the same sums in
+    # another order, so every per-cycle iterate stays within the FP64 bar of the oracle
+    name, g, cm, H = case
+    P = lamg.import_levels(oracle_levels(H), **FORMS[form])
+    rng = np.random.default_rng(5)
+    r = rng.standard_normal(g.n)
+    r -= r.mean()
+    assert rel(P.cycle(r), H.cycle(r)) <= RTOL, (name, form, P.schedule()["forms"])
+    b = gg.rhs(g, 2)
+    ref = H.fcg(b, tol=1e-300, maxit=4, record=True)
+    x, st = P.solve(b, tol=1e-300, maxit=ref["iters"], allow_unconverged=True)
+    assert rel(x, ref["iterates"][-1]) <= RTOL, (name, form)
+    forms = P.schedule()["forms"]
+    if form == "csr_1lane":
+        assert all(f == (1, 1) for f in forms[:-1]), forms
+    if form == "sell_all" and name.startswith(("grid", "aniso")):
+        assert any(f[0] == 0 for f in forms), forms   # mesh levels have rows of <= 64 entries
     P.close()
 
 
@@ -169,6 +229,17 @@ def test_aniso1024_full_size():
     P = lamg.setup(g)
     x, st = P.solve(b, 1e-8, 200)
     assert st["relres_true"] <= 1e-8
+    # with the same kernel forms, a cluster sub-cycle computes the same bits as one kernel
+    # per step
+    Q = lamg.setup(g, cluster_rows=-1, autotune=0)
+    R = lamg.setup(g, cluster_rows=40000, autotune=0)
+    assert R.schedule()["cluster_from"] > 0
+    xq, stq = Q.solve(b, 1e-8, 200)
+    xr, str_ = R.solve(b, 1e-8, 200)
+    assert np.array_equal(xr, xq) and str_["iters"] == stq["iters"]
+    assert rel(xq, x) <= 1e-9
+    Q.close()
+    R.close()
     H = oracle.Hierarchy(g)
     assert [i["n"] for i in P.info] == [L["n"] for L in H.levels]
     ref = H.fcg(b, 1e-8, 200)

@@ -31,7 +31,7 @@ def test_served_results_equal_solo_results():
     reqs = mix()
     alone = []
     for g, b in reqs:
-        P = lamg.setup(g)
+        P = lamg.setup(g, autotune=0, cluster_rows=-1)   # the options a served setup runs with
         x, st = P.solve(b, 1e-8, 200)
         alone.append((x, st["iters"]))
         P.close()
@@ -49,20 +49,26 @@ def test_served_results_equal_solo_results():
     S.close()
 
 
-def test_requests_of_equal_size_share_the_device():
-    # eight equal requests submitted together: the setup threads finish them in groups within
-    # a fraction of a solve, and the executor must interleave their solves instead of running
-    # one request to completion before launching the next
-    reqs = [(gg.grid2d(128, 128, 1.0, 1e-3), None) for _ in range(8)]
-    reqs = [(g, gg.rhs(g, seed=40 + i)) for i, (g, _) in enumerate(reqs)]
-    S = lamg.Server(budget_bytes=2e9, max_inflight=8, setup_threads=4, tol=1e-10, maxit=200)
-    tickets = [S.submit(g, b) for g, b in reqs]
+def test_requests_arriving_during_a_solve_share_the_device():
+    # a long solve is on the device when four small requests arrive; their setups finish
+    # within milliseconds, and the executor must run their solves alongside the long one
+    # instead of waiting for it to finish
+    import time
+    big = gg.grid3d(64, 64, 64, "loguniform", seed=3)
+    S = lamg.Server(budget_bytes=4e9, max_inflight=8, setup_threads=4, tol=1e-12, maxit=400)
+    t_big = S.submit(big, gg.rhs(big, seed=50))
+    t0 = time.time()
+    while S.poll(t_big)["t_ready_ms"] == 0.0 and time.time() - t0 < 120:
+        time.sleep(0.0005)
+    small = [gg.grid2d(16, 16, 1.0, 0.1 * (i + 1)) for i in range(4)]
+    ts = [S.submit(g, gg.rhs(g, seed=60 + i)) for i, g in enumerate(small)]
     S.drain(120)
-    infos = [S.poll(t, g.n) for t, (g, _) in zip(tickets, reqs)]
-    assert all(i["done"] and i["status"] == 0 and i["relres_true"] <= 2e-10 for i in infos)
-    spans = [(i["t_ready_ms"], i["t_done_ms"]) for i in infos]
-    overlap = max(sum(1 for a, b in spans if a <= t < b) for t, _ in spans)
-    assert overlap >= 2, spans
+    ib = S.poll(t_big, big.n)
+    infos = [S.poll(t, g.n) for t, g in zip(ts, small)]
+    assert ib["done"] and ib["status"] == 0 and ib["relres_true"] <= 2e-12
+    assert all(i["done"] and i["status"] == 0 and i["relres_true"] <= 2e-12 for i in infos)
+    inside = [i for i in infos if ib["t_ready_ms"] < i["t_done_ms"] <= ib["t_done_ms"]]
+    assert inside, (ib["t_ready_ms"], ib["t_done_ms"], [(i["t_ready_ms"], i["t_done_ms"]) for i in infos])
     S.close()
 
 

@@ -36,7 +36,7 @@ def test_random_families_are_connected():
     import scipy.sparse as sp
     import scipy.sparse.csgraph as csg
     for g in [gg.chung_lu(3000, 2.1, 16, seed=1), gg.rgg(2000, 10, seed=1), gg.barabasi_albert(1500, 4, seed=1),
-              gg.random_connected(300, 100, seed=2)]:
+              gg.random_connected(300, 100, seed=2), gg.grid_with_hubs(20, 20, 3, 150, seed=1)]:
         check(g)
         A = sp.csr_matrix((g.w, g.ci, g.rp), shape=(g.n, g.n))
         assert csg.connected_components(A, directed=False)[0] == 1
@@ -50,3 +50,12 @@ def test_aniso_weights_and_rhs():
     B = gg.rhs(g, 2, k=3)
     assert B.shape == (256, 3) and np.allclose(B.sum(axis=0), 0, atol=1e-12)
     assert np.array_equal(gg.rhs(g, 2), gg.rhs(g, 2))
+
+
+def test_grid_with_hubs_degrees():
+    g = gg.grid_with_hubs(30, 30, 4, 200, seed=3)
+    check(g)
+    deg = np.diff(g.rp)
+    # each hub: its 200 grid neighbours plus the neighbouring hubs in the chain
+    assert list(deg[900:]) == [201, 202, 202, 201]
+    assert deg[:900].max() <= 4 + 4   # grid degree plus at most a few hub links per node
