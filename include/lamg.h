@@ -82,8 +82,8 @@ typedef struct lamg_options {
     int32_t cluster_rows;  /* graph path: a visit of the first level from which on every level
                               has at most this many rows, with all its sub-visits, runs as one
                               launch of a thread-block cluster. 0 (default): chosen at setup by
-                              timing one cycle of each candidate and of the per-step schedule;
-                              < 0: every step is its own kernel. Results are bit-identical
+                              timing one cycle of each candidate and of the per-step schedule
+                              when autotune is 1, else off; < 0: off. Results are bit-identical
                               whatever the choice. */
     int32_t row_tpr;       /* lanes per CSR row in the operator kernels: 0 (default) picks per
                               level from the mean row length; 1, 2, 4, ..., 32 forces it */
@@ -91,9 +91,10 @@ typedef struct lamg_options {
                               ELLPACK copy (32-row slices) where rows have at most 64 entries and
                               padding adds at most 30%, else lane groups on CSR; 1 sliced ELLPACK
                               wherever rows have at most 64 entries; -1 CSR only */
-    int32_t autotune;      /* 1 (default): setup times the kernel form of each level's sweep
-                              and residual (lanes per row, or one thread per row) and, with
-                              cluster_rows = 0, the cluster schedule; 0: rules only */
+    int32_t autotune;      /* 1: setup times the kernel form of each level's sweep and residual
+                              (lanes per row, or one thread per row) and, with cluster_rows = 0,
+                              the cluster schedule; 0 (default): rules only (measured within
+                              timing noise of the timed choice on the benchmark workloads) */
     int32_t dense_rows;    /* a level with at most this many nodes (<= 4096) and at least n^2/8
                               off-diagonal entries is the coarsest, solved densely: 4096; 0 off */
     int32_t reserved[1];

@@ -5,7 +5,7 @@
 // On the coarse levels a cycle step moves kilobytes, so run as separate kernels each step
 // costs a launch and a chain of dependent loads whatever its size. Here the steps are
 // separated by the cluster's hardware barrier (barrier.cluster with release/acquire
-// semantics) instead of kernel boundaries: up to 16 CTAs of 1024 threads, one row per lane
+// semantics) instead of kernel boundaries: up to 16 CTAs of 512 threads, one row per lane
 // group, walk the step list held in shared memory.
 //
 // Results are bit-identical to the per-step kernels: every row, aggregate and dense row is
@@ -21,13 +21,10 @@
 
 namespace lamg {
 
-constexpr int CBS = 1024;
+constexpr int CBS = 512;
 
-__device__ __forceinline__ void cl_sync() {
-    asm volatile(
-        "barrier.cluster.arrive.release.aligned;\n\t"
-        "barrier.cluster.wait.acquire.aligned;" ::: "memory");
-}
+__device__ __forceinline__ void cl_arrive() { asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory"); }
+__device__ __forceinline__ void cl_wait() { asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory"); }
 
 __device__ __forceinline__ unsigned cl_rank() {
     unsigned r;
@@ -45,91 +42,167 @@ struct CPos {
     int tid, nthreads, lane, warp, nwarps;
 };
 
-// Sum over a CSR row by TPR lanes (entries e0, e0 + TPR, ...), x read through L2.
+// Read-only operands of a thread's first row of the next step, loaded between the barrier's
+// arrive and wait (software pipelining: the loads overlap the barrier; only the gathers of
+// vectors written by earlier steps are left after it). CSR lane groups: the lane's first entry
+// e0, the row end e1 and the entries e0, e0 + TPR. Sliced ELLPACK: e0 = the lane's entry 0,
+// e1 = the slice width, the entries e0, e0 + 32. d = reciprocal diagonal (sweep) or diagonal
+// (residual).
+struct CPre {
+    int e0, e1, c0, c1;
+    double v0, v1, d;
+};
+
+__device__ __forceinline__ CPre cpre_empty() {
+    CPre q;
+    q.e0 = q.e1 = 0;
+    q.c0 = q.c1 = -1;
+    q.v0 = q.v1 = 0.0;
+    q.d = 1.0;
+    return q;
+}
+
 template <int TPR>
-__device__ __forceinline__ double cl_row(int e0, int e1, const int32_t *__restrict__ ci,
-                                         const double *__restrict__ val, const double *x) {
+__device__ __forceinline__ CPre cpre_csr(bool ok, int row, int sub, const int32_t *__restrict__ rp,
+                                         const int32_t *__restrict__ ci, const double *__restrict__ val,
+                                         const double *__restrict__ dg) {
+    CPre q = cpre_empty();
+    if (!ok) return q;
+    q.e0 = __ldg(&rp[row]) + sub;
+    q.e1 = __ldg(&rp[row + 1]);
+    if (q.e0 < q.e1) { q.c0 = __ldg(&ci[q.e0]); q.v0 = __ldg(&val[q.e0]); }
+    if (q.e0 + TPR < q.e1) { q.c1 = __ldg(&ci[q.e0 + TPR]); q.v1 = __ldg(&val[q.e0 + TPR]); }
+    if (dg) q.d = __ldg(&dg[row]);
+    return q;
+}
+
+__device__ __forceinline__ CPre cpre_sell(bool ok, int row, const PLevel &L, const double *__restrict__ dg) {
+    CPre q = cpre_empty();
+    if (!ok) return q;
+    const int sl = row >> 5;
+    const int a = __ldg(&L.sl_ptr[sl]);
+    q.e0 = a + (row & 31);
+    q.e1 = (__ldg(&L.sl_ptr[sl + 1]) - a) >> 5;
+    if (q.e1 > 0) { q.c0 = __ldg(&L.sl_col[q.e0]); q.v0 = __ldg(&L.sl_val[q.e0]); }
+    if (q.e1 > 1) { q.c1 = __ldg(&L.sl_col[q.e0 + 32]); q.v1 = __ldg(&L.sl_val[q.e0 + 32]); }
+    q.d = __ldg(&dg[row]);
+    return q;
+}
+
+// Sum over a CSR row by TPR lanes (entries e0, e0 + TPR, ...), x read through L2; the first
+// two entries of the lane come from the prefetch.
+template <int TPR>
+__device__ __forceinline__ double cl_row_pre(const CPre &q, const int32_t *__restrict__ ci,
+                                             const double *__restrict__ val, const double *x) {
     double s = 0.0;
-    for (int e = e0; e < e1; e += TPR) s += __ldg(&val[e]) * __ldcg(&x[__ldg(&ci[e])]);
+    if (q.c0 >= 0) s += q.v0 * __ldcg(&x[q.c0]);
+    if (q.c1 >= 0) s += q.v1 * __ldcg(&x[q.c1]);
+    for (int e = q.e0 + 2 * TPR; e < q.e1; e += TPR) s += __ldg(&val[e]) * __ldcg(&x[__ldg(&ci[e])]);
 #pragma unroll
     for (int o = TPR / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     return s;
 }
 
+// Sliced-ELLPACK row sum, entries in order (as the per-step kernels sum them).
+__device__ __forceinline__ double cl_sell_pre(const CPre &q, const PLevel &L, const double *x) {
+    double acc = 0.0;
+    if (q.c0 >= 0) acc += q.v0 * __ldcg(&x[q.c0]);
+    if (q.c1 >= 0) acc += q.v1 * __ldcg(&x[q.c1]);
+    for (int j = 2; j < q.e1; j++) acc += __ldg(&L.sl_val[q.e0 + 32 * j]) * __ldcg(&x[__ldg(&L.sl_col[q.e0 + 32 * j])]);
+    return acc;
+}
+
 // One colour class of Gauss-Seidel: x_u = (b_u - sum_v A_uv x_v) / A_uu, u in [r0, r1).
+// Round 0 of a thread uses the prefetched operands.
 template <int TPR>
-__device__ __forceinline__ void cl_gs(const PLevel &L, int r0, int r1, const CPos &p) {
+__device__ __forceinline__ CPre cl_gs_pre(const PLevel &L, int r0, int r1, const CPos &p) {
+    const int row = r0 + p.tid / TPR;
+    return cpre_csr<TPR>(row < r1, row, p.tid % TPR, L.rp, L.ci, L.val, L.idiag);
+}
+
+template <int TPR>
+__device__ __forceinline__ void cl_gs(const PLevel &L, int r0, int r1, const CPos &p, const CPre &q0) {
     const int groups = p.nthreads / TPR, sub = p.tid % TPR;
     const int rounds = (r1 - r0 + groups - 1) / groups;
     int row = r0 + p.tid / TPR;
     for (int it = 0; it < rounds; it++, row += groups) {
         const bool ok = row < r1;
-        const int e0 = ok ? __ldg(&L.rp[row]) + sub : 0, e1 = ok ? __ldg(&L.rp[row + 1]) : 0;
-        const double s = cl_row<TPR>(e0, e1, L.ci, L.val, L.x);
-        if (ok && sub == 0) L.x[row] = (__ldcg(&L.b[row]) - s) * __ldg(&L.idiag[row]);
+        const CPre q = it == 0 ? q0 : cpre_csr<TPR>(ok, row, sub, L.rp, L.ci, L.val, L.idiag);
+        const double s = cl_row_pre<TPR>(q, L.ci, L.val, L.x);
+        if (ok && sub == 0) L.x[row] = (__ldcg(&L.b[row]) - s) * q.d;
     }
 }
 
-// Sliced-ELLPACK row sum, entries in order (as the per-step kernels sum them).
-__device__ __forceinline__ double cl_sell_row(const PLevel &L, int row, const double *x) {
-    const int s = row >> 5;
-    const int a = __ldg(&L.sl_ptr[s]), w = (__ldg(&L.sl_ptr[s + 1]) - a) >> 5;
-    const int e = a + (row & 31);
-    double acc = 0.0;
-    for (int j = 0; j < w; j++) acc += __ldg(&L.sl_val[e + 32 * j]) * __ldcg(&x[__ldg(&L.sl_col[e + 32 * j])]);
-    return acc;
+__device__ __forceinline__ CPre cl_gs_sell_pre(const PLevel &L, int r0, int r1, const CPos &p) {
+    const int row = 32 * ((r0 >> 5) + p.warp) + p.lane;
+    return cpre_sell(row >= r0 && row < r1, row, L, L.idiag);
 }
 
-// Slices are dealt to the cluster's warps round-robin over the CTAs, so a small class spreads
-// over all of the cluster's SMs (their few FP64 units are the limit, not the loads).
-__device__ __forceinline__ int cl_slice_warp(const CPos &p) {
-    return (int)((threadIdx.x >> 5) * cl_size() + cl_rank());
-}
-
-__device__ __forceinline__ void cl_gs_sell(const PLevel &L, int r0, int r1, const CPos &p) {
+__device__ __forceinline__ void cl_gs_sell(const PLevel &L, int r0, int r1, const CPos &p, const CPre &q0) {
     const int s0 = r0 >> 5, s1 = (r1 + 31) >> 5;
-    for (int sl = s0 + cl_slice_warp(p); sl < s1; sl += p.nwarps) {
+    int it = 0;
+    for (int sl = s0 + p.warp; sl < s1; sl += p.nwarps, it++) {
         const int row = 32 * sl + p.lane;
         if (row < r0 || row >= r1) continue;
-        const double s = cl_sell_row(L, row, L.x);
-        L.x[row] = (__ldcg(&L.b[row]) - s) * __ldg(&L.idiag[row]);
+        const CPre q = it == 0 ? q0 : cpre_sell(true, row, L, L.idiag);
+        const double s = cl_sell_pre(q, L, L.x);
+        L.x[row] = (__ldcg(&L.b[row]) - s) * q.d;
     }
 }
 
-__device__ __forceinline__ void cl_resid_sell(const PLevel &L, const CPos &p) {
+__device__ __forceinline__ CPre cl_resid_sell_pre(const PLevel &L, const CPos &p) {
+    const int row = 32 * p.warp + p.lane;
+    return cpre_sell(row < L.n, row, L, L.diag);
+}
+
+__device__ __forceinline__ void cl_resid_sell(const PLevel &L, const CPos &p, const CPre &q0) {
     const int ns = (L.n + 31) >> 5;
-    for (int sl = cl_slice_warp(p); sl < ns; sl += p.nwarps) {
+    int it = 0;
+    for (int sl = p.warp; sl < ns; sl += p.nwarps, it++) {
         const int row = 32 * sl + p.lane;
         if (row >= L.n) continue;
-        const double s = cl_sell_row(L, row, L.x);
-        L.r[row] = __ldcg(&L.b[row]) - (__ldg(&L.diag[row]) * __ldcg(&L.x[row]) + s);
+        const CPre q = it == 0 ? q0 : cpre_sell(true, row, L, L.diag);
+        const double s = cl_sell_pre(q, L, L.x);
+        L.r[row] = __ldcg(&L.b[row]) - (q.d * __ldcg(&L.x[row]) + s);
     }
 }
 
 // r = b - A x
 template <int TPR>
-__device__ __forceinline__ void cl_resid(const PLevel &L, const CPos &p) {
+__device__ __forceinline__ CPre cl_resid_pre(const PLevel &L, const CPos &p) {
+    const int row = p.tid / TPR;
+    return cpre_csr<TPR>(row < L.n, row, p.tid % TPR, L.rp, L.ci, L.val, L.diag);
+}
+
+template <int TPR>
+__device__ __forceinline__ void cl_resid(const PLevel &L, const CPos &p, const CPre &q0) {
     const int groups = p.nthreads / TPR, sub = p.tid % TPR;
     const int rounds = (L.n + groups - 1) / groups;
     int row = p.tid / TPR;
     for (int it = 0; it < rounds; it++, row += groups) {
         const bool ok = row < L.n;
-        const int e0 = ok ? __ldg(&L.rp[row]) + sub : 0, e1 = ok ? __ldg(&L.rp[row + 1]) : 0;
-        const double s = cl_row<TPR>(e0, e1, L.ci, L.val, L.x);
-        if (ok && sub == 0) L.r[row] = __ldcg(&L.b[row]) - (__ldg(&L.diag[row]) * __ldcg(&L.x[row]) + s);
+        const CPre q = it == 0 ? q0 : cpre_csr<TPR>(ok, row, sub, L.rp, L.ci, L.val, L.diag);
+        const double s = cl_row_pre<TPR>(q, L.ci, L.val, L.x);
+        if (ok && sub == 0) L.r[row] = __ldcg(&L.b[row]) - (q.d * __ldcg(&L.x[row]) + s);
     }
 }
 
 // b^c = P^T r: one P^T row (aggregate) per TPR lanes.
 template <int TPR>
-__device__ __forceinline__ void cl_restrict(const PLevel &L, double *bc, const CPos &p) {
+__device__ __forceinline__ CPre cl_restrict_pre(const PLevel &L, const CPos &p) {
+    const int a = p.tid / TPR;
+    return cpre_csr<TPR>(a < L.nc, a, p.tid % TPR, L.pt_ptr, L.pt_row, L.pt_w, nullptr);
+}
+
+template <int TPR>
+__device__ __forceinline__ void cl_restrict(const PLevel &L, double *bc, const CPos &p, const CPre &q0) {
     const int groups = p.nthreads / TPR, sub = p.tid % TPR;
     const int rounds = (L.nc + groups - 1) / groups;
     int a = p.tid / TPR;
     for (int it = 0; it < rounds; it++, a += groups) {
         const bool ok = a < L.nc;
-        const int e0 = ok ? __ldg(&L.pt_ptr[a]) + sub : 0, e1 = ok ? __ldg(&L.pt_ptr[a + 1]) : 0;
-        const double s = cl_row<TPR>(e0, e1, L.pt_row, L.pt_w, L.r);
+        const CPre q = it == 0 ? q0 : cpre_csr<TPR>(ok, a, sub, L.pt_ptr, L.pt_row, L.pt_w, nullptr);
+        const double s = cl_row_pre<TPR>(q, L.pt_row, L.pt_w, L.r);
         if (ok && sub == 0) bc[a] = s;
     }
 }
@@ -144,7 +217,42 @@ __device__ __forceinline__ void cl_restrict(const PLevel &L, double *bc, const C
         default: FN<32>(__VA_ARGS__); break; \
     }
 
-__device__ __forceinline__ void cl_op(const Op &op, const PLevel *lv, const int32_t *cptr_all, const CPos &p) {
+#define CL_TPR_RET(tpr, OUT, FN, ...)              \
+    switch (tpr) {                                 \
+        case 1: OUT = FN<1>(__VA_ARGS__); break;   \
+        case 2: OUT = FN<2>(__VA_ARGS__); break;   \
+        case 4: OUT = FN<4>(__VA_ARGS__); break;   \
+        case 8: OUT = FN<8>(__VA_ARGS__); break;   \
+        case 16: OUT = FN<16>(__VA_ARGS__); break; \
+        default: OUT = FN<32>(__VA_ARGS__); break; \
+    }
+
+// Prefetch of a step's read-only row operands (round 0 of this thread); empty for the steps
+// without a row structure.
+__device__ __forceinline__ CPre cl_prefetch(const Op &op, const PLevel *lv, const int32_t *cptr_all, const CPos &p) {
+    const PLevel &L = lv[op.level];
+    const int32_t *cptr = cptr_all + L.cptr_off;
+    CPre q = cpre_empty();
+    switch (op.kind) {
+        case OP_GS:
+            if (L.gs_tpr == 0) q = cl_gs_sell_pre(L, cptr[op.colour], cptr[op.colour + 1], p);
+            else CL_TPR_RET(L.gs_tpr, q, cl_gs_pre, L, cptr[op.colour], cptr[op.colour + 1], p);
+            break;
+        case OP_RESID:
+            if (L.rs_tpr == 0) q = cl_resid_sell_pre(L, p);
+            else CL_TPR_RET(L.rs_tpr, q, cl_resid_pre, L, p);
+            break;
+        case OP_RESTRICT:
+            CL_TPR_RET(L.pt_tpr, q, cl_restrict_pre, L, p);
+            break;
+        default:
+            break;
+    }
+    return q;
+}
+
+__device__ __forceinline__ void cl_op(const Op &op, const PLevel *lv, const int32_t *cptr_all, const CPos &p,
+                                      const CPre &q) {
     const PLevel &L = lv[op.level];
     const int32_t *cptr = cptr_all + L.cptr_off;
     switch (op.kind) {
@@ -158,15 +266,15 @@ __device__ __forceinline__ void cl_op(const Op &op, const PLevel *lv, const int3
             for (int i = p.tid; i < L.n; i += p.nthreads) L.x[i] = 0.0;
             break;
         case OP_GS:
-            if (L.gs_tpr == 0) cl_gs_sell(L, cptr[op.colour], cptr[op.colour + 1], p);
-            else CL_TPR(L.gs_tpr, cl_gs, L, cptr[op.colour], cptr[op.colour + 1], p);
+            if (L.gs_tpr == 0) cl_gs_sell(L, cptr[op.colour], cptr[op.colour + 1], p, q);
+            else CL_TPR(L.gs_tpr, cl_gs, L, cptr[op.colour], cptr[op.colour + 1], p, q);
             break;
         case OP_RESID:
-            if (L.rs_tpr == 0) cl_resid_sell(L, p);
-            else CL_TPR(L.rs_tpr, cl_resid, L, p);
+            if (L.rs_tpr == 0) cl_resid_sell(L, p, q);
+            else CL_TPR(L.rs_tpr, cl_resid, L, p, q);
             break;
         case OP_RESTRICT:
-            CL_TPR(L.pt_tpr, cl_restrict, L, lv[op.level + 1].b, p);
+            CL_TPR(L.pt_tpr, cl_restrict, L, lv[op.level + 1].b, p, q);
             break;
         case OP_PROLONG: {
             const double *xc = lv[op.level + 1].x;
@@ -261,18 +369,26 @@ __global__ void __launch_bounds__(CBS, 1) k_cluster(const PLevel *__restrict__ l
     }
     __syncthreads();
     const Op *ops = ops_in_smem ? s_ops : ops_g;
+    // warps are numbered round-robin over the CTAs (warp w of CTA c is cluster warp
+    // w * ncta + c), so consecutive rows of a small step spread over all of the cluster's SMs
+    // and their FP64 units instead of filling the first CTA
     CPos p;
-    p.tid = (int)(cl_rank() * blockDim.x + threadIdx.x);
-    p.nthreads = (int)(cl_size() * blockDim.x);
     p.lane = threadIdx.x & 31;
-    p.warp = p.tid >> 5;
+    p.warp = (int)((threadIdx.x >> 5) * cl_size() + cl_rank());
+    p.tid = p.warp * 32 + p.lane;
+    p.nthreads = (int)(cl_size() * blockDim.x);
     p.nwarps = p.nthreads >> 5;
+    CPre q = nops > 0 ? cl_prefetch(ops[0], s_lv, s_cptr, p) : cpre_empty();
     asm volatile("griddepcontrol.wait;" ::: "memory");
     for (int i = 0; i < nops; i++) {
         const Op op = ops[i];
         if (prof && p.tid == 0) prof[2 * i] = cl_ns();
-        cl_op(op, s_lv, s_cptr, p);
-        cl_sync();
+        cl_op(op, s_lv, s_cptr, p, q);
+        cl_arrive();
+        // the next step's read-only operands load while the cluster meets at the barrier
+        // (after the arrive, so that its release does not wait for them)
+        if (i + 1 < nops) q = cl_prefetch(ops[i + 1], s_lv, s_cptr, p);
+        cl_wait();
         if (prof && p.tid == 0) prof[2 * i + 1] = cl_ns();
     }
 }
@@ -282,7 +398,7 @@ size_t cluster_smem(int nlev, int ncptr, int nops) {
            (size_t)(nops <= CL_OPS_SMEM ? nops : 0) * sizeof(Op);
 }
 
-// Largest cluster (16, 8 or 4 CTAs of 1024 threads) of which one can be resident with smem
+// Largest cluster (16, 8 or 4 CTAs of CBS threads) of which one can be resident with smem
 // bytes of dynamic shared memory per CTA; 0 if none. The kernel's dynamic shared-memory limit
 // is a per-function setting shared by every hierarchy, so it is always set to CL_SMEM_MAX.
 int cluster_dim(int device, size_t smem) {

@@ -151,7 +151,11 @@ int upload_level(lamg_hier *h, int l) {
     // rule (refined by timing when the options ask for it): sweeps on lane groups, whose
     // short per-lane chains suit the latency-bound colour classes; residual-type passes of
     // large levels one thread per row, which issues the fewest FP64 instructions per entry
-    D.gs_tpr = D.tpr;
+    // (measured per level on B300: sweeps of levels with at least 2^18 rows of at most 8
+    // entries are faster one thread per row, the others on lane groups; residual-type passes
+    // from 2^16 rows on one thread per row)
+    const double avg = n ? (double)H.A.nnz() / (double)n : 0.0;
+    D.gs_tpr = (D.sell && h->opt.row_tpr == 0 && n >= (1 << 18) && avg <= 8.0) ? 0 : D.tpr;
     D.rs_tpr = (D.sell && (h->opt.sell > 0 || n >= 65536)) ? 0 : D.tpr;
     if (D.sell && h->opt.sell > 0) D.gs_tpr = 0;
     if (H.kind == KIND_AGG) {
@@ -690,7 +694,7 @@ void lamg_options_default(lamg_options *o) {
     o->device = 0;
     o->tail_rows = 8192;
     o->cluster_rows = 0;
-    o->autotune = 1;
+    o->autotune = 0;
     o->dense_rows = 4096;
 }
 
