@@ -269,6 +269,22 @@ int lamg_op_list(const lamg_hier *h, int32_t *out, int64_t cap, int64_t *count);
  * int64 entries; *count = entries written. Errors: INVALID. */
 int lamg_schedule_info(const lamg_hier *h, int64_t *out, int64_t cap, int64_t *count);
 
+/* Solve G independent systems L_g phi_g = b_g (Eq. 1), each on its own hierarchy, with one
+ * kernel launch: one thread-block cluster per system runs that system's whole flexible-CG solve
+ * (projection of b, every cycle of Section 2, the stopping test, the true residual), with
+ * deterministic cluster-scope reductions; the clusters share nothing. Meant for many small
+ * graphs, whose solves would otherwise be a few hundred small launches each. A hierarchy the
+ * cluster kernel cannot take (FP32 cycle, rows longer than 256 entries, no cluster launch on the
+ * device, level tables over the shared-memory limit) is solved by lamg_solve after the launch.
+ * No counterpart in the paper (it batches solves of the same method).
+ * hs, b, phi: G entries; b[g], phi[g] of hs[g]'s size, host pointers, or device pointers with
+ * LAMG_DEVICE_PTRS; all hierarchies on one device; the work goes to so->stream (0: the first
+ * hierarchy's stream). st: NULL or G entries (solve_ms and kernel_ms are the whole launch).
+ * Returns LAMG_OK when every system converged, LAMG_ERR_NOT_CONVERGED when one did not (all
+ * stats valid). Errors: INVALID, CUDA, TIMEOUT. */
+int lamg_solve_many(int32_t G, lamg_hier *const *hs, const double *const *b, double *const *phi,
+                    const lamg_solve_opts *so, lamg_stats *st);
+
 /* Per-step device time of one cycle (r = 0) with the steps on levels >= from_level run as
  * cluster launches (from_level < 0: none), outside any graph: out receives 3 int64 per step
  * (step index, 1 if the step ran inside a cluster launch, nanoseconds). A step inside a

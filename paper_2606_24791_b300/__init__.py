@@ -116,6 +116,7 @@ def lib():
         L.lamg_server_destroy.restype = None
         L.lamg_op_list.argtypes = [P, P, C.c_int64, C.POINTER(C.c_int64)]
         L.lamg_schedule_info.argtypes = [P, P, C.c_int64, C.POINTER(C.c_int64)]
+        L.lamg_solve_many.argtypes = [C.c_int32, P, P, P, C.POINTER(SolveOpts), P]
         L.lamg_profile_schedule.argtypes = [P, C.c_int32, P, C.c_int64, C.POINTER(C.c_int64)]
         _lib = L
     return _lib
@@ -312,6 +313,32 @@ def _stats(st: Stats, hist) -> dict:
     if hist is not None:
         d["hist"] = hist[: st.iters + 1].copy()
     return d
+
+
+def solve_many(hs: list, bs: list, tol: float = 1e-8, maxit: int = 100, hist: bool = False,
+               allow_unconverged: bool = False):
+    """lamg_solve_many: G independent systems, one hierarchy each, in one kernel launch (one
+    thread-block cluster per system). Returns ([phi_g], [stats_g])."""
+    G = len(hs)
+    if G != len(bs) or G == 0:
+        raise ValueError("one right-hand side per hierarchy")
+    barr = [_c(b, np.float64) for b in bs]
+    for h, b in zip(hs, barr):
+        if b.shape != (h.n,):
+            raise ValueError("right-hand side size")
+    xs = [np.zeros(h.n) for h in hs]
+    hp = (C.c_void_p * G)(*[h._h for h in hs])
+    bp = (C.c_void_p * G)(*[b.ctypes.data for b in barr])
+    xp = (C.c_void_p * G)(*[x.ctypes.data for x in xs])
+    so = SolveOpts(tol, maxit, 0, None)
+    st = (Stats * G)()
+    hbuf = [np.zeros(maxit + 1) for _ in range(G)] if hist else [None] * G
+    for j in range(G):
+        if hbuf[j] is not None:
+            st[j].hist = hbuf[j].ctypes.data
+    rc = lib().lamg_solve_many(G, hp, bp, xp, C.byref(so), st)
+    _check(rc, "lamg_solve_many", (LAMG_OK, 5) if allow_unconverged else (LAMG_OK,))
+    return xs, [_stats(st[j], hbuf[j]) for j in range(G)]
 
 
 class Server:

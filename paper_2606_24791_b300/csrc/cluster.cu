@@ -339,7 +339,7 @@ __device__ __forceinline__ void cl_op(const Op &op, const PLevel *lv, const int3
     }
 }
 
-// Steps ops[0 .. nops) on the levels of lv (device tables), run by one cluster.
+
 // prof (optional): CTA 0 records %globaltimer before step i (prof[2i]) and after its barrier
 // (prof[2i + 1]).
 __device__ __forceinline__ unsigned long long cl_ns() {
@@ -348,27 +348,44 @@ __device__ __forceinline__ unsigned long long cl_ns() {
     return t;
 }
 
-__global__ void __launch_bounds__(CBS, 1) k_cluster(const PLevel *__restrict__ lv_g, int nlev,
-                                                    const int32_t *__restrict__ cptr_g, int ncptr,
-                                                    const Op *__restrict__ ops_g, int nops,
-                                                    unsigned long long *prof) {
-    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-    extern __shared__ __align__(16) unsigned char smem[];
+// The step loop: step i, barrier; the operands of step i + 1 are prefetched between the
+// barrier's arrive and wait (after the arrive, so that its release does not wait for them).
+__device__ __forceinline__ void cl_steps(const Op *ops, int nops, const PLevel *lv, const int32_t *cptr,
+                                         const CPos &p, CPre q, unsigned long long *prof) {
+    for (int i = 0; i < nops; i++) {
+        const Op op = ops[i];
+        if (prof && p.tid == 0) prof[2 * i] = cl_ns();
+        cl_op(op, lv, cptr, p, q);
+        cl_arrive();
+        if (i + 1 < nops) q = cl_prefetch(ops[i + 1], lv, cptr, p);
+        cl_wait();
+        if (prof && p.tid == 0) prof[2 * i + 1] = cl_ns();
+    }
+}
+
+// Level tables of one hierarchy into this CTA's shared memory; returns the step list (shared
+// memory when it has at most CL_OPS_SMEM steps, else global).
+__device__ __forceinline__ const Op *cl_load_tables(unsigned char *smem, const PLevel *lv_g, int nlev,
+                                                    const int32_t *cptr_g, int ncptr, const Op *ops_g,
+                                                    int nops, PLevel **s_lv_out, int32_t **s_cptr_out) {
     PLevel *s_lv = reinterpret_cast<PLevel *>(smem);
     int32_t *s_cptr = reinterpret_cast<int32_t *>(s_lv + nlev);
     Op *s_ops = reinterpret_cast<Op *>(s_cptr + ((ncptr + 3) & ~3));
     const bool ops_in_smem = nops <= CL_OPS_SMEM;
-    {
-        const long long *src = reinterpret_cast<const long long *>(lv_g);
-        long long *dst = reinterpret_cast<long long *>(s_lv);
-        const int nw = (int)(nlev * sizeof(PLevel) / sizeof(long long));
-        for (int i = threadIdx.x; i < nw; i += blockDim.x) dst[i] = src[i];
-        for (int i = threadIdx.x; i < ncptr; i += blockDim.x) s_cptr[i] = cptr_g[i];
-        if (ops_in_smem)
-            for (int i = threadIdx.x; i < nops; i += blockDim.x) s_ops[i] = ops_g[i];
-    }
+    const long long *src = reinterpret_cast<const long long *>(lv_g);
+    long long *dst = reinterpret_cast<long long *>(s_lv);
+    const int nw = (int)(nlev * sizeof(PLevel) / sizeof(long long));
+    for (int i = threadIdx.x; i < nw; i += blockDim.x) dst[i] = src[i];
+    for (int i = threadIdx.x; i < ncptr; i += blockDim.x) s_cptr[i] = cptr_g[i];
+    if (ops_in_smem)
+        for (int i = threadIdx.x; i < nops; i += blockDim.x) s_ops[i] = ops_g[i];
     __syncthreads();
-    const Op *ops = ops_in_smem ? s_ops : ops_g;
+    *s_lv_out = s_lv;
+    *s_cptr_out = s_cptr;
+    return ops_in_smem ? s_ops : ops_g;
+}
+
+__device__ __forceinline__ CPos cl_pos() {
     // warps are numbered round-robin over the CTAs (warp w of CTA c is cluster warp
     // w * ncta + c), so consecutive rows of a small step spread over all of the cluster's SMs
     // and their FP64 units instead of filling the first CTA
@@ -378,19 +395,254 @@ __global__ void __launch_bounds__(CBS, 1) k_cluster(const PLevel *__restrict__ l
     p.tid = p.warp * 32 + p.lane;
     p.nthreads = (int)(cl_size() * blockDim.x);
     p.nwarps = p.nthreads >> 5;
+    return p;
+}
+
+// Steps ops[0 .. nops) on the levels of lv (device tables), run by one cluster.
+__global__ void __launch_bounds__(CBS, 1) k_cluster(const PLevel *__restrict__ lv_g, int nlev,
+                                                    const int32_t *__restrict__ cptr_g, int ncptr,
+                                                    const Op *__restrict__ ops_g, int nops,
+                                                    unsigned long long *prof) {
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    extern __shared__ __align__(16) unsigned char smem[];
+    PLevel *s_lv;
+    int32_t *s_cptr;
+    const Op *ops = cl_load_tables(smem, lv_g, nlev, cptr_g, ncptr, ops_g, nops, &s_lv, &s_cptr);
+    const CPos p = cl_pos();
     CPre q = nops > 0 ? cl_prefetch(ops[0], s_lv, s_cptr, p) : cpre_empty();
     asm volatile("griddepcontrol.wait;" ::: "memory");
-    for (int i = 0; i < nops; i++) {
-        const Op op = ops[i];
-        if (prof && p.tid == 0) prof[2 * i] = cl_ns();
-        cl_op(op, s_lv, s_cptr, p, q);
-        cl_arrive();
-        // the next step's read-only operands load while the cluster meets at the barrier
-        // (after the arrive, so that its release does not wait for them)
-        if (i + 1 < nops) q = cl_prefetch(ops[i + 1], s_lv, s_cptr, p);
-        cl_wait();
-        if (prof && p.tid == 0) prof[2 * i + 1] = cl_ns();
+    cl_steps(ops, nops, s_lv, s_cptr, p, q, prof);
+}
+
+// ------------------------------------------------------------ whole solves, one cluster each
+
+// Deterministic all-reduce of NV doubles over the cluster: a fixed-order block sum per CTA,
+// the CTA totals through a global partial buffer (alternating halves), then every thread adds
+// them in CTA-rank order, so every thread of the cluster holds the same bits.
+template <int NV>
+__device__ __forceinline__ void cl_allreduce(double (&v)[NV], double *part, unsigned &phase) {
+    block_sum<NV>(v);
+    double *buf = part + (size_t)(phase & 1u) * (RED_NV * 16);
+    phase++;
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int k = 0; k < NV; k++) __stcg(&buf[k * 16 + cl_rank()], v[k]);
     }
+    cl_arrive();
+    cl_wait();
+    const int nc = (int)cl_size();
+#pragma unroll
+    for (int k = 0; k < NV; k++) {
+        double s = 0.0;
+        for (int c = 0; c < nc; c++) s += __ldcg(&buf[k * 16 + c]);
+        v[k] = s;
+    }
+}
+
+// q = A p and the partial p . q of this thread's rows (level-0 form, lane groups or sliced).
+template <int TPR>
+__device__ __forceinline__ double cl_spmv_part(const PLevel &F, const double *pv, double *qv, const CPos &p) {
+    const int groups = p.nthreads / TPR, sub = p.tid % TPR;
+    const int rounds = (F.n + groups - 1) / groups;
+    double acc = 0.0;
+    int row = p.tid / TPR;
+    for (int it = 0; it < rounds; it++, row += groups) {
+        const bool ok = row < F.n;
+        const CPre q = cpre_csr<TPR>(ok, row, sub, F.rp, F.ci, F.val, F.diag);
+        const double s = cl_row_pre<TPR>(q, F.ci, F.val, pv);
+        if (ok && sub == 0) {
+            const double pi = __ldcg(&pv[row]);
+            const double qi = q.d * pi + s;
+            __stcg(&qv[row], qi);
+            acc += pi * qi;
+        }
+    }
+    return acc;
+}
+
+__device__ __forceinline__ double cl_spmv_part_sell(const PLevel &F, const double *pv, double *qv, const CPos &p) {
+    const int ns = (F.n + 31) >> 5;
+    double acc = 0.0;
+    for (int sl = p.warp; sl < ns; sl += p.nwarps) {
+        const int row = 32 * sl + p.lane;
+        if (row >= F.n) continue;
+        const CPre q = cpre_sell(true, row, F, F.diag);
+        const double s = cl_sell_pre(q, F, pv);
+        const double pi = __ldcg(&pv[row]);
+        const double qi = q.d * pi + s;
+        __stcg(&qv[row], qi);
+        acc += pi * qi;
+    }
+    return acc;
+}
+
+// ||b - A x||^2 partial of this thread's rows.
+template <int TPR>
+__device__ __forceinline__ double cl_rr_part(const PLevel &F, const double *x, const double *b, const CPos &p) {
+    const int groups = p.nthreads / TPR, sub = p.tid % TPR;
+    const int rounds = (F.n + groups - 1) / groups;
+    double acc = 0.0;
+    int row = p.tid / TPR;
+    for (int it = 0; it < rounds; it++, row += groups) {
+        const bool ok = row < F.n;
+        const CPre q = cpre_csr<TPR>(ok, row, sub, F.rp, F.ci, F.val, F.diag);
+        const double s = cl_row_pre<TPR>(q, F.ci, F.val, x);
+        if (ok && sub == 0) {
+            const double ri = __ldcg(&b[row]) - (q.d * __ldcg(&x[row]) + s);
+            acc += ri * ri;
+        }
+    }
+    return acc;
+}
+
+__device__ __forceinline__ double cl_rr_part_sell(const PLevel &F, const double *x, const double *b, const CPos &p) {
+    const int ns = (F.n + 31) >> 5;
+    double acc = 0.0;
+    for (int sl = p.warp; sl < ns; sl += p.nwarps) {
+        const int row = 32 * sl + p.lane;
+        if (row >= F.n) continue;
+        const CPre q = cpre_sell(true, row, F, F.diag);
+        const double s = cl_sell_pre(q, F, x);
+        const double ri = __ldcg(&b[row]) - (q.d * __ldcg(&x[row]) + s);
+        acc += ri * ri;
+    }
+    return acc;
+}
+
+// One cycle (the static step list), then the flexible-CG update of z = the level-0 iterate:
+// z -= mean(z); beta = r.(z - zold) / rz; rz = r.z; p = z + beta p; zold = z.
+__device__ __forceinline__ void cl_cycle_and_tail(const MGraph &G, const Op *ops, const PLevel *lv,
+                                                  const int32_t *cptr, const CPos &p, unsigned &phase,
+                                                  double &rz) {
+    const int n = G.n0;
+    CPre q = G.nops > 0 ? cl_prefetch(ops[0], lv, cptr, p) : cpre_empty();
+    cl_steps(ops, G.nops, lv, cptr, p, q, nullptr);
+    double *z = lv[0].x;
+    double s1[1] = {0.0};
+    for (int i = p.tid; i < n; i += p.nthreads) s1[0] += __ldcg(&z[i]);
+    cl_allreduce<1>(s1, G.part, phase);
+    const double mean = s1[0] / (double)n;
+    double s2[2] = {0.0, 0.0};
+    for (int i = p.tid; i < n; i += p.nthreads) {
+        const double zi = __ldcg(&z[i]) - mean;
+        __stcg(&z[i], zi);
+        const double ri = __ldcg(&G.r[i]);
+        s2[0] += ri * (zi - __ldcg(&G.zold[i]));
+        s2[1] += ri * zi;
+    }
+    cl_allreduce<2>(s2, G.part, phase);
+    const double beta = rz != 0.0 ? s2[0] / rz : 0.0;
+    rz = s2[1];
+    for (int i = p.tid; i < n; i += p.nthreads) {
+        const double zi = __ldcg(&z[i]);
+        __stcg(&G.p[i], zi + beta * __ldcg(&G.p[i]));
+        __stcg(&G.zold[i], zi);
+    }
+    cl_arrive();
+    cl_wait();
+}
+
+// Cluster c solves system c of gs[]: projection of b (Eq. 1), flexible CG preconditioned by
+// the cycle of Section 2, stopping test on the recursive residual, true residual, scatter.
+// The clusters share nothing and never wait for one another.
+__global__ void __launch_bounds__(CBS, 1) k_cluster_solve(const MGraph *__restrict__ gs) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const MGraph G = gs[blockIdx.x / cl_size()];
+    PLevel *lv;
+    int32_t *cptr;
+    const Op *ops = cl_load_tables(smem, G.lv, G.nlev, G.cptr, G.ncptr, G.ops, G.nops, &lv, &cptr);
+    const CPos p = cl_pos();
+    const PLevel &F = lv[0];
+    const int n = G.n0;
+    unsigned phase = 0;
+
+    double s[1] = {0.0};
+    for (int i = p.tid; i < n; i += p.nthreads) {
+        const double v = __ldg(&G.b_in[__ldg(&G.perm0[i])]);
+        __stcg(&G.r[i], v);
+        s[0] += v;
+    }
+    cl_allreduce<1>(s, G.part, phase);
+    const double bmean = s[0] / (double)n;
+    s[0] = 0.0;
+    for (int i = p.tid; i < n; i += p.nthreads) {
+        const double v = __ldcg(&G.r[i]) - bmean;
+        __stcg(&G.r[i], v);
+        __stcg(&G.bkeep[i], v);
+        __stcg(&G.xs[i], 0.0);
+        __stcg(&G.p[i], 0.0);
+        __stcg(&G.zold[i], 0.0);
+        s[0] += v * v;
+    }
+    cl_allreduce<1>(s, G.part, phase);
+    const double bn2 = s[0];
+    double rz = 1.0;
+    cl_cycle_and_tail(G, ops, lv, cptr, p, phase, rz);
+    int it = 0;
+    double rr = 0.0;
+    const bool lead = cl_rank() == 0 && threadIdx.x == 0;
+    if (lead && G.hist) G.hist[0] = 1.0;
+    while (it < G.maxit) {
+        double pq[1];
+        if (F.rs_tpr == 0) pq[0] = cl_spmv_part_sell(F, G.p, G.q, p);
+        else CL_TPR_RET(F.rs_tpr, pq[0], cl_spmv_part, F, G.p, G.q, p);
+        cl_allreduce<1>(pq, G.part, phase);
+        const double alpha = pq[0] != 0.0 ? rz / pq[0] : 0.0;
+        double r2[1] = {0.0};
+        for (int i = p.tid; i < n; i += p.nthreads) {
+            __stcg(&G.xs[i], __ldcg(&G.xs[i]) + alpha * __ldcg(&G.p[i]));
+            const double ri = __ldcg(&G.r[i]) - alpha * __ldcg(&G.q[i]);
+            __stcg(&G.r[i], ri);
+            r2[0] += ri * ri;
+        }
+        cl_allreduce<1>(r2, G.part, phase);
+        rr = r2[0];
+        it++;
+        const double rel = bn2 > 0.0 ? sqrt(rr / bn2) : 0.0;
+        if (lead && G.hist) G.hist[it] = rel;
+        if (!(rel > G.tol)) break;
+        cl_cycle_and_tail(G, ops, lv, cptr, p, phase, rz);
+    }
+    double tr[1];
+    if (F.rs_tpr == 0) tr[0] = cl_rr_part_sell(F, G.xs, G.bkeep, p);
+    else CL_TPR_RET(F.rs_tpr, tr[0], cl_rr_part, F, G.xs, G.bkeep, p);
+    cl_allreduce<1>(tr, G.part, phase);
+    for (int i = p.tid; i < n; i += p.nthreads) G.phi_out[__ldg(&G.perm0[i])] = __ldcg(&G.xs[i]);
+    if (lead) {
+        G.out[MG_ITERS] = (double)it;
+        G.out[MG_RR] = rr;
+        G.out[MG_BN2] = bn2;
+        G.out[MG_TRUE_RR] = tr[0];
+        G.out[MG_BMEAN] = bmean;
+    }
+    // no CTA leaves while another may still read its partials
+    cl_arrive();
+    cl_wait();
+}
+
+cudaError_t launch_cluster_solve(const MGraph *g, int G, int cl, size_t smem, cudaStream_t s) {
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(k_cluster_solve, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)CL_SMEM_MAX);
+        if (e != cudaSuccess) return e;
+        cudaFuncSetAttribute(k_cluster_solve, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        cudaGetLastError();
+        attr_set = true;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(G * cl));
+    cfg.blockDim = dim3(CBS);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = cl;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_cluster_solve, g);
 }
 
 size_t cluster_smem(int nlev, int ncptr, int nops) {

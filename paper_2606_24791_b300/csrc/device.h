@@ -138,6 +138,26 @@ cudaError_t launch_persistent(const PSolve *P, int grid, size_t smem, int mode, 
                               const double *b_in, double *phi_out, cudaStream_t s,
                               unsigned long long *prof = nullptr);
 
+// A whole solve run by one thread-block cluster (lamg_solve_many): device pointers of one
+// hierarchy and its right-hand side.
+enum { MG_ITERS = 0, MG_RR, MG_BN2, MG_TRUE_RR, MG_BMEAN, MG_OUT = 8 };
+struct MGraph {
+    const PLevel *lv;
+    const int32_t *cptr;
+    const Op *ops;
+    const int32_t *perm0;
+    int nlev, ncptr, nops, n0;
+    int maxit, pad_;
+    double tol;
+    double *r, *p, *q, *zold, *xs, *bkeep;   // level-0 device order
+    const double *b_in;                      // caller order
+    double *phi_out;                         // caller order
+    double *part;                            // 2 x RED_NV x 16 cluster partial sums
+    double *out;                             // MG_OUT results
+    double *hist;                            // maxit + 1 relative residuals, or null
+};
+cudaError_t launch_cluster_solve(const MGraph *g, int G, int cl, size_t smem, cudaStream_t s);
+
 // cluster sub-cycle kernel (cluster.cu)
 constexpr int CL_OPS_SMEM = 4096;               // longer step lists are read from global memory
 constexpr size_t CL_SMEM_MAX = 160 * 1024;      // dynamic shared memory limit of the kernel

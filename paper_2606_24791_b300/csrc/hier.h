@@ -58,6 +58,9 @@ struct lamg_hier {
     int cluster_from = -1;        // -1: every step is its own kernel
     std::vector<double> tune_ms;  // cycle time of each candidate tried by the automatic choice
     std::vector<int> tune_from;
+    // lamg_solve_many: cluster partial sums, results, residual history
+    double *mg_part = nullptr, *mg_out = nullptr, *mg_hist = nullptr;
+    int mg_hist_cap = 0;
     // multi-RHS / FP32 workspaces, one per (k, precision) used so far
     std::vector<lamg::BatchCtx *> batch;
     std::vector<void *> allocs;

@@ -924,6 +924,116 @@ int lamg_solve(lamg_hier *h, const double *b, double *phi, const lamg_solve_opts
     return solve_persistent(h, b, phi, so, st);
 }
 
+int lamg_solve_many(int32_t G, lamg_hier *const *hs, const double *const *b, double *const *phi,
+                    const lamg_solve_opts *so, lamg_stats *st) {
+    if (G < 1 || !hs || !b || !phi || !so || !(so->tol > 0) || so->maxit < 1) return LAMG_ERR_INVALID;
+    for (int g = 0; g < G; g++)
+        if (!hs[g] || !b[g] || !phi[g] || hs[g]->device != hs[0]->device) return LAMG_ERR_INVALID;
+    lamg_hier *h0 = hs[0];
+    CKR(cudaSetDevice(h0->device));
+    cudaStream_t s = so->stream ? (cudaStream_t)so->stream : h0->stream;
+    const bool devp = so->flags & LAMG_DEVICE_PTRS;
+    // eligible: FP64 cycle, cluster launch available, no block-per-row long rows
+    std::vector<int> cl_idx, other;
+    int cl = 16;
+    size_t smem = 0;
+    for (int g = 0; g < G; g++) {
+        lamg_hier *h = hs[g];
+        int64_t nl = 0;
+        for (const DevLevel &D : h->dev) nl += D.nlong;
+        const size_t sm = cluster_smem((int)h->dev.size(), h->ncptr, (int)h->ops.size());
+        if (h->opt.precision == LAMG_FP64 && h->cl_dim > 0 && nl == 0 && sm <= CL_SMEM_MAX) {
+            cl_idx.push_back(g);
+            cl = std::min(cl, h->cl_dim);
+            smem = std::max(smem, sm);
+        } else {
+            other.push_back(g);
+        }
+    }
+    int rc = LAMG_OK;
+    std::vector<MGraph> desc(cl_idx.size());
+    for (size_t k = 0; k < cl_idx.size(); k++) {
+        lamg_hier *h = hs[cl_idx[k]];
+        const int64_t n = h->dev[0].n;
+        if (!h->mg_part && ((rc = dalloc(h, &h->mg_part, 2 * RED_NV * 16)) || (rc = dalloc(h, &h->mg_out, MG_OUT))))
+            return rc;
+        if (h->mg_hist_cap < so->maxit + 1) {
+            if ((rc = dalloc(h, &h->mg_hist, so->maxit + 1))) return rc;
+            h->mg_hist_cap = so->maxit + 1;
+        }
+        MGraph &M = desc[k];
+        std::memset(&M, 0, sizeof(M));
+        M.lv = h->d_lv; M.cptr = h->d_cptr; M.ops = h->d_ops; M.perm0 = h->perm0;
+        M.nlev = (int)h->dev.size(); M.ncptr = h->ncptr; M.nops = (int)h->ops.size(); M.n0 = (int)n;
+        M.maxit = so->maxit; M.tol = so->tol;
+        M.r = h->r; M.p = h->p; M.q = h->q; M.zold = h->zold; M.xs = h->xs; M.bkeep = h->bkeep;
+        M.part = h->mg_part; M.out = h->mg_out; M.hist = h->mg_hist;
+        if (devp) {
+            M.b_in = b[cl_idx[k]];
+            M.phi_out = phi[cl_idx[k]];
+        } else {
+            CKR(cudaMemcpyAsync(h->nat_in, b[cl_idx[k]], n * sizeof(double), cudaMemcpyHostToDevice, s));
+            M.b_in = h->nat_in;
+            M.phi_out = h->nat_out;
+        }
+    }
+    float ms = 0.f;
+    if (!desc.empty()) {
+        MGraph *d_desc = nullptr;
+        CKR(cudaMallocAsync(&d_desc, desc.size() * sizeof(MGraph), s));
+        CKR(cudaMemcpyAsync(d_desc, desc.data(), desc.size() * sizeof(MGraph), cudaMemcpyHostToDevice, s));
+        CKR(cudaEventRecord(h0->ev_k0, s));
+        CKR(launch_cluster_solve(d_desc, (int)desc.size(), cl, smem, s));
+        CKR(cudaEventRecord(h0->ev_k1, s));
+        CKR(cudaFreeAsync(d_desc, s));
+        std::vector<double> outs(desc.size() * MG_OUT);
+        for (size_t k = 0; k < cl_idx.size(); k++) {
+            lamg_hier *h = hs[cl_idx[k]];
+            const int64_t n = h->dev[0].n;
+            if (!devp)
+                CKR(cudaMemcpyAsync(phi[cl_idx[k]], h->nat_out, n * sizeof(double), cudaMemcpyDeviceToHost, s));
+            CKR(cudaMemcpyAsync(&outs[k * MG_OUT], h->mg_out, MG_OUT * sizeof(double), cudaMemcpyDeviceToHost, s));
+        }
+        CKR(cudaEventRecord(h0->ev_b, s));
+        if ((rc = wait_event(h0, h0->ev_b))) return rc;
+        CKR(cudaGetLastError());
+        cudaEventElapsedTime(&ms, h0->ev_k0, h0->ev_k1);
+        for (size_t k = 0; k < cl_idx.size(); k++) {
+            const int g = cl_idx[k];
+            lamg_hier *h = hs[g];
+            const double *o = &outs[k * MG_OUT];
+            const int it = (int)o[MG_ITERS];
+            const double bn2 = o[MG_BN2];
+            const double rel = bn2 > 0 ? std::sqrt(o[MG_RR] / bn2) : 0.0;
+            if (st) {
+                lamg_stats &S = st[g];
+                if (S.hist) {
+                    CKR(cudaMemcpy(S.hist, h->mg_hist, (it + 1) * sizeof(double), cudaMemcpyDeviceToHost));
+                }
+                S.iters = it;
+                S.nlevels = (int32_t)h->dev.size();
+                S.relres = rel;
+                S.relres_true = bn2 > 0 ? std::sqrt(o[MG_TRUE_RR] / bn2) : 0.0;
+                S.b_mean = o[MG_BMEAN];
+                S.solve_ms = ms;
+                S.kernel_ms = ms;
+                const double z0 = (double)h->dev[0].nnz, n0 = (double)h->dev[0].n;
+                S.alg_bytes = (double)it * (h->cycle_bytes + 12 * z0 + 148 * n0) + h->cycle_bytes + 72 * n0 +
+                              (12 * z0 + 36 * n0) + 16 * n0;
+                S.launches = 1;
+            }
+            if (!(rel <= so->tol) && rc == LAMG_OK) rc = LAMG_ERR_NOT_CONVERGED;
+        }
+    }
+    // the others on their own per-step path, one after another
+    for (int g : other) {
+        lamg_solve_opts o1 = *so;
+        const int r1 = lamg_solve(hs[g], b[g], phi[g], &o1, st ? &st[g] : nullptr);
+        if (r1 != LAMG_OK && (rc == LAMG_OK || r1 != LAMG_ERR_NOT_CONVERGED)) rc = r1;
+    }
+    return rc;
+}
+
 int lamg_cycle(lamg_hier *h, const double *r, double *z, uint32_t flags) {
     if (!h || !r || !z) return LAMG_ERR_INVALID;
     CKR(cudaSetDevice(h->device));
