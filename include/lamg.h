@@ -274,8 +274,9 @@ int lamg_schedule_info(const lamg_hier *h, int64_t *out, int64_t cap, int64_t *c
  * (projection of b, every cycle of Section 2, the stopping test, the true residual), with
  * deterministic cluster-scope reductions; the clusters share nothing. Meant for many small
  * graphs, whose solves would otherwise be a few hundred small launches each. A hierarchy the
- * cluster kernel cannot take (FP32 cycle, rows longer than 256 entries, no cluster launch on the
- * device, level tables over the shared-memory limit) is solved by lamg_solve after the launch.
+ * cluster kernel should not take (FP32 cycle, rows longer than 256 entries, more than 2^19
+ * stored entries in the finest operator, no cluster launch on the device, level tables over the
+ * shared-memory limit) is solved by lamg_solve after the launch.
  * No counterpart in the paper (it batches solves of the same method).
  * hs, b, phi: G entries; b[g], phi[g] of hs[g]'s size, host pointers, or device pointers with
  * LAMG_DEVICE_PTRS; all hierarchies on one device; the work goes to so->stream (0: the first
@@ -341,7 +342,10 @@ int lamg_serve_poll(lamg_server *s, int64_t ticket, lamg_ticket_info *info, doub
  * Errors: TIMEOUT. */
 int lamg_server_drain(lamg_server *s, double timeout_s);
 /* out[0] device bytes held by in-flight requests, out[1] requests in flight, out[2] requests
- * waiting for admission, out[3] requests not yet finished. */
+ * waiting for admission, out[3] requests not yet finished, out[4] grouped launches so far (the
+ * requests that became ready since the executor's previous pass and that the cluster kernel
+ * takes are solved together, one thread-block cluster each, as in lamg_solve_many), out[5]
+ * requests solved in such launches, out[6] the largest group. 7 entries. */
 int lamg_server_stats(lamg_server *s, int64_t *out);
 /* Stop the threads and release everything; unfinished requests are dropped. */
 void lamg_server_destroy(lamg_server *s);

@@ -373,10 +373,11 @@ class Server:
         _check(lib().lamg_server_drain(self._s, timeout_s), "lamg_server_drain")
 
     def stats(self) -> dict:
-        out = np.zeros(4, np.int64)
+        out = np.zeros(7, np.int64)
         lib().lamg_server_stats(self._s, _p(out))
         return dict(bytes_in_flight=int(out[0]), inflight=int(out[1]), waiting=int(out[2]),
-                    unfinished=int(out[3]))
+                    unfinished=int(out[3]), grouped_launches=int(out[4]), grouped_requests=int(out[5]),
+                    largest_group=int(out[6]))
 
     def close(self):
         if getattr(self, "_s", None):

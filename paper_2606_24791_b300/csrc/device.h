@@ -141,6 +141,7 @@ cudaError_t launch_persistent(const PSolve *P, int grid, size_t smem, int mode, 
 // A whole solve run by one thread-block cluster (lamg_solve_many): device pointers of one
 // hierarchy and its right-hand side.
 enum { MG_ITERS = 0, MG_RR, MG_BN2, MG_TRUE_RR, MG_BMEAN, MG_OUT = 8 };
+constexpr int64_t MANY_MAX_ENTRIES = (int64_t)1 << 19;   // n + off-diagonal entries of level 0
 struct MGraph {
     const PLevel *lv;
     const int32_t *cptr;

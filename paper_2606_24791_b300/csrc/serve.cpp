@@ -117,6 +117,14 @@ size_t estimate_bytes(int64_t n, int64_t nnz) {
 
 }  // namespace
 
+// Requests solved together by one launch of the cluster solve kernel (one cluster each).
+struct Group {
+    std::vector<Request *> reqs;
+    cudaEvent_t ev = nullptr;
+    MGraph *d_desc = nullptr;
+    double *pin_out = nullptr;   // MG_OUT results per request
+};
+
 struct lamg_server {
     lamg_server_opts so{};
     lamg_options opt{};
@@ -133,6 +141,10 @@ struct lamg_server {
     std::thread exec;
     std::chrono::steady_clock::time_point t0 = std::chrono::steady_clock::now();
     PinPool pins;
+    // grouped launches (executor thread only, counters read under mu)
+    cudaStream_t gstream = nullptr;
+    std::vector<Group> groups;
+    int64_t n_groups = 0, n_grouped = 0, max_group = 0;
 
     double now_ms() const {
         return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
@@ -258,16 +270,115 @@ struct lamg_server {
         return true;
     }
 
+    // Launch every request in `fresh` (ready, not started, taken by the cluster kernel) as one
+    // group: copies in, one k_cluster_solve launch, copies out, an event; phase 6 until done.
+    void launch_group(std::vector<Request *> &fresh) {
+        Group g;
+        std::vector<MGraph> desc(fresh.size());
+        int cl = 16;
+        size_t smem = 0;
+        cudaError_t e = cudaSuccess;
+        g.pin_out = pins.get(MG_OUT * fresh.size());
+        for (size_t k = 0; k < fresh.size() && e == cudaSuccess; k++) {
+            Request *r = fresh[k];
+            lamg_hier *h = r->h;
+            const int64_t n = h->dev[0].n;
+            size_t sm = 0;
+            many_eligible(h, &sm);
+            cl = std::min(cl, h->cl_dim);
+            smem = std::max(smem, sm);
+            r->pin_b = pins.get(n);
+            r->pin_x = pins.get(n);
+            if (!r->pin_b || !r->pin_x || !g.pin_out) { e = cudaErrorMemoryAllocation; break; }
+            std::copy(r->b.begin(), r->b.end(), r->pin_b);
+            e = cudaMemcpyAsync(h->nat_in, r->pin_b, n * sizeof(double), cudaMemcpyHostToDevice, gstream);
+            if (e == cudaSuccess && many_prepare(h, so.maxit, so.tol, h->nat_in, h->nat_out, &desc[k]) != LAMG_OK)
+                e = cudaErrorMemoryAllocation;
+        }
+        if (e == cudaSuccess) e = cudaMallocAsync(&g.d_desc, desc.size() * sizeof(MGraph), gstream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(g.d_desc, desc.data(), desc.size() * sizeof(MGraph), cudaMemcpyHostToDevice, gstream);
+        if (e == cudaSuccess) e = launch_cluster_solve(g.d_desc, (int)fresh.size(), cl, smem, gstream);
+        for (size_t k = 0; k < fresh.size() && e == cudaSuccess; k++) {
+            lamg_hier *h = fresh[k]->h;
+            e = cudaMemcpyAsync(fresh[k]->pin_x, h->nat_out, h->dev[0].n * sizeof(double), cudaMemcpyDeviceToHost,
+                                gstream);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(g.pin_out + k * MG_OUT, h->mg_out, MG_OUT * sizeof(double),
+                                    cudaMemcpyDeviceToHost, gstream);
+        }
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&g.ev, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventRecord(g.ev, gstream);
+        g.reqs = fresh;
+        for (Request *r : fresh) r->phase = 6;
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            for (Request *r : fresh) { r->status = cuda_status(e); r->phase = 4; }
+            if (g.ev) cudaEventDestroy(g.ev);
+            pins.put(g.pin_out);
+            return;
+        }
+        {
+            std::lock_guard<std::mutex> lock(mu);
+            n_groups++;
+            n_grouped += (int64_t)fresh.size();
+            max_group = std::max<int64_t>(max_group, (int64_t)fresh.size());
+        }
+        groups.push_back(std::move(g));
+    }
+
+    // Finish the groups whose launch has completed; true if any did.
+    bool poll_groups() {
+        bool any = false;
+        for (size_t i = 0; i < groups.size();) {
+            Group &g = groups[i];
+            const cudaError_t e = cudaEventQuery(g.ev);
+            if (e == cudaErrorNotReady) { i++; continue; }
+            for (size_t k = 0; k < g.reqs.size(); k++) {
+                Request *r = g.reqs[k];
+                if (e != cudaSuccess) {
+                    r->status = cuda_status(e);
+                } else {
+                    const double *o = g.pin_out + k * MG_OUT;
+                    const double bn2 = o[MG_BN2];
+                    r->it = (int)o[MG_ITERS];
+                    r->rel = bn2 > 0 ? std::sqrt(o[MG_RR] / bn2) : 0.0;
+                    r->relres_true = bn2 > 0 ? std::sqrt(o[MG_TRUE_RR] / bn2) : 0.0;
+                    r->phi.assign(r->pin_x, r->pin_x + r->h->dev[0].n);
+                    r->status = r->rel <= so.tol ? LAMG_OK : LAMG_ERR_NOT_CONVERGED;
+                }
+                r->phase = 4;
+            }
+            cudaEventDestroy(g.ev);
+            cudaFreeAsync(g.d_desc, gstream);
+            pins.put(g.pin_out);
+            groups.erase(groups.begin() + i);
+            any = true;
+        }
+        return any;
+    }
+
     void executor() {
         cudaSetDevice(so.device);
-        std::vector<Request *> act;
+        cudaStreamCreateWithFlags(&gstream, cudaStreamNonBlocking);
+        std::vector<Request *> act, fresh;
         for (;;) {
             {
                 std::lock_guard<std::mutex> lock(mu);
-                if (stop) return;
+                if (stop) break;
                 act = running;
             }
+            // continuous batching: every request whose setup finished since the last pass and
+            // that the cluster kernel takes joins one launch
+            fresh.clear();
+            for (Request *r : act)
+                if (r->phase == 0 && many_eligible(r->h, nullptr)) fresh.push_back(r);
             bool progressed = false;
+            if (!fresh.empty()) {
+                launch_group(fresh);
+                progressed = true;
+            }
+            progressed |= poll_groups();
             for (Request *r : act) {
                 progressed |= step(r);
                 if (r->phase == 4) {
@@ -285,6 +396,14 @@ struct lamg_server {
             }
             if (!progressed) std::this_thread::sleep_for(std::chrono::microseconds(20));
         }
+        // stopping: let launched groups finish before their hierarchies are released
+        if (gstream) cudaStreamSynchronize(gstream);
+        for (Group &g : groups) {
+            cudaEventDestroy(g.ev);
+            pins.put(g.pin_out);
+        }
+        groups.clear();
+        if (gstream) cudaStreamDestroy(gstream);
     }
 };
 
@@ -372,6 +491,9 @@ int lamg_server_stats(lamg_server *s, int64_t *out) {
     out[1] = s->inflight;
     out[2] = (int64_t)s->waiting.size();
     out[3] = s->outstanding;
+    out[4] = s->n_groups;
+    out[5] = s->n_grouped;
+    out[6] = s->max_group;
     return LAMG_OK;
 }
 

@@ -924,6 +924,46 @@ int lamg_solve(lamg_hier *h, const double *b, double *phi, const lamg_solve_opts
     return solve_persistent(h, b, phi, so, st);
 }
 
+}  // extern "C"
+
+// Whether a hierarchy can be solved by one cluster of k_cluster_solve (FP64 cycle, cluster
+// launch available, no block-per-row long rows, tables within the shared-memory limit, at most
+// MANY_MAX_ENTRIES stored entries in the finest operator: one cluster has 16 SMs' share of the
+// GPU's FP64 units and bandwidth, so a larger system is faster on the whole GPU), and the
+// dynamic shared memory its tables take.
+bool lamg::many_eligible(const lamg_hier *h, size_t *smem) {
+    int64_t nl = 0;
+    for (const DevLevel &D : h->dev) nl += D.nlong;
+    const size_t sm = cluster_smem((int)h->dev.size(), h->ncptr, (int)h->ops.size());
+    if (smem) *smem = sm;
+    const int64_t entries = h->dev[0].n + h->dev[0].nnz;
+    return h->opt.precision == LAMG_FP64 && h->cl_dim > 0 && nl == 0 && sm <= CL_SMEM_MAX &&
+           entries <= MANY_MAX_ENTRIES;
+}
+
+// Device buffers of a cluster solve (partials, results, history of maxit + 1 entries) and its
+// descriptor.
+int lamg::many_prepare(lamg_hier *h, int maxit, double tol, const double *b_in, double *phi_out, MGraph *M) {
+    int rc;
+    if (!h->mg_part && ((rc = dalloc(h, &h->mg_part, 2 * RED_NV * 16)) || (rc = dalloc(h, &h->mg_out, MG_OUT))))
+        return rc;
+    if (h->mg_hist_cap < maxit + 1) {
+        if ((rc = dalloc(h, &h->mg_hist, maxit + 1))) return rc;
+        h->mg_hist_cap = maxit + 1;
+    }
+    std::memset(M, 0, sizeof(*M));
+    M->lv = h->d_lv; M->cptr = h->d_cptr; M->ops = h->d_ops; M->perm0 = h->perm0;
+    M->nlev = (int)h->dev.size(); M->ncptr = h->ncptr; M->nops = (int)h->ops.size(); M->n0 = (int)h->dev[0].n;
+    M->maxit = maxit; M->tol = tol;
+    M->r = h->r; M->p = h->p; M->q = h->q; M->zold = h->zold; M->xs = h->xs; M->bkeep = h->bkeep;
+    M->part = h->mg_part; M->out = h->mg_out; M->hist = h->mg_hist;
+    M->b_in = b_in;
+    M->phi_out = phi_out;
+    return LAMG_OK;
+}
+
+extern "C" {
+
 int lamg_solve_many(int32_t G, lamg_hier *const *hs, const double *const *b, double *const *phi,
                     const lamg_solve_opts *so, lamg_stats *st) {
     if (G < 1 || !hs || !b || !phi || !so || !(so->tol > 0) || so->maxit < 1) return LAMG_ERR_INVALID;
@@ -938,13 +978,10 @@ int lamg_solve_many(int32_t G, lamg_hier *const *hs, const double *const *b, dou
     int cl = 16;
     size_t smem = 0;
     for (int g = 0; g < G; g++) {
-        lamg_hier *h = hs[g];
-        int64_t nl = 0;
-        for (const DevLevel &D : h->dev) nl += D.nlong;
-        const size_t sm = cluster_smem((int)h->dev.size(), h->ncptr, (int)h->ops.size());
-        if (h->opt.precision == LAMG_FP64 && h->cl_dim > 0 && nl == 0 && sm <= CL_SMEM_MAX) {
+        size_t sm = 0;
+        if (many_eligible(hs[g], &sm)) {
             cl_idx.push_back(g);
-            cl = std::min(cl, h->cl_dim);
+            cl = std::min(cl, hs[g]->cl_dim);
             smem = std::max(smem, sm);
         } else {
             other.push_back(g);
@@ -955,27 +992,11 @@ int lamg_solve_many(int32_t G, lamg_hier *const *hs, const double *const *b, dou
     for (size_t k = 0; k < cl_idx.size(); k++) {
         lamg_hier *h = hs[cl_idx[k]];
         const int64_t n = h->dev[0].n;
-        if (!h->mg_part && ((rc = dalloc(h, &h->mg_part, 2 * RED_NV * 16)) || (rc = dalloc(h, &h->mg_out, MG_OUT))))
-            return rc;
-        if (h->mg_hist_cap < so->maxit + 1) {
-            if ((rc = dalloc(h, &h->mg_hist, so->maxit + 1))) return rc;
-            h->mg_hist_cap = so->maxit + 1;
-        }
-        MGraph &M = desc[k];
-        std::memset(&M, 0, sizeof(M));
-        M.lv = h->d_lv; M.cptr = h->d_cptr; M.ops = h->d_ops; M.perm0 = h->perm0;
-        M.nlev = (int)h->dev.size(); M.ncptr = h->ncptr; M.nops = (int)h->ops.size(); M.n0 = (int)n;
-        M.maxit = so->maxit; M.tol = so->tol;
-        M.r = h->r; M.p = h->p; M.q = h->q; M.zold = h->zold; M.xs = h->xs; M.bkeep = h->bkeep;
-        M.part = h->mg_part; M.out = h->mg_out; M.hist = h->mg_hist;
-        if (devp) {
-            M.b_in = b[cl_idx[k]];
-            M.phi_out = phi[cl_idx[k]];
-        } else {
+        if (!devp)
             CKR(cudaMemcpyAsync(h->nat_in, b[cl_idx[k]], n * sizeof(double), cudaMemcpyHostToDevice, s));
-            M.b_in = h->nat_in;
-            M.phi_out = h->nat_out;
-        }
+        if ((rc = many_prepare(h, so->maxit, so->tol, devp ? b[cl_idx[k]] : h->nat_in,
+                               devp ? phi[cl_idx[k]] : h->nat_out, &desc[k])))
+            return rc;
     }
     float ms = 0.f;
     if (!desc.empty()) {

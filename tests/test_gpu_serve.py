@@ -28,11 +28,15 @@ def rel(a, b):
 
 
 def test_served_results_equal_solo_results():
+    # alone: the same system by itself through lamg_solve_many, which takes the same path a
+    # served request takes (one thread-block cluster, or its per-step path when the cluster
+    # kernel cannot take it); each cluster is deterministic and shares nothing, so a served
+    # result does not depend on what it was batched with
     reqs = mix()
     alone = []
     for g, b in reqs:
         P = lamg.setup(g, autotune=0, cluster_rows=-1)   # the options a served setup runs with
-        x, st = P.solve(b, 1e-8, 200)
+        (x,), (st,) = lamg.solve_many([P], [b], 1e-8, 200)
         alone.append((x, st["iters"]))
         P.close()
     # a budget that holds only a few hierarchies at once forces queueing and admission
@@ -45,7 +49,9 @@ def test_served_results_equal_solo_results():
         assert info["relres_true"] <= 2e-8
         assert info["iters"] == iters
         assert rel(info["phi"], x) <= 1e-12
-    assert S.stats()["unfinished"] == 0 and S.stats()["bytes_in_flight"] == 0
+    st = S.stats()
+    assert st["unfinished"] == 0 and st["bytes_in_flight"] == 0
+    assert st["grouped_requests"] >= 6 and st["grouped_launches"] >= 1   # the small meshes at least
     S.close()
 
 
