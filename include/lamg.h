@@ -269,6 +269,13 @@ int lamg_op_list(const lamg_hier *h, int32_t *out, int64_t cap, int64_t *count);
  * int64 entries; *count = entries written. Errors: INVALID. */
 int lamg_schedule_info(const lamg_hier *h, int64_t *out, int64_t cap, int64_t *count);
 
+/* Wall time (ms) of the setup phases of a hierarchy built by lamg_setup, 9 entries: input
+ * validation and Laplacian; elimination (Eq. 2); colouring; test vectors and affinities on the
+ * GPU (Section 2, Eq. 3, Eq. 9) with their copies; aggregation and caliber-2 (Eqs. 4, 13);
+ * Galerkin products; dense pseudo-inverse of the coarsest level; device layout and uploads;
+ * step list, timing trials and graph capture. cap >= 9. Errors: INVALID. */
+int lamg_setup_times(const lamg_hier *h, double *out, int32_t cap);
+
 /* Solve G independent systems L_g phi_g = b_g (Eq. 1), each on its own hierarchy, with one
  * kernel launch: one thread-block cluster per system runs that system's whole flexible-CG solve
  * (projection of b, every cycle of Section 2, the stopping test, the true residual), with

@@ -117,6 +117,7 @@ def lib():
         L.lamg_op_list.argtypes = [P, P, C.c_int64, C.POINTER(C.c_int64)]
         L.lamg_schedule_info.argtypes = [P, P, C.c_int64, C.POINTER(C.c_int64)]
         L.lamg_solve_many.argtypes = [C.c_int32, P, P, P, C.POINTER(SolveOpts), P]
+        L.lamg_setup_times.argtypes = [P, P, C.c_int32]
         L.lamg_profile_schedule.argtypes = [P, C.c_int32, P, C.c_int64, C.POINTER(C.c_int64)]
         _lib = L
     return _lib
@@ -266,6 +267,15 @@ class Hierarchy:
         out = np.zeros(3 * cnt.value, np.int32)
         lib().lamg_op_list(self._h, _p(out), cnt.value, C.byref(cnt))
         return [(self.OP_KINDS[k], int(l), int(c)) for k, l, c in out.reshape(-1, 3)]
+
+    SETUP_PHASES = ("input", "elimination", "colouring", "testvectors_affinity", "aggregation",
+                    "galerkin", "dense_coarsest", "device_layout", "schedule")
+
+    def setup_times(self) -> dict:
+        """Wall milliseconds of each setup phase (lamg_setup hierarchies)."""
+        out = np.zeros(len(self.SETUP_PHASES))
+        _check(lib().lamg_setup_times(self._h, _p(out), out.size), "lamg_setup_times")
+        return {k: round(float(v), 3) for k, v in zip(self.SETUP_PHASES, out)}
 
     def schedule(self) -> dict:
         """Launch schedule of the graph path: first level of the cluster sub-cycle (-1: none),

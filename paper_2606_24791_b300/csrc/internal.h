@@ -47,7 +47,21 @@ struct Status {
 
 // host setup (setup_host.cpp)
 int validate_graph(const lamg_graph *g);
-int build_hierarchy(const lamg_graph *g, const lamg_options &o, std::vector<HostLevel> &levels);
+// Setup phases timed by build_hierarchy and finalize (milliseconds, lamg_setup_times).
+enum SetupPhase {
+    SETUP_INPUT = 0,     // validation and Laplacian
+    SETUP_ELIM,          // degree-<=4 independent set and Schur complement (Eq. 2)
+    SETUP_COLOUR,        // greedy colouring
+    SETUP_TV_AFFINITY,   // test vectors and affinities on the GPU, with their copies
+    SETUP_AGGREGATE,     // guarded aggregation and caliber-2 (Eqs. 3-4, 9, 13)
+    SETUP_GALERKIN,      // P^T A P
+    SETUP_DENSE,         // dense pseudo-inverse of the coarsest level
+    SETUP_DEVICE,        // device orders, uploads, sliced copies
+    SETUP_SCHEDULE,      // step list, kernel-form timing, cluster choice, graph capture
+    SETUP_NPHASE
+};
+int build_hierarchy(const lamg_graph *g, const lamg_options &o, std::vector<HostLevel> &levels,
+                    double *times = nullptr);
 int greedy_colour(const HostMat &A, std::vector<int32_t> &colour);
 int dense_pinv(const HostMat &A, std::vector<double> &pinv);
 double cycle_index(int64_t El, int64_t El1, int64_t E0);

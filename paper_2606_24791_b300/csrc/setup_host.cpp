@@ -8,6 +8,7 @@
 // compiled with -ffp-contract=off), so that decisions taken from them (guard admissibility,
 // affinity maxima, caliber-2 gates) are reproducible.
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <cstring>
 #include <numeric>
@@ -365,6 +366,21 @@ static void galerkin(const HostLevel &L, HostMat &Ac) {
 
 // A^+ = (A + J/n)^{-1} - J/n for a connected Laplacian-like operator (null space span{1}),
 // through a Cholesky factorisation of A + J/n.
+// a . b over len entries with four independent partial sums (k mod 4), added as
+// (s0 + s1) + (s2 + s3): four dependency chains instead of one
+static inline double dot4(const double *a, const double *b, int64_t len) {
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+    int64_t k = 0;
+    for (; k + 4 <= len; k += 4) {
+        s0 += a[k] * b[k];
+        s1 += a[k + 1] * b[k + 1];
+        s2 += a[k + 2] * b[k + 2];
+        s3 += a[k + 3] * b[k + 3];
+    }
+    for (; k < len; k++) s0 += a[k] * b[k];
+    return (s0 + s1) + (s2 + s3);
+}
+
 int dense_pinv(const HostMat &A, std::vector<double> &pinv) {
     const int64_t n = A.n;
     std::vector<double> M(n * n, 1.0 / (double)n);
@@ -373,61 +389,73 @@ int dense_pinv(const HostMat &A, std::vector<double> &pinv) {
         for (int64_t e = A.rp[i]; e < A.rp[i + 1]; e++) M[i * n + A.ci[e]] += A.val[e];
     }
     const int nthr = (int)std::max<unsigned>(1u, std::min<unsigned>(16u, std::thread::hardware_concurrency()));
-    // lower Cholesky factor G (row-major, in place): M = G G^T, column by column. Rows below
-    // the diagonal of one column are independent; for large n they are split over threads that
-    // meet at a barrier after each column.
+    // lower Cholesky factor G (row-major, in place): M = G G^T, right-looking in panels of NB
+    // columns. Per panel: the diagonal block by one thread, then the rows below it (a forward
+    // substitution each) and the trailing lower triangle (one dot product of NB per entry)
+    // split over threads by rows, with a barrier after each of the three parts.
+    constexpr int64_t NB = 64;
     bool spd = true;
-    if (n < 512 || nthr == 1) {
-        for (int64_t j = 0; j < n && spd; j++) {
-            double s = M[j * n + j];
-            for (int64_t k = 0; k < j; k++) s -= M[j * n + k] * M[j * n + k];
-            if (!(s > 0.0)) { spd = false; break; }
-            const double gjj = std::sqrt(s);
-            M[j * n + j] = gjj;
-            for (int64_t i = j + 1; i < n; i++) {
-                double t = M[i * n + j];
-                for (int64_t k = 0; k < j; k++) t -= M[i * n + k] * M[j * n + k];
-                M[i * n + j] = t / gjj;
-            }
+    std::mutex mu;
+    std::condition_variable cv;
+    int arrived = 0;
+    int64_t phase = 0;
+    const int T = n < 256 ? 1 : nthr;
+    auto barrier = [&]() {
+        if (T == 1) return;
+        std::unique_lock<std::mutex> lk(mu);
+        const int64_t my = phase;
+        if (++arrived == T) {
+            arrived = 0;
+            phase++;
+            cv.notify_all();
+        } else {
+            cv.wait(lk, [&] { return phase != my; });
         }
-    } else {
-        std::mutex mu;
-        std::condition_variable cv;
-        int arrived = 0;
-        int64_t phase = 0;
-        auto barrier = [&]() {
-            std::unique_lock<std::mutex> lk(mu);
-            const int64_t my = phase;
-            if (++arrived == nthr) {
-                arrived = 0;
-                phase++;
-                cv.notify_all();
-            } else {
-                cv.wait(lk, [&] { return phase != my; });
-            }
-        };
-        std::vector<std::thread> th;
-        for (int t = 0; t < nthr; t++)
-            th.emplace_back([&, t] {
-                for (int64_t j = 0; j < n; j++) {
-                    if (t == 0) {
-                        double s = M[j * n + j];
-                        for (int64_t k = 0; k < j; k++) s -= M[j * n + k] * M[j * n + k];
-                        if (!(s > 0.0)) spd = false;
-                        M[j * n + j] = spd ? std::sqrt(s) : 1.0;
-                    }
-                    barrier();
-                    const double gjj = M[j * n + j];
-                    const double *gj = &M[j * n];
-                    for (int64_t i = j + 1 + t; i < n; i += nthr) {
+    };
+    auto worker = [&](int t) {
+        for (int64_t k0 = 0; k0 < n; k0 += NB) {
+            const int64_t k1 = std::min(n, k0 + NB);
+            if (t == 0) {
+                for (int64_t j = k0; j < k1 && spd; j++) {
+                    double *gj = &M[j * n];
+                    double d = gj[j];
+                    for (int64_t k = k0; k < j; k++) d -= gj[k] * gj[k];
+                    if (!(d > 0.0)) { spd = false; break; }
+                    gj[j] = std::sqrt(d);
+                    for (int64_t i = j + 1; i < k1; i++) {
                         double *gi = &M[i * n];
                         double v = gi[j];
-                        for (int64_t k = 0; k < j; k++) v -= gi[k] * gj[k];
-                        gi[j] = v / gjj;
+                        for (int64_t k = k0; k < j; k++) v -= gi[k] * gj[k];
+                        gi[j] = v / gj[j];
                     }
-                    barrier();
                 }
-            });
+            }
+            barrier();
+            if (!spd) return;
+            // rows below the panel: G[i, k0:k1] = M[i, k0:k1] D^{-T}
+            for (int64_t i = k1 + t; i < n; i += T) {
+                double *gi = &M[i * n];
+                for (int64_t j = k0; j < k1; j++) {
+                    const double *gj = &M[j * n];
+                    double v = gi[j];
+                    for (int64_t k = k0; k < j; k++) v -= gi[k] * gj[k];
+                    gi[j] = v / gj[j];
+                }
+            }
+            barrier();
+            // trailing lower triangle: M[i, j] -= G[i, k0:k1] . G[j, k0:k1], k1 <= j <= i
+            for (int64_t i = k1 + t; i < n; i += T) {
+                double *gi = &M[i * n];
+                for (int64_t j = k1; j <= i; j++) gi[j] -= dot4(gi + k0, &M[j * n + k0], k1 - k0);
+            }
+            barrier();
+        }
+    };
+    if (T == 1) {
+        worker(0);
+    } else {
+        std::vector<std::thread> th;
+        for (int t = 0; t < T; t++) th.emplace_back(worker, t);
         for (auto &x : th) x.join();
     }
     if (!spd) return LAMG_ERR_DISCONNECTED;
@@ -452,20 +480,13 @@ int dense_pinv(const HostMat &A, std::vector<double> &pinv) {
         y[c] = 1.0 / M[c * n + c];
         for (int64_t i = c + 1; i < n; i++) {
             const double *gi = &M[i * n];
-            double t = 0.0;
-            for (int64_t k = c; k < i; k++) t -= gi[k] * y[k];
-            y[i] = t / gi[i];
+            y[i] = -dot4(gi + c, y + c, i - c) / gi[i];
         }
     });
     pinv.assign(n * n, 0.0);
     parallel_rows([&](int64_t i) {
         const double *hi = &H[i * n];
-        for (int64_t j = 0; j <= i; j++) {
-            const double *hj = &H[j * n];
-            double s = 0.0;
-            for (int64_t k = i; k < n; k++) s += hi[k] * hj[k];
-            pinv[i * n + j] = s - 1.0 / (double)n;
-        }
+        for (int64_t j = 0; j <= i; j++) pinv[i * n + j] = dot4(hi + i, &H[j * n + i], n - i) - 1.0 / (double)n;
     });
     for (int64_t i = 0; i < n; i++)
         for (int64_t j = 0; j < i; j++) pinv[j * n + i] = pinv[i * n + j];
@@ -482,7 +503,15 @@ double cycle_index(int64_t El, int64_t El1, int64_t E0) {
 
 // ----------------------------------------------------------------------------------- driver
 
-int build_hierarchy(const lamg_graph *g, const lamg_options &o, std::vector<HostLevel> &levels) {
+int build_hierarchy(const lamg_graph *g, const lamg_options &o, std::vector<HostLevel> &levels, double *times) {
+    using clk = std::chrono::steady_clock;
+    auto t = clk::now();
+    // wall time of each setup phase (SETUP_* order) added to times[]
+    auto lap = [&](int phase) {
+        const auto now = clk::now();
+        if (times) times[phase] += std::chrono::duration<double, std::milli>(now - t).count();
+        t = now;
+    };
     int rc = validate_graph(g);
     if (rc) return rc;
     if (o.K < 1 || o.K > 16 || o.nu_tv < 0 || o.coarsest_max < 1 || o.max_levels < 1 || o.dense_rows < 0 ||
@@ -492,6 +521,7 @@ int build_hierarchy(const lamg_graph *g, const lamg_options &o, std::vector<Host
     HostMat A;
     laplacian(g, A);
     const int64_t E0 = A.nnz() / 2;
+    lap(SETUP_INPUT);
     for (int l = 0;; l++) {
         levels.emplace_back();
         HostLevel &L = levels.back();
@@ -509,18 +539,23 @@ int build_hierarchy(const lamg_graph *g, const lamg_options &o, std::vector<Host
         if (nF > 0 && (double)nF >= o.elim_min_frac * (double)n) {
             L.kind = KIND_ELIM;
             schur(L.A, inF, L, Ac);
+            lap(SETUP_ELIM);
         } else {
+            lap(SETUP_ELIM);
             L.kind = KIND_AGG;
             L.ncol = greedy_colour(L.A, L.colour);
+            lap(SETUP_COLOUR);
             L.X.resize(n * o.K);
             L.aff.resize(L.A.nnz());
             L.strong.resize(L.A.nnz());
             rc = gpu_tv_and_affinity(L.A, L.colour, l, o.seed, o.K, o.nu_tv, o.tau_soc, o.veto,
                                      L.X.data(), L.aff.data(), L.strong.data());
             if (rc) return rc;
+            lap(SETUP_TV_AFFINITY);
             std::vector<int32_t> status, seed;
             aggregate(L, o, status, seed);
             if (o.caliber2) upgrade_caliber2(L, o, status, seed);
+            lap(SETUP_AGGREGATE);
             if (L.nc >= n || ((double)L.nc > 0.9 * (double)n && n <= 4096)) {
                 // no useful coarsening: this level becomes the coarsest
                 L.kind = KIND_COARSEST;
@@ -528,12 +563,14 @@ int build_hierarchy(const lamg_graph *g, const lamg_options &o, std::vector<Host
                 break;
             }
             galerkin(L, Ac);
+            lap(SETUP_GALERKIN);
         }
         A = std::move(Ac);
     }
     HostLevel &last = levels.back();
     if (last.A.n > 4096) return LAMG_ERR_SETUP;
     if (dense_pinv(last.A, last.pinv)) return LAMG_ERR_SETUP;
+    lap(SETUP_DENSE);
     for (size_t l = 0; l < levels.size(); l++) {
         HostLevel &L = levels[l];
         if (L.kind == KIND_ELIM) L.gamma = 1.0;

@@ -13,6 +13,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <thread>
 
 #include "hier.h"
@@ -604,6 +605,7 @@ int finalize(lamg_hier *h) {
     CKR(cudaEventCreate(&h->ev_a));
     CKR(cudaEventCreate(&h->ev_b));
     CKR(cudaEventCreateWithFlags(&h->ev_poll, cudaEventDisableTiming));
+    auto t_dev = std::chrono::steady_clock::now();
     build_orders(h);
     const int L = (int)h->host.size();
     for (int l = 0; l < L; l++)
@@ -633,6 +635,8 @@ int finalize(lamg_hier *h) {
     CKR(cudaMemsetAsync(h->red.scal, 0, S_COUNT * sizeof(double), h->stream));
     h->h_scal = pinned_slot();
     if (!h->h_scal) return LAMG_ERR_OOM;
+    auto t_sched = std::chrono::steady_clock::now();
+    h->setup_ms[SETUP_DEVICE] += std::chrono::duration<double, std::milli>(t_sched - t_dev).count();
     if ((rc = tune_kernels(h))) return rc;
     std::vector<int64_t> visits(L, 0);
     h->ops.clear();
@@ -655,15 +659,35 @@ int finalize(lamg_hier *h) {
     h->cycle_launches = count_cycle_launches(h);
     if ((rc = setup_persistent(h))) return rc;
     CKR(cudaStreamSynchronize(h->stream));
+    h->setup_ms[SETUP_SCHEDULE] +=
+        std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_sched).count();
     return LAMG_OK;
 }
+
+// The device's default stream-ordered memory pool keeps up to POOL_KEEP bytes of freed memory
+// (this process only) instead of returning it to the driver at every synchronisation: a setup
+// makes a few hundred allocations, and re-mapping memory for each was most of its device-layout
+// time.
+constexpr uint64_t POOL_KEEP = (uint64_t)4 << 30;
 
 int set_device(int dev) {
     int cnt = 0;
     cudaError_t e = cudaGetDeviceCount(&cnt);
     if (e != cudaSuccess || cnt == 0) return LAMG_ERR_NO_DEVICE;
     if (dev < 0 || dev >= cnt) return LAMG_ERR_INVALID;
-    return cuda_status(cudaSetDevice(dev));
+    e = cudaSetDevice(dev);
+    if (e != cudaSuccess) return cuda_status(e);
+    static std::once_flag once[64];
+    if (dev < 64)
+        std::call_once(once[dev], [dev] {
+            cudaMemPool_t pool = nullptr;
+            if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+                uint64_t keep = POOL_KEEP;
+                cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+            }
+            cudaGetLastError();
+        });
+    return LAMG_OK;
 }
 
 }  // namespace
@@ -725,7 +749,7 @@ int lamg_setup(const lamg_graph *g, const lamg_options *opt, lamg_hier **out) {
     lamg_hier *h = new lamg_hier();
     h->device = o.device;
     h->opt = o;
-    rc = build_hierarchy(g, o, h->host);
+    rc = build_hierarchy(g, o, h->host, h->setup_ms);
     if (!rc) rc = finalize(h);
     if (rc) { delete h; return rc; }
     *out = h;
@@ -1161,6 +1185,12 @@ int lamg_profile_schedule(lamg_hier *h, int32_t from_level, int64_t *out, int64_
     cudaFree(dprof);
     *count = 3 * (int64_t)nops;
     return rc;
+}
+
+int lamg_setup_times(const lamg_hier *h, double *out, int32_t cap) {
+    if (!h || !out || cap < SETUP_NPHASE) return LAMG_ERR_INVALID;
+    for (int i = 0; i < SETUP_NPHASE; i++) out[i] = h->setup_ms[i];
+    return LAMG_OK;
 }
 
 int lamg_schedule_info(const lamg_hier *h, int64_t *out, int64_t cap, int64_t *count) {
