@@ -119,6 +119,23 @@ static int64_t pick_F(const HostMat &A, int dmax, std::vector<uint8_t> &inF) {
 }
 
 // Sparse accumulator for one output row.
+// fn(t, begin, end) on T contiguous chunks of [0, n), one thread each (one thread when n is
+// below min_rows per thread). Chunks are in order, so per-chunk outputs concatenated in thread
+// order equal a sequential pass.
+template <class F>
+static void parallel_chunks(int64_t n, int64_t min_rows, F &&fn) {
+    const int hw = (int)std::max<unsigned>(1u, std::min<unsigned>(16u, std::thread::hardware_concurrency()));
+    const int T = (int)std::max<int64_t>(1, std::min<int64_t>(hw, n / std::max<int64_t>(1, min_rows)));
+    if (T == 1) {
+        fn(0, (int64_t)0, n);
+        return;
+    }
+    std::vector<std::thread> th;
+    for (int t = 0; t < T; t++)
+        th.emplace_back([&fn, t, T, n] { fn(t, n * t / T, n * (t + 1) / T); });
+    for (auto &x : th) x.join();
+}
+
 struct RowAcc {
     std::vector<double> v;
     std::vector<int64_t> stamp;
@@ -335,30 +352,47 @@ static void galerkin(const HostLevel &L, HostMat &Ac) {
     Ac.diag.assign(nc, 0.0);
     Ac.ci.clear();
     Ac.val.clear();
-    RowAcc acc(nc);
-    for (int64_t a = 0; a < nc; a++) {
-        acc.start(a);
-        for (int64_t t = ptr[a]; t < ptr[a + 1]; t++) {
-            const int64_t u = rows[t];
-            const double pa = pw[t];
-            int32_t c[2]; double p[2];
-            int k = p_row(L, u, c, p);
-            for (int s = 0; s < k; s++) acc.at(c[s]) += pa * A.diag[u] * p[s];
-            for (int64_t e = A.rp[u]; e < A.rp[u + 1]; e++) {
-                k = p_row(L, A.ci[e], c, p);
-                for (int s = 0; s < k; s++) acc.at(c[s]) += pa * A.val[e] * p[s];
+    // coarse rows in contiguous chunks, one accumulator per thread; each row is summed by one
+    // thread in the same order as a sequential pass
+    std::vector<std::vector<int32_t>> tci(16);
+    std::vector<std::vector<double>> tval(16);
+    std::vector<int64_t> len(nc, 0);
+    parallel_chunks(nc, 65536, [&](int t, int64_t a0, int64_t a1) {
+        RowAcc acc(nc);
+        std::vector<int32_t> &oc = tci[t];
+        std::vector<double> &ov = tval[t];
+        for (int64_t a = a0; a < a1; a++) {
+            acc.start(a);
+            for (int64_t q = ptr[a]; q < ptr[a + 1]; q++) {
+                const int64_t u = rows[q];
+                const double pa = pw[q];
+                int32_t c[2]; double p[2];
+                int k = p_row(L, u, c, p);
+                for (int s = 0; s < k; s++) acc.at(c[s]) += pa * A.diag[u] * p[s];
+                for (int64_t e = A.rp[u]; e < A.rp[u + 1]; e++) {
+                    k = p_row(L, A.ci[e], c, p);
+                    for (int s = 0; s < k; s++) acc.at(c[s]) += pa * A.val[e] * p[s];
+                }
             }
+            std::sort(acc.cols.begin(), acc.cols.end());
+            double d = 0.0;
+            const size_t before = oc.size();
+            for (int32_t j : acc.cols) {
+                if (j == a) { d = acc.v[j]; continue; }
+                if (acc.v[j] == 0.0) continue;
+                oc.push_back(j);
+                ov.push_back(acc.v[j]);
+            }
+            Ac.diag[a] = d;
+            len[a] = (int64_t)(oc.size() - before);
         }
-        std::sort(acc.cols.begin(), acc.cols.end());
-        double d = 0.0;
-        for (int32_t j : acc.cols) {
-            if (j == a) { d = acc.v[j]; continue; }
-            if (acc.v[j] == 0.0) continue;
-            Ac.ci.push_back(j);
-            Ac.val.push_back(acc.v[j]);
-        }
-        Ac.diag[a] = d;
-        Ac.rp[a + 1] = (int64_t)Ac.ci.size();
+    });
+    for (int64_t a = 0; a < nc; a++) Ac.rp[a + 1] = Ac.rp[a] + len[a];
+    Ac.ci.reserve(Ac.rp[nc]);
+    Ac.val.reserve(Ac.rp[nc]);
+    for (int t = 0; t < 16; t++) {
+        Ac.ci.insert(Ac.ci.end(), tci[t].begin(), tci[t].end());
+        Ac.val.insert(Ac.val.end(), tval[t].begin(), tval[t].end());
     }
 }
 

@@ -22,6 +22,21 @@ using namespace lamg;
 
 namespace {
 
+// fn(begin, end) on contiguous chunks of [0, n), one host thread each (up to 16; one thread
+// when n is below min_items per thread).
+template <class F>
+void host_chunks(int64_t n, int64_t min_items, F &&fn) {
+    const int hw = (int)std::max<unsigned>(1u, std::min<unsigned>(16u, std::thread::hardware_concurrency()));
+    const int T = (int)std::max<int64_t>(1, std::min<int64_t>(hw, n / std::max<int64_t>(1, min_items)));
+    if (T == 1) {
+        fn((int64_t)0, n);
+        return;
+    }
+    std::vector<std::thread> th;
+    for (int t = 0; t < T; t++) th.emplace_back([&fn, t, T, n] { fn(n * t / T, n * (t + 1) / T); });
+    for (auto &x : th) x.join();
+}
+
 // Device orders of all levels, from the coarsest up (see DevLevel).
 void build_orders(lamg_hier *h) {
     const int L = (int)h->host.size();
@@ -75,19 +90,21 @@ int upload_level(lamg_hier *h, int l) {
     std::vector<int32_t> iperm(n);
     for (int64_t i = 0; i < n; i++) iperm[D.perm[i]] = (int32_t)i;
     if (H.A.nnz() >= (int64_t)INT32_MAX) return LAMG_ERR_INVALID;
-    // operator in device order, columns ascending
+    // operator in device order, columns ascending (rows filled in parallel chunks)
     std::vector<int32_t> rp(n + 1, 0), ci(H.A.nnz());
     std::vector<double> val(H.A.nnz()), diag(n);
-    std::vector<std::pair<int32_t, double>> row;
-    for (int64_t i = 0; i < n; i++) {
-        const int32_t u = D.perm[i];
-        row.clear();
-        for (int64_t e = H.A.rp[u]; e < H.A.rp[u + 1]; e++) row.emplace_back(iperm[H.A.ci[e]], H.A.val[e]);
-        std::sort(row.begin(), row.end(), [](auto &a, auto &b) { return a.first < b.first; });
-        for (size_t k = 0; k < row.size(); k++) { ci[rp[i] + k] = row[k].first; val[rp[i] + k] = row[k].second; }
-        rp[i + 1] = rp[i] + (int32_t)row.size();
-        diag[i] = H.A.diag[u];
-    }
+    for (int64_t i = 0; i < n; i++) rp[i + 1] = rp[i] + (int32_t)(H.A.rp[D.perm[i] + 1] - H.A.rp[D.perm[i]]);
+    host_chunks(n, 65536, [&](int64_t i0, int64_t i1) {
+        std::vector<std::pair<int32_t, double>> row;
+        for (int64_t i = i0; i < i1; i++) {
+            const int32_t u = D.perm[i];
+            row.clear();
+            for (int64_t e = H.A.rp[u]; e < H.A.rp[u + 1]; e++) row.emplace_back(iperm[H.A.ci[e]], H.A.val[e]);
+            std::sort(row.begin(), row.end(), [](auto &a, auto &b) { return a.first < b.first; });
+            for (size_t k = 0; k < row.size(); k++) { ci[rp[i] + k] = row[k].first; val[rp[i] + k] = row[k].second; }
+            diag[i] = H.A.diag[u];
+        }
+    });
     std::vector<double> idiag(n);
     for (int64_t i = 0; i < n; i++) idiag[i] = 1.0 / diag[i];
     if ((rc = dupload(h, &D.rp, rp)) || (rc = dupload(h, &D.ci, ci)) || (rc = dupload(h, &D.val, val)) ||
@@ -115,17 +132,19 @@ int upload_level(lamg_hier *h, int l) {
         if (use) {
             std::vector<int32_t> sc(tot);
             std::vector<double> sv(tot, 0.0);
-            for (int64_t sl = 0; sl < ns; sl++) {
-                const int64_t w = (sp[sl + 1] - sp[sl]) / 32;
-                for (int64_t l = 0; l < 32; l++) {
-                    const int64_t i = 32 * sl + l;
-                    for (int64_t j = 0; j < w; j++) {
-                        const int64_t e = sp[sl] + 32 * j + l;
-                        if (i < n && j < rp[i + 1] - rp[i]) { sc[e] = ci[rp[i] + j]; sv[e] = val[rp[i] + j]; }
-                        else sc[e] = (int32_t)std::min<int64_t>(i, n - 1);
+            host_chunks(ns, 4096, [&](int64_t s0, int64_t s1) {
+                for (int64_t sl = s0; sl < s1; sl++) {
+                    const int64_t w = (sp[sl + 1] - sp[sl]) / 32;
+                    for (int64_t l = 0; l < 32; l++) {
+                        const int64_t i = 32 * sl + l;
+                        for (int64_t j = 0; j < w; j++) {
+                            const int64_t e = sp[sl] + 32 * j + l;
+                            if (i < n && j < rp[i + 1] - rp[i]) { sc[e] = ci[rp[i] + j]; sv[e] = val[rp[i] + j]; }
+                            else sc[e] = (int32_t)std::min<int64_t>(i, n - 1);
+                        }
                     }
                 }
-            }
+            });
             if ((rc = dupload(h, &D.sl_ptr, sp)) || (rc = dupload(h, &D.sl_col, sc)) || (rc = dupload(h, &D.sl_val, sv)))
                 return rc;
             D.sell = 1;
