@@ -205,6 +205,65 @@ __global__ void __launch_bounds__(BBS) bk_resid(int n, int k, const int32_t *__r
     }
 }
 
+// One right-hand side, one thread per row on the sliced-ELLPACK copy (entry j of row 32 s + l
+// at sp[s] + 32 j + l, value-0 padding at a valid column); entries summed in order.
+template <typename T>
+__device__ __forceinline__ T sell_row1(int row, const int32_t *__restrict__ sp, const int32_t *__restrict__ sc,
+                                       const T *__restrict__ sv, const T *x, int &e, int &w) {
+    const int s = row >> 5;
+    const int a = sp[s];
+    e = a + (row & 31);
+    w = (sp[s + 1] - a) >> 5;
+    T acc = T(0);
+    for (int j = 0; j < w; j += 4) {
+        int c[4];
+        T v[4], xv[4];
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+            const bool h = j + q < w;
+            c[q] = h ? sc[e + 32 * (j + q)] : 0;
+            v[q] = h ? sv[e + 32 * (j + q)] : T(0);
+        }
+#pragma unroll
+        for (int q = 0; q < 4; q++) xv[q] = j + q < w ? x[c[q]] : T(0);
+#pragma unroll
+        for (int q = 0; q < 4; q++)
+            if (j + q < w) acc += v[q] * xv[q];
+    }
+    return acc;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(64) bk_gs_sell(int r0, int r1, int s0, const int32_t *__restrict__ sp,
+                                                 const int32_t *__restrict__ sc, const T *__restrict__ sv,
+                                                 const T *__restrict__ idiag, const T *__restrict__ b, T *x) {
+    b_trigger();
+    const int row = 32 * s0 + (int)(blockIdx.x * blockDim.x + threadIdx.x);
+    const bool ok = row >= r0 && row < r1;
+    const T id = ok ? idiag[row] : T(1);
+    b_wait();
+    if (!ok) return;
+    int e, w;
+    const T s = sell_row1<T>(row, sp, sc, sv, x, e, w);
+    x[row] = (b[row] - s) * id;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(BBS) bk_resid_sell(int n, const int32_t *__restrict__ sp,
+                                                     const int32_t *__restrict__ sc, const T *__restrict__ sv,
+                                                     const T *__restrict__ diag, const T *__restrict__ x,
+                                                     const T *__restrict__ b, T *r) {
+    b_trigger();
+    const int row = (int)(blockIdx.x * blockDim.x + threadIdx.x);
+    const bool ok = row < n;
+    const T d = ok ? diag[row] : T(0);
+    b_wait();
+    if (!ok) return;
+    int e, w;
+    const T s = sell_row1<T>(row, sp, sc, sv, x, e, w);
+    r[row] = b[row] - (d * x[row] + s);
+}
+
 // b^c = P^T r
 template <typename T, int KL, int TPR>
 __global__ void __launch_bounds__(BBS) bk_restrict(int nc, int k, const int32_t *__restrict__ ptr,
@@ -580,6 +639,20 @@ static void blaunch(void (*kernel)(KArgs...), int64_t grid, cudaStream_t s, Args
     cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
 }
 
+template <typename... KArgs, typename... Args>
+static void blaunch_bs(void (*kernel)(KArgs...), int64_t grid, unsigned bs, cudaStream_t s, Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(grid < 1 ? 1 : grid));
+    cfg.blockDim = dim3(bs);
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+
 static inline int64_t nblocks(int64_t threads) { return (threads + BBS - 1) / BBS; }
 static inline int64_t rblocks(int64_t threads) {
     int64_t b = (threads + BBS - 1) / BBS;
@@ -625,10 +698,13 @@ static int row_tpr(int KL, int level_tpr) {
 
 struct BLev {
     int kind = 0, ncol = 0, tpr = 1, pt_tpr = 1;
+    int gs_tpr = 1, rs_tpr = 1;   // one right-hand side: the level's kernel forms (0: sliced)
     int64_t n = 0, nc = 0, nF = 0, nlong = 0;
     std::vector<int64_t> cptr, lptr;
     const int32_t *lrows = nullptr;
     const void *idiag = nullptr;
+    const int32_t *sl_ptr = nullptr, *sl_col = nullptr;
+    const void *sl_val = nullptr;
     const int32_t *rp = nullptr, *ci = nullptr, *agg = nullptr, *agg2 = nullptr, *pt_ptr = nullptr,
                   *pt_row = nullptr, *pf_col = nullptr, *pft_ptr = nullptr, *pft_f = nullptr;
     const void *val = nullptr, *diag = nullptr, *wt = nullptr, *pt_w = nullptr, *pf_val = nullptr,
@@ -682,6 +758,8 @@ static int build_ctx(lamg_hier *h, BatchCtx *c) {
         B.kind = D.kind; B.ncol = D.ncol; B.tpr = D.tpr; B.pt_tpr = D.pt_tpr;
         B.n = D.n; B.nc = D.nc; B.nF = D.nF; B.cptr = D.cptr;
         B.nlong = D.nlong; B.lptr = D.lptr; B.lrows = D.lrows;
+        B.gs_tpr = D.gs_tpr; B.rs_tpr = D.rs_tpr; B.sl_ptr = D.sl_ptr; B.sl_col = D.sl_col;
+        if (D.sell && (rc = typed_copy<T>(h, D.sl_val, D.sell_nnz, &B.sl_val))) return rc;
         B.rp = D.rp; B.ci = D.ci; B.agg = D.agg; B.agg2 = D.agg2; B.pt_ptr = D.pt_ptr; B.pt_row = D.pt_row;
         B.pf_col = D.pf_col; B.pft_ptr = D.pft_ptr; B.pft_f = D.pft_f; B.pinv = D.pinv;
         const int64_t pte = (D.kind == KIND_AGG) ? (int64_t)h->host[l].A.n * 2 : 0;
@@ -769,7 +847,13 @@ static void bop(const Op &op, BatchCtx *c, cudaStream_t s) {
         case OP_GS: {
             const int r0 = (int)L.cptr[op.colour], r1 = (int)L.cptr[op.colour + 1];
             if (r1 <= r0) break;
-            const int tpr = row_tpr(KL, L.tpr);
+            if (KL == 1 && L.gs_tpr == 0) {
+                const int s0 = r0 / 32, s1 = (r1 + 31) / 32;
+                blaunch_bs(bk_gs_sell<T>, (32 * (s1 - s0) + 63) / 64, 64, s, r0, r1, s0, L.sl_ptr, L.sl_col,
+                           (const T *)L.sl_val, idiag, (const T *)b, x);
+                break;
+            }
+            const int tpr = KL == 1 ? L.gs_tpr : row_tpr(KL, L.tpr);
             const int nl = L.nlong ? (int)(L.lptr[op.colour + 1] - L.lptr[op.colour]) : 0;
 #define C2(KLv, TPRv, ...) case KT_CODE(KLv, TPRv): blaunch(bk_gs<T, KLv, TPRv>, nl + nblocks((int64_t)(r1 - r0 - nl) * KLv * TPRv), s, r0, r1, nl, k, L.rp, L.ci, val, idiag, (const T *)b, x); break;
             switch (KT_CODE(KL, tpr)) { KT_CASES(C2) }
@@ -777,7 +861,12 @@ static void bop(const Op &op, BatchCtx *c, cudaStream_t s) {
             break;
         }
         case OP_RESID: {
-            const int tpr = row_tpr(KL, L.tpr);
+            if (KL == 1 && L.rs_tpr == 0) {
+                blaunch(bk_resid_sell<T>, nblocks(n), s, n, L.sl_ptr, L.sl_col, (const T *)L.sl_val, diag,
+                        (const T *)x, (const T *)b, r);
+                break;
+            }
+            const int tpr = KL == 1 ? L.rs_tpr : row_tpr(KL, L.tpr);
 #define C3(KLv, TPRv, ...) case KT_CODE(KLv, TPRv): blaunch(bk_resid<T, KLv, TPRv>, L.nlong + nblocks((int64_t)n * KLv * TPRv), s, n, k, L.rp, L.ci, val, diag, (const T *)x, (const T *)b, r, L.lrows, (int)L.nlong); break;
             switch (KT_CODE(KL, tpr)) { KT_CASES(C3) }
 #undef C3
