@@ -269,6 +269,18 @@ int lamg_op_list(const lamg_hier *h, int32_t *out, int64_t cap, int64_t *count);
  * int64 entries; *count = entries written. Errors: INVALID. */
 int lamg_schedule_info(const lamg_hier *h, int64_t *out, int64_t cap, int64_t *count);
 
+/* The paper's own outer iteration (Section 2): the stationary iteration x <- x + M(b - A x)
+ * with M one cycle, each step followed by the min-residual recombination of the last kappa
+ * saved iterates, alpha = argmin || (b - A x) - A E alpha || with E = [x_1 - x, ..., x_m - x]
+ * (normal equations solved by Gaussian elimination with partial pivoting), x <- x + E alpha,
+ * then the mean-zero projection (Eq. 1). kappa = 0: plain stationary cycles. The per-cycle
+ * relative residuals (stats.hist) are what the paper's convergence factor is measured on.
+ * Same conventions as lamg_solve (b projected, stop when ||b - A x|| / ||b|| <= tol, checked
+ * every cycle on the true residual); FP64 hierarchies only; 0 <= kappa <= 16.
+ * Errors: INVALID, NOT_CONVERGED (stats valid), CUDA, TIMEOUT. */
+int lamg_solve_stationary(lamg_hier *h, const double *b, double *phi, int32_t kappa,
+                          const lamg_solve_opts *so, lamg_stats *st);
+
 /* Wall time (ms) of the setup phases of a hierarchy built by lamg_setup, 9 entries: input
  * validation and Laplacian; elimination (Eq. 2); colouring; test vectors and affinities on the
  * GPU (Section 2, Eq. 3, Eq. 9) with their copies; aggregation and caliber-2 (Eqs. 4, 13);

@@ -118,6 +118,7 @@ def lib():
         L.lamg_schedule_info.argtypes = [P, P, C.c_int64, C.POINTER(C.c_int64)]
         L.lamg_solve_many.argtypes = [C.c_int32, P, P, P, C.POINTER(SolveOpts), P]
         L.lamg_setup_times.argtypes = [P, P, C.c_int32]
+        L.lamg_solve_stationary.argtypes = [P, P, P, C.c_int32, C.POINTER(SolveOpts), P]
         L.lamg_profile_schedule.argtypes = [P, C.c_int32, P, C.c_int64, C.POINTER(C.c_int64)]
         _lib = L
     return _lib
@@ -209,6 +210,20 @@ class Hierarchy:
         rc = lib().lamg_solve(self._h, _p(b), _p(phi), C.byref(so), C.byref(st))
         _check(rc, "lamg_solve", (LAMG_OK, 5) if allow_unconverged else (LAMG_OK,))
         return phi, _stats(st, hist)
+
+    def stationary(self, b, tol: float = 1e-8, maxit: int = 100, kappa: int = 4,
+                   allow_unconverged: bool = False):
+        """lamg_solve_stationary: cycles with min-residual recombination of the last kappa
+        iterates (the paper's solver loop); returns (phi, stats with the residual history)."""
+        b = _c(b, np.float64)
+        x = np.zeros(self.n)
+        so = SolveOpts(tol, maxit, 0, None)
+        st = Stats()
+        h = np.zeros(maxit + 1)
+        st.hist = h.ctypes.data
+        rc = lib().lamg_solve_stationary(self._h, _p(b), _p(x), kappa, C.byref(so), C.byref(st))
+        _check(rc, "lamg_solve_stationary", (LAMG_OK, 5) if allow_unconverged else (LAMG_OK,))
+        return x, _stats(st, h)
 
     def solve_ptr(self, b_ptr: int, phi_ptr: int, tol: float = 1e-8, maxit: int = 100,
                   stream: int = 0, device: bool = True, hist: bool = False, persistent: bool = False):
