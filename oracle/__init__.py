@@ -23,10 +23,11 @@ _lib = None
 
 DEFAULTS = dict(K=4, nu_tv=3, dmax=4, nu_pre=1, nu_post=2, coarsest_max=1024, max_levels=100,
                 veto=1, caliber2=1, tv_lex=0, symmetric=0, seed=3, dense_rows=4096,
+                cheb_colours=32, cheb_degree=2,
                 Q=2.5, tau_soc=0.05, elim_min_frac=0.01, snap=1e-3, guard_eps=1e-10,
                 gamma_fixed=0.0)
 _IKEYS = ["K", "nu_tv", "dmax", "nu_pre", "nu_post", "coarsest_max", "max_levels", "veto",
-          "caliber2", "tv_lex", "symmetric", "seed", "dense_rows"]
+          "caliber2", "tv_lex", "symmetric", "seed", "dense_rows", "cheb_colours", "cheb_degree"]
 _DKEYS = ["Q", "tau_soc", "elim_min_frac", "snap", "guard_eps", "gamma_fixed"]
 
 KIND = {0: "elim", 1: "agg", 2: "coarsest"}
@@ -82,6 +83,7 @@ def lib():
         L.oracle_galerkin.argtypes = [C.c_int64, P, P, P, P, C.c_int64, P, P, P]
         L.oracle_pinv.restype = C.c_int
         L.oracle_pinv.argtypes = [C.c_int64, P, P, P, P, P]
+        L.oracle_cheb_apply.argtypes = [C.c_int64, P, P, P, P, C.c_int, P, P, P]
         L.oracle_mat_meta.argtypes = [P, P]
         L.oracle_mat_get.argtypes = [P, P, P, P, P]
         L.oracle_mat_free.argtypes = [P]
@@ -201,6 +203,15 @@ def pinv(A: Matrix) -> np.ndarray:
     return out
 
 
+def cheb_apply(A: Matrix, x, b, m: int = 2):
+    """One Chebyshev smoothing polynomial of degree m on A x = b; returns (x, lambda)."""
+    x = _c(x, np.float64).copy()
+    b = _c(b, np.float64)
+    coef = np.zeros(17)
+    lib().oracle_cheb_apply(*A.args(), m, _p(x), _p(b), _p(coef))
+    return x, float(coef[0])
+
+
 class Hierarchy:
     """An oracle hierarchy built from a graph (Section 2 setup)."""
 
@@ -230,10 +241,12 @@ class Hierarchy:
 
     def level(self, l: int) -> dict:
         L = lib()
-        meta = np.zeros(6, np.int64); dmeta = np.zeros(1)
+        meta = np.zeros(7, np.int64); dmeta = np.zeros(18)
         L.oracle_level_meta(self._h, l, _p(meta), _p(dmeta))
         d = dict(kind=KIND[int(meta[0])], n=int(meta[1]), nnz=int(meta[2]), ncol=int(meta[3]),
-                 nc=int(meta[4]), n_caliber2=int(meta[5]), gamma=float(dmeta[0]))
+                 nc=int(meta[4]), n_caliber2=int(meta[5]), gamma=float(dmeta[0]),
+                 cheb=bool(meta[6]), cheb_lambda=float(dmeta[1]), cheb_c1=dmeta[2:10].copy(),
+                 cheb_c2=dmeta[10:18].copy())
         dtypes = dict(rp=np.int64, ci=np.int32, val=np.float64, diag=np.float64, colour=np.int32,
                       cidx=np.int32, agg=np.int32, agg2=np.int32, wt=np.float64, seed_of=np.int32,
                       X=np.float64, aff=np.float64, strong=np.uint8, pinv=np.float64)

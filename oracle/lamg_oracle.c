@@ -47,6 +47,9 @@ typedef struct {
     int coarsest_max;   /* dense coarsest level when n <= this */
     int dense_rows;     /* dense coarsest level also when n <= this and the level has at least
                            n^2 / 8 off-diagonal entries (0: off) */
+    int cheb_colours;   /* an aggregation level with more colours than this is smoothed by a
+                           Chebyshev polynomial instead of Gauss-Seidel (0: never) */
+    int cheb_degree;    /* degree of the polynomial that replaces one Gauss-Seidel sweep */
     int max_levels;
     int veto;           /* strength-of-connection veto on/off (Eq. 9) */
     int caliber2;       /* selective caliber-2 on/off (Section 3.2) */
@@ -82,6 +85,10 @@ typedef struct {
     double *aff;           /* affinity per off-diagonal entry */
     uint8_t *strong;       /* 1 if the entry survives the veto (u's view) */
     double gamma;
+    /* Chebyshev smoothing (levels with many colours): step k of one polynomial is
+       d <- c1[k] d + c2[k] D^{-1}(b - A x), x <- x + d */
+    int cheb;
+    double cheb_lambda, cheb_c1[8], cheb_c2[8];
     /* coarsest */
     double *pinv;          /* dense n x n pseudo-inverse */
     /* cycle state */
@@ -217,6 +224,51 @@ static void gs_sweep_colour(const Level *L, double *x, const double *b, int reve
     for (int ci = 0; ci < L->ncol; ci++) {
         int c = reverse ? L->ncol - 1 - ci : ci;
         for (int64_t t = L->cptr[c]; t < L->cptr[c + 1]; t++) gs_row(&L->A, L->corder[t], x, b);
+    }
+}
+
+/* Chebyshev smoothing of A x = b (polynomial smoothing; a reading for levels whose colouring
+ * makes a Gauss-Seidel sweep hundreds of parallel steps): the Jacobi-preconditioned Chebyshev
+ * iteration of degree m on the interval [lambda/30, lambda] of D^{-1} A, lambda the Gershgorin
+ * bound max_u (1 + sum_v |A_uv| / A_uu). With theta = (hi + lo)/2, delta = (hi - lo)/2,
+ * sigma = theta/delta and rho_0 = 1/sigma, rho_k = 1/(2 sigma - rho_{k-1}), step k updates every
+ * row from the previous iterate: d <- c1[k] d + c2[k] D^{-1}(b - A x), x <- x + d, with
+ * c1[0] = 0, c2[0] = 1/theta, c1[k] = rho_k rho_{k-1}, c2[k] = 2 rho_k / delta. */
+static void cheb_coefficients(Level *L, int m) {
+    const Mat *A = &L->A;
+    double lam = 0.0;
+    for (int64_t u = 0; u < A->n; u++) {
+        double s = 0.0;
+        for (int64_t e = A->rp[u]; e < A->rp[u + 1]; e++) s += fabs(A->val[e]);
+        const double g = 1.0 + s / A->diag[u];
+        if (g > lam) lam = g;
+    }
+    const double hi = lam, lo = lam / 30.0;
+    const double theta = (hi + lo) / 2.0, delta = (hi - lo) / 2.0, sigma = theta / delta;
+    double rho = 1.0 / sigma;
+    L->cheb_lambda = lam;
+    L->cheb_c1[0] = 0.0;
+    L->cheb_c2[0] = 1.0 / theta;
+    for (int k = 1; k < m && k < 8; k++) {
+        const double rn = 1.0 / (2.0 * sigma - rho);
+        L->cheb_c1[k] = rn * rho;
+        L->cheb_c2[k] = 2.0 * rn / delta;
+        rho = rn;
+    }
+}
+
+static void cheb_poly(const Level *L, double *x, const double *b, int m, double *d, double *xn) {
+    const Mat *A = &L->A;
+    const int64_t n = A->n;
+    for (int k = 0; k < m; k++) {
+        for (int64_t u = 0; u < n; u++) {
+            double s = A->diag[u] * x[u];
+            for (int64_t e = A->rp[u]; e < A->rp[u + 1]; e++) s += A->val[e] * x[A->ci[e]];
+            const double du = (k == 0 ? 0.0 : L->cheb_c1[k] * d[u]) + L->cheb_c2[k] * (b[u] - s) / A->diag[u];
+            d[u] = du;
+            xn[u] = x[u] + du;
+        }
+        memcpy(x, xn, n * sizeof(double));
     }
 }
 
@@ -636,6 +688,7 @@ static void fill_opts(Opts *o, const int64_t *iopt, const double *dopt) {
     o->max_levels = (int)iopt[6]; o->veto = (int)iopt[7]; o->caliber2 = (int)iopt[8];
     o->tv_lex = (int)iopt[9]; o->symmetric = (int)iopt[10]; o->seed = (uint64_t)iopt[11];
     o->dense_rows = (int)iopt[12];
+    o->cheb_colours = (int)iopt[13]; o->cheb_degree = (int)iopt[14];
     o->Q = dopt[0]; o->tau_soc = dopt[1]; o->elim_min_frac = dopt[2]; o->snap = dopt[3];
     o->guard_eps = dopt[4]; o->gamma_fixed = dopt[5];
 }
@@ -784,6 +837,10 @@ int oracle_setup(int64_t n, const int64_t *rp, const int32_t *ci, const double *
             free(inF);
             L->kind = LV_AGG;
             colour_level(L);
+            if (o->cheb_colours > 0 && L->ncol > o->cheb_colours) {
+                L->cheb = 1;
+                cheb_coefficients(L, o->cheb_degree);
+            }
             test_vectors(L, o, l);
             affinity_and_veto(L, o);
             aggregate(L, o);
@@ -863,8 +920,13 @@ static void visit(Hier *H, int l, int first) {
     }
     /* aggregation level */
     const Opts *o = &H->o;
+    double *cd = NULL, *cx = NULL;
+    if (L->cheb) { cd = xcalloc(n, sizeof(double)); cx = xcalloc(n, sizeof(double)); }
     if (first) memset(L->x, 0, n * sizeof(double));
-    for (int s = 0; s < o->nu_pre; s++) gs_sweep_colour(L, L->x, L->b, 0);
+    for (int s = 0; s < o->nu_pre; s++) {
+        if (L->cheb) cheb_poly(L, L->x, L->b, o->cheb_degree, cd, cx);
+        else gs_sweep_colour(L, L->x, L->b, 0);
+    }
     residual(A, L->x, L->b, L->r);
     memset(C->b, 0, C->A.n * sizeof(double));
     for (int64_t u = 0; u < n; u++) {
@@ -882,7 +944,12 @@ static void visit(Hier *H, int l, int first) {
         for (int t = 0; t < k; t++) s += p[t] * C->x[c[t]];
         L->x[u] += s;
     }
-    for (int s = 0; s < o->nu_post; s++) gs_sweep_colour(L, L->x, L->b, 1);
+    for (int s = 0; s < o->nu_post; s++) {
+        if (L->cheb) cheb_poly(L, L->x, L->b, o->cheb_degree, cd, cx);
+        else gs_sweep_colour(L, L->x, L->b, 1);
+    }
+    free(cd);
+    free(cx);
 }
 
 /* The preconditioner: one cycle on A_0 z = r from z = 0, then the mean-zero projection.
@@ -1032,14 +1099,18 @@ int64_t oracle_stationary(Hier *H, const double *b_in, double *x, double tol, in
 
 int oracle_nlevels(const Hier *H) { return H->nlev; }
 
-/* meta: kind, n, nnz, ncol, nc, n_caliber2 ; dmeta: gamma */
+/* meta: kind, n, nnz, ncol, nc, n_caliber2, Chebyshev smoothing; dmeta: gamma, lambda,
+ * c1[8], c2[8] */
 void oracle_level_meta(const Hier *H, int l, int64_t *meta, double *dmeta) {
     const Level *L = &H->lv[l];
     meta[0] = L->kind; meta[1] = L->A.n; meta[2] = L->A.nnz; meta[3] = L->ncol; meta[4] = L->nc;
     int64_t c2 = 0;
     if (L->kind == LV_AGG) for (int64_t u = 0; u < L->A.n; u++) if (L->agg2[u] >= 0) c2++;
     meta[5] = c2;
+    meta[6] = L->cheb;
     dmeta[0] = L->gamma;
+    dmeta[1] = L->cheb_lambda;
+    for (int k = 0; k < 8; k++) { dmeta[2 + k] = L->cheb_c1[k]; dmeta[10 + k] = L->cheb_c2[k]; }
 }
 
 /* Copy a named per-level array into dst; returns the number of elements (0 if absent). */
@@ -1153,6 +1224,23 @@ int oracle_pinv(int64_t n, const int64_t *rp, const int32_t *ci, const double *v
     int rc = coarsest_pinv(&L);
     if (rc == OK) { memcpy(pinv, L.pinv, n * n * sizeof(double)); free(L.pinv); }
     return rc;
+}
+
+/* One Chebyshev smoothing polynomial of degree m on A x = b (x updated in place); coef
+ * (optional) receives lambda, c1[0..m), c2[0..m). */
+void oracle_cheb_apply(int64_t n, const int64_t *rp, const int32_t *ci, const double *val, const double *diag,
+                       int m, double *x, const double *b, double *coef) {
+    Level L; memset(&L, 0, sizeof(L));
+    L.A.n = n; L.A.nnz = rp[n]; L.A.rp = (int64_t *)rp; L.A.ci = (int32_t *)ci;
+    L.A.val = (double *)val; L.A.diag = (double *)diag;
+    cheb_coefficients(&L, m);
+    double *d = xcalloc(n, sizeof(double)), *xn = xcalloc(n, sizeof(double));
+    cheb_poly(&L, x, b, m, d, xn);
+    free(d); free(xn);
+    if (coef) {
+        coef[0] = L.cheb_lambda;
+        for (int k = 0; k < m && k < 8; k++) { coef[1 + k] = L.cheb_c1[k]; coef[9 + k] = L.cheb_c2[k]; }
+    }
 }
 
 void oracle_mat_meta(const OMat *M, int64_t *nnz_n) { nnz_n[0] = M->A.n; nnz_n[1] = M->A.nnz; }

@@ -358,6 +358,58 @@ def test_dense_level_becomes_the_coarsest():
     assert oracle.Hierarchy(g, coarsest_max=16, dense_rows=g.n - 1).nlevels > 1
 
 
+def _laplacian_matrix(g):
+    rows = np.repeat(np.arange(g.n), np.diff(g.rp))
+    return oracle.Matrix(g.rp, g.ci, -g.w, np.bincount(rows, weights=g.w, minlength=g.n))
+
+
+@pytest.mark.parametrize("m", [1, 2, 3, 5])
+def test_chebyshev_smoother_is_the_chebyshev_error_polynomial(m):
+    # one application maps the error e = x* - x to C_m((theta I - D^-1 A)/delta) e / C_m(sigma),
+    # C_m the Chebyshev polynomial of the first kind, on [lambda/30, lambda]: evaluated here
+    # densely from that definition, with a signed coarse-like operator (a positive entry)
+    rng = np.random.default_rng(m)
+    g = gg.random_connected(40, 60, seed=m)
+    A = _laplacian_matrix(g)
+    val = A.val.copy()
+    val[0] = abs(val[0]) * 0.3                      # one positive off-diagonal (signed coarse weights)
+    j = np.where((np.repeat(np.arange(g.n), np.diff(g.rp)) == g.ci[0]) & (g.ci == 0))[0][0]
+    val[j] = val[0]                                 # keep it symmetric
+    A = oracle.Matrix(A.rp, A.ci, val, A.diag)
+    M = A.dense()
+    xs = rng.standard_normal(g.n)
+    b = M @ xs
+    x0 = rng.standard_normal(g.n)
+    x1, lam = oracle.cheb_apply(A, x0, b, m)
+    D = np.diag(M)
+    assert lam == pytest.approx(max(1 + np.abs(M[i] - np.diag(D)[i]).sum() / D[i] for i in range(g.n)), rel=1e-15)
+    hi, lo = lam, lam / 30
+    th, de = (hi + lo) / 2, (hi - lo) / 2
+    Y = (th * np.eye(g.n) - M / D[:, None]) / de
+    C0, C1 = np.eye(g.n), Y
+    c0, c1 = 1.0, th / de
+    for _ in range(m - 1):
+        C0, C1 = C1, 2 * Y @ C1 - C0
+        c0, c1 = c1, 2 * (th / de) * c1 - c0
+    e1 = (C1 / c1) @ (xs - x0)
+    assert np.linalg.norm((xs - x1) - e1) <= 1e-11 * np.linalg.norm(xs - x0)
+
+
+def test_chebyshev_bound_is_two_on_a_laplacian_and_the_solver_still_solves():
+    g = gg.grid2d(24, 20, 1.0, 0.05)
+    _, lam = oracle.cheb_apply(_laplacian_matrix(g), np.zeros(g.n), np.zeros(g.n), 2)
+    assert lam == pytest.approx(2.0, abs=1e-14)
+    # every aggregation level smoothed by the polynomial (colour threshold 1)
+    H = oracle.Hierarchy(g, coarsest_max=16, cheb_colours=1)
+    assert all(L["cheb"] for L in H.levels if L["kind"] == "agg")
+    b = gg.rhs(g, 3)
+    out = H.fcg(b, tol=1e-10, maxit=100)
+    ref = np.linalg.pinv(dense_L(g), rcond=1e-10, hermitian=True) @ (b - b.mean())
+    assert np.linalg.norm(out["x"] - ref) <= 1e-8 * np.linalg.norm(ref)
+    # and the default keeps Gauss-Seidel on levels with few colours
+    assert not any(L["cheb"] for L in oracle.Hierarchy(g, coarsest_max=16).levels)
+
+
 @pytest.mark.parametrize("gamma", [1.0, 2.0])
 def test_symmetric_cycle_is_symmetric(gamma):
     # With nu_pre = nu_post, forward pre- and reverse post-smoothing, P^T restriction and exact
