@@ -97,8 +97,14 @@ typedef struct lamg_options {
                               timing noise of the timed choice on the benchmark workloads) */
     int32_t dense_rows;    /* a level with at most this many nodes (<= 4096) and at least n^2/8
                               off-diagonal entries is the coarsest, solved densely: 4096; 0 off */
-    int32_t reserved[1];
-} lamg_options;
+    int32_t cheb_colours;  /* an aggregation level with more colour classes than this is smoothed
+                              by a Chebyshev polynomial instead of colour-ordered Gauss-Seidel
+                              (polynomial smoothers, the paper's Conclusion): 32; 0 never */
+    int32_t cheb_degree;   /* degree of the Jacobi-preconditioned Chebyshev polynomial (interval
+                              [lambda/30, lambda], lambda the Gershgorin bound of D^-1 A) that
+                              replaces one sweep: 2 (1..8) */
+    int32_t reserved[3];
+} lamg_options;                    /* 144 bytes */
 
 typedef struct lamg_graph {
     int64_t n;
@@ -255,7 +261,8 @@ int lamg_profile_cycle(lamg_hier *h, int64_t *out, int64_t cap, int64_t *count);
 
 /* The static step list of one cycle: 3 int32 per step (kind, level, colour); kinds 0 first
  * GS colour from zero, 1 GS colour class, 2 zero, 3 residual, 4 restriction, 5 prolongation,
- * 6 elimination restriction, 7 elimination interpolation, 8 coarsest solve. out may be NULL
+ * 6 elimination restriction, 7 elimination interpolation, 8 coarsest solve, 9 Chebyshev
+ * smoothing step (colour = step index), 10 copy after a polynomial of odd degree. out may be NULL
  * to query *count. Errors: INVALID. */
 int lamg_op_list(const lamg_hier *h, int32_t *out, int64_t cap, int64_t *count);
 

@@ -39,7 +39,8 @@ class Options(C.Structure):
                 ("seed", C.c_uint64), ("Q", C.c_double), ("tau_soc", C.c_double),
                 ("elim_min_frac", C.c_double), ("snap", C.c_double), ("guard_eps", C.c_double),
                 ("gamma_fixed", C.c_double), ("device", C.c_int32), ("tail_rows", C.c_int32),
-                ("cluster_rows", C.c_int32), ("row_tpr", C.c_int32), ("sell", C.c_int32), ("autotune", C.c_int32), ("dense_rows", C.c_int32), ("reserved", C.c_int32 * 1)]
+                ("cluster_rows", C.c_int32), ("row_tpr", C.c_int32), ("sell", C.c_int32), ("autotune", C.c_int32), ("dense_rows", C.c_int32), ("cheb_colours", C.c_int32), ("cheb_degree", C.c_int32),
+                ("reserved", C.c_int32 * 3)]
 
 
 class Graph(C.Structure):
@@ -274,7 +275,7 @@ class Hierarchy:
                     gbs=float(out[1]) / (float(out[0]) * 1e-3) / 1e9)
 
     OP_KINDS = ["gs_first", "gs", "zero", "resid", "restrict", "prolong", "elim_restrict",
-                "elim_interp", "coarse"]
+                "elim_interp", "coarse", "cheb", "cheb_copy"]
 
     def op_list(self) -> list:
         cnt = C.c_int64()

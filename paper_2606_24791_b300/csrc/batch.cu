@@ -264,6 +264,58 @@ __global__ void __launch_bounds__(BBS) bk_resid_sell(int n, const int32_t *__res
     r[row] = b[row] - (d * x[row] + s);
 }
 
+// One step of the Chebyshev smoothing polynomial for k columns (as k_cheb): every row from the
+// previous iterate xin, d <- c1 d + c2 (b - A xin) / A_uu (first step: c1 term absent),
+// xout = xin + d. Blocks b < nl take the long rows lr[b].
+template <typename T, int KL, int TPR>
+__global__ void __launch_bounds__(BBS) bk_cheb(int n, int k, const int32_t *__restrict__ rp,
+                                               const int32_t *__restrict__ ci, const T *__restrict__ val,
+                                               const T *__restrict__ diag, const T *__restrict__ idiag,
+                                               const T *__restrict__ b, const T *xin, T *xout, T *d, T c1, T c2,
+                                               int first, const int32_t *__restrict__ lr, int nl) {
+    b_trigger();
+    if ((int)blockIdx.x < nl) {
+        const int row = lr[blockIdx.x];
+        const int e0 = rp[row], e1 = rp[row + 1];
+        const T dg = diag[row], id = idiag[row];
+        b_wait();
+        const T s = block_row_k<T, KL>(e0, e1, k, ci, val, xin);
+        if ((int)threadIdx.x < k) {
+            const size_t i = (size_t)row * k + threadIdx.x;
+            const T r = b[i] - (dg * xin[i] + s);
+            const T dn = (first ? T(0) : c1 * d[i]) + c2 * r * id;
+            d[i] = dn;
+            xout[i] = xin[i] + dn;
+        }
+        return;
+    }
+    const int t = (blockIdx.x - nl) * BBS + threadIdx.x;
+    constexpr int G = KL * TPR;
+    const int lig = t % G, j = lig % KL, sub = lig / KL;
+    const int row = t / G;
+    bool ok = row < n;
+    int e0 = ok ? rp[row] + sub : 0, e1 = ok ? rp[row + 1] : 0;
+    if (ok && e1 - (e0 - sub) > LONG_ROW) { ok = false; e0 = e1; }
+    const T dg = ok ? diag[row] : T(0), id = ok ? idiag[row] : T(0);
+    b_wait();
+    const T s = rowsum_k<T, KL, TPR>(e0, e1, k, j, ci, val, xin);
+    if (ok && sub == 0 && j < k) {
+        const size_t i = (size_t)row * k + j;
+        const T r = b[i] - (dg * xin[i] + s);
+        const T dn = (first ? T(0) : c1 * d[i]) + c2 * r * id;
+        d[i] = dn;
+        xout[i] = xin[i] + dn;
+    }
+}
+
+template <typename T>
+__global__ void bk_copy(int64_t cnt, const T *__restrict__ src, T *dst) {
+    b_trigger();
+    b_wait();
+    const int64_t t = (int64_t)blockIdx.x * BBS + threadIdx.x;
+    if (t < cnt) dst[t] = src[t];
+}
+
 // b^c = P^T r
 template <typename T, int KL, int TPR>
 __global__ void __launch_bounds__(BBS) bk_restrict(int nc, int k, const int32_t *__restrict__ ptr,
@@ -705,6 +757,9 @@ struct BLev {
     const void *idiag = nullptr;
     const int32_t *sl_ptr = nullptr, *sl_col = nullptr;
     const void *sl_val = nullptr;
+    int cheb = 0;
+    double cheb_c1[8] = {0}, cheb_c2[8] = {0};
+    void *t = nullptr, *d = nullptr;   // Chebyshev second iterate and direction, n x k
     const int32_t *rp = nullptr, *ci = nullptr, *agg = nullptr, *agg2 = nullptr, *pt_ptr = nullptr,
                   *pt_row = nullptr, *pf_col = nullptr, *pft_ptr = nullptr, *pft_f = nullptr;
     const void *val = nullptr, *diag = nullptr, *wt = nullptr, *pt_w = nullptr, *pf_val = nullptr,
@@ -759,6 +814,8 @@ static int build_ctx(lamg_hier *h, BatchCtx *c) {
         B.n = D.n; B.nc = D.nc; B.nF = D.nF; B.cptr = D.cptr;
         B.nlong = D.nlong; B.lptr = D.lptr; B.lrows = D.lrows;
         B.gs_tpr = D.gs_tpr; B.rs_tpr = D.rs_tpr; B.sl_ptr = D.sl_ptr; B.sl_col = D.sl_col;
+        B.cheb = D.cheb;
+        for (int q = 0; q < 8; q++) { B.cheb_c1[q] = D.cheb_c1[q]; B.cheb_c2[q] = D.cheb_c2[q]; }
         if (D.sell && (rc = typed_copy<T>(h, D.sl_val, D.sell_nnz, &B.sl_val))) return rc;
         B.rp = D.rp; B.ci = D.ci; B.agg = D.agg; B.agg2 = D.agg2; B.pt_ptr = D.pt_ptr; B.pt_row = D.pt_row;
         B.pf_col = D.pf_col; B.pft_ptr = D.pft_ptr; B.pft_f = D.pft_f; B.pinv = D.pinv;
@@ -810,6 +867,12 @@ static int build_ctx(lamg_hier *h, BatchCtx *c) {
         }
         if (B.kind == KIND_AGG && (rc = dalloc(h, &r, B.n * k))) return rc;
         B.x = x; B.b = b; B.r = r;
+        if (B.cheb) {
+            T *tt = nullptr, *dd = nullptr;
+            if ((rc = dalloc(h, &tt, B.n * k)) || (rc = dalloc(h, &dd, B.n * k))) return rc;
+            B.t = tt;
+            B.d = dd;
+        }
     }
     if (c->prec == LAMG_FP32) {
         if ((rc = dalloc(h, &c->z64, n0 * k))) return rc;
@@ -908,6 +971,20 @@ static void bop(const Op &op, BatchCtx *c, cudaStream_t s) {
 #define C8(KLv, ...) case KLv: blaunch(bk_coarse<T, KLv>, rblocks((int64_t)n * 32), s, n, k, L.pinv, (const T *)b, x); break;
             switch (KL) { K_CASES(C8) }
 #undef C8
+            break;
+        case OP_CHEB: {
+            const int q = op.colour;
+            const T *xin = (q & 1) ? (const T *)L.t : (const T *)x;
+            T *xout = (q & 1) ? x : (T *)L.t;
+            const int tpr = row_tpr(KL, L.tpr);
+            const T c1 = (T)L.cheb_c1[q], c2 = (T)L.cheb_c2[q];
+#define C11(KLv, TPRv, ...) case KT_CODE(KLv, TPRv): blaunch(bk_cheb<T, KLv, TPRv>, L.nlong + nblocks((int64_t)n * KLv * TPRv), s, n, k, L.rp, L.ci, val, diag, idiag, (const T *)b, xin, xout, (T *)L.d, c1, c2, q == 0 ? 1 : 0, L.lrows, (int)L.nlong); break;
+            switch (KT_CODE(KL, tpr)) { KT_CASES(C11) }
+#undef C11
+            break;
+        }
+        case OP_CHEB_COPY:
+            blaunch(bk_copy<T>, nblocks((int64_t)n * k), s, (int64_t)n * k, (const T *)L.t, x);
             break;
     }
 }

@@ -279,6 +279,53 @@ __global__ void __launch_bounds__(BS) k_resid(int n, const int32_t *__restrict__
     if (ok && sub == 0) r[g] = b[g] - (d * x[g] + s);
 }
 
+// One step of the Chebyshev smoothing polynomial: every row from the previous iterate xin,
+// r_u = b_u - (A xin)_u, d_u <- c1 d_u + c2 r_u / A_uu (first step: d_u = c2 r_u / A_uu),
+// xout_u = xin_u + d_u. Blocks b < nl take the long rows lr[b].
+template <int TPR>
+__global__ void __launch_bounds__(BS) k_cheb(int n, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
+                                             const double *__restrict__ val, const double *__restrict__ diag,
+                                             const double *__restrict__ idiag, const double *__restrict__ b,
+                                             const double *xin, double *xout, double *d, double c1, double c2,
+                                             int first, const int32_t *__restrict__ lr, int nl) {
+    pdl_trigger();
+    if ((int)blockIdx.x < nl) {
+        const int row = lr[blockIdx.x];
+        const int e0 = rp[row], e1 = rp[row + 1];
+        const double dg = diag[row], id = idiag[row];
+        pdl_wait();
+        const double s = block_row(e0, e1, ci, val, xin);
+        if (threadIdx.x == 0) {
+            const double r = b[row] - (dg * xin[row] + s);
+            const double dn = (first ? 0.0 : c1 * d[row]) + c2 * r * id;
+            d[row] = dn;
+            xout[row] = xin[row] + dn;
+        }
+        return;
+    }
+    const int g = (int)(((blockIdx.x - nl) * (unsigned)BS + threadIdx.x) / TPR);
+    const int sub = threadIdx.x % TPR;
+    bool ok = g < n;
+    RowPre p = row_pre<TPR>(ok, g, sub, rp, ci, val);
+    drop_long(p, ok, sub);
+    const double dg = ok ? diag[g] : 0.0, id = ok ? idiag[g] : 0.0;
+    pdl_wait();
+    const double s = row_finish<TPR>(p, ci, val, xin);
+    if (ok && sub == 0) {
+        const double r = b[g] - (dg * xin[g] + s);
+        const double dn = (first ? 0.0 : c1 * d[g]) + c2 * r * id;
+        d[g] = dn;
+        xout[g] = xin[g] + dn;
+    }
+}
+
+__global__ void k_copy(int n, const double *__restrict__ src, double *dst) {
+    pdl_trigger();
+    pdl_wait();
+    const int i = blockIdx.x * BS + threadIdx.x;
+    if (i < n) dst[i] = src[i];
+}
+
 // Restriction b^c = P^T r (Section 2): segmented sum over the fine rows of each aggregate,
 // caliber-2 rows contributing w or 1 - w.
 template <int TPR>
@@ -731,6 +778,21 @@ void launch_op(const Op &op, std::vector<DevLevel> &lv, const Reduce &red, cudaS
             break;
         case OP_COARSE:
             launch(k_coarse, red_blocks((int64_t)n * 32), s, n, (const double *)L.pinv, (const double *)L.b, L.x);
+            break;
+        case OP_CHEB: {
+            const int k = op.colour;
+            const double *xin = (k & 1) ? L.t : L.x;
+            double *xout = (k & 1) ? L.x : L.t;
+            const int tpr = L.gs_tpr > 0 ? L.gs_tpr : L.tpr;
+#define GRID_C(T) (unsigned)L.nlong + blocks((int64_t)n * (T))
+            TPR_DISPATCH(tpr, k_cheb, GRID_C, n, (const int32_t *)L.rp, (const int32_t *)L.ci, (const double *)L.val,
+                         (const double *)L.diag, (const double *)L.idiag, (const double *)L.b, xin, xout, L.d,
+                         L.cheb_c1[k], L.cheb_c2[k], k == 0 ? 1 : 0, (const int32_t *)L.lrows, (int)L.nlong);
+#undef GRID_C
+            break;
+        }
+        case OP_CHEB_COPY:
+            launch(k_copy, blocks(n), s, n, (const double *)L.t, L.x);
             break;
     }
 }

@@ -41,6 +41,11 @@ struct DevLevel {
     // residual, A p with its dot product, true residual): 0 one thread per row on the sliced
     // copy, else that many lanes per CSR row; set by rule and refined by timing at setup
     int gs_tpr = 1, rs_tpr = 1;
+    // Chebyshev smoothing (levels with many colours): coefficients of each step, the second
+    // iterate buffer and the step direction
+    int cheb = 0;
+    double cheb_c1[8] = {0}, cheb_c2[8] = {0};
+    double *t = nullptr, *d = nullptr;
     int32_t *sl_ptr = nullptr, *sl_col = nullptr;
     double *sl_val = nullptr;
     // aggregation: P rows (coarse device ids) and P^T as CSR over coarse rows
@@ -71,6 +76,8 @@ enum OpKind {
     OP_ELIM_RESTRICT, // b_{l+1} = b_C + P_F^T b_F
     OP_ELIM_INTERP,   // x_F = P_F x_C + b_F / d_F
     OP_COARSE,        // x = A^+ b, then the mean-zero projection
+    OP_CHEB,          // step `colour` of the Chebyshev smoothing polynomial (x <-> t alternate)
+    OP_CHEB_COPY,     // x = t (after a polynomial of odd degree)
 };
 
 struct Op {

@@ -38,6 +38,10 @@ struct HostLevel {
     std::vector<uint8_t> strong;  // per off-diagonal entry (lamg_setup only)
     std::vector<double> pinv;     // coarsest: dense pseudo-inverse
     double gamma = 0.0;
+    // Chebyshev smoothing instead of Gauss-Seidel (aggregation levels with many colours):
+    // step k of one polynomial is d <- c1[k] d + c2[k] D^{-1}(b - A x), x <- x + d
+    int cheb = 0;
+    double cheb_lambda = 0.0, cheb_c1[8] = {0}, cheb_c2[8] = {0};
 };
 
 struct Status {
@@ -63,6 +67,8 @@ enum SetupPhase {
 int build_hierarchy(const lamg_graph *g, const lamg_options &o, std::vector<HostLevel> &levels,
                     double *times = nullptr);
 int greedy_colour(const HostMat &A, std::vector<int32_t> &colour);
+// Chebyshev smoothing decision and coefficients of an aggregation level (ncol set).
+void cheb_setup(HostLevel &L, const lamg_options &o);
 int dense_pinv(const HostMat &A, std::vector<double> &pinv);
 double cycle_index(int64_t El, int64_t El1, int64_t E0);
 

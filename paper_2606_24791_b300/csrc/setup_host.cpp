@@ -535,6 +535,37 @@ double cycle_index(int64_t El, int64_t El1, int64_t E0) {
     return std::max(1.0, g);
 }
 
+// Chebyshev smoothing of an aggregation level whose colouring has more than cheb_colours
+// classes (a sweep would be that many dependent parallel steps): the Jacobi-preconditioned
+// Chebyshev iteration of degree cheb_degree on [lambda/30, lambda], lambda the Gershgorin
+// bound max_u (1 + sum_v |A_uv| / A_uu) of D^{-1} A. With theta = (hi + lo)/2,
+// delta = (hi - lo)/2, sigma = theta/delta, rho_0 = 1/sigma and rho_k = 1/(2 sigma - rho_{k-1}):
+// c1[0] = 0, c2[0] = 1/theta, c1[k] = rho_k rho_{k-1}, c2[k] = 2 rho_k / delta.
+void cheb_setup(HostLevel &L, const lamg_options &o) {
+    L.cheb = (o.cheb_colours > 0 && L.ncol > o.cheb_colours) ? 1 : 0;
+    if (!L.cheb) return;
+    const HostMat &A = L.A;
+    double lam = 0.0;
+    for (int64_t u = 0; u < A.n; u++) {
+        double s = 0.0;
+        for (int64_t e = A.rp[u]; e < A.rp[u + 1]; e++) s += std::fabs(A.val[e]);
+        const double g = 1.0 + s / A.diag[u];
+        if (g > lam) lam = g;
+    }
+    const double hi = lam, lo = lam / 30.0;
+    const double theta = (hi + lo) / 2.0, delta = (hi - lo) / 2.0, sigma = theta / delta;
+    double rho = 1.0 / sigma;
+    L.cheb_lambda = lam;
+    L.cheb_c1[0] = 0.0;
+    L.cheb_c2[0] = 1.0 / theta;
+    for (int k = 1; k < o.cheb_degree && k < 8; k++) {
+        const double rn = 1.0 / (2.0 * sigma - rho);
+        L.cheb_c1[k] = rn * rho;
+        L.cheb_c2[k] = 2.0 * rn / delta;
+        rho = rn;
+    }
+}
+
 // ----------------------------------------------------------------------------------- driver
 
 int build_hierarchy(const lamg_graph *g, const lamg_options &o, std::vector<HostLevel> &levels, double *times) {
@@ -549,7 +580,7 @@ int build_hierarchy(const lamg_graph *g, const lamg_options &o, std::vector<Host
     int rc = validate_graph(g);
     if (rc) return rc;
     if (o.K < 1 || o.K > 16 || o.nu_tv < 0 || o.coarsest_max < 1 || o.max_levels < 1 || o.dense_rows < 0 ||
-        o.dense_rows > 4096)
+        o.dense_rows > 4096 || o.cheb_colours < 0 || (o.cheb_colours > 0 && (o.cheb_degree < 1 || o.cheb_degree > 8)))
         return LAMG_ERR_INVALID;
     levels.clear();
     HostMat A;
@@ -578,6 +609,7 @@ int build_hierarchy(const lamg_graph *g, const lamg_options &o, std::vector<Host
             lap(SETUP_ELIM);
             L.kind = KIND_AGG;
             L.ncol = greedy_colour(L.A, L.colour);
+            cheb_setup(L, o);
             lap(SETUP_COLOUR);
             L.X.resize(n * o.K);
             L.aff.resize(L.A.nnz());

@@ -20,6 +20,8 @@
 
 using namespace lamg;
 
+static_assert(sizeof(lamg_options) == 144, "lamg_options layout changed: update the header's size note");
+
 namespace {
 
 // fn(begin, end) on contiguous chunks of [0, n), one host thread each (up to 16; one thread
@@ -211,6 +213,11 @@ int upload_level(lamg_hier *h, int l) {
             return rc;
         D.pt_tpr = choose_tpr(H.nc ? (double)cnt[H.nc] / (double)H.nc : 1.0);
         if ((rc = dalloc(h, &D.r, n))) return rc;
+        D.cheb = H.cheb;
+        if (H.cheb) {
+            for (int k = 0; k < 8; k++) { D.cheb_c1[k] = H.cheb_c1[k]; D.cheb_c2[k] = H.cheb_c2[k]; }
+            if ((rc = dalloc(h, &D.t, n)) || (rc = dalloc(h, &D.d, n))) return rc;
+        }
     } else if (H.kind == KIND_ELIM) {
         const int64_t nc = H.nc, nF = n - nc;
         std::vector<int32_t> pfc(4 * nF, -1);
@@ -265,11 +272,22 @@ void emit_visit(lamg_hier *h, std::vector<int64_t> &visits, int l, bool first) {
         return;
     }
     const int npre = h->opt.nu_pre, npost = h->opt.nu_post;
-    if (first && npre == 0) h->ops.push_back({OP_ZERO, l, 0});
-    for (int s = 0; s < npre; s++) {
-        int c0 = 0;
-        if (s == 0 && first) { h->ops.push_back({OP_GS_FIRST, l, 0}); c0 = 1; }
-        for (int c = c0; c < D.ncol; c++) h->ops.push_back({OP_GS, l, c});
+    // one Chebyshev polynomial: m steps alternating between x and t, back into x
+    auto cheb_poly = [&]() {
+        const int m = h->opt.cheb_degree;
+        for (int k = 0; k < m; k++) h->ops.push_back({OP_CHEB, l, k});
+        if (m & 1) h->ops.push_back({OP_CHEB_COPY, l, 0});
+    };
+    if (D.cheb) {
+        if (first) h->ops.push_back({OP_ZERO, l, 0});
+        for (int s = 0; s < npre; s++) cheb_poly();
+    } else {
+        if (first && npre == 0) h->ops.push_back({OP_ZERO, l, 0});
+        for (int s = 0; s < npre; s++) {
+            int c0 = 0;
+            if (s == 0 && first) { h->ops.push_back({OP_GS_FIRST, l, 0}); c0 = 1; }
+            for (int c = c0; c < D.ncol; c++) h->ops.push_back({OP_GS, l, c});
+        }
     }
     h->ops.push_back({OP_RESID, l, 0});
     h->ops.push_back({OP_RESTRICT, l, 0});
@@ -278,8 +296,11 @@ void emit_visit(lamg_hier *h, std::vector<int64_t> &visits, int l, bool first) {
     const int64_t nv = (int64_t)std::floor((double)(j + 1) * g) - (int64_t)std::floor((double)j * g);
     for (int64_t i = 0; i < nv; i++) emit_visit(h, visits, l + 1, i == 0);
     h->ops.push_back({OP_PROLONG, l, 0});
-    for (int s = 0; s < npost; s++)
-        for (int c = D.ncol - 1; c >= 0; c--) h->ops.push_back({OP_GS, l, c});
+    for (int s = 0; s < npost; s++) {
+        if (D.cheb) cheb_poly();
+        else
+            for (int c = D.ncol - 1; c >= 0; c--) h->ops.push_back({OP_GS, l, c});
+    }
 }
 
 int capture(lamg_hier *h, cudaGraphExec_t *out, int which) {
@@ -368,6 +389,8 @@ void lamg::op_bytes(const lamg_hier *h, const Op &op, double s, double *mat, dou
         }
         case OP_ELIM_INTERP: m = 16 * nF + 5 * s * nF; v = s * nc + 2 * s * nF; break;
         case OP_COARSE: m = 8 * n * n; v = 2 * s * n; break;
+        case OP_CHEB: m = (4 + s) * z + 4 * (n + 1) + 2 * s * n; v = s * (n + std::min(z, n)) + 3 * s * n; break;
+        case OP_CHEB_COPY: v = 2 * s * n; break;
     }
     *mat = m;
     *vec = v;
@@ -405,9 +428,12 @@ int upload_tables(lamg_hier *h) {
     return LAMG_OK;
 }
 
-// Device tables of the persistent solve kernel.
+// Device tables of the persistent solve kernel (not for hierarchies with Chebyshev levels,
+// whose steps it does not run).
 int setup_persistent(lamg_hier *h) {
     int rc;
+    for (const DevLevel &D : h->dev)
+        if (D.cheb) return LAMG_OK;
     const int L = (int)h->dev.size();
     const int64_t tail_rows = h->opt.tail_rows > 0 ? h->opt.tail_rows : 8192;
     // single-CTA segments: maximal runs of steps on levels with at most tail_rows rows (the
@@ -590,7 +616,7 @@ int choose_cluster(lamg_hier *h) {
     std::vector<int64_t> smax(L + 1, 0), lng(L + 1, 0);
     for (int l = L - 1; l >= 0; l--) {
         smax[l] = std::max(smax[l + 1], h->dev[l].n);
-        lng[l] = lng[l + 1] + h->dev[l].nlong;
+        lng[l] = lng[l + 1] + h->dev[l].nlong + (h->dev[l].cheb ? 1 : 0);   // nor Chebyshev levels
     }
     std::vector<int> cand;
     for (int l = 0; l < L; l++)
@@ -739,6 +765,8 @@ void lamg_options_default(lamg_options *o) {
     o->cluster_rows = 0;
     o->autotune = 0;
     o->dense_rows = 4096;
+    o->cheb_colours = 32;
+    o->cheb_degree = 2;
 }
 
 const char *lamg_strerror(int c) {
@@ -763,6 +791,7 @@ int lamg_setup(const lamg_graph *g, const lamg_options *opt, lamg_hier **out) {
     lamg_options o;
     if (opt) o = *opt; else lamg_options_default(&o);
     if (o.row_tpr < 0 || o.row_tpr > 32 || (o.row_tpr & (o.row_tpr - 1))) return LAMG_ERR_INVALID;
+    if (o.cheb_colours < 0 || (o.cheb_colours > 0 && (o.cheb_degree < 1 || o.cheb_degree > 8))) return LAMG_ERR_INVALID;
     int rc = set_device(o.device);
     if (rc) return rc;
     lamg_hier *h = new lamg_hier();
@@ -781,6 +810,7 @@ int lamg_import(const lamg_level_desc *lv, int32_t nl, const lamg_options *opt, 
     lamg_options o;
     if (opt) o = *opt; else lamg_options_default(&o);
     if (o.row_tpr < 0 || o.row_tpr > 32 || (o.row_tpr & (o.row_tpr - 1))) return LAMG_ERR_INVALID;
+    if (o.cheb_colours < 0 || (o.cheb_colours > 0 && (o.cheb_degree < 1 || o.cheb_degree > 8))) return LAMG_ERR_INVALID;
     int rc = set_device(o.device);
     if (rc) return rc;
     lamg_hier *h = new lamg_hier();
@@ -816,6 +846,9 @@ int lamg_import(const lamg_level_desc *lv, int32_t nl, const lamg_options *opt, 
             for (int64_t u = 0; u < n; u++)
                 for (int64_t e = H.A.rp[u]; e < H.A.rp[u + 1]; e++)
                     if (H.colour[H.A.ci[e]] == H.colour[u]) { delete h; return LAMG_ERR_INVALID; }
+            H.ncol = 0;
+            for (int32_t c : H.colour) H.ncol = std::max(H.ncol, c + 1);
+            cheb_setup(H, o);
         } else if (d.kind == KIND_ELIM) {
             if (!d.cidx) { delete h; return LAMG_ERR_INVALID; }
             H.cidx.assign(d.cidx, d.cidx + n);
@@ -976,7 +1009,7 @@ int lamg_solve(lamg_hier *h, const double *b, double *phi, const lamg_solve_opts
 // dynamic shared memory its tables take.
 bool lamg::many_eligible(const lamg_hier *h, size_t *smem) {
     int64_t nl = 0;
-    for (const DevLevel &D : h->dev) nl += D.nlong;
+    for (const DevLevel &D : h->dev) nl += D.nlong + (D.cheb ? 1 : 0);   // nor Chebyshev levels
     const size_t sm = cluster_smem((int)h->dev.size(), h->ncptr, (int)h->ops.size());
     if (smem) *smem = sm;
     const int64_t entries = h->dev[0].n + h->dev[0].nnz;
@@ -1115,7 +1148,7 @@ int lamg_cycle(lamg_hier *h, const double *r, double *z, uint32_t flags) {
     }
     CKR(cudaMemcpyAsync(z, h->nat_out, n * sizeof(double), devp ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
     GridBar hb{};
-    CKR(cudaMemcpyAsync(&hb, h->bar, sizeof(GridBar), cudaMemcpyDeviceToHost, s));
+    if (h->bar) CKR(cudaMemcpyAsync(&hb, h->bar, sizeof(GridBar), cudaMemcpyDeviceToHost, s));
     CKR(cudaEventRecord(h->ev_b, s));
     int rc = wait_event(h, h->ev_b);
     if (rc) return rc;

@@ -1,0 +1,83 @@
+"""Chebyshev smoothing on levels with many colours, GPU against the oracle (B300).
+
+The smoothing polynomial is the same arithmetic on both sides up to summation order and the
+reciprocal diagonal, so the FP64 bars are those of Gauss-Seidel levels: cycle and FCG iterates
+within 1e-10 of the oracle on its own hierarchy, solutions to 1e-9 with equal iteration counts.
+"""
+import numpy as np
+import pytest
+
+import graphgen as gg
+import oracle
+import paper_2606_24791_b300 as lamg
+from test_gpu_parity import oracle_levels
+
+pytestmark = pytest.mark.gpu
+
+
+def rel(a, b):
+    return np.linalg.norm(np.asarray(a) - np.asarray(b)) / max(np.linalg.norm(b), 1e-300)
+
+
+CASES = {
+    # every aggregation level smoothed by the polynomial (colour threshold 1)
+    "grid_all": (lambda: gg.grid2d(40, 36, 1.0, 0.1), dict(coarsest_max=16, cheb_colours=1)),
+    "hubs_all": (lambda: gg.grid_with_hubs(40, 40, 4, 500, seed=3), dict(coarsest_max=16, cheb_colours=1)),
+    # the default threshold: only the coarse power-law level with 43 colours
+    "chunglu5000": (lambda: gg.chung_lu(5000, 2.1, 16, seed=1), dict(coarsest_max=24)),
+}
+
+
+@pytest.mark.parametrize("name", sorted(CASES))
+@pytest.mark.parametrize("degree", [1, 2, 3])
+def test_cheb_cycle_and_iterates_match_oracle(name, degree):
+    make, opts = CASES[name]
+    g = make()
+    o = dict(opts, cheb_degree=degree)
+    H = oracle.Hierarchy(g, **o)
+    assert any(L["cheb"] for L in H.levels)
+    P = lamg.import_levels(oracle_levels(H), cheb_colours=o.get("cheb_colours", 32), cheb_degree=degree)
+    kinds = {k for k, _, _ in P.op_list()}
+    assert "cheb" in kinds and (("cheb_copy" in kinds) == (degree % 2 == 1))
+    rng = np.random.default_rng(4)
+    r = rng.standard_normal(g.n)
+    r -= r.mean()
+    assert rel(P.cycle(r), H.cycle(r)) <= 1e-10, name
+    b = gg.rhs(g, 2)
+    ref = H.fcg(b, tol=1e-300, maxit=4, record=True)
+    for k in range(1, ref["iters"] + 1):
+        x, _ = P.solve(b, tol=1e-300, maxit=k, allow_unconverged=True)
+        assert rel(x, ref["iterates"][k - 1]) <= 1e-10, (name, k)
+    P.close()
+
+
+def test_cheb_setup_matches_oracle_and_solves():
+    g = gg.chung_lu(20000, 2.1, 16, seed=1)
+    b = gg.rhs(g, 2)
+    H = oracle.Hierarchy(g)
+    P = lamg.setup(g)
+    assert [i["n"] for i in P.info] == [L["n"] for L in H.levels]
+    assert sum(L["cheb"] for L in H.levels) >= 1
+    x, st = P.solve(b, 1e-8, 200)
+    ref = H.fcg(b, 1e-8, 200)
+    assert st["iters"] == ref["iters"] and st["relres_true"] <= 2e-8
+    assert rel(x, ref["x"]) <= 1e-9
+    # multi-RHS columns equal single solves; the FP32 cycle reaches the tolerance
+    B = gg.rhs(g, seed=5, k=3)
+    X, sts = P.solve_batch(B, 1e-8, 200)
+    for j in range(3):
+        xj, stj = P.solve(B[:, j], 1e-8, 200)
+        assert sts[j]["iters"] == stj["iters"] and rel(X[:, j], xj) <= 1e-10
+    P32 = lamg.setup(g, precision=lamg.FP32)
+    x32, st32 = P32.solve(b, 1e-8, 200)
+    assert st32["relres_true"] <= 2e-8 and rel(x32, ref["x"]) <= 1e-5
+    P.close()
+    P32.close()
+
+
+def test_cheb_rejects_bad_degree():
+    g = gg.grid2d(16, 16)
+    with pytest.raises(lamg.LamgError):
+        lamg.setup(g, cheb_degree=9)
+    with pytest.raises(lamg.LamgError):
+        lamg.setup(g, cheb_degree=0)
