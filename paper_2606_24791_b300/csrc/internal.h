@@ -49,6 +49,11 @@ struct Status {
     std::string msg;
 };
 
+// Host threads one setup may use: min(16, hardware threads). (Measured: giving each of the
+// server's concurrent setups an equal share of the host made served latency worse; a setup's
+// own latency is what a request waits for.)
+int setup_threads();
+
 // host setup (setup_host.cpp)
 int validate_graph(const lamg_graph *g);
 // Setup phases timed by build_hierarchy and finalize (milliseconds, lamg_setup_times).

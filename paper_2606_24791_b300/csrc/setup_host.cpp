@@ -119,12 +119,16 @@ static int64_t pick_F(const HostMat &A, int dmax, std::vector<uint8_t> &inF) {
 }
 
 // Sparse accumulator for one output row.
+int setup_threads() {
+    return (int)std::max<unsigned>(1u, std::min<unsigned>(16u, std::thread::hardware_concurrency()));
+}
+
 // fn(t, begin, end) on T contiguous chunks of [0, n), one thread each (one thread when n is
 // below min_rows per thread). Chunks are in order, so per-chunk outputs concatenated in thread
 // order equal a sequential pass.
 template <class F>
 static void parallel_chunks(int64_t n, int64_t min_rows, F &&fn) {
-    const int hw = (int)std::max<unsigned>(1u, std::min<unsigned>(16u, std::thread::hardware_concurrency()));
+    const int hw = setup_threads();
     const int T = (int)std::max<int64_t>(1, std::min<int64_t>(hw, n / std::max<int64_t>(1, min_rows)));
     if (T == 1) {
         fn(0, (int64_t)0, n);
@@ -422,7 +426,7 @@ int dense_pinv(const HostMat &A, std::vector<double> &pinv) {
         M[i * n + i] += A.diag[i];
         for (int64_t e = A.rp[i]; e < A.rp[i + 1]; e++) M[i * n + A.ci[e]] += A.val[e];
     }
-    const int nthr = (int)std::max<unsigned>(1u, std::min<unsigned>(16u, std::thread::hardware_concurrency()));
+    const int nthr = setup_threads();
     // lower Cholesky factor G (row-major, in place): M = G G^T, right-looking in panels of NB
     // columns. Per panel: the diagonal block by one thread, then the rows below it (a forward
     // substitution each) and the trailing lower triangle (one dot product of NB per entry)

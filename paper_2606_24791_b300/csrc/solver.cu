@@ -28,7 +28,7 @@ namespace {
 // when n is below min_items per thread).
 template <class F>
 void host_chunks(int64_t n, int64_t min_items, F &&fn) {
-    const int hw = (int)std::max<unsigned>(1u, std::min<unsigned>(16u, std::thread::hardware_concurrency()));
+    const int hw = setup_threads();
     const int T = (int)std::max<int64_t>(1, std::min<int64_t>(hw, n / std::max<int64_t>(1, min_items)));
     if (T == 1) {
         fn((int64_t)0, n);
