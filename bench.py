@@ -276,16 +276,42 @@ def cpu_baseline(g, b, reps: int = 3) -> dict:
             "setup_s": setup_s}
 
 
+# the source a kernel's counters depend on: its own definition and the device helpers it calls
+KERNEL_SOURCES = {"k_gs": ["struct RowPre {", "RowPre row_pre(", "double row_finish(", "double block_row(",
+                           "void __launch_bounds__(BS) k_gs("]}
+
+
+def _definition(src: str, signature: str) -> str:
+    """Text of the definition that starts at `signature`, up to its matching closing brace."""
+    i = src.index(signature)
+    j = src.index("{", i)
+    depth = 0
+    for k in range(j, len(src)):
+        if src[k] == "{":
+            depth += 1
+        elif src[k] == "}":
+            depth -= 1
+            if depth == 0:
+                return src[i:k + 1]
+    raise ValueError(signature)
+
+
+def kernel_source_sha(kernel: str) -> str:
+    src = open(os.path.join(ROOT, "paper_2606_24791_b300", "csrc", "cycle_kernels.cu")).read()
+    text = "\n".join(_definition(src, sig) for sig in KERNEL_SOURCES[kernel])
+    return hashlib.sha256(text.encode()).hexdigest()
+
+
 def traffic_for(kernel: str):
-    """ncu DRAM bytes per launch recorded for `kernel`, if the kernel source is unchanged."""
+    """ncu DRAM bytes per launch recorded for `kernel`, if the kernel's source is unchanged."""
     path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
-    if not os.path.exists(path):
+    if not os.path.exists(path) or kernel not in KERNEL_SOURCES:
         return None
     rec = json.load(open(path))
-    src = open(os.path.join(ROOT, "paper_2606_24791_b300", "csrc", "cycle_kernels.cu"), "rb").read()
-    if rec.get("source_sha256") != hashlib.sha256(src).hexdigest():
+    k = rec.get("kernels", {}).get(kernel)
+    if not k or k.get("source_sha256") != kernel_source_sha(kernel):
         return None
-    return rec.get("kernels", {}).get(kernel)
+    return k.get("dram_bytes")
 
 
 def schedule_counts(P, iters: int) -> dict:
