@@ -36,6 +36,7 @@ struct HostLevel {
     std::vector<double> X;        // test vectors n x K (lamg_setup only)
     std::vector<double> aff;      // per off-diagonal entry (lamg_setup only)
     std::vector<uint8_t> strong;  // per off-diagonal entry (lamg_setup only)
+    std::vector<uint8_t> adm;     // strong and passes the energy-ratio guard (lamg_setup only)
     std::vector<double> pinv;     // coarsest: dense pseudo-inverse
     double gamma = 0.0;
     // Chebyshev smoothing instead of Gauss-Seidel (aggregation levels with many colours):
@@ -84,9 +85,11 @@ int gpu_testvectors(const HostMat &A, const std::vector<int32_t> &colour, int le
                     uint64_t seed, int K, int nu, double *X);
 int gpu_affinity(const HostMat &A, const double *X, int K, double tau, double *aff,
                  uint8_t *strong);
+// ... and the guard of Eq. 4 per entry (adm[e]: strong and energy ratio <= Q), from the
+// moments of Appendix B computed on the GPU.
 int gpu_tv_and_affinity(const HostMat &A, const std::vector<int32_t> &colour, int level,
                         uint64_t seed, int K, int nu, double tau, int veto, double *X,
-                        double *aff, uint8_t *strong);
+                        double *aff, uint8_t *strong, double Q, double eps, uint8_t *adm);
 
 int cuda_status(cudaError_t e);
 

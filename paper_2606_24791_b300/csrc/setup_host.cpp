@@ -235,15 +235,22 @@ static void aggregate(HostLevel &L, const lamg_options &o, std::vector<int32_t> 
     const HostMat &A = L.A;
     const int64_t n = A.n;
     const int K = o.K;
-    std::vector<double> s0(n, 0.0), s1(n * K, 0.0), s2(n * K, 0.0);
-    for (int64_t u = 0; u < n; u++) {
-        for (int64_t e = A.rp[u]; e < A.rp[u + 1]; e++) {
-            const double w = -A.val[e];
-            const double *xv = &L.X[(int64_t)A.ci[e] * K];
-            s0[u] += w;
-            for (int k = 0; k < K; k++) {
-                s1[u * K + k] += w * xv[k];
-                s2[u * K + k] += w * xv[k] * xv[k];
+    // the guard per entry: from the GPU (L.adm), or the moments and ratios evaluated here
+    const bool have_adm = (int64_t)L.adm.size() == A.nnz();
+    std::vector<double> s0, s1, s2;
+    if (!have_adm) {
+        s0.assign(n, 0.0);
+        s1.assign(n * K, 0.0);
+        s2.assign(n * K, 0.0);
+        for (int64_t u = 0; u < n; u++) {
+            for (int64_t e = A.rp[u]; e < A.rp[u + 1]; e++) {
+                const double w = -A.val[e];
+                const double *xv = &L.X[(int64_t)A.ci[e] * K];
+                s0[u] += w;
+                for (int k = 0; k < K; k++) {
+                    s1[u * K + k] += w * xv[k];
+                    s2[u * K + k] += w * xv[k] * xv[k];
+                }
             }
         }
     }
@@ -256,9 +263,13 @@ static void aggregate(HostLevel &L, const lamg_options &o, std::vector<int32_t> 
         for (int64_t e = A.rp[u]; e < A.rp[u + 1]; e++) {
             const int32_t s = A.ci[e];
             if (!L.strong[e] || status[s] == ASSOCIATE) continue;
-            const double q = energy_ratio(s0[u], &s1[u * K], &s2[u * K], &L.X[(int64_t)s * K], K,
-                                          o.guard_eps);
-            if (!(q <= o.Q)) continue;
+            if (have_adm) {
+                if (!L.adm[e]) continue;
+            } else {
+                const double q = energy_ratio(s0[u], &s1[u * K], &s2[u * K], &L.X[(int64_t)s * K], K,
+                                              o.guard_eps);
+                if (!(q <= o.Q)) continue;
+            }
             const double c = L.aff[e];
             if (c > pick_aff || (c == pick_aff && s < pick)) { pick_aff = c; pick = s; }
         }
@@ -618,8 +629,10 @@ int build_hierarchy(const lamg_graph *g, const lamg_options &o, std::vector<Host
             L.X.resize(n * o.K);
             L.aff.resize(L.A.nnz());
             L.strong.resize(L.A.nnz());
+            L.adm.resize(L.A.nnz());
             rc = gpu_tv_and_affinity(L.A, L.colour, l, o.seed, o.K, o.nu_tv, o.tau_soc, o.veto,
-                                     L.X.data(), L.aff.data(), L.strong.data());
+                                     L.X.data(), L.aff.data(), L.strong.data(), o.Q, o.guard_eps,
+                                     L.adm.data());
             if (rc) return rc;
             lap(SETUP_TV_AFFINITY);
             std::vector<int32_t> status, seed;

@@ -7,6 +7,7 @@
 // neighbour sum runs over the row's entries in stored order, one thread per row. The result
 // is then the exactly rounded value of that left-to-right sum, the same on every run.
 #include <cuda_runtime.h>
+#include <math_constants.h>
 
 #include <cstdio>
 #include <vector>
@@ -112,6 +113,53 @@ __global__ void k_affinity(int64_t n, int K, double tau, int veto, const int64_t
     }
 }
 
+// Energy-ratio guard of Eq. 4 from the moments of Appendix B, per entry (u, s) of u's row:
+// s0 = sum_v w_uv, s1_k = sum_v w_uv x_vk, s2_k = sum_v w_uv x_vk^2 (w_uv = -A_uv, stored
+// order); per column k, relaxed = (s2 - s1^2/s0)/2, forced = (x_sk^2 s0 - 2 x_sk s1 + s2)/2,
+// scale = (|s2| + s1^2/|s0|)/2; ratio = forced/relaxed, or 1 / infinity when relaxed <= eps
+// scale (1 if forced is as small too); q = the largest ratio over k. adm[e] = strong[e] and
+// q <= Q. One thread per row, every operation explicitly rounded (no contraction), so the
+// decisions are those of the same formula evaluated on the host.
+constexpr int GUARD_KMAX = 16;
+
+__global__ void k_guard(int64_t n, int K, double Q, double eps, const int64_t *__restrict__ rp,
+                        const int32_t *__restrict__ ci, const double *__restrict__ val,
+                        const double *__restrict__ X, const uint8_t *__restrict__ strong, uint8_t *adm) {
+    const int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (u >= n) return;
+    double s0 = 0.0, s1[GUARD_KMAX], s2[GUARD_KMAX];
+    for (int k = 0; k < K; k++) { s1[k] = 0.0; s2[k] = 0.0; }
+    for (int64_t e = rp[u]; e < rp[u + 1]; e++) {
+        const double w = -val[e];
+        const double *xv = X + (int64_t)ci[e] * K;
+        s0 = __dadd_rn(s0, w);
+        for (int k = 0; k < K; k++) {
+            const double wx = __dmul_rn(w, xv[k]);
+            s1[k] = __dadd_rn(s1[k], wx);
+            s2[k] = __dadd_rn(s2[k], __dmul_rn(wx, xv[k]));
+        }
+    }
+    for (int64_t e = rp[u]; e < rp[u + 1]; e++) {
+        if (!strong[e]) { adm[e] = 0; continue; }
+        const double *xs = X + (int64_t)ci[e] * K;
+        double worst = 0.0;
+        for (int k = 0; k < K; k++) {
+            const double s11 = __dmul_rn(s1[k], s1[k]);
+            const double relaxed = __dmul_rn(0.5, __dsub_rn(s2[k], __ddiv_rn(s11, s0)));
+            const double forced = __dmul_rn(0.5, __dadd_rn(__dsub_rn(__dmul_rn(__dmul_rn(xs[k], xs[k]), s0),
+                                                                     __dmul_rn(__dmul_rn(2.0, xs[k]), s1[k])),
+                                                           s2[k]));
+            const double scale = __dmul_rn(0.5, __dadd_rn(fabs(s2[k]), __ddiv_rn(s11, fabs(s0))));
+            const double lim = __dmul_rn(eps, scale);
+            double r;
+            if (relaxed <= lim) r = (forced <= lim) ? 1.0 : CUDART_INF;
+            else r = __ddiv_rn(forced, relaxed);
+            worst = (worst < r) ? r : worst;
+        }
+        adm[e] = worst <= Q ? 1 : 0;
+    }
+}
+
 static inline unsigned nblk(int64_t work, int bs) { return (unsigned)((work + bs - 1) / bs); }
 
 // Upload a level operator (natural order) and run K9 (and K10 when aff != nullptr). Everything is
@@ -119,13 +167,14 @@ static inline unsigned nblk(int64_t work, int bs) { return (unsigned)((work + bs
 // thread never synchronises the whole device (solves of other hierarchies keep running).
 static int run_setup_kernels(const HostMat &A, const std::vector<int32_t> *colour, int level,
                              uint64_t seed, int K, int nu, double tau, int veto, double *X,
-                             const double *Xin, double *aff, uint8_t *strong) {
+                             const double *Xin, double *aff, uint8_t *strong, double Q = 0.0,
+                             double eps = 0.0, uint8_t *adm = nullptr) {
     int rc = LAMG_OK;
     const int64_t n = A.n, z = A.nnz();
     int64_t *d_rp = nullptr;
     int32_t *d_ci = nullptr, *d_rows = nullptr;
     double *d_val = nullptr, *d_diag = nullptr, *d_X = nullptr, *d_aff = nullptr;
-    uint8_t *d_strong = nullptr;
+    uint8_t *d_strong = nullptr, *d_adm = nullptr;
     const int bs = 128;
     cudaStream_t st = nullptr;
     std::vector<int32_t> rows;
@@ -175,11 +224,17 @@ static int run_setup_kernels(const HostMat &A, const std::vector<int32_t> *colou
         CK(cudaGetLastError());
         if (z) CK(cudaMemcpyAsync(aff, d_aff, z * sizeof(double), cudaMemcpyDeviceToHost, st));
         if (z) CK(cudaMemcpyAsync(strong, d_strong, z, cudaMemcpyDeviceToHost, st));
+        if (adm && K <= GUARD_KMAX) {
+            CK(cudaMallocAsync((void **)&d_adm, (z ? z : 1), st));
+            k_guard<<<nblk(n, bs), bs, 0, st>>>(n, K, Q, eps, d_rp, d_ci, d_val, d_X, d_strong, d_adm);
+            CK(cudaGetLastError());
+            if (z) CK(cudaMemcpyAsync(adm, d_adm, z, cudaMemcpyDeviceToHost, st));
+        }
     }
     CK(cudaStreamSynchronize(st));
 out:
     if (st) {
-        void *ptrs[] = {d_rp, d_ci, d_val, d_diag, d_X, d_rows, d_aff, d_strong};
+        void *ptrs[] = {d_rp, d_ci, d_val, d_diag, d_X, d_rows, d_aff, d_strong, d_adm};
         for (void *q : ptrs)
             if (q) cudaFreeAsync(q, st);
         cudaStreamSynchronize(st);
@@ -200,8 +255,8 @@ int gpu_affinity(const HostMat &A, const double *X, int K, double tau, double *a
 
 int gpu_tv_and_affinity(const HostMat &A, const std::vector<int32_t> &colour, int level,
                         uint64_t seed, int K, int nu, double tau, int veto, double *X,
-                        double *aff, uint8_t *strong) {
-    return run_setup_kernels(A, &colour, level, seed, K, nu, tau, veto, X, nullptr, aff, strong);
+                        double *aff, uint8_t *strong, double Q, double eps, uint8_t *adm) {
+    return run_setup_kernels(A, &colour, level, seed, K, nu, tau, veto, X, nullptr, aff, strong, Q, eps, adm);
 }
 
 }  // namespace lamg
