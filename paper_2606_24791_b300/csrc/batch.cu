@@ -316,19 +316,25 @@ __global__ void bk_copy(int64_t cnt, const T *__restrict__ src, T *dst) {
     if (t < cnt) dst[t] = src[t];
 }
 
-// b^c = P^T r
+// b^c = P^T r; with xc set also the row-local start of the coarse level's first visit (x = b / A
+// on its rows a < c1, 0 elsewhere, as bk_gs_first / bk_zero)
 template <typename T, int KL, int TPR>
 __global__ void __launch_bounds__(BBS) bk_restrict(int nc, int k, const int32_t *__restrict__ ptr,
                                                    const int32_t *__restrict__ row, const T *__restrict__ w,
-                                                   const T *__restrict__ r, T *bc) {
+                                                   const T *__restrict__ r, T *bc, T *xc, int c1,
+                                                   const T *__restrict__ idc) {
     b_trigger();
     const Lanes<KL, TPR> L;
     const int a = L.row_in_grid;
     const bool ok = a < nc;
     const int e0 = ok ? ptr[a] + L.sub : 0, e1 = ok ? ptr[a + 1] : 0;
+    const T id = (xc && ok && a < c1) ? idc[a] : T(0);
     b_wait();
     const T s = rowsum_k<T, KL, TPR>(e0, e1, k, L.j, row, w, r);
-    if (ok && L.sub == 0 && L.j < k) bc[(size_t)a * k + L.j] = s;
+    if (ok && L.sub == 0 && L.j < k) {
+        bc[(size_t)a * k + L.j] = s;
+        if (xc) xc[(size_t)a * k + L.j] = a < c1 ? s * id : T(0);
+    }
 }
 
 // Element-wise steps: thread -> (row i, column j = threadIdx.x % KL).
@@ -382,18 +388,21 @@ __global__ void bk_prolong(int n, int k, const int32_t *__restrict__ agg, const 
 
 template <typename T, int KL>
 __global__ void bk_elim_restrict(int nc, int k, const int32_t *__restrict__ ptr, const int32_t *__restrict__ f,
-                                 const T *__restrict__ pv, const T *__restrict__ b, T *bc) {
+                                 const T *__restrict__ pv, const T *__restrict__ b, T *bc, T *xc, int c1,
+                                 const T *__restrict__ idc) {
     b_trigger();
     int i, j;
     elem_pos<KL>(i, j);
     const bool ok = i < nc;
     const int e0 = ok ? ptr[i] : 0, e1 = ok ? ptr[i + 1] : 0;
+    const T id = (xc && ok && i < c1) ? idc[i] : T(0);
     b_wait();
     if (!ok || j >= k) return;
     const T *bF = b + (size_t)nc * k;
     T s = b[(size_t)i * k + j];
     for (int e = e0; e < e1; e++) s += pv[e] * bF[(size_t)f[e] * k + j];
     bc[(size_t)i * k + j] = s;
+    if (xc) xc[(size_t)i * k + j] = i < c1 ? s * id : T(0);
 }
 
 template <typename T, int KL>
@@ -891,10 +900,18 @@ static int build_ctx(lamg_hier *h, BatchCtx *c) {
     return LAMG_OK;
 }
 
-// One step of the cycle schedule for k columns in type T.
+// One step of the cycle schedule for k columns in type T (start: as for launch_op).
 template <typename T>
-static void bop(const Op &op, BatchCtx *c, cudaStream_t s) {
+static void bop(const Op &op, BatchCtx *c, cudaStream_t s, const Op *start) {
     BLev &L = c->lv[op.level];
+    T *xs = nullptr;
+    const T *ids = nullptr;
+    int c1 = 0;
+    if (start) {
+        const BLev &Cs = c->lv[start->level];
+        xs = (T *)Cs.x;
+        if (start->kind == OP_GS_FIRST) { c1 = (int)Cs.cptr[1]; ids = (const T *)Cs.idiag; }
+    }
     const int n = (int)L.n, k = c->k, KL = c->KL;
     const T *val = (const T *)L.val, *diag = (const T *)L.diag, *idiag = (const T *)L.idiag;
     T *x = (T *)L.x, *b = (T *)L.b, *r = (T *)L.r;
@@ -939,7 +956,7 @@ static void bop(const Op &op, BatchCtx *c, cudaStream_t s) {
             const int nc = (int)L.nc;
             const int tpr = row_tpr(KL, L.pt_tpr);
             T *bc = (T *)c->lv[op.level + 1].b;
-#define C4(KLv, TPRv, ...) case KT_CODE(KLv, TPRv): blaunch(bk_restrict<T, KLv, TPRv>, nblocks((int64_t)nc * KLv * TPRv), s, nc, k, L.pt_ptr, L.pt_row, (const T *)L.pt_w, (const T *)r, bc); break;
+#define C4(KLv, TPRv, ...) case KT_CODE(KLv, TPRv): blaunch(bk_restrict<T, KLv, TPRv>, nblocks((int64_t)nc * KLv * TPRv), s, nc, k, L.pt_ptr, L.pt_row, (const T *)L.pt_w, (const T *)r, bc, xs, c1, ids); break;
             switch (KT_CODE(KL, tpr)) { KT_CASES(C4) }
 #undef C4
             break;
@@ -954,7 +971,7 @@ static void bop(const Op &op, BatchCtx *c, cudaStream_t s) {
         case OP_ELIM_RESTRICT: {
             T *bc = (T *)c->lv[op.level + 1].b;
             const int nc = (int)L.nc;
-#define C6(KLv, ...) case KLv: blaunch(bk_elim_restrict<T, KLv>, nblocks((int64_t)nc * KLv), s, nc, k, L.pft_ptr, L.pft_f, (const T *)L.pft_val, (const T *)b, bc); break;
+#define C6(KLv, ...) case KLv: blaunch(bk_elim_restrict<T, KLv>, nblocks((int64_t)nc * KLv), s, nc, k, L.pft_ptr, L.pft_f, (const T *)L.pft_val, (const T *)b, bc, xs, c1, ids); break;
             switch (KL) { K_CASES(C6) }
 #undef C6
             break;
@@ -1023,7 +1040,14 @@ static void cg_tail(lamg_hier *h, BatchCtx *c, cudaStream_t s) {
     const int n = (int)h->dev[0].n, k = c->k;
     const int64_t cnt = (int64_t)n * k;
     if (c->prec == LAMG_FP32) blaunch(bk_cast<double, float>, nblocks(cnt), s, cnt, (const double *)c->r, (float *)c->b0);
-    for (const Op &op : h->ops) bop<T>(op, c, s);
+    for (int i = 0; i < (int)h->ops.size(); i++) {
+        if (start_fusable(h, i, false)) {
+            bop<T>(h->ops[i], c, s, &h->ops[i + 1]);
+            i++;
+        } else {
+            bop<T>(h->ops[i], c, s, nullptr);
+        }
+    }
     if (c->prec == LAMG_FP32) blaunch(bk_cast<float, double>, nblocks(cnt), s, cnt, (const float *)c->lv[0].x, c->z64);
     KL_SWITCH(c->KL, blaunch(bk_sum<KLc>, rblocks((int64_t)n * KLc), s, n, k, (const double *)c->z64, c->red));
     KL_SWITCH(c->KL, blaunch(bk_proj_dots<KLc>, rblocks((int64_t)n * KLc), s, n, k, c->z64, (const double *)c->zold,

@@ -328,19 +328,29 @@ __global__ void k_copy(int n, const double *__restrict__ src, double *dst) {
 
 // Restriction b^c = P^T r (Section 2): segmented sum over the fine rows of each aggregate,
 // caliber-2 rows contributing w or 1 - w.
+//
+// With xc set, the kernel also starts the coarse level's first visit, which begins from x = 0:
+// xc_a = b^c_a / A_aa on the coarse rows a < c1 (its first colour class, as k_gs_first), 0 on
+// the others (c1 = 0: the whole iterate zeroed, as k_zero). Those steps are row-local, so they
+// need no launch of their own.
 template <int TPR>
 __global__ void __launch_bounds__(BS) k_restrict(int nc, const int32_t *__restrict__ ptr,
                                                  const int32_t *__restrict__ row,
                                                  const double *__restrict__ w,
-                                                 const double *__restrict__ r, double *bc) {
+                                                 const double *__restrict__ r, double *bc, double *xc, int c1,
+                                                 const double *__restrict__ idc) {
     pdl_trigger();
     const int a = (int)((blockIdx.x * (unsigned)BS + threadIdx.x) / TPR);
     const int sub = threadIdx.x % TPR;
     const bool ok = a < nc;
     const RowPre p = row_pre<TPR>(ok, a, sub, ptr, row, w);
+    const double id = (xc && ok && a < c1) ? idc[a] : 0.0;
     pdl_wait();
     const double s = row_finish<TPR>(p, row, w, r);
-    if (ok && sub == 0) bc[a] = s;
+    if (ok && sub == 0) {
+        bc[a] = s;
+        if (xc) xc[a] = a < c1 ? s * id : 0.0;
+    }
 }
 
 // Prolongation x += P x^c: caliber-1 rows gather one coarse value, caliber-2 rows
@@ -365,8 +375,11 @@ __global__ void k_prolong(int n, const int32_t *__restrict__ agg, const int32_t 
 }
 
 // Elimination restriction (Eq. 2): b^c_i = b_i + sum_f (P_F)_{f,i} b_f over the F neighbours.
+// xc, c1, idc: the start of the coarse level's first visit, as in k_restrict (the kernel reads
+// no iterate, so the coarse iterate may share the fine one's memory).
 __global__ void k_elim_restrict(int nc, const int32_t *__restrict__ ptr, const int32_t *__restrict__ f,
-                                const double *__restrict__ pv, const double *__restrict__ b, double *bc) {
+                                const double *__restrict__ pv, const double *__restrict__ b, double *bc,
+                                double *xc, int c1, const double *__restrict__ idc) {
     pdl_trigger();
     const int i = blockIdx.x * BS + threadIdx.x;
     const bool ok = i < nc;
@@ -375,6 +388,7 @@ __global__ void k_elim_restrict(int nc, const int32_t *__restrict__ ptr, const i
     double p0 = 0.0, p1 = 0.0;
     if (e0 < e1) { f0 = f[e0]; p0 = pv[e0]; }
     if (e0 + 1 < e1) { f1 = f[e0 + 1]; p1 = pv[e0 + 1]; }
+    const double id = (xc && ok && i < c1) ? idc[i] : 0.0;
     pdl_wait();
     if (!ok) return;
     const double *bF = b + nc;
@@ -383,6 +397,7 @@ __global__ void k_elim_restrict(int nc, const int32_t *__restrict__ ptr, const i
     if (f1 >= 0) s += p1 * bF[f1];
     for (int e = e0 + 2; e < e1; e++) s += pv[e] * bF[f[e]];
     bc[i] = s;
+    if (xc) xc[i] = i < c1 ? s * id : 0.0;
 }
 
 // Elimination interpolation (Eq. 2): x_F = P_F x_C + b_F / A_FF, ELL-4 rows.
@@ -710,9 +725,18 @@ int choose_tpr(double avg_row) {
         default: launch(KERNEL<32>, GRID(32), s, __VA_ARGS__); break; \
     }
 
-void launch_op(const Op &op, std::vector<DevLevel> &lv, const Reduce &red, cudaStream_t s) {
+void launch_op(const Op &op, std::vector<DevLevel> &lv, const Reduce &red, cudaStream_t s, const Op *start) {
     (void)red;
     DevLevel &L = lv[op.level];
+    // a restriction followed by the row-local start of the coarse level's first visit
+    double *xs = nullptr;
+    const double *ids = nullptr;
+    int c1 = 0;
+    if (start) {
+        const DevLevel &Cs = lv[start->level];
+        xs = Cs.x;
+        if (start->kind == OP_GS_FIRST) { c1 = (int)Cs.cptr[1]; ids = Cs.idiag; }
+    }
     const int n = (int)L.n;
     switch (op.kind) {
         case OP_GS_FIRST:
@@ -758,7 +782,7 @@ void launch_op(const Op &op, std::vector<DevLevel> &lv, const Reduce &red, cudaS
             const int nc = (int)L.nc;
 #define GRID_P(T) blocks((int64_t)nc * (T))
             TPR_DISPATCH(L.pt_tpr, k_restrict, GRID_P, nc, (const int32_t *)L.pt_ptr, (const int32_t *)L.pt_row,
-                         (const double *)L.pt_w, (const double *)L.r, Cl.b);
+                         (const double *)L.pt_w, (const double *)L.r, Cl.b, xs, c1, ids);
 #undef GRID_P
             break;
         }
@@ -769,7 +793,7 @@ void launch_op(const Op &op, std::vector<DevLevel> &lv, const Reduce &red, cudaS
         case OP_ELIM_RESTRICT:
             launch(k_elim_restrict, blocks(L.nc), s, (int)L.nc, (const int32_t *)L.pft_ptr,
                    (const int32_t *)L.pft_f, (const double *)L.pft_val, (const double *)L.b,
-                   lv[op.level + 1].b);
+                   lv[op.level + 1].b, xs, c1, ids);
             break;
         case OP_ELIM_INTERP:
             if (L.nF > 0)

@@ -176,7 +176,10 @@ void launch_cluster(const PLevel *lv, int nlev, const int32_t *cptr, int ncptr, 
 bool pdl_enabled();
 
 // launchers (cycle_kernels.cu)
-void launch_op(const Op &op, std::vector<DevLevel> &lv, const Reduce &red, cudaStream_t s);
+// start: the first step of the coarse level's first visit (OP_GS_FIRST or OP_ZERO on level + 1)
+// when op is a restriction that performs it too (start_fusable), else null
+void launch_op(const Op &op, std::vector<DevLevel> &lv, const Reduce &red, cudaStream_t s,
+               const Op *start = nullptr);
 void launch_gather(int64_t n, const int32_t *perm, const double *src, double *dst, cudaStream_t s);
 void launch_scatter(int64_t n, const int32_t *perm, const double *src, double *dst, cudaStream_t s);
 void launch_sum(int64_t n, const double *v, const Reduce &red, cudaStream_t s);  // S_MEAN = sum / n

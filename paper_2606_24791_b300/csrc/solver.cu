@@ -22,6 +22,18 @@ using namespace lamg;
 
 static_assert(sizeof(lamg_options) == 144, "lamg_options layout changed: update the header's size note");
 
+// True when step i is a restriction (aggregation or elimination) that also performs step i + 1,
+// the row-local start (OP_GS_FIRST or OP_ZERO) of the coarse level's first visit; both steps are
+// then one launch in the graph and multi-column paths. Cluster segments keep their steps.
+bool lamg::start_fusable(const lamg_hier *h, int i, bool clusters) {
+    if (i + 1 >= (int)h->ops.size()) return false;
+    const Op &a = h->ops[i], &b = h->ops[i + 1];
+    if (a.kind != OP_RESTRICT && a.kind != OP_ELIM_RESTRICT) return false;
+    if ((b.kind != OP_GS_FIRST && b.kind != OP_ZERO) || b.level != a.level + 1) return false;
+    if (clusters && h->cluster_from >= 0 && b.level >= h->cluster_from) return false;
+    return b.kind == OP_ZERO || h->dev[b.level].ncol >= 1;
+}
+
 namespace {
 
 // fn(begin, end) on contiguous chunks of [0, n), one host thread each (up to 16; one thread
@@ -318,6 +330,9 @@ int capture(lamg_hier *h, cudaGraphExec_t *out, int which) {
                 launch_cluster(h->d_lv, nlev, h->d_cptr, h->ncptr, h->d_ops + i, j - i, h->cl_dim,
                                pdl_enabled(), cs);
                 i = j;
+            } else if (start_fusable(h, i)) {
+                launch_op(h->ops[i], h->dev, h->red, cs, &h->ops[i + 1]);
+                i += 2;
             } else {
                 launch_op(h->ops[i++], h->dev, h->red, cs);
             }
@@ -557,6 +572,11 @@ int64_t count_cycle_launches(const lamg_hier *h) {
         const Op &op = h->ops[i];
         if (h->cluster_from >= 0 && op.level >= h->cluster_from) {
             while (i < nops && h->ops[i].level >= h->cluster_from) i++;
+            k++;
+            continue;
+        }
+        if (start_fusable(h, i)) {
+            i += 2;
             k++;
             continue;
         }
