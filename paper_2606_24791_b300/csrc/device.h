@@ -178,6 +178,14 @@ bool pdl_enabled();
 // launchers (cycle_kernels.cu)
 // start: the first step of the coarse level's first visit (OP_GS_FIRST or OP_ZERO on level + 1)
 // when op is a restriction that performs it too (start_fusable), else null
+// setup: device-order operator of a level from its natural-order CSR (row i = natural row
+// perm[i], columns renamed by iperm, entries in the natural row's order), and its sliced-ELLPACK
+// copy from that operator (slice pointers sp, 32-row slices)
+void launch_layout_rows(int64_t n, const int32_t *perm, const int32_t *iperm, const int64_t *nrp,
+                        const int32_t *nci, const double *nval, const double *ndiag, const int32_t *rp,
+                        int32_t *ci, double *val, double *diag, double *idiag, cudaStream_t s);
+void launch_layout_sell(int64_t n, int64_t ns, const int32_t *sp, const int32_t *rp, const int32_t *ci,
+                        const double *val, int32_t *sc, double *sv, cudaStream_t s);
 void launch_op(const Op &op, std::vector<DevLevel> &lv, const Reduce &red, cudaStream_t s,
                const Op *start = nullptr);
 void launch_gather(int64_t n, const int32_t *perm, const double *src, double *dst, cudaStream_t s);

@@ -96,6 +96,38 @@ void build_orders(lamg_hier *h) {
     }
 }
 
+// Temporary device copies for a setup step: stream-ordered allocations on `s`, freed (after
+// the stream has finished with them) by finish(); rc keeps the first error.
+struct TmpUpload {
+    cudaStream_t s;
+    std::vector<void *> ptrs;
+    int rc = LAMG_OK;
+    explicit TmpUpload(cudaStream_t st) : s(st) {}
+    template <typename T>
+    const T *put(const std::vector<T> &v) {
+        void *q = nullptr;
+        if (rc) return nullptr;
+        cudaError_t e = cudaMallocAsync(&q, std::max<size_t>(1, v.size()) * sizeof(T), s);
+        if (e == cudaSuccess && !v.empty())
+            e = cudaMemcpyAsync(q, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, s);
+        if (e != cudaSuccess) { rc = cuda_status(e); return nullptr; }
+        ptrs.push_back(q);
+        return (const T *)q;
+    }
+    int finish() {
+        cudaError_t e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        for (void *q : ptrs) cudaFreeAsync(q, s);
+        ptrs.clear();
+        return e == cudaSuccess ? rc : cuda_status(e);
+    }
+    ~TmpUpload() {
+        if (ptrs.empty()) return;
+        cudaStreamSynchronize(s);
+        for (void *q : ptrs) cudaFreeAsync(q, s);
+    }
+};
+
 int upload_level(lamg_hier *h, int l) {
     const HostLevel &H = h->host[l];
     DevLevel &D = h->dev[l];
@@ -103,27 +135,25 @@ int upload_level(lamg_hier *h, int l) {
     int rc;
     std::vector<int32_t> iperm(n);
     for (int64_t i = 0; i < n; i++) iperm[D.perm[i]] = (int32_t)i;
-    if (H.A.nnz() >= (int64_t)INT32_MAX) return LAMG_ERR_INVALID;
-    // operator in device order, columns ascending (rows filled in parallel chunks)
-    std::vector<int32_t> rp(n + 1, 0), ci(H.A.nnz());
-    std::vector<double> val(H.A.nnz()), diag(n);
+    const int64_t z = H.A.nnz();
+    if (z >= (int64_t)INT32_MAX) return LAMG_ERR_INVALID;
+    // operator in device order, built on the device from one upload of the natural-order CSR:
+    // device row i is natural row perm[i], entries in that row's order (ascending natural id),
+    // columns renamed to device indices
+    std::vector<int32_t> rp(n + 1, 0);
     for (int64_t i = 0; i < n; i++) rp[i + 1] = rp[i] + (int32_t)(H.A.rp[D.perm[i] + 1] - H.A.rp[D.perm[i]]);
-    host_chunks(n, 65536, [&](int64_t i0, int64_t i1) {
-        std::vector<std::pair<int32_t, double>> row;
-        for (int64_t i = i0; i < i1; i++) {
-            const int32_t u = D.perm[i];
-            row.clear();
-            for (int64_t e = H.A.rp[u]; e < H.A.rp[u + 1]; e++) row.emplace_back(iperm[H.A.ci[e]], H.A.val[e]);
-            std::sort(row.begin(), row.end(), [](auto &a, auto &b) { return a.first < b.first; });
-            for (size_t k = 0; k < row.size(); k++) { ci[rp[i] + k] = row[k].first; val[rp[i] + k] = row[k].second; }
-            diag[i] = H.A.diag[u];
-        }
-    });
-    std::vector<double> idiag(n);
-    for (int64_t i = 0; i < n; i++) idiag[i] = 1.0 / diag[i];
-    if ((rc = dupload(h, &D.rp, rp)) || (rc = dupload(h, &D.ci, ci)) || (rc = dupload(h, &D.val, val)) ||
-        (rc = dupload(h, &D.diag, diag)) || (rc = dupload(h, &D.idiag, idiag)))
+    if ((rc = dupload(h, &D.rp, rp)) || (rc = dalloc(h, &D.ci, z)) || (rc = dalloc(h, &D.val, z)) ||
+        (rc = dalloc(h, &D.diag, n)) || (rc = dalloc(h, &D.idiag, n)))
         return rc;
+    {
+        TmpUpload t(h->stream);
+        const int64_t *nrp = t.put(H.A.rp);
+        const int32_t *nci = t.put(H.A.ci), *dperm = t.put(D.perm), *diperm = t.put(iperm);
+        const double *nval = t.put(H.A.val), *ndiag = t.put(H.A.diag);
+        if (t.rc) return t.rc;
+        launch_layout_rows(n, dperm, diperm, nrp, nci, nval, ndiag, D.rp, D.ci, D.val, D.diag, D.idiag, h->stream);
+        if ((rc = t.finish())) return rc;
+    }
     D.tpr = h->opt.row_tpr > 0 ? h->opt.row_tpr : choose_tpr(n ? (double)H.A.nnz() / (double)n : 1.0);
     // sliced ELLPACK copy of the operator (32-row slices, entry j of row 32 s + l at
     // sl_ptr[s] + 32 j + l, padded with value 0 at the row's own column), used by the
@@ -140,27 +170,14 @@ int upload_level(lamg_hier *h, int l) {
             tot += 32 * w;
         }
         sp[ns] = (int32_t)tot;
-        const int64_t z = H.A.nnz();
         const bool use = h->opt.sell >= 0 && tot < (int64_t)INT32_MAX && maxlen <= SELL_MAX_ROW &&
                          (h->opt.sell > 0 || (double)tot <= 1.5 * (double)z + 64.0);
         if (use) {
-            std::vector<int32_t> sc(tot);
-            std::vector<double> sv(tot, 0.0);
-            host_chunks(ns, 4096, [&](int64_t s0, int64_t s1) {
-                for (int64_t sl = s0; sl < s1; sl++) {
-                    const int64_t w = (sp[sl + 1] - sp[sl]) / 32;
-                    for (int64_t l = 0; l < 32; l++) {
-                        const int64_t i = 32 * sl + l;
-                        for (int64_t j = 0; j < w; j++) {
-                            const int64_t e = sp[sl] + 32 * j + l;
-                            if (i < n && j < rp[i + 1] - rp[i]) { sc[e] = ci[rp[i] + j]; sv[e] = val[rp[i] + j]; }
-                            else sc[e] = (int32_t)std::min<int64_t>(i, n - 1);
-                        }
-                    }
-                }
-            });
-            if ((rc = dupload(h, &D.sl_ptr, sp)) || (rc = dupload(h, &D.sl_col, sc)) || (rc = dupload(h, &D.sl_val, sv)))
+            if ((rc = dupload(h, &D.sl_ptr, sp)) || (rc = dalloc(h, &D.sl_col, tot)) || (rc = dalloc(h, &D.sl_val, tot)))
                 return rc;
+            launch_layout_sell(n, ns, D.sl_ptr, D.rp, D.ci, D.val, D.sl_col, D.sl_val, h->stream);
+            CKR(cudaGetLastError());
+            CKR(cudaStreamSynchronize(h->stream));
             D.sell = 1;
             D.sell_nnz = tot;
         }
@@ -234,7 +251,6 @@ int upload_level(lamg_hier *h, int l) {
         const int64_t nc = H.nc, nF = n - nc;
         std::vector<int32_t> pfc(4 * nF, -1);
         std::vector<double> pfv(4 * nF, 0.0), dF(nF);
-        std::vector<std::vector<std::pair<int32_t, double>>> byc(nc);
         for (int64_t t = 0; t < nF; t++) {
             const int32_t u = D.perm[nc + t];
             const int64_t deg = H.A.rp[u + 1] - H.A.rp[u];
@@ -245,15 +261,21 @@ int upload_level(lamg_hier *h, int l) {
                 const double pv = -H.A.val[e] / H.A.diag[u];
                 pfc[4 * t + j] = c;
                 pfv[4 * t + j] = pv;
-                byc[c].emplace_back((int32_t)t, pv);
             }
             dF[t] = H.A.diag[u];
         }
-        std::vector<int32_t> ptr(nc + 1, 0), fidx;
-        std::vector<double> fval;
-        for (int64_t i = 0; i < nc; i++) {
-            for (auto &pr : byc[i]) { fidx.push_back(pr.first); fval.push_back(pr.second); }
-            ptr[i + 1] = (int32_t)fidx.size();
+        // the transpose P_F^T by coarse row, each row's F entries in ascending F index
+        std::vector<int32_t> ptr(nc + 1, 0);
+        for (int64_t q = 0; q < 4 * nF; q++)
+            if (pfc[q] >= 0) ptr[pfc[q] + 1]++;
+        for (int64_t i = 0; i < nc; i++) ptr[i + 1] += ptr[i];
+        std::vector<int32_t> fidx(ptr[nc]), fill(ptr.begin(), ptr.end() - 1);
+        std::vector<double> fval(ptr[nc]);
+        for (int64_t q = 0; q < 4 * nF; q++) {
+            const int32_t c = pfc[q];
+            if (c < 0) continue;
+            fidx[fill[c]] = (int32_t)(q / 4);
+            fval[fill[c]++] = pfv[q];
         }
         if ((rc = dupload(h, &D.pf_col, pfc)) || (rc = dupload(h, &D.pf_val, pfv)) || (rc = dupload(h, &D.dF, dF)) ||
             (rc = dupload(h, &D.pft_ptr, ptr)) || (rc = dupload(h, &D.pft_f, fidx)) || (rc = dupload(h, &D.pft_val, fval)))
