@@ -3,6 +3,7 @@
 
 #include <cstdint>
 #include <string>
+#include <functional>
 #include <vector>
 
 #include <cuda_runtime.h>
@@ -87,6 +88,15 @@ int gpu_affinity(const HostMat &A, const double *X, int K, double tau, double *a
                  uint8_t *strong);
 // ... and the guard of Eq. 4 per entry (adm[e]: strong and energy ratio <= Q), from the
 // moments of Appendix B computed on the GPU.
+// Galerkin P^T A P of an aggregation level on the GPU (setup_kernels.cu): ptr/rows/pw is P^T by
+// coarse row (galerkin_pt); every coarse entry is the same ordered sum of explicitly rounded
+// products as the host's, so Ac equals the host result bit for bit. Rows with more than
+// GAL_CAP distinct coarse columns come from host_row(a, cols, vals) -> diagonal, which appends
+// the row's nonzero off-diagonal entries in ascending column order.
+constexpr int GAL_CAP = 128;
+int gpu_galerkin(const HostLevel &L, const std::vector<int64_t> &ptr, const std::vector<int32_t> &rows,
+                 const std::vector<double> &pw, HostMat &Ac,
+                 const std::function<double(int64_t, std::vector<int32_t> &, std::vector<double> &)> &host_row);
 int gpu_tv_and_affinity(const HostMat &A, const std::vector<int32_t> &colour, int level,
                         uint64_t seed, int K, int nu, double tau, int veto, double *X,
                         double *aff, uint8_t *strong, double Q, double eps, uint8_t *adm);

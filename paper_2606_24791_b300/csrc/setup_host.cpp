@@ -342,33 +342,72 @@ static inline int p_row(const HostLevel &L, int64_t u, int32_t *col, double *p) 
     return k + 1;
 }
 
-// Galerkin coarse operator P^T A P, one coarse row at a time over the fine rows that
-// interpolate from it (fine rows ascending).
-static void galerkin(const HostLevel &L, HostMat &Ac) {
-    const HostMat &A = L.A;
-    const int64_t n = A.n, nc = L.nc;
-    std::vector<int64_t> ptr(nc + 1, 0);
+// P^T by coarse row: for aggregate a, the fine rows u with P_ua != 0 in ascending order
+// (rows[ptr[a] .. ptr[a + 1])) and their weights P_ua (pw).
+void galerkin_pt(const HostLevel &L, std::vector<int64_t> &ptr, std::vector<int32_t> &rows,
+                 std::vector<double> &pw) {
+    const int64_t n = L.A.n, nc = L.nc;
+    ptr.assign(nc + 1, 0);
     for (int64_t u = 0; u < n; u++) {
         int32_t c[2]; double p[2];
         int k = p_row(L, u, c, p);
         for (int t = 0; t < k; t++) ptr[c[t] + 1]++;
     }
     for (int64_t a = 0; a < nc; a++) ptr[a + 1] += ptr[a];
-    std::vector<int32_t> rows(ptr[nc]);
-    std::vector<double> pw(ptr[nc]);
+    rows.resize(ptr[nc]);
+    pw.resize(ptr[nc]);
     std::vector<int64_t> pos(ptr.begin(), ptr.end() - 1);
     for (int64_t u = 0; u < n; u++) {
         int32_t c[2]; double p[2];
         int k = p_row(L, u, c, p);
         for (int t = 0; t < k; t++) { rows[pos[c[t]]] = (int32_t)u; pw[pos[c[t]]] = p[t]; pos[c[t]]++; }
     }
+}
+
+// Row a of the Galerkin coarse operator P^T A P: every product P_ua A_uv P_vb (u over the fine
+// rows of a ascending, v over u's diagonal then u's entries in order, b over v's row of P) is
+// added to entry b in that order. Appends the row's nonzero off-diagonal entries (ascending
+// column) to oc/ov and returns its diagonal.
+static double galerkin_row(const HostLevel &L, const std::vector<int64_t> &ptr, const std::vector<int32_t> &rows,
+                           const std::vector<double> &pw, int64_t a, RowAcc &acc, std::vector<int32_t> &oc,
+                           std::vector<double> &ov) {
+    const HostMat &A = L.A;
+    acc.start(a);
+    for (int64_t q = ptr[a]; q < ptr[a + 1]; q++) {
+        const int64_t u = rows[q];
+        const double pa = pw[q];
+        int32_t c[2]; double p[2];
+        int k = p_row(L, u, c, p);
+        for (int s = 0; s < k; s++) acc.at(c[s]) += pa * A.diag[u] * p[s];
+        for (int64_t e = A.rp[u]; e < A.rp[u + 1]; e++) {
+            k = p_row(L, A.ci[e], c, p);
+            for (int s = 0; s < k; s++) acc.at(c[s]) += pa * A.val[e] * p[s];
+        }
+    }
+    std::sort(acc.cols.begin(), acc.cols.end());
+    double d = 0.0;
+    for (int32_t j : acc.cols) {
+        if (j == a) { d = acc.v[j]; continue; }
+        if (acc.v[j] == 0.0) continue;
+        oc.push_back(j);
+        ov.push_back(acc.v[j]);
+    }
+    return d;
+}
+
+// Galerkin coarse operator P^T A P on the host, coarse rows in contiguous chunks on up to 16
+// threads, each row summed by one thread as in a sequential pass.
+static void galerkin(const HostLevel &L, HostMat &Ac) {
+    const int64_t nc = L.nc;
+    std::vector<int64_t> ptr;
+    std::vector<int32_t> rows;
+    std::vector<double> pw;
+    galerkin_pt(L, ptr, rows, pw);
     Ac.n = nc;
     Ac.rp.assign(nc + 1, 0);
     Ac.diag.assign(nc, 0.0);
     Ac.ci.clear();
     Ac.val.clear();
-    // coarse rows in contiguous chunks, one accumulator per thread; each row is summed by one
-    // thread in the same order as a sequential pass
     std::vector<std::vector<int32_t>> tci(16);
     std::vector<std::vector<double>> tval(16);
     std::vector<int64_t> len(nc, 0);
@@ -377,28 +416,8 @@ static void galerkin(const HostLevel &L, HostMat &Ac) {
         std::vector<int32_t> &oc = tci[t];
         std::vector<double> &ov = tval[t];
         for (int64_t a = a0; a < a1; a++) {
-            acc.start(a);
-            for (int64_t q = ptr[a]; q < ptr[a + 1]; q++) {
-                const int64_t u = rows[q];
-                const double pa = pw[q];
-                int32_t c[2]; double p[2];
-                int k = p_row(L, u, c, p);
-                for (int s = 0; s < k; s++) acc.at(c[s]) += pa * A.diag[u] * p[s];
-                for (int64_t e = A.rp[u]; e < A.rp[u + 1]; e++) {
-                    k = p_row(L, A.ci[e], c, p);
-                    for (int s = 0; s < k; s++) acc.at(c[s]) += pa * A.val[e] * p[s];
-                }
-            }
-            std::sort(acc.cols.begin(), acc.cols.end());
-            double d = 0.0;
             const size_t before = oc.size();
-            for (int32_t j : acc.cols) {
-                if (j == a) { d = acc.v[j]; continue; }
-                if (acc.v[j] == 0.0) continue;
-                oc.push_back(j);
-                ov.push_back(acc.v[j]);
-            }
-            Ac.diag[a] = d;
+            Ac.diag[a] = galerkin_row(L, ptr, rows, pw, a, acc, oc, ov);
             len[a] = (int64_t)(oc.size() - before);
         }
     });
@@ -409,6 +428,25 @@ static void galerkin(const HostLevel &L, HostMat &Ac) {
         Ac.ci.insert(Ac.ci.end(), tci[t].begin(), tci[t].end());
         Ac.val.insert(Ac.val.end(), tval[t].begin(), tval[t].end());
     }
+}
+
+// Galerkin on the GPU (same sums, same order, explicitly rounded: the same coarse operator),
+// with the rows the GPU leaves (more distinct coarse columns than its per-row accumulator
+// holds) summed here; levels below GAL_MIN_ROWS fine rows stay on the host.
+constexpr int64_t GAL_MIN_ROWS = 32768;
+static int galerkin_device(const HostLevel &L, HostMat &Ac) {
+    if (L.A.n < GAL_MIN_ROWS) {  // uploads and launches cost more than the host sums
+        galerkin(L, Ac);
+        return LAMG_OK;
+    }
+    std::vector<int64_t> ptr;
+    std::vector<int32_t> rows;
+    std::vector<double> pw;
+    galerkin_pt(L, ptr, rows, pw);
+    RowAcc acc(L.nc);
+    return gpu_galerkin(L, ptr, rows, pw, Ac, [&](int64_t a, std::vector<int32_t> &oc, std::vector<double> &ov) {
+        return galerkin_row(L, ptr, rows, pw, a, acc, oc, ov);
+    });
 }
 
 // ----------------------------------------------------------------------------------- coarsest
@@ -645,7 +683,7 @@ int build_hierarchy(const lamg_graph *g, const lamg_options &o, std::vector<Host
                 L.agg.clear(); L.agg2.clear(); L.wt.clear();
                 break;
             }
-            galerkin(L, Ac);
+            if ((rc = galerkin_device(L, Ac))) return rc;
             lap(SETUP_GALERKIN);
         }
         A = std::move(Ac);

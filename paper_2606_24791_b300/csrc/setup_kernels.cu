@@ -1,5 +1,6 @@
-// GPU setup kernels (Section 2): the K test vectors (K9) and the per-edge affinity with the
-// strength-of-connection flag (K10).
+// GPU setup kernels (Section 2): the K test vectors (K9), the per-edge affinity with the
+// strength-of-connection flag (K10), the energy-ratio guard of Eq. 4, and the Galerkin coarse
+// operator P^T A P.
 //
 // These kernels feed integer decisions on the host (which seed a node joins, whether a row is
 // upgraded to caliber-2), so they evaluate their sums in a fixed order with explicitly
@@ -9,6 +10,7 @@
 #include <cuda_runtime.h>
 #include <math_constants.h>
 
+#include <algorithm>
 #include <cstdio>
 #include <vector>
 
@@ -160,6 +162,104 @@ __global__ void k_guard(int64_t n, int K, double Q, double eps, const int64_t *_
     }
 }
 
+// Galerkin coarse operator P^T A P (Section 2), row a by one thread, in the host's order: u
+// over the fine rows of aggregate a ascending (P_ua = pa), v over u's diagonal then u's
+// entries in stored order, b over v's row of P; each product (pa * A_uv) * P_vb is rounded
+// twice and added to entry b (starting from 0.0), all explicitly rounded. The row's entries are
+// kept sorted by column in shared memory ([slot][thread], conflict-free), up to GAL_CAP of
+// them; a row with more is left to the host (len = -1). Pass 1 (WRITE = false) stores the
+// number of nonzero off-diagonal entries of each row, pass 2 writes them at orp[a] in ascending
+// column order with the diagonal.
+constexpr int GAL_BS = 32;
+
+__device__ __forceinline__ int gal_prow(int32_t v, const int32_t *__restrict__ agg, const int32_t *__restrict__ agg2,
+                                        const double *__restrict__ wt, int32_t *c, double *p) {
+    if (agg2[v] < 0) { c[0] = agg[v]; p[0] = 1.0; return 1; }
+    const double w = wt[v];
+    int k = 0;
+    if (w != 0.0) { c[k] = agg[v]; p[k] = w; k++; }
+    c[k] = agg2[v];
+    p[k] = __dsub_rn(1.0, w);
+    return k + 1;
+}
+
+// add x to entry j of thread t's row; false when the row holds GAL_CAP entries and j is new
+__device__ __forceinline__ bool gal_add(int32_t (*key)[GAL_BS], double (*acc)[GAL_BS], int t, int &cnt, int32_t j,
+                                        double x) {
+    int lo = 0, hi = cnt;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (key[mid][t] < j) lo = mid + 1;
+        else hi = mid;
+    }
+    if (lo < cnt && key[lo][t] == j) {
+        acc[lo][t] = __dadd_rn(acc[lo][t], x);
+        return true;
+    }
+    if (cnt == GAL_CAP) return false;
+    for (int k = cnt; k > lo; k--) {
+        key[k][t] = key[k - 1][t];
+        acc[k][t] = acc[k - 1][t];
+    }
+    key[lo][t] = j;
+    acc[lo][t] = __dadd_rn(0.0, x);
+    cnt++;
+    return true;
+}
+
+// the products pv * P_vb of one term pv = pa * A_uv over v's row of P
+__device__ __forceinline__ bool gal_term(int32_t (*key)[GAL_BS], double (*acc)[GAL_BS], int t, int &cnt, int32_t v,
+                                         double pv, const int32_t *__restrict__ agg,
+                                         const int32_t *__restrict__ agg2, const double *__restrict__ wt) {
+    int32_t c[2];
+    double p[2];
+    const int k = gal_prow(v, agg, agg2, wt, c, p);
+    for (int s = 0; s < k; s++)
+        if (!gal_add(key, acc, t, cnt, c[s], __dmul_rn(pv, p[s]))) return false;
+    return true;
+}
+
+template <bool WRITE>
+__global__ void __launch_bounds__(GAL_BS) k_galerkin(
+    int64_t nc, const int64_t *__restrict__ ptr, const int32_t *__restrict__ rows, const double *__restrict__ pw,
+    const int64_t *__restrict__ rp, const int32_t *__restrict__ ci, const double *__restrict__ val,
+    const double *__restrict__ diag, const int32_t *__restrict__ agg, const int32_t *__restrict__ agg2,
+    const double *__restrict__ wt, int32_t *__restrict__ len, const int64_t *__restrict__ orp,
+    int32_t *__restrict__ oci, double *__restrict__ oval, double *__restrict__ odiag) {
+    __shared__ int32_t key[GAL_CAP][GAL_BS];
+    __shared__ double acc[GAL_CAP][GAL_BS];
+    const int t = threadIdx.x;
+    const int64_t a = (int64_t)blockIdx.x * GAL_BS + t;
+    if (a >= nc) return;
+    if (WRITE && len[a] < 0) return;
+    int cnt = 0;
+    bool ok = true;
+    for (int64_t q = ptr[a]; q < ptr[a + 1] && ok; q++) {
+        const int32_t u = rows[q];
+        const double pa = pw[q];
+        ok = gal_term(key, acc, t, cnt, u, __dmul_rn(pa, diag[u]), agg, agg2, wt);  // the diagonal
+        for (int64_t e = rp[u]; e < rp[u + 1] && ok; e++)
+            ok = gal_term(key, acc, t, cnt, ci[e], __dmul_rn(pa, val[e]), agg, agg2, wt);
+    }
+    if (!WRITE) {
+        int m = 0;
+        for (int k = 0; k < cnt; k++)
+            if (key[k][t] != (int32_t)a && acc[k][t] != 0.0) m++;
+        len[a] = ok ? m : -1;
+        return;
+    }
+    int64_t o = orp[a];
+    double d = 0.0;
+    for (int k = 0; k < cnt; k++) {
+        if (key[k][t] == (int32_t)a) { d = acc[k][t]; continue; }
+        if (acc[k][t] == 0.0) continue;
+        oci[o] = key[k][t];
+        oval[o] = acc[k][t];
+        o++;
+    }
+    odiag[a] = d;
+}
+
 static inline unsigned nblk(int64_t work, int bs) { return (unsigned)((work + bs - 1) / bs); }
 
 // Upload a level operator (natural order) and run K9 (and K10 when aff != nullptr). Everything is
@@ -235,6 +335,100 @@ static int run_setup_kernels(const HostMat &A, const std::vector<int32_t> *colou
 out:
     if (st) {
         void *ptrs[] = {d_rp, d_ci, d_val, d_diag, d_X, d_rows, d_aff, d_strong, d_adm};
+        for (void *q : ptrs)
+            if (q) cudaFreeAsync(q, st);
+        cudaStreamSynchronize(st);
+        cudaStreamDestroy(st);
+    }
+    return rc;
+}
+
+int gpu_galerkin(const HostLevel &L, const std::vector<int64_t> &ptr, const std::vector<int32_t> &rows,
+                 const std::vector<double> &pw, HostMat &Ac,
+                 const std::function<double(int64_t, std::vector<int32_t> &, std::vector<double> &)> &host_row) {
+    int rc = LAMG_OK;
+    const HostMat &A = L.A;
+    const int64_t n = A.n, z = A.nnz(), nc = L.nc, np = ptr[nc];
+    int64_t *d_rp = nullptr, *d_ptr = nullptr, *d_orp = nullptr;
+    int32_t *d_ci = nullptr, *d_agg = nullptr, *d_agg2 = nullptr, *d_rows = nullptr, *d_len = nullptr,
+            *d_oci = nullptr;
+    double *d_val = nullptr, *d_diag = nullptr, *d_wt = nullptr, *d_pw = nullptr, *d_oval = nullptr,
+           *d_odiag = nullptr;
+    cudaStream_t st = nullptr;
+    std::vector<int32_t> len(nc);
+    std::vector<int64_t> big;
+    std::vector<std::vector<int32_t>> bcol;
+    std::vector<std::vector<double>> bval;
+    std::vector<double> bdiag;
+    int64_t tot = 0;
+    if ((int64_t)L.agg.size() != n || (int64_t)L.agg2.size() != n || (int64_t)L.wt.size() != n)
+        return LAMG_ERR_INVALID;
+    CK(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+    CK(cudaMallocAsync((void **)&d_rp, (n + 1) * sizeof(int64_t), st));
+    CK(cudaMallocAsync((void **)&d_ci, (z ? z : 1) * sizeof(int32_t), st));
+    CK(cudaMallocAsync((void **)&d_val, (z ? z : 1) * sizeof(double), st));
+    CK(cudaMallocAsync((void **)&d_diag, n * sizeof(double), st));
+    CK(cudaMallocAsync((void **)&d_agg, n * sizeof(int32_t), st));
+    CK(cudaMallocAsync((void **)&d_agg2, n * sizeof(int32_t), st));
+    CK(cudaMallocAsync((void **)&d_wt, n * sizeof(double), st));
+    CK(cudaMallocAsync((void **)&d_ptr, (nc + 1) * sizeof(int64_t), st));
+    CK(cudaMallocAsync((void **)&d_rows, (np ? np : 1) * sizeof(int32_t), st));
+    CK(cudaMallocAsync((void **)&d_pw, (np ? np : 1) * sizeof(double), st));
+    CK(cudaMallocAsync((void **)&d_len, nc * sizeof(int32_t), st));
+    CK(cudaMemcpyAsync(d_rp, A.rp.data(), (n + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, st));
+    if (z) CK(cudaMemcpyAsync(d_ci, A.ci.data(), z * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    if (z) CK(cudaMemcpyAsync(d_val, A.val.data(), z * sizeof(double), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(d_diag, A.diag.data(), n * sizeof(double), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(d_agg, L.agg.data(), n * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(d_agg2, L.agg2.data(), n * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(d_wt, L.wt.data(), n * sizeof(double), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(d_ptr, ptr.data(), (nc + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, st));
+    if (np) CK(cudaMemcpyAsync(d_rows, rows.data(), np * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    if (np) CK(cudaMemcpyAsync(d_pw, pw.data(), np * sizeof(double), cudaMemcpyHostToDevice, st));
+    k_galerkin<false><<<nblk(nc, GAL_BS), GAL_BS, 0, st>>>(nc, d_ptr, d_rows, d_pw, d_rp, d_ci, d_val, d_diag, d_agg,
+                                                            d_agg2, d_wt, d_len, nullptr, nullptr, nullptr, nullptr);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(len.data(), d_len, nc * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    // rows with more distinct columns than the GPU accumulator holds: summed on the host
+    for (int64_t a = 0; a < nc; a++)
+        if (len[a] < 0) big.push_back(a);
+    bcol.resize(big.size());
+    bval.resize(big.size());
+    bdiag.resize(big.size());
+    for (size_t i = 0; i < big.size(); i++) {
+        bdiag[i] = host_row(big[i], bcol[i], bval[i]);
+        len[big[i]] = (int32_t)bcol[i].size();
+    }
+    Ac.n = nc;
+    Ac.rp.assign(nc + 1, 0);
+    for (int64_t a = 0; a < nc; a++) Ac.rp[a + 1] = Ac.rp[a] + len[a];
+    tot = Ac.rp[nc];
+    Ac.ci.resize(tot);
+    Ac.val.resize(tot);
+    Ac.diag.assign(nc, 0.0);
+    CK(cudaMallocAsync((void **)&d_orp, (nc + 1) * sizeof(int64_t), st));
+    CK(cudaMallocAsync((void **)&d_oci, (tot ? tot : 1) * sizeof(int32_t), st));
+    CK(cudaMallocAsync((void **)&d_oval, (tot ? tot : 1) * sizeof(double), st));
+    CK(cudaMallocAsync((void **)&d_odiag, nc * sizeof(double), st));
+    CK(cudaMemcpyAsync(d_orp, Ac.rp.data(), (nc + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, st));
+    k_galerkin<true><<<nblk(nc, GAL_BS), GAL_BS, 0, st>>>(nc, d_ptr, d_rows, d_pw, d_rp, d_ci, d_val, d_diag, d_agg,
+                                                           d_agg2, d_wt, d_len, d_orp, d_oci, d_oval, d_odiag);
+    CK(cudaGetLastError());
+    if (tot) CK(cudaMemcpyAsync(Ac.ci.data(), d_oci, tot * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    if (tot) CK(cudaMemcpyAsync(Ac.val.data(), d_oval, tot * sizeof(double), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(Ac.diag.data(), d_odiag, nc * sizeof(double), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    for (size_t i = 0; i < big.size(); i++) {
+        const int64_t a = big[i];
+        std::copy(bcol[i].begin(), bcol[i].end(), Ac.ci.begin() + Ac.rp[a]);
+        std::copy(bval[i].begin(), bval[i].end(), Ac.val.begin() + Ac.rp[a]);
+        Ac.diag[a] = bdiag[i];
+    }
+out:
+    if (st) {
+        void *ptrs[] = {d_rp, d_ci, d_val, d_diag, d_agg, d_agg2, d_wt, d_ptr, d_rows, d_pw, d_len,
+                        d_orp, d_oci, d_oval, d_odiag};
         for (void *q : ptrs)
             if (q) cudaFreeAsync(q, st);
         cudaStreamSynchronize(st);

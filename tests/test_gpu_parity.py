@@ -102,6 +102,32 @@ def test_setup_matches_oracle(case):
     P.close()
 
 
+# Levels of at least 32768 fine rows form P^T A P on the GPU (one thread per coarse row, the
+# host's order of explicitly rounded products and sums); coarse rows with more distinct columns
+# than the GPU row accumulator holds (hub aggregates of the BA graph) are summed on the host.
+# Either way the coarse operators must equal the oracle's bit for bit.
+GALERKIN_CASES = {
+    "aniso256": lambda: gg.grid2d(256, 256, 1.0, 1e-3),
+    "grid3d40_hetero": lambda: gg.grid3d(40, 40, 40, "loguniform", seed=1),
+    "rgg60000": lambda: gg.rgg(60000, 10.0, seed=1),
+    "ba60000": lambda: gg.barabasi_albert(60000, 4, seed=1),
+}
+
+
+@pytest.mark.parametrize("name", sorted(GALERKIN_CASES))
+def test_gpu_galerkin_matches_oracle_bitwise(name):
+    g = GALERKIN_CASES[name]()
+    H = oracle.Hierarchy(g)
+    P = lamg.setup(g)
+    assert P.nlevels == H.nlevels, name
+    assert any(L["kind"] == "agg" and L["n"] >= 32768 for L in H.levels), name
+    for l, L in enumerate(H.levels):
+        assert P.info[l]["n"] == L["n"], (name, l)
+        for key in ("rp", "ci", "val", "diag"):
+            assert np.array_equal(P.array(l, key), L[key]), (name, l, key)
+    P.close()
+
+
 # ------------------------------------------------------------------------ cycle and CG
 
 # graph: every cycle step its own kernel; cluster: the whole cycle as one launch of a
