@@ -382,7 +382,30 @@ static void eliminate(const Mat *A, const uint8_t *inF, Level *L, Mat *Ac) {
 
 /* ------------------------------------------------------------------ test vectors, affinity */
 
-/* K test vectors, each nu_tv GS sweeps on A x = 0 from the random start (Section 2). */
+/* One relaxation step of a test vector at row u (Section 2: GS on A x = 0). The paper fixes no
+ * summation order for the neighbour sum; the reading used here (and on the GPU, where the
+ * rounded result feeds integer aggregation decisions): a row of at most TV_STRIDE entries is
+ * summed in stored order; a longer row as TV_STRIDE strided partial sums, partial j taking
+ * entries j, j + TV_STRIDE, j + 2 TV_STRIDE, ... in order, the partials then added in order
+ * of j. Every addition starts from 0.0. */
+#define TV_STRIDE 32
+static void tv_row(const Mat *A, int64_t u, double *x) {
+    const int64_t e0 = A->rp[u], e1 = A->rp[u + 1];
+    double s = 0.0;
+    if (e1 - e0 <= TV_STRIDE) {
+        for (int64_t e = e0; e < e1; e++) s += A->val[e] * x[A->ci[e]];
+    } else {
+        for (int j = 0; j < TV_STRIDE; j++) {
+            double p = 0.0;
+            for (int64_t e = e0 + j; e < e1; e += TV_STRIDE) p += A->val[e] * x[A->ci[e]];
+            s += p;
+        }
+    }
+    x[u] = (0.0 - s) / A->diag[u];
+}
+
+/* K test vectors, each nu_tv GS sweeps on A x = 0 from the random start (Section 2), in
+ * lexicographic or colour order (colours ascending, rows of a colour in ascending index). */
 static void test_vectors(Level *L, const Opts *o, int level) {
     int64_t n = L->A.n;
     int K = o->K;
@@ -391,8 +414,12 @@ static void test_vectors(Level *L, const Opts *o, int level) {
     for (int k = 0; k < K; k++) {
         for (int64_t u = 0; u < n; u++) x[u] = oracle_random_start(o->seed, level, u, k);
         for (int s = 0; s < o->nu_tv; s++) {
-            if (o->tv_lex) gs_sweep_lex(&L->A, x, NULL);
-            else gs_sweep_colour(L, x, NULL, 0);
+            if (o->tv_lex) {
+                for (int64_t u = 0; u < n; u++) tv_row(&L->A, u, x);
+            } else {
+                for (int c = 0; c < L->ncol; c++)
+                    for (int64_t t = L->cptr[c]; t < L->cptr[c + 1]; t++) tv_row(&L->A, L->corder[t], x);
+            }
         }
         for (int64_t u = 0; u < n; u++) L->X[u * K + k] = x[u];
     }

@@ -53,7 +53,11 @@ __global__ void k_tv_start(int64_t n, int K, uint64_t seed, int lvl, double *X) 
 }
 
 // One Gauss-Seidel colour class on A X = 0 for all K columns: X_u <- -(sum_v A_uv X_v) / A_uu.
-// Rows of one colour are pairwise non-adjacent, so they update independently.
+// Rows of one colour are pairwise non-adjacent, so they update independently. The neighbour sum
+// of a row of at most TV_STRIDE entries runs in stored order (one thread per row, these
+// kernels); a longer row is summed as TV_STRIDE strided partial sums added in order (one warp
+// per row, k_tv_long), the same order as the oracle's, which the paper leaves open.
+constexpr int TV_STRIDE = 32;
 template <int K>
 __global__ void k_tv_colour(int64_t cnt, const int32_t *__restrict__ rows,
                             const int64_t *__restrict__ rp, const int32_t *__restrict__ ci,
@@ -74,6 +78,27 @@ __global__ void k_tv_colour(int64_t cnt, const int32_t *__restrict__ rows,
     const double d = diag[u];
 #pragma unroll
     for (int k = 0; k < K; k++) X[(int64_t)u * K + k] = __ddiv_rn(__dsub_rn(0.0, s[k]), d);
+}
+
+// Rows longer than TV_STRIDE entries, one warp per row: lane j sums entries j, j + 32, ... in
+// order (from 0.0), lane 0 then adds the 32 partials in lane order (from 0.0).
+__global__ void k_tv_long(int K, int64_t cnt, const int32_t *__restrict__ rows, const int64_t *__restrict__ rp,
+                          const int32_t *__restrict__ ci, const double *__restrict__ val,
+                          const double *__restrict__ diag, double *X) {
+    const int64_t t = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (t >= cnt) return;  // whole warps leave together
+    const int32_t u = rows[t];
+    const int64_t e0 = rp[u], e1 = rp[u + 1];
+    const double d = diag[u];
+    for (int k = 0; k < K; k++) {
+        double p = 0.0;
+        for (int64_t e = e0 + lane; e < e1; e += TV_STRIDE)
+            p = __dadd_rn(p, __dmul_rn(val[e], X[(int64_t)ci[e] * K + k]));
+        double s = 0.0;
+        for (int j = 0; j < TV_STRIDE; j++) s = __dadd_rn(s, __shfl_sync(0xffffffffu, p, j));
+        if (lane == 0) X[(int64_t)u * K + k] = __ddiv_rn(__dsub_rn(0.0, s), d);
+    }
 }
 
 // Generic-K variant.
@@ -278,7 +303,7 @@ static int run_setup_kernels(const HostMat &A, const std::vector<int32_t> *colou
     const int bs = 128;
     cudaStream_t st = nullptr;
     std::vector<int32_t> rows;
-    std::vector<int64_t> cptr;
+    std::vector<int64_t> cptr, lptr;
     int ncol = 0;
     CK(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
     CK(cudaMallocAsync((void **)&d_rp, (n + 1) * sizeof(int64_t), st));
@@ -291,25 +316,39 @@ static int run_setup_kernels(const HostMat &A, const std::vector<int32_t> *colou
     if (z) CK(cudaMemcpyAsync(d_val, A.val.data(), z * sizeof(double), cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(d_diag, A.diag.data(), n * sizeof(double), cudaMemcpyHostToDevice, st));
     if (colour) {
-        // rows grouped by colour, ascending within a colour
+        // rows grouped by colour; within a colour the rows of at most TV_STRIDE entries, then
+        // the longer ones (from lptr[c]), each group ascending
         for (int32_t c : *colour) ncol = std::max(ncol, c + 1);
         cptr.assign(ncol + 1, 0);
+        lptr.assign(ncol, 0);
         for (int32_t c : *colour) cptr[c + 1]++;
         for (int c = 0; c < ncol; c++) cptr[c + 1] += cptr[c];
+        for (int64_t u = 0; u < n; u++)
+            if (A.rp[u + 1] - A.rp[u] <= TV_STRIDE) lptr[(*colour)[u]]++;
+        for (int c = 0; c < ncol; c++) lptr[c] += cptr[c];
         rows.resize(n);
-        std::vector<int64_t> fill(cptr.begin(), cptr.end() - 1);
-        for (int64_t u = 0; u < n; u++) rows[fill[(*colour)[u]]++] = (int32_t)u;
+        std::vector<int64_t> fill(cptr.begin(), cptr.end() - 1), lfill(lptr);
+        for (int64_t u = 0; u < n; u++) {
+            const int32_t c = (*colour)[u];
+            if (A.rp[u + 1] - A.rp[u] <= TV_STRIDE) rows[fill[c]++] = (int32_t)u;
+            else rows[lfill[c]++] = (int32_t)u;
+        }
         CK(cudaMallocAsync((void **)&d_rows, n * sizeof(int32_t), st));
         CK(cudaMemcpyAsync(d_rows, rows.data(), n * sizeof(int32_t), cudaMemcpyHostToDevice, st));
         k_tv_start<<<nblk(n * K, bs), bs, 0, st>>>(n, K, seed, level, d_X);
         for (int s = 0; s < nu; s++) {
             for (int c = 0; c < ncol; c++) {
-                const int64_t cnt = cptr[c + 1] - cptr[c];
-                if (!cnt) continue;
-                if (K == 4)
-                    k_tv_colour<4><<<nblk(cnt, bs), bs, 0, st>>>(cnt, d_rows + cptr[c], d_rp, d_ci, d_val, d_diag, d_X);
-                else
-                    k_tv_colour_any<<<nblk(cnt, bs), bs, 0, st>>>(K, cnt, d_rows + cptr[c], d_rp, d_ci, d_val, d_diag, d_X);
+                const int64_t cnt = lptr[c] - cptr[c], lcnt = cptr[c + 1] - lptr[c];
+                if (cnt) {
+                    if (K == 4)
+                        k_tv_colour<4><<<nblk(cnt, bs), bs, 0, st>>>(cnt, d_rows + cptr[c], d_rp, d_ci, d_val, d_diag, d_X);
+                    else
+                        k_tv_colour_any<<<nblk(cnt, bs), bs, 0, st>>>(K, cnt, d_rows + cptr[c], d_rp, d_ci, d_val, d_diag,
+                                                                    d_X);
+                }
+                if (lcnt)
+                    k_tv_long<<<nblk(32 * lcnt, bs), bs, 0, st>>>(K, lcnt, d_rows + lptr[c], d_rp, d_ci, d_val, d_diag,
+                                                                 d_X);
             }
         }
         CK(cudaGetLastError());
