@@ -117,43 +117,36 @@ __global__ void k_tv_colour_any(int K, int64_t cnt, const int32_t *__restrict__ 
     }
 }
 
-// Affinity (Eq. 3) per off-diagonal entry and the veto flag of Eq. 9 from the row's side:
-// strong = |A_uv| >= tau * max_t |A_ut|.
-__global__ void k_affinity(int64_t n, int K, double tau, int veto, const int64_t *__restrict__ rp,
-                           const int32_t *__restrict__ ci, const double *__restrict__ val,
-                           const double *__restrict__ X, double *aff, uint8_t *strong) {
-    int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+// Affinity (Eq. 3) per off-diagonal entry, the veto flag of Eq. 9 from the row's side
+// (strong = |A_uv| >= tau * max_t |A_ut|), and the energy-ratio guard of Eq. 4 from the moments
+// of Appendix B: s0 = sum_v w_uv, s1_k = sum_v w_uv x_vk, s2_k = sum_v w_uv x_vk^2 (w_uv = -A_uv,
+// stored order); per column k, relaxed = (s2 - s1^2/s0)/2, forced = (x_sk^2 s0 - 2 x_sk s1 +
+// s2)/2, scale = (|s2| + s1^2/|s0|)/2; ratio = forced/relaxed, or 1 / infinity when relaxed <=
+// eps scale (1 if forced is as small too); q = the largest ratio over k; adm[e] = strong[e] and
+// q <= Q. Every operation is explicitly rounded (no contraction), so the values and decisions
+// are those of the same formulas evaluated on the host and in the oracle.
+//
+// Two passes: one thread per row for the row quantities (the veto threshold, sum_k x_uk^2 and
+// the moments, summed in stored order), then one thread per stored entry for everything that
+// is per entry, so a hub row's entries are spread over the GPU instead of one thread.
+constexpr int GUARD_KMAX = 16;
+
+// row quantities: rs[u * (3 + 2K)] = {tau max|A_ut|, sum_k x_uk^2, s0, s1[K], s2[K]} (the
+// moments only with moments set)
+__global__ void k_row_stats(int64_t n, int K, double tau, int moments, const int64_t *__restrict__ rp,
+                            const int32_t *__restrict__ ci, const double *__restrict__ val,
+                            const double *__restrict__ X, double *__restrict__ rs) {
+    const int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (u >= n) return;
+    double *r = rs + u * (3 + 2 * K);
     double mx = 0.0;
     for (int64_t e = rp[u]; e < rp[u + 1]; e++) mx = fmax(mx, fabs(val[e]));
-    const double thr = __dmul_rn(tau, mx);
+    r[0] = __dmul_rn(tau, mx);
     const double *xu = X + u * K;
     double uu = 0.0;
     for (int k = 0; k < K; k++) uu = __dadd_rn(uu, __dmul_rn(xu[k], xu[k]));
-    for (int64_t e = rp[u]; e < rp[u + 1]; e++) {
-        const double *xv = X + (int64_t)ci[e] * K;
-        double uv = 0.0, vv = 0.0;
-        for (int k = 0; k < K; k++) uv = __dadd_rn(uv, __dmul_rn(xu[k], xv[k]));
-        for (int k = 0; k < K; k++) vv = __dadd_rn(vv, __dmul_rn(xv[k], xv[k]));
-        aff[e] = __ddiv_rn(__dmul_rn(uv, uv), __dmul_rn(uu, vv));
-        strong[e] = veto ? (fabs(val[e]) >= thr) : 1;
-    }
-}
-
-// Energy-ratio guard of Eq. 4 from the moments of Appendix B, per entry (u, s) of u's row:
-// s0 = sum_v w_uv, s1_k = sum_v w_uv x_vk, s2_k = sum_v w_uv x_vk^2 (w_uv = -A_uv, stored
-// order); per column k, relaxed = (s2 - s1^2/s0)/2, forced = (x_sk^2 s0 - 2 x_sk s1 + s2)/2,
-// scale = (|s2| + s1^2/|s0|)/2; ratio = forced/relaxed, or 1 / infinity when relaxed <= eps
-// scale (1 if forced is as small too); q = the largest ratio over k. adm[e] = strong[e] and
-// q <= Q. One thread per row, every operation explicitly rounded (no contraction), so the
-// decisions are those of the same formula evaluated on the host.
-constexpr int GUARD_KMAX = 16;
-
-__global__ void k_guard(int64_t n, int K, double Q, double eps, const int64_t *__restrict__ rp,
-                        const int32_t *__restrict__ ci, const double *__restrict__ val,
-                        const double *__restrict__ X, const uint8_t *__restrict__ strong, uint8_t *adm) {
-    const int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (u >= n) return;
+    r[1] = uu;
+    if (!moments) return;
     double s0 = 0.0, s1[GUARD_KMAX], s2[GUARD_KMAX];
     for (int k = 0; k < K; k++) { s1[k] = 0.0; s2[k] = 0.0; }
     for (int64_t e = rp[u]; e < rp[u + 1]; e++) {
@@ -166,25 +159,52 @@ __global__ void k_guard(int64_t n, int K, double Q, double eps, const int64_t *_
             s2[k] = __dadd_rn(s2[k], __dmul_rn(wx, xv[k]));
         }
     }
-    for (int64_t e = rp[u]; e < rp[u + 1]; e++) {
-        if (!strong[e]) { adm[e] = 0; continue; }
-        const double *xs = X + (int64_t)ci[e] * K;
-        double worst = 0.0;
-        for (int k = 0; k < K; k++) {
-            const double s11 = __dmul_rn(s1[k], s1[k]);
-            const double relaxed = __dmul_rn(0.5, __dsub_rn(s2[k], __ddiv_rn(s11, s0)));
-            const double forced = __dmul_rn(0.5, __dadd_rn(__dsub_rn(__dmul_rn(__dmul_rn(xs[k], xs[k]), s0),
-                                                                     __dmul_rn(__dmul_rn(2.0, xs[k]), s1[k])),
-                                                           s2[k]));
-            const double scale = __dmul_rn(0.5, __dadd_rn(fabs(s2[k]), __ddiv_rn(s11, fabs(s0))));
-            const double lim = __dmul_rn(eps, scale);
-            double r;
-            if (relaxed <= lim) r = (forced <= lim) ? 1.0 : CUDART_INF;
-            else r = __ddiv_rn(forced, relaxed);
-            worst = (worst < r) ? r : worst;
-        }
-        adm[e] = worst <= Q ? 1 : 0;
+    r[2] = s0;
+    for (int k = 0; k < K; k++) { r[3 + k] = s1[k]; r[3 + K + k] = s2[k]; }
+}
+
+// per stored entry e (row u found by binary search in rp): aff[e], strong[e] and, with adm
+// set, adm[e]
+__global__ void k_entry_affinity(int64_t n, int64_t z, int K, int veto, double Q, double eps,
+                                 const int64_t *__restrict__ rp, const int32_t *__restrict__ ci,
+                                 const double *__restrict__ val, const double *__restrict__ X,
+                                 const double *__restrict__ rs, double *aff, uint8_t *strong, uint8_t *adm) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= z) return;
+    int64_t lo = 0, hi = n - 1;  // the row u with rp[u] <= e < rp[u + 1]
+    while (lo < hi) {
+        const int64_t mid = (lo + hi + 1) >> 1;
+        if (rp[mid] <= e) lo = mid;
+        else hi = mid - 1;
     }
+    const int64_t u = lo;
+    const double *r = rs + u * (3 + 2 * K);
+    const double *xu = X + u * K, *xv = X + (int64_t)ci[e] * K;
+    double uv = 0.0, vv = 0.0;
+    for (int k = 0; k < K; k++) uv = __dadd_rn(uv, __dmul_rn(xu[k], xv[k]));
+    for (int k = 0; k < K; k++) vv = __dadd_rn(vv, __dmul_rn(xv[k], xv[k]));
+    aff[e] = __ddiv_rn(__dmul_rn(uv, uv), __dmul_rn(r[1], vv));
+    const uint8_t st = veto ? (fabs(val[e]) >= r[0]) : 1;
+    strong[e] = st;
+    if (!adm) return;
+    if (!st) { adm[e] = 0; return; }
+    const double s0 = r[2];
+    double worst = 0.0;
+    for (int k = 0; k < K; k++) {
+        const double s1 = r[3 + k], s2 = r[3 + K + k], xs = xv[k];
+        const double s11 = __dmul_rn(s1, s1);
+        const double relaxed = __dmul_rn(0.5, __dsub_rn(s2, __ddiv_rn(s11, s0)));
+        const double forced = __dmul_rn(0.5, __dadd_rn(__dsub_rn(__dmul_rn(__dmul_rn(xs, xs), s0),
+                                                                 __dmul_rn(__dmul_rn(2.0, xs), s1)),
+                                                       s2));
+        const double scale = __dmul_rn(0.5, __dadd_rn(fabs(s2), __ddiv_rn(s11, fabs(s0))));
+        const double lim = __dmul_rn(eps, scale);
+        double q;
+        if (relaxed <= lim) q = (forced <= lim) ? 1.0 : CUDART_INF;
+        else q = __ddiv_rn(forced, relaxed);
+        worst = (worst < q) ? q : worst;
+    }
+    adm[e] = worst <= Q ? 1 : 0;
 }
 
 // Galerkin coarse operator P^T A P (Section 2), row a by one thread, in the host's order: u
@@ -298,7 +318,7 @@ static int run_setup_kernels(const HostMat &A, const std::vector<int32_t> *colou
     const int64_t n = A.n, z = A.nnz();
     int64_t *d_rp = nullptr;
     int32_t *d_ci = nullptr, *d_rows = nullptr;
-    double *d_val = nullptr, *d_diag = nullptr, *d_X = nullptr, *d_aff = nullptr;
+    double *d_val = nullptr, *d_diag = nullptr, *d_X = nullptr, *d_aff = nullptr, *d_rs = nullptr;
     uint8_t *d_strong = nullptr, *d_adm = nullptr;
     const int bs = 128;
     cudaStream_t st = nullptr;
@@ -357,23 +377,24 @@ static int run_setup_kernels(const HostMat &A, const std::vector<int32_t> *colou
         CK(cudaMemcpyAsync(d_X, Xin, n * K * sizeof(double), cudaMemcpyHostToDevice, st));
     }
     if (aff) {
+        const bool moments = adm && K <= GUARD_KMAX;
         CK(cudaMallocAsync((void **)&d_aff, (z ? z : 1) * sizeof(double), st));
         CK(cudaMallocAsync((void **)&d_strong, (z ? z : 1), st));
-        k_affinity<<<nblk(n, bs), bs, 0, st>>>(n, K, tau, veto, d_rp, d_ci, d_val, d_X, d_aff, d_strong);
+        CK(cudaMallocAsync((void **)&d_rs, n * (3 + 2 * K) * sizeof(double), st));
+        if (moments) CK(cudaMallocAsync((void **)&d_adm, (z ? z : 1), st));
+        k_row_stats<<<nblk(n, bs), bs, 0, st>>>(n, K, tau, moments ? 1 : 0, d_rp, d_ci, d_val, d_X, d_rs);
+        if (z)
+            k_entry_affinity<<<nblk(z, 256), 256, 0, st>>>(n, z, K, veto, Q, eps, d_rp, d_ci, d_val, d_X, d_rs, d_aff,
+                                                           d_strong, moments ? d_adm : nullptr);
         CK(cudaGetLastError());
         if (z) CK(cudaMemcpyAsync(aff, d_aff, z * sizeof(double), cudaMemcpyDeviceToHost, st));
         if (z) CK(cudaMemcpyAsync(strong, d_strong, z, cudaMemcpyDeviceToHost, st));
-        if (adm && K <= GUARD_KMAX) {
-            CK(cudaMallocAsync((void **)&d_adm, (z ? z : 1), st));
-            k_guard<<<nblk(n, bs), bs, 0, st>>>(n, K, Q, eps, d_rp, d_ci, d_val, d_X, d_strong, d_adm);
-            CK(cudaGetLastError());
-            if (z) CK(cudaMemcpyAsync(adm, d_adm, z, cudaMemcpyDeviceToHost, st));
-        }
+        if (moments && z) CK(cudaMemcpyAsync(adm, d_adm, z, cudaMemcpyDeviceToHost, st));
     }
     CK(cudaStreamSynchronize(st));
 out:
     if (st) {
-        void *ptrs[] = {d_rp, d_ci, d_val, d_diag, d_X, d_rows, d_aff, d_strong, d_adm};
+        void *ptrs[] = {d_rp, d_ci, d_val, d_diag, d_X, d_rows, d_aff, d_strong, d_adm, d_rs};
         for (void *q : ptrs)
             if (q) cudaFreeAsync(q, st);
         cudaStreamSynchronize(st);
