@@ -91,12 +91,14 @@ int gpu_affinity(const HostMat &A, const double *X, int K, double tau, double *a
 // Galerkin P^T A P of an aggregation level on the GPU (setup_kernels.cu): ptr/rows/pw is P^T by
 // coarse row (galerkin_pt); every coarse entry is the same ordered sum of explicitly rounded
 // products as the host's, so Ac equals the host result bit for bit. Rows with more than
-// GAL_CAP distinct coarse columns come from host_row(a, cols, vals) -> diagonal, which appends
-// the row's nonzero off-diagonal entries in ascending column order.
+// GAL_CAP distinct coarse columns come from host_rows(rows, cols, vals, diags), which fills, for
+// each listed coarse row, its nonzero off-diagonal entries in ascending column order and its
+// diagonal.
 constexpr int GAL_CAP = 128;
+using GalerkinHostRows = std::function<void(const std::vector<int64_t> &, std::vector<std::vector<int32_t>> &,
+                                            std::vector<std::vector<double>> &, std::vector<double> &)>;
 int gpu_galerkin(const HostLevel &L, const std::vector<int64_t> &ptr, const std::vector<int32_t> &rows,
-                 const std::vector<double> &pw, HostMat &Ac,
-                 const std::function<double(int64_t, std::vector<int32_t> &, std::vector<double> &)> &host_row);
+                 const std::vector<double> &pw, HostMat &Ac, const GalerkinHostRows &host_rows);
 int gpu_tv_and_affinity(const HostMat &A, const std::vector<int32_t> &colour, int level,
                         uint64_t seed, int K, int nu, double tau, int veto, double *X,
                         double *aff, uint8_t *strong, double Q, double eps, uint8_t *adm);

@@ -443,10 +443,17 @@ static int galerkin_device(const HostLevel &L, HostMat &Ac) {
     std::vector<int32_t> rows;
     std::vector<double> pw;
     galerkin_pt(L, ptr, rows, pw);
-    RowAcc acc(L.nc);
-    return gpu_galerkin(L, ptr, rows, pw, Ac, [&](int64_t a, std::vector<int32_t> &oc, std::vector<double> &ov) {
-        return galerkin_row(L, ptr, rows, pw, a, acc, oc, ov);
-    });
+    // the rows the GPU leaves: each heavy (more than GAL_CAP distinct columns), so they are spread
+    // over the setup threads, each row summed by one thread as in a sequential pass
+    return gpu_galerkin(L, ptr, rows, pw, Ac,
+                        [&](const std::vector<int64_t> &big, std::vector<std::vector<int32_t>> &oc,
+                            std::vector<std::vector<double>> &ov, std::vector<double> &od) {
+                            parallel_chunks((int64_t)big.size(), 8, [&](int, int64_t i0, int64_t i1) {
+                                RowAcc acc(L.nc);
+                                for (int64_t i = i0; i < i1; i++)
+                                    od[i] = galerkin_row(L, ptr, rows, pw, big[i], acc, oc[i], ov[i]);
+                            });
+                        });
 }
 
 // ----------------------------------------------------------------------------------- coarsest

@@ -405,7 +405,7 @@ out:
 
 int gpu_galerkin(const HostLevel &L, const std::vector<int64_t> &ptr, const std::vector<int32_t> &rows,
                  const std::vector<double> &pw, HostMat &Ac,
-                 const std::function<double(int64_t, std::vector<int32_t> &, std::vector<double> &)> &host_row) {
+                 const GalerkinHostRows &host_rows) {
     int rc = LAMG_OK;
     const HostMat &A = L.A;
     const int64_t n = A.n, z = A.nnz(), nc = L.nc, np = ptr[nc];
@@ -456,10 +456,8 @@ int gpu_galerkin(const HostLevel &L, const std::vector<int64_t> &ptr, const std:
     bcol.resize(big.size());
     bval.resize(big.size());
     bdiag.resize(big.size());
-    for (size_t i = 0; i < big.size(); i++) {
-        bdiag[i] = host_row(big[i], bcol[i], bval[i]);
-        len[big[i]] = (int32_t)bcol[i].size();
-    }
+    host_rows(big, bcol, bval, bdiag);
+    for (size_t i = 0; i < big.size(); i++) len[big[i]] = (int32_t)bcol[i].size();
     Ac.n = nc;
     Ac.rp.assign(nc + 1, 0);
     for (int64_t a = 0; a < nc; a++) Ac.rp[a + 1] = Ac.rp[a] + len[a];
