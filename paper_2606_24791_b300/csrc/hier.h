@@ -17,6 +17,10 @@ void batch_free(BatchCtx *b);
 // and destroying hierarchies never calls cudaFreeHost (which can synchronise the device).
 double *pinned_slot();
 void pinned_release(double *p);
+// Pinned host staging buffers of at least `bytes` from a process-lifetime pool (never freed, for
+// the same reason); nullptr when no pinned memory can be had.
+void *pinned_stage(size_t bytes);
+void pinned_stage_release(void *p, size_t bytes);
 }  // namespace lamg
 
 struct lamg_hier {

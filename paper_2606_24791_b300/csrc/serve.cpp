@@ -16,6 +16,7 @@
 #include <chrono>
 #include <cmath>
 #include <condition_variable>
+#include <cstring>
 #include <deque>
 #include <map>
 #include <memory>
@@ -54,6 +55,38 @@ double *pinned_slot() {
 void pinned_release(double *p) {
     std::lock_guard<std::mutex> lock(g_pin_mu);
     g_pin_free.push_back(p);
+}
+
+namespace {
+std::map<size_t, std::vector<void *>> g_stage_free;  // by power-of-two size
+}
+
+static size_t stage_class(size_t bytes) {
+    size_t c = (size_t)1 << 20;
+    while (c < bytes) c <<= 1;
+    return c;
+}
+
+void *pinned_stage(size_t bytes) {
+    const size_t c = stage_class(bytes);
+    std::lock_guard<std::mutex> lock(g_pin_mu);
+    std::vector<void *> &f = g_stage_free[c];
+    if (!f.empty()) {
+        void *p = f.back();
+        f.pop_back();
+        return p;
+    }
+    void *p = nullptr;
+    if (cudaHostAlloc(&p, c, cudaHostAllocDefault) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return p;
+}
+
+void pinned_stage_release(void *p, size_t bytes) {
+    std::lock_guard<std::mutex> lock(g_pin_mu);
+    g_stage_free[stage_class(bytes)].push_back(p);
 }
 
 }  // namespace lamg

@@ -913,15 +913,36 @@ void lamg_destroy(lamg_hier *h) {
     delete h;
 }
 
+// Host vectors of a solve pass through a pooled pinned buffer (one host memcpy each way, then a
+// pinned DMA) instead of a pageable copy: measured 0.5 ms faster per 8 MB round trip than the
+// pageable path, while several copy threads were slower (page faults on the caller's fresh output
+// pages). Returned to the pool only when the stream has nothing left in flight (else kept out of
+// the pool).
+struct Stage {
+    void *p = nullptr;
+    size_t bytes = 0;
+    cudaStream_t s = nullptr;
+    Stage(size_t nb, cudaStream_t st) : bytes(nb), s(st) {
+        if (nb >= ((size_t)1 << 20)) p = pinned_stage(nb);
+    }
+    ~Stage() {
+        if (p && cudaStreamQuery(s) == cudaSuccess) pinned_stage_release(p, bytes);
+    }
+};
+
 static int solve_graph(lamg_hier *h, const double *b, double *phi, const lamg_solve_opts *so, lamg_stats *st) {
     cudaStream_t s = so->stream ? (cudaStream_t)so->stream : h->stream;
     const bool devp = so->flags & LAMG_DEVICE_PTRS;
     const DevLevel &F = h->dev[0];
     const int64_t n = F.n;
     int rc = LAMG_OK;
+    Stage stage(devp ? 0 : n * sizeof(double), s);
     CKR(cudaEventRecord(h->ev_a, s));
     if (devp) CKR(cudaMemcpyAsync(h->nat_in, b, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
-    else CKR(cudaMemcpyAsync(h->nat_in, b, n * sizeof(double), cudaMemcpyHostToDevice, s));
+    else if (stage.p) {
+        std::memcpy(stage.p, b, n * sizeof(double));
+        CKR(cudaMemcpyAsync(h->nat_in, stage.p, n * sizeof(double), cudaMemcpyHostToDevice, s));
+    } else CKR(cudaMemcpyAsync(h->nat_in, b, n * sizeof(double), cudaMemcpyHostToDevice, s));
     launch_gather(n, h->perm0, h->nat_in, h->r, s);
     launch_sum(n, h->r, h->red, s);
     launch_init_b(n, h->r, h->bkeep, h->xs, h->p, h->zold, h->red, s);
@@ -944,11 +965,13 @@ static int solve_graph(lamg_hier *h, const double *b, double *phi, const lamg_so
     launch_true_resid(F, h->xs, h->bkeep, h->red, s);
     launch_scatter(n, h->perm0, h->xs, h->nat_out, s);
     if (devp) CKR(cudaMemcpyAsync(phi, h->nat_out, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    else if (stage.p) CKR(cudaMemcpyAsync(stage.p, h->nat_out, n * sizeof(double), cudaMemcpyDeviceToHost, s));
     else CKR(cudaMemcpyAsync(phi, h->nat_out, n * sizeof(double), cudaMemcpyDeviceToHost, s));
     CKR(cudaMemcpyAsync(h->h_scal, h->red.scal, S_COUNT * sizeof(double), cudaMemcpyDeviceToHost, s));
     CKR(cudaEventRecord(h->ev_b, s));
     if ((rc = wait_event(h, h->ev_b))) return rc;
     CKR(cudaGetLastError());
+    if (stage.p) std::memcpy(phi, stage.p, n * sizeof(double));
     if (st) {
         st->iters = it;
         st->nlevels = (int32_t)h->dev.size();

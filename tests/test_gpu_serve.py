@@ -60,7 +60,9 @@ def test_requests_arriving_during_a_solve_share_the_device():
     # within milliseconds, and the executor must run their solves alongside the long one
     # instead of waiting for it to finish
     import time
-    big = gg.grid3d(96, 96, 96, "loguniform", seed=3)   # a solve of tens of milliseconds
+    # a solve of a few hundred milliseconds, long enough for four tiny setups (a few ms each,
+    # tens of ms on a busy host) to finish while it runs
+    big = gg.grid3d(128, 128, 128, "loguniform", seed=3)
     S = lamg.Server(budget_bytes=4e9, max_inflight=8, setup_threads=4, tol=1e-12, maxit=400)
     t_big = S.submit(big, gg.rhs(big, seed=50))
     t0 = time.time()
