@@ -922,11 +922,12 @@ struct Stage {
     void *p = nullptr;
     size_t bytes = 0;
     cudaStream_t s = nullptr;
+    bool drained = false;  // set once the last copy through the buffer is known complete
     Stage(size_t nb, cudaStream_t st) : bytes(nb), s(st) {
         if (nb >= ((size_t)1 << 20)) p = pinned_stage(nb);
     }
     ~Stage() {
-        if (p && cudaStreamQuery(s) == cudaSuccess) pinned_stage_release(p, bytes);
+        if (p && (drained || cudaStreamQuery(s) == cudaSuccess)) pinned_stage_release(p, bytes);
     }
 };
 
@@ -971,7 +972,10 @@ static int solve_graph(lamg_hier *h, const double *b, double *phi, const lamg_so
     CKR(cudaEventRecord(h->ev_b, s));
     if ((rc = wait_event(h, h->ev_b))) return rc;
     CKR(cudaGetLastError());
-    if (stage.p) std::memcpy(phi, stage.p, n * sizeof(double));
+    if (stage.p) {
+        std::memcpy(phi, stage.p, n * sizeof(double));
+        stage.drained = true;  // ev_b followed the copy into the buffer
+    }
     if (st) {
         st->iters = it;
         st->nlevels = (int32_t)h->dev.size();
