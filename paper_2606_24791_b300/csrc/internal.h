@@ -99,6 +99,12 @@ using GalerkinHostRows = std::function<void(const std::vector<int64_t> &, std::v
                                             std::vector<std::vector<double>> &, std::vector<double> &)>;
 int gpu_galerkin(const HostLevel &L, const std::vector<int64_t> &ptr, const std::vector<int32_t> &rows,
                  const std::vector<double> &pw, HostMat &Ac, const GalerkinHostRows &host_rows);
+// Exact Schur complement onto C of an elimination level on the GPU (setup_kernels.cu): row i is
+// node cnode[i]; the same ordered, explicitly rounded sums as the host's row, so Ac equals the
+// host result bit for bit. Rows with more than GAL_CAP distinct coarse columns come from
+// host_rows (as for gpu_galerkin, rows given by coarse index).
+int gpu_schur(const HostMat &A, const std::vector<uint8_t> &inF, const std::vector<int32_t> &cidx,
+              const std::vector<int32_t> &cnode, HostMat &Ac, const GalerkinHostRows &host_rows);
 int gpu_tv_and_affinity(const HostMat &A, const std::vector<int32_t> &colour, int level,
                         uint64_t seed, int K, int nu, double tau, int veto, double *X,
                         double *aff, uint8_t *strong, double Q, double eps, uint8_t *adm);

@@ -153,14 +153,60 @@ struct RowAcc {
     }
 };
 
-// Exact Schur complement onto C (Eq. 2); C keeps ascending node order.
-static void schur(const HostMat &A, const std::vector<uint8_t> &inF, HostLevel &L, HostMat &Ac) {
+// Row i (node u) of the exact Schur complement onto C (Eq. 2): A_uv for the C neighbours v, minus
+// A_uv A_vt / A_vv over every F neighbour v and its neighbours t (u's own diagonal for t = u), in
+// the order of u's entries and then v's. Appends the row's nonzero off-diagonal entries
+// (ascending column) to oc/ov and returns its diagonal.
+static double schur_row(const HostMat &A, const std::vector<uint8_t> &inF, const std::vector<int32_t> &cidx,
+                        int64_t u, int64_t i, RowAcc &acc, std::vector<int32_t> &oc, std::vector<double> &ov) {
+    acc.start(i);
+    double d = A.diag[u];
+    for (int64_t e = A.rp[u]; e < A.rp[u + 1]; e++) {
+        const int32_t v = A.ci[e];
+        if (!inF[v]) {
+            acc.at(cidx[v]) += A.val[e];
+            continue;
+        }
+        const double avv = A.diag[v], auv = A.val[e];
+        for (int64_t f = A.rp[v]; f < A.rp[v + 1]; f++) {
+            const int32_t t = A.ci[f];
+            const double term = auv * A.val[f] / avv;
+            if (t == u) d -= term;
+            else acc.at(cidx[t]) -= term;
+        }
+    }
+    std::sort(acc.cols.begin(), acc.cols.end());
+    for (int32_t j : acc.cols) {
+        if (acc.v[j] == 0.0) continue;
+        oc.push_back(j);
+        ov.push_back(acc.v[j]);
+    }
+    return d;
+}
+
+// Exact Schur complement onto C (Eq. 2); C keeps ascending node order. Levels of at least
+// SCHUR_MIN_ROWS rows form it on the GPU (the same ordered, explicitly rounded sums: the same
+// operator), rows the GPU leaves on the setup threads; smaller levels here.
+constexpr int64_t SCHUR_MIN_ROWS = 32768;
+
+static int schur(const HostMat &A, const std::vector<uint8_t> &inF, HostLevel &L, HostMat &Ac) {
     const int64_t n = A.n;
     L.cidx.assign(n, -1);
-    int64_t nc = 0;
+    std::vector<int32_t> cnode;
     for (int64_t u = 0; u < n; u++)
-        if (!inF[u]) L.cidx[u] = (int32_t)nc++;
+        if (!inF[u]) { L.cidx[u] = (int32_t)cnode.size(); cnode.push_back((int32_t)u); }
+    const int64_t nc = (int64_t)cnode.size();
     L.nc = nc;
+    if (n >= SCHUR_MIN_ROWS)
+        return gpu_schur(A, inF, L.cidx, cnode, Ac,
+                         [&](const std::vector<int64_t> &big, std::vector<std::vector<int32_t>> &oc,
+                             std::vector<std::vector<double>> &ov, std::vector<double> &od) {
+                             parallel_chunks((int64_t)big.size(), 8, [&](int, int64_t i0, int64_t i1) {
+                                 RowAcc acc(nc);
+                                 for (int64_t i = i0; i < i1; i++)
+                                     od[i] = schur_row(A, inF, L.cidx, cnode[big[i]], big[i], acc, oc[i], ov[i]);
+                             });
+                         });
     Ac.n = nc;
     Ac.rp.assign(nc + 1, 0);
     Ac.diag.assign(nc, 0.0);
@@ -169,35 +215,11 @@ static void schur(const HostMat &A, const std::vector<uint8_t> &inF, HostLevel &
     Ac.ci.reserve(A.nnz());
     Ac.val.reserve(A.nnz());
     RowAcc acc(nc);
-    int64_t i = 0;
-    for (int64_t u = 0; u < n; u++) {
-        if (inF[u]) continue;
-        acc.start(i);
-        double d = A.diag[u];
-        for (int64_t e = A.rp[u]; e < A.rp[u + 1]; e++) {
-            const int32_t v = A.ci[e];
-            if (!inF[v]) {
-                acc.at(L.cidx[v]) += A.val[e];
-                continue;
-            }
-            const double avv = A.diag[v], auv = A.val[e];
-            for (int64_t f = A.rp[v]; f < A.rp[v + 1]; f++) {
-                const int32_t t = A.ci[f];
-                const double term = auv * A.val[f] / avv;
-                if (t == u) d -= term;
-                else acc.at(L.cidx[t]) -= term;
-            }
-        }
-        std::sort(acc.cols.begin(), acc.cols.end());
-        for (int32_t j : acc.cols) {
-            if (acc.v[j] == 0.0) continue;
-            Ac.ci.push_back(j);
-            Ac.val.push_back(acc.v[j]);
-        }
-        Ac.diag[i] = d;
+    for (int64_t i = 0; i < nc; i++) {
+        Ac.diag[i] = schur_row(A, inF, L.cidx, cnode[i], i, acc, Ac.ci, Ac.val);
         Ac.rp[i + 1] = (int64_t)Ac.ci.size();
-        i++;
     }
+    return LAMG_OK;
 }
 
 // ----------------------------------------------------------------------------------- aggregation
@@ -663,7 +685,7 @@ int build_hierarchy(const lamg_graph *g, const lamg_options &o, std::vector<Host
         HostMat Ac;
         if (nF > 0 && (double)nF >= o.elim_min_frac * (double)n) {
             L.kind = KIND_ELIM;
-            schur(L.A, inF, L, Ac);
+            if ((rc = schur(L.A, inF, L, Ac))) return rc;
             lap(SETUP_ELIM);
         } else {
             lap(SETUP_ELIM);

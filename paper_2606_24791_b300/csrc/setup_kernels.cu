@@ -1,6 +1,6 @@
 // GPU setup kernels (Section 2): the K test vectors (K9), the per-edge affinity with the
-// strength-of-connection flag (K10), the energy-ratio guard of Eq. 4, and the Galerkin coarse
-// operator P^T A P.
+// strength-of-connection flag (K10), the energy-ratio guard of Eq. 4, the Galerkin coarse
+// operator P^T A P and the elimination's Schur complement.
 //
 // These kernels feed integer decisions on the host (which seed a node joins, whether a row is
 // upgraded to caliber-2), so they evaluate their sums in a fixed order with explicitly
@@ -305,6 +305,58 @@ __global__ void __launch_bounds__(GAL_BS) k_galerkin(
     odiag[a] = d;
 }
 
+// Exact Schur complement onto C (Eq. 2), row i (node u = cnode[i]) by one thread in the host's
+// order: u's entries in stored order; a C neighbour v adds A_uv to entry cidx[v], an F neighbour
+// v subtracts (A_uv A_vt) / A_vv (rounded twice) for each of its entries t, from the diagonal
+// when t = u, else from entry cidx[t]. Same accumulator and two passes as k_galerkin (a - b is
+// a + (-b) exactly, so subtracting through the accumulator's addition keeps the host's bits).
+template <bool WRITE>
+__global__ void __launch_bounds__(GAL_BS) k_schur(
+    int64_t nc, const int32_t *__restrict__ cnode, const int64_t *__restrict__ rp, const int32_t *__restrict__ ci,
+    const double *__restrict__ val, const double *__restrict__ diag, const uint8_t *__restrict__ inF,
+    const int32_t *__restrict__ cidx, int32_t *__restrict__ len, const int64_t *__restrict__ orp,
+    int32_t *__restrict__ oci, double *__restrict__ oval, double *__restrict__ odiag) {
+    __shared__ int32_t key[GAL_CAP][GAL_BS];
+    __shared__ double acc[GAL_CAP][GAL_BS];
+    const int t = threadIdx.x;
+    const int64_t i = (int64_t)blockIdx.x * GAL_BS + t;
+    if (i >= nc) return;
+    if (WRITE && len[i] < 0) return;
+    const int32_t u = cnode[i];
+    double d = diag[u];
+    int cnt = 0;
+    bool ok = true;
+    for (int64_t e = rp[u]; e < rp[u + 1] && ok; e++) {
+        const int32_t v = ci[e];
+        if (!inF[v]) {
+            ok = gal_add(key, acc, t, cnt, cidx[v], val[e]);
+            continue;
+        }
+        const double avv = diag[v], auv = val[e];
+        for (int64_t f = rp[v]; f < rp[v + 1] && ok; f++) {
+            const int32_t w = ci[f];
+            const double term = __ddiv_rn(__dmul_rn(auv, val[f]), avv);
+            if (w == u) d = __dsub_rn(d, term);
+            else ok = gal_add(key, acc, t, cnt, cidx[w], -term);
+        }
+    }
+    if (!WRITE) {
+        int m = 0;
+        for (int k = 0; k < cnt; k++)
+            if (acc[k][t] != 0.0) m++;
+        len[i] = ok ? m : -1;
+        return;
+    }
+    int64_t o = orp[i];
+    for (int k = 0; k < cnt; k++) {
+        if (acc[k][t] == 0.0) continue;
+        oci[o] = key[k][t];
+        oval[o] = acc[k][t];
+        o++;
+    }
+    odiag[i] = d;
+}
+
 static inline unsigned nblk(int64_t work, int bs) { return (unsigned)((work + bs - 1) / bs); }
 
 // Upload a level operator (natural order) and run K9 (and K10 when aff != nullptr). Everything is
@@ -487,6 +539,91 @@ out:
     if (st) {
         void *ptrs[] = {d_rp, d_ci, d_val, d_diag, d_agg, d_agg2, d_wt, d_ptr, d_rows, d_pw, d_len,
                         d_orp, d_oci, d_oval, d_odiag};
+        for (void *q : ptrs)
+            if (q) cudaFreeAsync(q, st);
+        cudaStreamSynchronize(st);
+        cudaStreamDestroy(st);
+    }
+    return rc;
+}
+
+int gpu_schur(const HostMat &A, const std::vector<uint8_t> &inF, const std::vector<int32_t> &cidx,
+              const std::vector<int32_t> &cnode, HostMat &Ac, const GalerkinHostRows &host_rows) {
+    int rc = LAMG_OK;
+    const int64_t n = A.n, z = A.nnz(), nc = (int64_t)cnode.size();
+    int64_t *d_rp = nullptr, *d_orp = nullptr;
+    int32_t *d_ci = nullptr, *d_cidx = nullptr, *d_cnode = nullptr, *d_len = nullptr, *d_oci = nullptr;
+    uint8_t *d_inF = nullptr;
+    double *d_val = nullptr, *d_diag = nullptr, *d_oval = nullptr, *d_odiag = nullptr;
+    cudaStream_t st = nullptr;
+    std::vector<int32_t> len(nc);
+    std::vector<int64_t> big;
+    std::vector<std::vector<int32_t>> bcol;
+    std::vector<std::vector<double>> bval;
+    std::vector<double> bdiag;
+    int64_t tot = 0;
+    if ((int64_t)inF.size() != n || (int64_t)cidx.size() != n) return LAMG_ERR_INVALID;
+    CK(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+    CK(cudaMallocAsync((void **)&d_rp, (n + 1) * sizeof(int64_t), st));
+    CK(cudaMallocAsync((void **)&d_ci, (z ? z : 1) * sizeof(int32_t), st));
+    CK(cudaMallocAsync((void **)&d_val, (z ? z : 1) * sizeof(double), st));
+    CK(cudaMallocAsync((void **)&d_diag, n * sizeof(double), st));
+    CK(cudaMallocAsync((void **)&d_inF, n, st));
+    CK(cudaMallocAsync((void **)&d_cidx, n * sizeof(int32_t), st));
+    CK(cudaMallocAsync((void **)&d_cnode, (nc ? nc : 1) * sizeof(int32_t), st));
+    CK(cudaMallocAsync((void **)&d_len, (nc ? nc : 1) * sizeof(int32_t), st));
+    CK(cudaMemcpyAsync(d_rp, A.rp.data(), (n + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, st));
+    if (z) CK(cudaMemcpyAsync(d_ci, A.ci.data(), z * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    if (z) CK(cudaMemcpyAsync(d_val, A.val.data(), z * sizeof(double), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(d_diag, A.diag.data(), n * sizeof(double), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(d_inF, inF.data(), n, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(d_cidx, cidx.data(), n * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    if (nc) CK(cudaMemcpyAsync(d_cnode, cnode.data(), nc * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    if (nc) {
+        k_schur<false><<<nblk(nc, GAL_BS), GAL_BS, 0, st>>>(nc, d_cnode, d_rp, d_ci, d_val, d_diag, d_inF, d_cidx,
+                                                             d_len, nullptr, nullptr, nullptr, nullptr);
+        CK(cudaGetLastError());
+        CK(cudaMemcpyAsync(len.data(), d_len, nc * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    }
+    CK(cudaStreamSynchronize(st));
+    // rows with more distinct columns than the GPU accumulator holds: summed on the host
+    for (int64_t a = 0; a < nc; a++)
+        if (len[a] < 0) big.push_back(a);
+    bcol.resize(big.size());
+    bval.resize(big.size());
+    bdiag.resize(big.size());
+    host_rows(big, bcol, bval, bdiag);
+    for (size_t i = 0; i < big.size(); i++) len[big[i]] = (int32_t)bcol[i].size();
+    Ac.n = nc;
+    Ac.rp.assign(nc + 1, 0);
+    for (int64_t a = 0; a < nc; a++) Ac.rp[a + 1] = Ac.rp[a] + len[a];
+    tot = Ac.rp[nc];
+    Ac.ci.resize(tot);
+    Ac.val.resize(tot);
+    Ac.diag.assign(nc, 0.0);
+    if (nc) {
+        CK(cudaMallocAsync((void **)&d_orp, (nc + 1) * sizeof(int64_t), st));
+        CK(cudaMallocAsync((void **)&d_oci, (tot ? tot : 1) * sizeof(int32_t), st));
+        CK(cudaMallocAsync((void **)&d_oval, (tot ? tot : 1) * sizeof(double), st));
+        CK(cudaMallocAsync((void **)&d_odiag, nc * sizeof(double), st));
+        CK(cudaMemcpyAsync(d_orp, Ac.rp.data(), (nc + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, st));
+        k_schur<true><<<nblk(nc, GAL_BS), GAL_BS, 0, st>>>(nc, d_cnode, d_rp, d_ci, d_val, d_diag, d_inF, d_cidx,
+                                                            d_len, d_orp, d_oci, d_oval, d_odiag);
+        CK(cudaGetLastError());
+        if (tot) CK(cudaMemcpyAsync(Ac.ci.data(), d_oci, tot * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+        if (tot) CK(cudaMemcpyAsync(Ac.val.data(), d_oval, tot * sizeof(double), cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(Ac.diag.data(), d_odiag, nc * sizeof(double), cudaMemcpyDeviceToHost, st));
+    }
+    CK(cudaStreamSynchronize(st));
+    for (size_t i = 0; i < big.size(); i++) {
+        const int64_t a = big[i];
+        std::copy(bcol[i].begin(), bcol[i].end(), Ac.ci.begin() + Ac.rp[a]);
+        std::copy(bval[i].begin(), bval[i].end(), Ac.val.begin() + Ac.rp[a]);
+        Ac.diag[a] = bdiag[i];
+    }
+out:
+    if (st) {
+        void *ptrs[] = {d_rp, d_ci, d_val, d_diag, d_inF, d_cidx, d_cnode, d_len, d_orp, d_oci, d_oval, d_odiag};
         for (void *q : ptrs)
             if (q) cudaFreeAsync(q, st);
         cudaStreamSynchronize(st);

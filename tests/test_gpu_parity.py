@@ -102,9 +102,10 @@ def test_setup_matches_oracle(case):
     P.close()
 
 
-# Levels of at least 32768 fine rows form P^T A P on the GPU (one thread per coarse row, the
-# host's order of explicitly rounded products and sums); coarse rows with more distinct columns
-# than the GPU row accumulator holds (hub aggregates of the BA graph) are summed on the host.
+# Levels of at least 32768 rows form their coarse operator on the GPU: P^T A P for aggregation
+# levels and the Schur complement of Eq. 2 for elimination levels (one thread per coarse row,
+# the host's order of explicitly rounded products and sums); coarse rows with more distinct
+# columns than the GPU row accumulator holds (hubs of the BA graph) are summed on the host.
 # Either way the coarse operators must equal the oracle's bit for bit.
 GALERKIN_CASES = {
     "aniso256": lambda: gg.grid2d(256, 256, 1.0, 1e-3),
@@ -115,12 +116,14 @@ GALERKIN_CASES = {
 
 
 @pytest.mark.parametrize("name", sorted(GALERKIN_CASES))
-def test_gpu_galerkin_matches_oracle_bitwise(name):
+def test_gpu_coarse_operators_match_oracle_bitwise(name):
     g = GALERKIN_CASES[name]()
     H = oracle.Hierarchy(g)
     P = lamg.setup(g)
     assert P.nlevels == H.nlevels, name
     assert any(L["kind"] == "agg" and L["n"] >= 32768 for L in H.levels), name
+    if name != "grid3d40_hetero":  # the others start with an elimination level of >= 32768 rows
+        assert H.levels[0]["kind"] == "elim" and H.levels[0]["n"] >= 32768, name
     for l, L in enumerate(H.levels):
         assert P.info[l]["n"] == L["n"], (name, l)
         for key in ("rp", "ci", "val", "diag"):
