@@ -105,6 +105,9 @@ int gpu_galerkin(const HostLevel &L, const std::vector<int64_t> &ptr, const std:
 // host_rows (as for gpu_galerkin, rows given by coarse index).
 int gpu_schur(const HostMat &A, const std::vector<uint8_t> &inF, const std::vector<int32_t> &cidx,
               const std::vector<int32_t> &cnode, HostMat &Ac, const GalerkinHostRows &host_rows);
+// The per-entry input checks of validate_graph on the GPU (setup_kernels.cu), for a graph whose
+// row pointers start at 0 and never decrease: *valid = every entry passes.
+int gpu_validate_entries(const lamg_graph *g, bool *valid);
 int gpu_tv_and_affinity(const HostMat &A, const std::vector<int32_t> &colour, int level,
                         uint64_t seed, int K, int nu, double tau, int veto, double *X,
                         double *aff, uint8_t *strong, double Q, double eps, uint8_t *adm);

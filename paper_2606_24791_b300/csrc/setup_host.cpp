@@ -20,28 +20,40 @@
 
 namespace lamg {
 
+// graphs with at least this many stored entries are checked on the GPU
+constexpr int64_t GPU_CHECK_MIN = (int64_t)1 << 16;
+
 int validate_graph(const lamg_graph *g) {
     if (!g || g->n < 1 || !g->rp || (g->rp[g->n] > 0 && (!g->ci || !g->w))) return LAMG_ERR_INVALID;
     const int64_t n = g->n;
     if (n >= (int64_t)INT32_MAX) return LAMG_ERR_INVALID;
     if (g->rp[0] != 0) return LAMG_ERR_INVALID;
-    for (int64_t u = 0; u < n; u++) {
+    for (int64_t u = 0; u < n; u++)
         if (g->rp[u + 1] < g->rp[u]) return LAMG_ERR_INVALID;
-        for (int64_t e = g->rp[u]; e < g->rp[u + 1]; e++) {
-            int32_t v = g->ci[e];
-            if (v < 0 || v >= n || v == u) return LAMG_ERR_INVALID;
-            if (e > g->rp[u] && v <= g->ci[e - 1]) return LAMG_ERR_INVALID;
-            double w = g->w[e];
-            if (!(w > 0.0) || !std::isfinite(w)) return LAMG_ERR_INVALID;
+    if (g->rp[n] >= GPU_CHECK_MIN) {
+        // per-entry checks and symmetry on the GPU, one thread per entry
+        bool valid = false;
+        const int rc = gpu_validate_entries(g, &valid);
+        if (rc) return rc;
+        if (!valid) return LAMG_ERR_INVALID;
+    } else {
+        for (int64_t u = 0; u < n; u++) {
+            for (int64_t e = g->rp[u]; e < g->rp[u + 1]; e++) {
+                int32_t v = g->ci[e];
+                if (v < 0 || v >= n || v == u) return LAMG_ERR_INVALID;
+                if (e > g->rp[u] && v <= g->ci[e - 1]) return LAMG_ERR_INVALID;
+                double w = g->w[e];
+                if (!(w > 0.0) || !std::isfinite(w)) return LAMG_ERR_INVALID;
+            }
         }
-    }
-    for (int64_t u = 0; u < n; u++) {
-        for (int64_t e = g->rp[u]; e < g->rp[u + 1]; e++) {
-            int32_t v = g->ci[e];
-            const int32_t *b = g->ci + g->rp[v], *end = g->ci + g->rp[v + 1];
-            const int32_t *f = std::lower_bound(b, end, (int32_t)u);
-            if (f == end || *f != u) return LAMG_ERR_INVALID;
-            if (g->w[g->rp[v] + (f - b)] != g->w[e]) return LAMG_ERR_INVALID;
+        for (int64_t u = 0; u < n; u++) {
+            for (int64_t e = g->rp[u]; e < g->rp[u + 1]; e++) {
+                int32_t v = g->ci[e];
+                const int32_t *b = g->ci + g->rp[v], *end = g->ci + g->rp[v + 1];
+                const int32_t *f = std::lower_bound(b, end, (int32_t)u);
+                if (f == end || *f != u) return LAMG_ERR_INVALID;
+                if (g->w[g->rp[v] + (f - b)] != g->w[e]) return LAMG_ERR_INVALID;
+            }
         }
     }
     // connectivity (breadth-first search from node 0)

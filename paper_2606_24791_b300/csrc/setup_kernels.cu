@@ -357,6 +357,38 @@ __global__ void __launch_bounds__(GAL_BS) k_schur(
     odiag[i] = d;
 }
 
+// Input checks of a graph (Eq. 1 needs a symmetric, positive weighting), one thread per stored
+// entry e of row u: 0 <= v < n, v != u, columns strictly ascending in the row, w finite and
+// positive, and u present in v's row with the same weight. The caller has checked that rp
+// starts at 0 and never decreases, so every index formed here is in range; v is used as a row
+// only once it is known to be in range. Any failure sets *bad.
+__global__ void k_validate(int64_t n, int64_t z, const int64_t *__restrict__ rp, const int32_t *__restrict__ ci,
+                           const double *__restrict__ w, int *bad) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= z) return;
+    int64_t lo = 0, hi = n - 1;  // the row u with rp[u] <= e < rp[u + 1]
+    while (lo < hi) {
+        const int64_t mid = (lo + hi + 1) >> 1;
+        if (rp[mid] <= e) lo = mid;
+        else hi = mid - 1;
+    }
+    const int64_t u = lo;
+    const int32_t v = ci[e];
+    const double we = w[e];
+    bool ok = v >= 0 && v < n && v != u && we > 0.0 && isfinite(we) && (e == rp[u] || v > ci[e - 1]);
+    if (ok) {
+        int64_t a = rp[v], b = rp[v + 1];
+        const int64_t end = b;
+        while (a < b) {
+            const int64_t mid = (a + b) >> 1;
+            if (ci[mid] < u) a = mid + 1;
+            else b = mid;
+        }
+        ok = a < end && ci[a] == u && w[a] == we;
+    }
+    if (!ok) atomicOr(bad, 1);
+}
+
 static inline unsigned nblk(int64_t work, int bs) { return (unsigned)((work + bs - 1) / bs); }
 
 // Upload a level operator (natural order) and run K9 (and K10 when aff != nullptr). Everything is
@@ -624,6 +656,41 @@ int gpu_schur(const HostMat &A, const std::vector<uint8_t> &inF, const std::vect
 out:
     if (st) {
         void *ptrs[] = {d_rp, d_ci, d_val, d_diag, d_inF, d_cidx, d_cnode, d_len, d_orp, d_oci, d_oval, d_odiag};
+        for (void *q : ptrs)
+            if (q) cudaFreeAsync(q, st);
+        cudaStreamSynchronize(st);
+        cudaStreamDestroy(st);
+    }
+    return rc;
+}
+
+int gpu_validate_entries(const lamg_graph *g, bool *valid) {
+    int rc = LAMG_OK;
+    const int64_t n = g->n, z = g->rp[n];
+    int64_t *d_rp = nullptr;
+    int32_t *d_ci = nullptr;
+    double *d_w = nullptr;
+    int *d_bad = nullptr;
+    int bad = 0;
+    cudaStream_t st = nullptr;
+    *valid = false;
+    CK(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+    CK(cudaMallocAsync((void **)&d_rp, (n + 1) * sizeof(int64_t), st));
+    CK(cudaMallocAsync((void **)&d_ci, (z ? z : 1) * sizeof(int32_t), st));
+    CK(cudaMallocAsync((void **)&d_w, (z ? z : 1) * sizeof(double), st));
+    CK(cudaMallocAsync((void **)&d_bad, sizeof(int), st));
+    CK(cudaMemsetAsync(d_bad, 0, sizeof(int), st));
+    CK(cudaMemcpyAsync(d_rp, g->rp, (n + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, st));
+    if (z) CK(cudaMemcpyAsync(d_ci, g->ci, z * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    if (z) CK(cudaMemcpyAsync(d_w, g->w, z * sizeof(double), cudaMemcpyHostToDevice, st));
+    if (z) k_validate<<<nblk(z, 256), 256, 0, st>>>(n, z, d_rp, d_ci, d_w, d_bad);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(&bad, d_bad, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    *valid = bad == 0;
+out:
+    if (st) {
+        void *ptrs[] = {d_rp, d_ci, d_w, d_bad};
         for (void *q : ptrs)
             if (q) cudaFreeAsync(q, st);
         cudaStreamSynchronize(st);

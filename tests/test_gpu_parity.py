@@ -315,6 +315,42 @@ def test_invalid_inputs_are_rejected():
         P.solve(np.ones(g.n), tol=0.0)
 
 
+def test_invalid_large_inputs_are_rejected_by_the_gpu_checks():
+    # graphs of at least 65536 stored entries are checked one thread per entry on the GPU: every
+    # kind of defect must still be reported as invalid, and the valid graph accepted
+    g = gg.grid2d(160, 160)
+    assert g.rp[-1] >= 65536
+    u = 5000
+    e0, e1 = int(g.rp[u]), int(g.rp[u + 1])
+
+    def variant(edit):
+        h = gg.Graph(g.n, g.rp.copy(), g.ci.copy(), g.w.copy())
+        edit(h)
+        return h
+
+    def swap(h):
+        h.ci[e0], h.ci[e0 + 1] = h.ci[e0 + 1], h.ci[e0]
+
+    defects = {
+        "asymmetric weight": lambda h: h.w.__setitem__(e0, h.w[e0] * 3.0),
+        "zero weight": lambda h: h.w.__setitem__(e1 - 1, 0.0),
+        "nan weight": lambda h: h.w.__setitem__(e0, np.nan),
+        "self loop": lambda h: h.ci.__setitem__(e0, u),
+        "column out of range": lambda h: h.ci.__setitem__(e1 - 1, g.n),
+        "negative column": lambda h: h.ci.__setitem__(e0, -1),
+        "unsorted row": swap,
+        "missing partner": lambda h: h.ci.__setitem__(e1 - 1, h.ci[e1 - 1] + 1 if h.ci[e1 - 1] + 1 < g.n else 0),
+    }
+    for name, edit in defects.items():
+        with pytest.raises(lamg.LamgError) as e:
+            lamg.setup(variant(edit))
+        assert e.value.code == 1, name
+    P = lamg.setup(g)
+    x, st = P.solve(gg.rhs(g, 2), 1e-8, 100)
+    assert st["relres_true"] <= 1e-8
+    P.close()
+
+
 def test_not_converged_is_reported():
     g = gg.grid2d(40, 40)
     P = lamg.setup(g, coarsest_max=16)
