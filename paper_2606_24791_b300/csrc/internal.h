@@ -77,6 +77,10 @@ int greedy_colour(const HostMat &A, std::vector<int32_t> &colour);
 // Chebyshev smoothing decision and coefficients of an aggregation level (ncol set).
 void cheb_setup(HostLevel &L, const lamg_options &o);
 int dense_pinv(const HostMat &A, std::vector<double> &pinv);
+// In-place inverse of the dense symmetric positive definite n x n row-major M on the GPU
+// (dense_kernels.cu, Gauss-Jordan without pivoting); LAMG_ERR_DISCONNECTED when a pivot is not
+// positive.
+int gpu_dense_inverse(int64_t n, std::vector<double> &M);
 double cycle_index(int64_t El, int64_t El1, int64_t E0);
 
 // GPU setup kernels (setup_kernels.cu): K test vectors by colour-ordered GS on A x = 0 and

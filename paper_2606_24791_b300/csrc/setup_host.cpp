@@ -492,8 +492,11 @@ static int galerkin_device(const HostLevel &L, HostMat &Ac) {
 
 // ----------------------------------------------------------------------------------- coarsest
 
-// A^+ = (A + J/n)^{-1} - J/n for a connected Laplacian-like operator (null space span{1}),
-// through a Cholesky factorisation of A + J/n.
+// A^+ = (A + J/n)^{-1} - J/n for a connected Laplacian-like operator (null space span{1}):
+// levels of at least DENSE_GPU_MIN rows invert A + J/n on the GPU (gpu_dense_inverse), smaller
+// ones through a Cholesky factorisation of A + J/n here.
+constexpr int64_t DENSE_GPU_MIN = 256;
+
 // a . b over len entries with four independent partial sums (k mod 4), added as
 // (s0 + s1) + (s2 + s3): four dependency chains instead of one
 static inline double dot4(const double *a, const double *b, int64_t len) {
@@ -515,6 +518,20 @@ int dense_pinv(const HostMat &A, std::vector<double> &pinv) {
     for (int64_t i = 0; i < n; i++) {
         M[i * n + i] += A.diag[i];
         for (int64_t e = A.rp[i]; e < A.rp[i + 1]; e++) M[i * n + A.ci[e]] += A.val[e];
+    }
+    if (n >= DENSE_GPU_MIN) {
+        // Gauss-Jordan inverse on the GPU, then the symmetric part minus J/n
+        const int rc = gpu_dense_inverse(n, M);
+        if (rc) return rc;
+        pinv.assign(n * n, 0.0);
+        const double jn = 1.0 / (double)n;
+        for (int64_t i = 0; i < n; i++)
+            for (int64_t j = 0; j <= i; j++) {
+                const double v = 0.5 * (M[i * n + j] + M[j * n + i]) - jn;
+                pinv[i * n + j] = v;
+                pinv[j * n + i] = v;
+            }
+        return LAMG_OK;
     }
     const int nthr = setup_threads();
     // lower Cholesky factor G (row-major, in place): M = G G^T, right-looking in panels of NB

@@ -351,6 +351,32 @@ def test_invalid_large_inputs_are_rejected_by_the_gpu_checks():
     P.close()
 
 
+@pytest.mark.parametrize("make", [lambda: gg.grid2d_random(30, 31, seed=4),
+                                  lambda: gg.grid3d(10, 10, 10, "loguniform", seed=5)])
+def test_dense_coarsest_inverse_is_the_pseudo_inverse(make):
+    # a graph of ~1000 nodes is its own coarsest level; its A^+ (inverted on the GPU for levels
+    # of >= 256 rows) must be the Moore-Penrose pseudo-inverse: A A^+ = I - J/n, and equal to
+    # the eigendecomposition-based one within the rounding of a dense inverse
+    g = make()
+    P = lamg.setup(g, coarsest_max=2048)
+    assert P.nlevels == 1 and P.info[0]["kind"] == "coarsest"
+    n = g.n
+    Ap = P.array(0, "pinv").reshape(n, n)
+    A = np.zeros((n, n))
+    for u in range(n):
+        for e in range(g.rp[u], g.rp[u + 1]):
+            A[u, g.ci[e]] = -g.w[e]
+        A[u, u] = g.w[g.rp[u]:g.rp[u + 1]].sum()
+    # reference: eigendecomposition with the null-space eigenvalue (1 / sqrt(n) constant vector)
+    # dropped
+    ref = np.linalg.pinv(A, rcond=1e-10, hermitian=True)
+    assert np.abs(Ap - ref).max() <= 1e-9 * np.abs(ref).max()
+    proj = np.eye(n) - 1.0 / n
+    assert np.abs(A @ Ap - proj).max() <= 1e-9
+    assert np.array_equal(Ap, Ap.T)
+    P.close()
+
+
 def test_not_converged_is_reported():
     g = gg.grid2d(40, 40)
     P = lamg.setup(g, coarsest_max=16)
