@@ -752,7 +752,7 @@ int finalize(lamg_hier *h) {
 }
 
 // The device's default stream-ordered memory pool keeps up to POOL_KEEP bytes of freed memory
-// (this process only) instead of returning it to the driver at every synchronisation: a setup
+// (this process only) instead of returning it to the CUDA driver at every synchronisation: a setup
 // makes a few hundred allocations, and re-mapping memory for each was most of its device-layout
 // time.
 constexpr uint64_t POOL_KEEP = (uint64_t)4 << 30;
