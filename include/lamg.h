@@ -64,7 +64,10 @@ typedef struct lamg_options {
     int32_t dmax;          /* elimination degree bound: 4 (Eq. 2) */
     int32_t nu_pre;        /* pre-smoothing sweeps: 1 */
     int32_t nu_post;       /* post-smoothing sweeps: 2 ((1,2) cycle, Appendix A Table 4) */
-    int32_t coarsest_max;  /* a level with at most this many nodes is solved densely: 1024 */
+    int32_t coarsest_max;  /* a level with at most this many nodes is solved densely; 0 (default):
+                              min(4096, max(1024, floor(sqrt(1.5 nnz(L))))) for the input's
+                              nnz(L) = n + 2m, so the dense coarsest matrix holds about as many
+                              bytes as the input operator */
     int32_t max_levels;    /* 100 */
     int32_t veto;          /* strength-of-connection veto on (1) / off (0), Eq. 9 */
     int32_t caliber2;      /* selective caliber-2 on (1) / off (0), Section 3.2 */

@@ -44,7 +44,7 @@ typedef struct {
     int nu_tv;          /* GS sweeps per test vector, Section 2: nu = 3 */
     int dmax;           /* low-degree elimination bound, Eq. 2: d_max = 4 */
     int nu_pre, nu_post;/* (1,2) cycle, Appendix A Table 4 */
-    int coarsest_max;   /* dense coarsest level when n <= this */
+    int coarsest_max;   /* dense coarsest level when n <= this; 0: the size rule of oracle_setup */
     int dense_rows;     /* dense coarsest level also when n <= this and the level has at least
                            n^2 / 8 off-diagonal entries (0: off) */
     int cheb_colours;   /* an aggregation level with more colours than this is smoothed by a
@@ -839,6 +839,14 @@ int oracle_setup(int64_t n, const int64_t *rp, const int32_t *ci, const double *
     if (rc) { free(H->lv); free(H); return rc; }
     if (!connected(&A)) { mat_free(&A); free(H->lv); free(H); return ERR_DISCONNECTED; }
     H->E0 = A.nnz / 2;
+    /* coarsest size: given, or the largest n whose dense matrix (8 n^2 bytes) is about the size
+     * of the input operator: floor(sqrt(1.5 nnz(L))), nnz(L) = n + 2m, within [1024, 4096] */
+    int64_t cmax = o->coarsest_max;
+    if (cmax <= 0) {
+        cmax = (int64_t)floor(sqrt(1.5 * (double)(A.n + A.nnz)));
+        if (cmax < 1024) cmax = 1024;
+        if (cmax > 4096) cmax = 4096;
+    }
     int l = 0;
     for (;;) {
         Level *L = &H->lv[l];
@@ -846,7 +854,7 @@ int oracle_setup(int64_t n, const int64_t *rp, const int32_t *ci, const double *
         alloc_vectors(L);
         H->nlev = l + 1;
         const int dense = A.n <= o->dense_rows && (double)A.nnz >= (double)A.n * (double)A.n / 8.0;
-        if (A.n <= o->coarsest_max || dense || l + 1 >= o->max_levels) {
+        if (A.n <= cmax || dense || l + 1 >= o->max_levels) {
             L->kind = LV_COARSEST;
             if (A.n > 4096) { oracle_free(H); return ERR_SETUP; }
             rc = coarsest_pinv(L);

@@ -430,10 +430,11 @@ __global__ void bk_elim_interp(int nc, int nF, int k, const int32_t *__restrict_
     x[e] = s + b[e] / d;
 }
 
-// Coarsest level (FP64 accumulation against the FP64 projected pseudo-inverse): one warp per
-// row, KL lanes per column times 32/KL lanes splitting the row.
+// Coarsest level against the projected pseudo-inverse in the cycle's type (FP64, or an FP32 copy
+// for the FP32 cycle, whose dense n^2 k products would otherwise run at the FP64 rate): one warp
+// per row, KL lanes per column times 32/KL lanes splitting the row.
 template <typename T, int KL>
-__global__ void __launch_bounds__(BBS) bk_coarse(int n, int k, const double *__restrict__ pinv,
+__global__ void __launch_bounds__(BBS) bk_coarse(int n, int k, const T *__restrict__ pinv,
                                                  const T *__restrict__ b, T *x) {
     b_trigger();
     b_wait();
@@ -442,10 +443,10 @@ __global__ void __launch_bounds__(BBS) bk_coarse(int n, int k, const double *__r
     const int j = lane % KL, sub = lane / KL;
     const int wg = (blockIdx.x * BBS + threadIdx.x) >> 5, nwarps = (gridDim.x * BBS) >> 5;
     for (int i = wg; i < n; i += nwarps) {
-        const double *row = pinv + (size_t)i * n;
-        double s = 0.0;
+        const T *row = pinv + (size_t)i * n;
+        T s = T(0);
         if (j < k)
-            for (int m = sub; m < n; m += TPR) s += row[m] * (double)b[(size_t)m * k + j];
+            for (int m = sub; m < n; m += TPR) s += row[m] * b[(size_t)m * k + j];
 #pragma unroll
         for (int o = KL; o < 32; o <<= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
         if (sub == 0 && j < k) x[(size_t)i * k + j] = (T)s;
@@ -773,7 +774,7 @@ struct BLev {
                   *pt_row = nullptr, *pf_col = nullptr, *pft_ptr = nullptr, *pft_f = nullptr;
     const void *val = nullptr, *diag = nullptr, *wt = nullptr, *pt_w = nullptr, *pf_val = nullptr,
                *dF = nullptr, *pft_val = nullptr;
-    const double *pinv = nullptr;
+    const void *pinv = nullptr;  // coarsest (I - J/n) A^+ in the cycle's type
     void *x = nullptr, *b = nullptr, *r = nullptr;
 };
 
@@ -827,7 +828,8 @@ static int build_ctx(lamg_hier *h, BatchCtx *c) {
         for (int q = 0; q < 8; q++) { B.cheb_c1[q] = D.cheb_c1[q]; B.cheb_c2[q] = D.cheb_c2[q]; }
         if (D.sell && (rc = typed_copy<T>(h, D.sl_val, D.sell_nnz, &B.sl_val))) return rc;
         B.rp = D.rp; B.ci = D.ci; B.agg = D.agg; B.agg2 = D.agg2; B.pt_ptr = D.pt_ptr; B.pt_row = D.pt_row;
-        B.pf_col = D.pf_col; B.pft_ptr = D.pft_ptr; B.pft_f = D.pft_f; B.pinv = D.pinv;
+        B.pf_col = D.pf_col; B.pft_ptr = D.pft_ptr; B.pft_f = D.pft_f;
+        if ((rc = typed_copy<T>(h, D.pinv, D.kind == KIND_COARSEST ? D.n * D.n : 0, &B.pinv))) return rc;
         const int64_t pte = (D.kind == KIND_AGG) ? (int64_t)h->host[l].A.n * 2 : 0;
         int32_t ent = 0;
         if (D.kind == KIND_AGG) {
@@ -985,7 +987,7 @@ static void bop(const Op &op, BatchCtx *c, cudaStream_t s, const Op *start) {
             break;
         }
         case OP_COARSE:
-#define C8(KLv, ...) case KLv: blaunch(bk_coarse<T, KLv>, rblocks((int64_t)n * 32), s, n, k, L.pinv, (const T *)b, x); break;
+#define C8(KLv, ...) case KLv: blaunch(bk_coarse<T, KLv>, rblocks((int64_t)n * 32), s, n, k, (const T *)L.pinv, (const T *)b, x); break;
             switch (KL) { K_CASES(C8) }
 #undef C8
             break;

@@ -690,13 +690,20 @@ int build_hierarchy(const lamg_graph *g, const lamg_options &o, std::vector<Host
     };
     int rc = validate_graph(g);
     if (rc) return rc;
-    if (o.K < 1 || o.K > 16 || o.nu_tv < 0 || o.coarsest_max < 1 || o.max_levels < 1 || o.dense_rows < 0 ||
+    if (o.K < 1 || o.K > 16 || o.nu_tv < 0 || o.coarsest_max < 0 || o.max_levels < 1 || o.dense_rows < 0 ||
         o.dense_rows > 4096 || o.cheb_colours < 0 || (o.cheb_colours > 0 && (o.cheb_degree < 1 || o.cheb_degree > 8)))
         return LAMG_ERR_INVALID;
     levels.clear();
     HostMat A;
     laplacian(g, A);
     const int64_t E0 = A.nnz() / 2;
+    // coarsest size (the paper's "small"): given, or by default the largest n whose dense matrix
+    // (8 n^2 bytes) is about the size of the input operator, floor(sqrt(1.5 nnz(L))) with
+    // nnz(L) = n + 2m, within [1024, 4096]
+    const int64_t cmax = o.coarsest_max > 0
+                             ? o.coarsest_max
+                             : std::min<int64_t>(4096, std::max<int64_t>(1024, (int64_t)std::floor(std::sqrt(
+                                                                                1.5 * (double)(A.n + A.nnz())))));
     lap(SETUP_INPUT);
     for (int l = 0;; l++) {
         levels.emplace_back();
@@ -705,7 +712,7 @@ int build_hierarchy(const lamg_graph *g, const lamg_options &o, std::vector<Host
         const int64_t n = L.A.n;
         // a small level with at least n^2/8 off-diagonal entries is solved directly
         const bool dense = n <= o.dense_rows && (double)L.A.nnz() >= (double)n * (double)n / 8.0;
-        if (n <= o.coarsest_max || dense || l + 1 >= o.max_levels) {
+        if (n <= cmax || dense || l + 1 >= o.max_levels) {
             L.kind = KIND_COARSEST;
             break;
         }

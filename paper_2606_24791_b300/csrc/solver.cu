@@ -790,7 +790,7 @@ void lamg_options_default(lamg_options *o) {
     o->dmax = 4;
     o->nu_pre = 1;
     o->nu_post = 2;
-    o->coarsest_max = 1024;
+    o->coarsest_max = 0;
     o->max_levels = 100;
     o->veto = 1;
     o->caliber2 = 1;
