@@ -357,7 +357,8 @@ typedef struct lamg_ticket_info {
 
 /* Create a server on device so->device with the given setup options (NULL: defaults), one
  * executor thread and so->setup_threads setup threads. A served setup runs no timing trials:
- * autotune is taken as 0 and cluster_rows = 0 as -1. Errors: INVALID, NO_DEVICE. */
+ * autotune is taken as 0 and cluster_rows = 0 as -1; coarsest_max = 0 is taken as 1024 (one
+ * solve per setup does not recover a larger dense inverse). Errors: INVALID, NO_DEVICE. */
 int lamg_server_create(const lamg_server_opts *so, const lamg_options *opt, lamg_server **out);
 /* Submit one request (graph + right-hand side, copied; same conventions as lamg_setup and
  * lamg_solve); returns at once with a ticket. A request whose estimated device memory alone

@@ -458,6 +458,9 @@ int lamg_server_create(const lamg_server_opts *so, const lamg_options *opt, lamg
     // behind other requests' solves and lengthen every setup
     s->opt.autotune = 0;
     if (s->opt.cluster_rows == 0) s->opt.cluster_rows = -1;
+    // one solve per setup: the default coarsest size rule trades a larger dense inverse at setup
+    // for fewer levels in every later solve, which a one-shot request never recovers
+    if (s->opt.coarsest_max == 0) s->opt.coarsest_max = 1024;
     const int nw = std::max(1, so->setup_threads);
     for (int i = 0; i < nw; i++) s->workers.emplace_back([s] { s->setup_worker(); });
     s->exec = std::thread([s] { s->executor(); });

@@ -35,7 +35,7 @@ def test_served_results_equal_solo_results():
     reqs = mix()
     alone = []
     for g, b in reqs:
-        P = lamg.setup(g, autotune=0, cluster_rows=-1)   # the options a served setup runs with
+        P = lamg.setup(g, autotune=0, cluster_rows=-1, coarsest_max=1024)   # a served setup's options
         (x,), (st,) = lamg.solve_many([P], [b], 1e-8, 200)
         alone.append((x, st["iters"]))
         P.close()
