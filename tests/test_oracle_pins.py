@@ -440,3 +440,21 @@ def test_fcg_converges_on_workload_shapes():
         assert out["hist"][-1] <= 1e-8 and out["iters"] <= 30, (g.name, out["iters"])
         r = gg.laplacian_apply(g, out["x"]) - (b - b.mean())
         assert np.linalg.norm(r) <= 2e-8 * np.linalg.norm(b - b.mean())
+
+
+def test_coarsest_size_rule():
+    # default coarsest size: floor(sqrt(1.5 nnz(L))) within [1024, 4096], nnz(L) = n + 2m; on a
+    # 420^2 anisotropic grid that is 1149, so its 1094-node level is the coarsest, where a fixed
+    # 1024 coarsens once more; an explicit coarsest_max still decides
+    g = gg.grid2d(420, 420, 1.0, 1e-3)
+    nnz_l = g.n + int(g.rp[-1])
+    cmax = min(4096, max(1024, math.floor(math.sqrt(1.5 * nnz_l))))
+    assert cmax == 1149
+    H = oracle.Hierarchy(g)
+    sizes = [L["n"] for L in H.levels]
+    assert H.levels[-1]["kind"] == "coarsest"
+    assert 1024 < sizes[-1] <= cmax and sizes[-2] > cmax
+    H2 = oracle.Hierarchy(g, coarsest_max=1024)
+    sizes2 = [L["n"] for L in H2.levels]
+    assert sizes2[-1] <= 1024 and len(sizes2) > len(sizes)
+    assert sizes2[:len(sizes) - 1] == sizes[:-1]
