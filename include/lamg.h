@@ -183,7 +183,8 @@ int lamg_import(const lamg_level_desc *levels, int32_t nlevels, const lamg_optio
 
 /* Solve L phi = b (Eq. 1) by flexible CG preconditioned with one cycle per iteration.
  * b (n values) is projected to mean zero first (the removed mean goes to st->b_mean);
- * phi (n values, output) has 1^T phi = 0. st may be NULL.
+ * phi (n values, output) has 1^T phi = 0. st may be NULL. Host vectors of at least 1 MiB pass
+ * through pinned staging buffers that the library pools for the life of the process.
  * Errors: INVALID (tol <= 0, maxit < 1), NOT_CONVERGED (phi and st valid), CUDA, TIMEOUT. */
 int lamg_solve(lamg_hier *h, const double *b, double *phi, const lamg_solve_opts *so,
                lamg_stats *st);
