@@ -14,7 +14,6 @@
 #include <cstdio>
 #include <cstring>
 #include <mutex>
-#include <thread>
 
 #include "hier.h"
 
@@ -35,21 +34,6 @@ bool lamg::start_fusable(const lamg_hier *h, int i, bool clusters) {
 }
 
 namespace {
-
-// fn(begin, end) on contiguous chunks of [0, n), one host thread each (up to 16; one thread
-// when n is below min_items per thread).
-template <class F>
-void host_chunks(int64_t n, int64_t min_items, F &&fn) {
-    const int hw = setup_threads();
-    const int T = (int)std::max<int64_t>(1, std::min<int64_t>(hw, n / std::max<int64_t>(1, min_items)));
-    if (T == 1) {
-        fn((int64_t)0, n);
-        return;
-    }
-    std::vector<std::thread> th;
-    for (int t = 0; t < T; t++) th.emplace_back([&fn, t, T, n] { fn(n * t / T, n * (t + 1) / T); });
-    for (auto &x : th) x.join();
-}
 
 // Device orders of all levels, from the coarsest up (see DevLevel).
 void build_orders(lamg_hier *h) {
