@@ -7,6 +7,7 @@ import subprocess
 
 import numpy as np
 
+import oracle
 import paper_2606_24791_b300 as lamg
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -42,6 +43,13 @@ def test_options_defaults_are_the_papers():
     assert (o.K, o.nu_tv, o.dmax, o.nu_pre, o.nu_post) == (4, 3, 4, 1, 2)
     assert o.Q == 2.5 and o.tau_soc == 0.05 and o.veto == 1 and o.caliber2 == 1
     assert ctypes.sizeof(lamg.Options) == 144   # the layout include/lamg.h states
+    # the readings' defaults, as include/lamg.h documents them: coarsest size by rule (0), dense
+    # small levels up to 4096 nodes, Chebyshev above 32 colours with degree 2, no timing trials,
+    # and the oracle's defaults agree wherever both have the option
+    assert (o.coarsest_max, o.dense_rows, o.cheb_colours, o.cheb_degree, o.autotune) == (0, 4096, 32, 2, 0)
+    for key in ("K", "nu_tv", "dmax", "nu_pre", "nu_post", "coarsest_max", "dense_rows", "cheb_colours",
+                "cheb_degree"):
+        assert oracle.DEFAULTS[key] == getattr(o, key), key
 
 
 def test_strerror_names_codes():
