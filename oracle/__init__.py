@@ -62,7 +62,11 @@ def lib():
         L.oracle_fcg.restype = C.c_int64
         L.oracle_fcg.argtypes = [P, P, P, C.c_double, C.c_int64, P, P]
         L.oracle_stationary.restype = C.c_int64
-        L.oracle_stationary.argtypes = [P, P, P, C.c_double, C.c_int64, C.c_int, P]
+        L.oracle_stationary.argtypes = [P, P, P, C.c_double, C.c_int64, C.c_int, P, P]
+        L.oracle_visit_counts.argtypes = [P, P]
+        L.oracle_set_gamma.argtypes = [P, C.c_int, C.c_double]
+        L.oracle_aggregate.restype = C.c_int64
+        L.oracle_aggregate.argtypes = [C.c_int64, P, P, P, P, P, C.c_int, P, P, C.c_double, C.c_double, P]
         L.oracle_splitmix64.restype = C.c_uint64
         L.oracle_splitmix64.argtypes = [C.c_uint64, C.c_uint64]
         L.oracle_random_start.restype = C.c_double
@@ -203,6 +207,15 @@ def pinv(A: Matrix) -> np.ndarray:
     return out
 
 
+def aggregate(A: Matrix, X, aff, strong, Q: float = 2.5, guard_eps: float = 1e-10):
+    """Caliber-1 aggregation on given test vectors, affinities and strong flags; returns
+    (seed_of, number of aggregates)."""
+    X = _c(X, np.float64); aff = _c(aff, np.float64); strong = _c(strong, np.uint8)
+    seed_of = np.zeros(A.n, np.int32)
+    nc = lib().oracle_aggregate(*A.args(), _p(X), X.shape[1], _p(aff), _p(strong), Q, guard_eps, _p(seed_of))
+    return seed_of, int(nc)
+
+
 def cheb_apply(A: Matrix, x, b, m: int = 2):
     """One Chebyshev smoothing polynomial of degree m on A x = b; returns (x, lambda)."""
     x = _c(x, np.float64).copy()
@@ -288,12 +301,31 @@ class Hierarchy:
             out["iterates"] = xs[:it]
         return out
 
-    def stationary(self, b, tol: float = 1e-8, maxit: int = 100, kappa: int = 0):
+    def stationary(self, b, tol: float = 1e-8, maxit: int = 100, kappa: int = 0, record: bool = False):
+        """Stationary cycles with recombination of the last kappa iterates; with record, also
+        the iterate after each cycle's correction ("pre") and the recombined iterate that was
+        saved, before the projection ("saved")."""
         b = _c(b, np.float64)
         x = np.zeros(self.n)
         hist = np.zeros(maxit + 1)
-        it = lib().oracle_stationary(self._h, _p(b), _p(x), tol, maxit, kappa, _p(hist))
-        return dict(x=x, iters=int(it), hist=hist[: it + 1])
+        xs = np.zeros((2 * maxit, self.n)) if record else None
+        it = lib().oracle_stationary(self._h, _p(b), _p(x), tol, maxit, kappa, _p(hist), _p(xs))
+        out = dict(x=x, iters=int(it), hist=hist[: it + 1])
+        if record:
+            out["pre"] = xs[0:2 * it:2]
+            out["saved"] = xs[1:2 * it:2]
+        return out
+
+    def set_gamma(self, level: int, gamma: float):
+        """Override the cycle index of one aggregation level."""
+        lib().oracle_set_gamma(self._h, level, gamma)
+        self._levels = None
+
+    def visit_counts(self) -> list:
+        """Visits of each level during the most recent cycle."""
+        out = np.zeros(self.nlevels, np.int64)
+        lib().oracle_visit_counts(self._h, _p(out))
+        return out.tolist()
 
     def summary(self) -> list:
         return [(l["kind"], l["n"], l["nnz"] // 2, l["ncol"], l["n_caliber2"], l["gamma"])

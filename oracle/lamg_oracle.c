@@ -94,6 +94,7 @@ typedef struct {
     /* cycle state */
     double *x, *b, *r;
     int64_t visits;        /* visit counter j within one finest-level cycle */
+    int64_t nvisits;       /* visits of this level in the last cycle (all kinds) */
 } Level;
 
 typedef struct {
@@ -165,9 +166,10 @@ uint64_t oracle_splitmix64(uint64_t seed, uint64_t i) {
 }
 
 /* Random start of test vector k at node u of level l (Section 2: "a random start").
- * Reading: U[-1, 1) from the top 53 bits of SplitMix64 output 1 + ((l << 44) | (u << 2) | k). */
+ * Reading: U[-1, 1) from the top 53 bits of SplitMix64 output 1 + ((l << 44) | (u << 4) | k),
+ * so every (level, node, column) with k < 16 and u < 2^40 has its own counter. */
 double oracle_random_start(uint64_t seed, int level, int64_t u, int k) {
-    uint64_t c = ((uint64_t)level << 44) | ((uint64_t)u << 2) | (uint64_t)k;
+    uint64_t c = ((uint64_t)level << 44) | ((uint64_t)u << 4) | (uint64_t)k;
     uint64_t z = oracle_splitmix64(seed, c + 1);
     double r = (double)(z >> 11) * (1.0 / 9007199254740992.0);
     return 2.0 * r - 1.0;
@@ -382,25 +384,12 @@ static void eliminate(const Mat *A, const uint8_t *inF, Level *L, Mat *Ac) {
 
 /* ------------------------------------------------------------------ test vectors, affinity */
 
-/* One relaxation step of a test vector at row u (Section 2: GS on A x = 0). The paper fixes no
- * summation order for the neighbour sum; the reading used here (and on the GPU, where the
- * rounded result feeds integer aggregation decisions): a row of at most TV_STRIDE entries is
- * summed in stored order; a longer row as TV_STRIDE strided partial sums, partial j taking
- * entries j, j + TV_STRIDE, j + 2 TV_STRIDE, ... in order, the partials then added in order
- * of j. Every addition starts from 0.0. */
-#define TV_STRIDE 32
+/* One relaxation step of a test vector at row u (Section 2: GS on A x = 0):
+ * x_u <- (0 - sum_{v != u} A_uv x_v) / A_uu, the neighbour sum taken in stored (ascending
+ * column) order from 0.0, as the relaxation formula is written. */
 static void tv_row(const Mat *A, int64_t u, double *x) {
-    const int64_t e0 = A->rp[u], e1 = A->rp[u + 1];
     double s = 0.0;
-    if (e1 - e0 <= TV_STRIDE) {
-        for (int64_t e = e0; e < e1; e++) s += A->val[e] * x[A->ci[e]];
-    } else {
-        for (int j = 0; j < TV_STRIDE; j++) {
-            double p = 0.0;
-            for (int64_t e = e0 + j; e < e1; e += TV_STRIDE) p += A->val[e] * x[A->ci[e]];
-            s += p;
-        }
-    }
+    for (int64_t e = A->rp[u]; e < A->rp[u + 1]; e++) s += A->val[e] * x[A->ci[e]];
     x[u] = (0.0 - s) / A->diag[u];
 }
 
@@ -833,6 +822,7 @@ int oracle_setup(int64_t n, const int64_t *rp, const int32_t *ci, const double *
     Hier *H = xcalloc(1, sizeof(Hier));
     fill_opts(&H->o, iopt, dopt);
     const Opts *o = &H->o;
+    if (o->K < 1 || o->K > 16 || o->max_levels < 1) { free(H); return ERR_INVALID; }
     H->lv = xcalloc(o->max_levels + 1, sizeof(Level));
     Mat A;
     int rc = laplacian_from_graph(n, rp, ci, w, &A);
@@ -921,6 +911,7 @@ static void visit(Hier *H, int l, int first) {
     Level *L = &H->lv[l];
     const Mat *A = &L->A;
     int64_t n = A->n;
+    L->nvisits++;
     if (L->kind == LV_COARSEST) {
         for (int64_t i = 0; i < n; i++) {
             double s = 0.0;
@@ -991,7 +982,7 @@ static void visit(Hier *H, int l, int first) {
  * All visit counters restart at every cycle. */
 static void apply_cycle(Hier *H, const double *r, double *z) {
     Level *F = &H->lv[0];
-    for (int l = 0; l < H->nlev; l++) H->lv[l].visits = 0;
+    for (int l = 0; l < H->nlev; l++) { H->lv[l].visits = 0; H->lv[l].nvisits = 0; }
     memcpy(F->b, r, F->A.n * sizeof(double));
     visit(H, 0, 1);
     memcpy(z, F->x, F->A.n * sizeof(double));
@@ -1049,9 +1040,11 @@ done:
 /* Stationary iteration x <- x + M(b - A x) with the finest-level min-residual recombination
  * of Section 2 over the last kappa iterates: alpha = argmin || r - A E alpha ||,
  * E = [x_1 - x, ..., x_kappa - x], x <- x + E alpha (kappa = 0: no recombination).
- * hist[i] = ||b - A x_i||/||b||. Returns the number of cycles. */
+ * hist[i] = ||b - A x_i||/||b||. xs (optional, 2 maxit x n) receives, for cycle i, the
+ * iterate after the cycle's correction (row 2i) and the recombined iterate that is saved,
+ * before the mean-zero projection (row 2i + 1). Returns the number of cycles. */
 int64_t oracle_stationary(Hier *H, const double *b_in, double *x, double tol, int64_t maxit,
-                          int kappa, double *hist) {
+                          int kappa, double *hist, double *xs) {
     int64_t n = H->lv[0].A.n;
     const Mat *A = &H->lv[0].A;
     double *b = xcalloc(n, sizeof(double)), *r = xcalloc(n, sizeof(double));
@@ -1070,6 +1063,7 @@ int64_t oracle_stationary(Hier *H, const double *b_in, double *x, double tol, in
         residual(A, x, b, r);
         apply_cycle(H, r, z);
         for (int64_t i = 0; i < n; i++) x[i] += z[i];
+        if (xs) memcpy(&xs[(2 * it) * n], x, n * sizeof(double));
         if (kappa > 0) {
             /* recombine with the saved iterates */
             int m = nsaved;
@@ -1119,6 +1113,7 @@ int64_t oracle_stationary(Hier *H, const double *b_in, double *x, double tol, in
             memcpy(&saved[nsaved * n], x, n * sizeof(double));
             nsaved++;
         }
+        if (xs) memcpy(&xs[(2 * it + 1) * n], x, n * sizeof(double));
         project_mean(x, n);
         residual(A, x, b, r);
         it++;
@@ -1133,6 +1128,16 @@ int64_t oracle_stationary(Hier *H, const double *b_in, double *x, double tol, in
 /* ------------------------------------------------------------------ accessors */
 
 int oracle_nlevels(const Hier *H) { return H->nlev; }
+
+/* Override the cycle index of one aggregation level (used by the pins of the visit rule). */
+void oracle_set_gamma(Hier *H, int l, double gamma) {
+    if (l >= 0 && l < H->nlev && H->lv[l].kind == LV_AGG) H->lv[l].gamma = gamma;
+}
+
+/* Visits of each level during the last cycle (apply_cycle restarts the counts). */
+void oracle_visit_counts(const Hier *H, int64_t *out) {
+    for (int l = 0; l < H->nlev; l++) out[l] = H->lv[l].nvisits;
+}
 
 /* meta: kind, n, nnz, ncol, nc, n_caliber2, Chebyshev smoothing; dmeta: gamma, lambda,
  * c1[8], c2[8] */
@@ -1276,6 +1281,25 @@ void oracle_cheb_apply(int64_t n, const int64_t *rp, const int32_t *ci, const do
         coef[0] = L.cheb_lambda;
         for (int k = 0; k < m && k < 8; k++) { coef[1 + k] = L.cheb_c1[k]; coef[9 + k] = L.cheb_c2[k]; }
     }
+}
+
+/* Caliber-1 aggregation (Section 2) on caller data: operator, K test vectors (n x K), the
+ * affinity and strong flag of every off-diagonal entry; seed_of (n) receives the seed node of
+ * each node's aggregate. Returns the number of aggregates. */
+int64_t oracle_aggregate(int64_t n, const int64_t *rp, const int32_t *ci, const double *val,
+                         const double *diag, const double *X, int K, const double *aff,
+                         const uint8_t *strong, double Qb, double guard_eps, int32_t *seed_of) {
+    Level L; memset(&L, 0, sizeof(L));
+    L.A.n = n; L.A.nnz = rp[n]; L.A.rp = (int64_t *)rp; L.A.ci = (int32_t *)ci;
+    L.A.val = (double *)val; L.A.diag = (double *)diag;
+    L.X = (double *)X; L.aff = (double *)aff; L.strong = (uint8_t *)strong;
+    Opts o; memset(&o, 0, sizeof(o));
+    o.K = K; o.Q = Qb; o.guard_eps = guard_eps;
+    aggregate(&L, &o);
+    memcpy(seed_of, L.seed_of, n * sizeof(int32_t));
+    int64_t nc = L.nc;
+    free(L.status); free(L.seed_of); free(L.agg); free(L.agg2); free(L.wt);
+    return nc;
 }
 
 void oracle_mat_meta(const OMat *M, int64_t *nnz_n) { nnz_n[0] = M->A.n; nnz_n[1] = M->A.nnz; }

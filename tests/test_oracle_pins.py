@@ -37,9 +37,9 @@ def test_splitmix64_published_values():
 
 
 def test_random_start_range_and_mapping():
-    # U[-1, 1) from the top 53 bits of SplitMix64 output 1 + ((level << 44) | (u << 2) | k)
-    for (lvl, u, k) in [(0, 0, 0), (3, 12345, 2), (7, 10**9, 3)]:
-        z = oracle.splitmix64(3, 1 + ((lvl << 44) | (u << 2) | k))
+    # U[-1, 1) from the top 53 bits of SplitMix64 output 1 + ((level << 44) | (u << 4) | k)
+    for (lvl, u, k) in [(0, 0, 0), (3, 12345, 2), (7, 10**9, 3), (2, 777, 15)]:
+        z = oracle.splitmix64(3, 1 + ((lvl << 44) | (u << 4) | k))
         expect = 2.0 * ((z >> 11) / 2.0**53) - 1.0
         v = oracle.random_start(3, lvl, u, k)
         assert v == expect and -1.0 <= v < 1.0
