@@ -92,7 +92,7 @@ typedef struct lamg_options {
                               level from the mean row length; 1, 2, 4, ..., 32 forces it */
     int32_t sell;          /* operator kernels: 0 (default) one thread per row on a sliced
                               ELLPACK copy (32-row slices) where rows have at most 64 entries and
-                              padding adds at most 30%, else lane groups on CSR; 1 sliced ELLPACK
+                              padding adds at most 50%, else lane groups on CSR; 1 sliced ELLPACK
                               wherever rows have at most 64 entries; -1 CSR only */
     int32_t autotune;      /* 1: setup times the kernel form of each level's sweep and residual
                               (lanes per row, or one thread per row) and, with cluster_rows = 0,
@@ -106,8 +106,23 @@ typedef struct lamg_options {
     int32_t cheb_degree;   /* degree of the Jacobi-preconditioned Chebyshev polynomial (interval
                               [lambda/30, lambda], lambda the Gershgorin bound of D^-1 A) that
                               replaces one sweep: 2 (1..8) */
-    int32_t reserved[3];
+    int32_t tv_order;      /* summation order of a test-vector row sum (Section 2 relaxation):
+                              LAMG_TV_STRIDED (default) or LAMG_TV_STORED, see below */
+    int32_t reserved[2];
 } lamg_options;                    /* 144 bytes */
+
+/* Test-vector row sums (lamg_options.tv_order, lamg_testvectors, lamg_testvectors_noalloc).
+ * The relaxation x_u <- -(sum_v A_uv x_v) / A_uu is written with the neighbour sum in stored
+ * order; the test vectors feed integer aggregation decisions, so the order matters bit for bit.
+ *  LAMG_TV_STORED:  every row summed in stored order, one dependent FP64 chain per row: the
+ *                   plain definition, bit-identical to the reference evaluation of Section 2.
+ *  LAMG_TV_STRIDED: rows of at most 32 entries as above; a longer row (hubs of power-law
+ *                   graphs, dense Galerkin rows) as 32 strided partial sums (partial j: entries
+ *                   j, j + 32, ... in order, each from 0.0) added in order of j, one warp per
+ *                   row. Same values up to rounding; a hub row's dependent chain is 32 times
+ *                   shorter, which is what keeps setup of power-law graphs fast on this GPU. */
+#define LAMG_TV_STRIDED 0
+#define LAMG_TV_STORED 1
 
 typedef struct lamg_graph {
     int64_t n;
@@ -148,6 +163,10 @@ typedef struct lamg_solve_opts {
     int32_t maxit;         /* outer CG iteration cap */
     uint32_t flags;        /* LAMG_DEVICE_PTRS */
     void *stream;          /* cudaStream_t for device-pointer calls, or 0 */
+    int32_t wait_us;       /* limit of each device-side wait (the grid barriers of the
+                              LAMG_PERSISTENT kernel): 0 = 2 s; > 0 = this many microseconds;
+                              < 0 = give up at once (every wait runs out: LAMG_ERR_TIMEOUT) */
+    int32_t pad;
 } lamg_solve_opts;
 
 typedef struct lamg_stats {
@@ -218,13 +237,15 @@ int lamg_level_get(const lamg_hier *h, int32_t level, const char *name, void *ds
 void lamg_destroy(lamg_hier *h);
 
 /* Setup kernel K9 on its own (test vectors, Section 2): for a level operator given by host
- * arrays (off-diagonal CSR rp/ci/val + diag, natural order) and a colouring, start each of
- * K columns at the SplitMix64 value of (seed, level, node, column) and run nu colour-ordered
- * GS sweeps on A x = 0 on the GPU. X (host, n x K row-major) receives the result.
- * Errors: INVALID, OOM, CUDA, NO_DEVICE. */
+ * arrays (off-diagonal CSR rp/ci/val + diag, natural order) and a colouring (colour[u] >= 0;
+ * rows of one colour pairwise non-adjacent), start each of K <= 16 columns at U[-1, 1) from
+ * SplitMix64 output 1 + ((level << 44) | (u << 4) | k) of the stream `seed` and run nu
+ * colour-ordered GS sweeps on A x = 0 (colours ascending) on the GPU, row sums in `order`
+ * (LAMG_TV_STRIDED or LAMG_TV_STORED). X (host, n x K row-major) receives the result.
+ * Errors: INVALID (sizes, K, order, a negative colour), OOM, CUDA, NO_DEVICE. */
 int lamg_testvectors(int64_t n, const int64_t *rp, const int32_t *ci, const double *val,
                      const double *diag, const int32_t *colour, int32_t level, uint64_t seed,
-                     int32_t K, int32_t nu, double *X);
+                     int32_t K, int32_t nu, double *X, int32_t order);
 
 /* Setup kernel K10 on its own (Eq. 3 affinity and Eq. 9 veto) on the GPU for host inputs:
  * aff[e] = affinity of off-diagonal entry e, strong[e] = 1 iff |A_e| >= tau * max |A_ut| over
@@ -241,21 +262,38 @@ int lamg_affinity(int64_t n, const int64_t *rp, const int32_t *ci, const double 
  * The kernels run on the hierarchy's current vectors. Errors: INVALID, OOM, CUDA, TIMEOUT. */
 int lamg_time_kernel(lamg_hier *h, int32_t which, int32_t level, int32_t reps, double *out);
 
-/* Allocation-free variant of lamg_testvectors for callers that cannot allocate device memory
- * (no counterpart in the paper: it is a deployment form of the same setup kernel). All
- * pointers are DEVICE pointers owned by the caller: rp[n+1] (int64), ci, val, diag, colour[n]
- * (values 0..ncol-1; rows of one colour pairwise non-adjacent) and the output X (n x K,
+/* Time one k-column kernel of the multi-right-hand-side solve in isolation (roofline figures
+ * of lamg_solve_batch, in the hierarchy's cycle precision): `reps` launches on the hierarchy's
+ * stream, each after a 256 MB device write that evicts the L2, timed with CUDA events. which: 0
+ * residual at an aggregation level, 1 one smoothing sweep at an aggregation level (all colour
+ * classes of Gauss-Seidel, or the degree-m Chebyshev polynomial on levels with many colours),
+ * 2 the outer CG product A p with its dot products (level 0, FP64). 1 <= k <= 32.
+ * out[0] = mean device ms per launch sequence, out[1] = its algorithmic DRAM bytes (operator once,
+ * each vector once per column), out[2] = kernels per sequence, out[3] = its algorithmic flops (a
+ * multiply-add per stored entry and column, plus per-row arithmetic). No counterpart in the
+ * paper. Errors: INVALID, OOM, CUDA, TIMEOUT. */
+int lamg_time_kernel_batch(lamg_hier *h, int32_t which, int32_t level, int32_t k, int32_t reps,
+                           double *out);
+
+/* Allocation-free variant of lamg_testvectors for callers that cannot allocate device memory:
+ * code running inside another framework's memory pool or a plugin that may only use the memory
+ * handed to it, and programs that must not allocate after start-up. No counterpart in the
+ * paper: it is a deployment form of the same setup kernel. All pointers are DEVICE pointers
+ * owned by the caller: rp[n+1] (int64), ci, val, diag, colour[n] and the output X (n x K,
  * row-major). The work is queued on `stream` (a cudaStream_t, 0 for the default stream) and
- * the call returns without waiting. X is bit-identical to lamg_testvectors on the same input.
- * Scratch (rows grouped by colour) lives in a fixed 8 MiB __device__ array held by every GPU
- * that loads the library until exit: n <= 2^21 and ncol <= 1024, else LAMG_ERR_INVALID. The
- * first call on a device looks up the array's device address and should come before any
- * stream capture on that device. Calls share the array; calls that overlap on the GPU race
- * and must be serialised by the caller. No device memory is allocated.
+ * the call returns without waiting. For colours in [0, ncol) (rows of one colour pairwise
+ * non-adjacent) X is bit-identical to lamg_testvectors with the same `order`; a row whose colour
+ * is outside [0, ncol) is never relaxed and keeps its random start.
+ * Scratch (rows grouped by colour class, the class offsets) lives in a fixed 8 MiB __device__
+ * array held by every GPU that loads the library until exit: n <= 2^21 and ncol <= 1024, else
+ * LAMG_ERR_INVALID. The first call on a device looks up the array's device address and should
+ * come before any stream capture on that device. Calls share the array; calls that overlap on
+ * the GPU race and must be serialised by the caller. No device memory is allocated.
  * Errors: INVALID, CUDA. */
 int lamg_testvectors_noalloc(int64_t n, const int64_t *rp, const int32_t *ci, const double *val,
                              const double *diag, const int32_t *colour, int32_t ncol, int32_t level,
-                             uint64_t seed, int32_t K, int32_t nu, double *X, void *stream);
+                             uint64_t seed, int32_t K, int32_t nu, double *X, void *stream,
+                             int32_t order);
 
 /* Per-step timing of one cycle of the persistent solve kernel (r = 0): out receives up to cap
  * pairs (next step index, nanoseconds since the previous pair), one per grid barrier, read

@@ -65,6 +65,7 @@ def lib():
         L.oracle_stationary.argtypes = [P, P, P, C.c_double, C.c_int64, C.c_int, P, P]
         L.oracle_visit_counts.argtypes = [P, P]
         L.oracle_set_gamma.argtypes = [P, C.c_int, C.c_double]
+        L.oracle_testvectors.argtypes = [C.c_int64, P, P, P, P, C.c_int, C.c_uint64, C.c_int, C.c_int, P]
         L.oracle_aggregate.restype = C.c_int64
         L.oracle_aggregate.argtypes = [C.c_int64, P, P, P, P, P, C.c_int, P, P, C.c_double, C.c_double, P]
         L.oracle_splitmix64.restype = C.c_uint64
@@ -205,6 +206,13 @@ def pinv(A: Matrix) -> np.ndarray:
     if rc:
         raise ValueError("operator is not connected")
     return out
+
+
+def testvectors(A: Matrix, level: int, seed: int = 3, K: int = 4, nu: int = 3) -> np.ndarray:
+    """K test vectors of a level operator (greedy colour order, Section 2): n x K."""
+    X = np.zeros((A.n, K))
+    lib().oracle_testvectors(*A.args(), level, seed, K, nu, _p(X))
+    return X
 
 
 def aggregate(A: Matrix, X, aff, strong, Q: float = 2.5, guard_eps: float = 1e-10):

@@ -1283,6 +1283,21 @@ void oracle_cheb_apply(int64_t n, const int64_t *rp, const int32_t *ci, const do
     }
 }
 
+/* K test vectors (Section 2) of a caller operator in the oracle's greedy colour order: X (n x K)
+ * receives nu sweeps on A x = 0 from the random start of (seed, level). */
+void oracle_testvectors(int64_t n, const int64_t *rp, const int32_t *ci, const double *val,
+                        const double *diag, int level, uint64_t seed, int K, int nu, double *X) {
+    Level L; memset(&L, 0, sizeof(L));
+    L.A.n = n; L.A.nnz = rp[n]; L.A.rp = (int64_t *)rp; L.A.ci = (int32_t *)ci;
+    L.A.val = (double *)val; L.A.diag = (double *)diag;
+    colour_level(&L);
+    Opts o; memset(&o, 0, sizeof(o));
+    o.K = K; o.nu_tv = nu; o.seed = seed;
+    test_vectors(&L, &o, level);
+    memcpy(X, L.X, n * K * sizeof(double));
+    free(L.X); free(L.colour); free(L.cptr); free(L.corder);
+}
+
 /* Caliber-1 aggregation (Section 2) on caller data: operator, K test vectors (n x K), the
  * affinity and strong flag of every off-diagonal entry; seed_of (n) receives the seed node of
  * each node's aggregate. Returns the number of aggregates. */

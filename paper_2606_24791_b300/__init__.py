@@ -40,7 +40,7 @@ class Options(C.Structure):
                 ("elim_min_frac", C.c_double), ("snap", C.c_double), ("guard_eps", C.c_double),
                 ("gamma_fixed", C.c_double), ("device", C.c_int32), ("tail_rows", C.c_int32),
                 ("cluster_rows", C.c_int32), ("row_tpr", C.c_int32), ("sell", C.c_int32), ("autotune", C.c_int32), ("dense_rows", C.c_int32), ("cheb_colours", C.c_int32), ("cheb_degree", C.c_int32),
-                ("reserved", C.c_int32 * 3)]
+                ("tv_order", C.c_int32), ("reserved", C.c_int32 * 2)]
 
 
 class Graph(C.Structure):
@@ -57,7 +57,7 @@ class LevelDesc(C.Structure):
 
 class SolveOpts(C.Structure):
     _fields_ = [("tol", C.c_double), ("maxit", C.c_int32), ("flags", C.c_uint32),
-                ("stream", C.c_void_p)]
+                ("stream", C.c_void_p), ("wait_us", C.c_int32), ("pad", C.c_int32)]
 
 
 class Stats(C.Structure):
@@ -102,12 +102,13 @@ def lib():
         L.lamg_destroy.argtypes = [P]
         L.lamg_destroy.restype = None
         L.lamg_testvectors.argtypes = [C.c_int64, P, P, P, P, P, C.c_int32, C.c_uint64, C.c_int32,
-                                       C.c_int32, P]
+                                       C.c_int32, P, C.c_int32]
         L.lamg_affinity.argtypes = [C.c_int64, P, P, P, P, C.c_int32, C.c_double, P, P]
         L.lamg_time_kernel.argtypes = [P, C.c_int32, C.c_int32, C.c_int32, P]
+        L.lamg_time_kernel_batch.argtypes = [P, C.c_int32, C.c_int32, C.c_int32, C.c_int32, P]
         L.lamg_profile_cycle.argtypes = [P, P, C.c_int64, C.POINTER(C.c_int64)]
         L.lamg_testvectors_noalloc.argtypes = [C.c_int64, P, P, P, P, P, C.c_int32, C.c_int32, C.c_uint64,
-                                               C.c_int32, C.c_int32, P, P]
+                                               C.c_int32, C.c_int32, P, P, C.c_int32]
         L.lamg_server_create.argtypes = [C.POINTER(ServerOpts), C.POINTER(Options), C.POINTER(P)]
         L.lamg_serve.argtypes = [P, C.POINTER(Graph), P, C.POINTER(C.c_int64)]
         L.lamg_serve_poll.argtypes = [P, C.c_int64, C.POINTER(TicketInfo), P]
@@ -198,14 +199,15 @@ class Hierarchy:
         return out
 
     def solve(self, b, tol: float = 1e-8, maxit: int = 100, allow_unconverged: bool = False,
-              persistent: bool = False):
-        """Host-pointer solve; returns (phi, stats dict with the residual history)."""
+              persistent: bool = False, wait_us: int = 0):
+        """Host-pointer solve; returns (phi, stats dict with the residual history). wait_us: limit
+        of each device-side wait (0: the library's 2 s; < 0: every wait gives up at once)."""
         b = _c(b, np.float64)
         if b.shape != (self.n,):
             raise ValueError("b has the wrong shape")
         phi = np.zeros(self.n)
         hist = np.zeros(maxit + 1)
-        so = SolveOpts(tol, maxit, PERSISTENT if persistent else 0, None)
+        so = SolveOpts(tol, maxit, PERSISTENT if persistent else 0, None, wait_us)
         st = Stats()
         st.hist = hist.ctypes.data
         rc = lib().lamg_solve(self._h, _p(b), _p(phi), C.byref(so), C.byref(st))
@@ -273,6 +275,18 @@ class Hierarchy:
                "lamg_time_kernel")
         return dict(ms=float(out[0]), bytes=float(out[1]), launches=int(out[2]),
                     gbs=float(out[1]) / (float(out[0]) * 1e-3) / 1e9)
+
+    BATCH_KERNELS = {"resid": 0, "sweep": 1, "spmv_dot": 2}
+
+    def time_kernel_batch(self, which: str, level: int, k: int, reps: int = 5) -> dict:
+        """Cold-L2 device time of one k-column kernel sequence (``BATCH_KERNELS``), its
+        algorithmic bytes and flops."""
+        out = np.zeros(4)
+        _check(lib().lamg_time_kernel_batch(self._h, self.BATCH_KERNELS[which], level, k, reps, _p(out)),
+               "lamg_time_kernel_batch")
+        ms = float(out[0])
+        return dict(ms=ms, bytes=float(out[1]), launches=int(out[2]), flops=float(out[3]),
+                    gbs=float(out[1]) / (ms * 1e-3) / 1e9, tflops=float(out[3]) / (ms * 1e-3) / 1e12)
 
     OP_KINDS = ["gs_first", "gs", "zero", "resid", "restrict", "prolong", "elim_restrict",
                 "elim_interp", "coarse", "cheb", "cheb_copy"]
@@ -454,23 +468,29 @@ def import_levels(levels: list, **opts) -> Hierarchy:
     return Hierarchy(h, keep)
 
 
-def testvectors(rp, ci, val, diag, colour, level: int, seed: int, K: int = 4, nu: int = 3):
+TV_STRIDED, TV_STORED = 0, 1
+
+
+def testvectors(rp, ci, val, diag, colour, level: int, seed: int, K: int = 4, nu: int = 3,
+                order: int = TV_STRIDED):
     rp, ci = _c(rp, np.int64), _c(ci, np.int32)
     val, diag, colour = _c(val, np.float64), _c(diag, np.float64), _c(colour, np.int32)
     n = len(diag)
     X = np.zeros((n, K))
     _check(lib().lamg_testvectors(n, _p(rp), _p(ci), _p(val), _p(diag), _p(colour), level, seed, K,
-                                  nu, _p(X)), "lamg_testvectors")
+                                  nu, _p(X), order), "lamg_testvectors")
     return X
 
 
 def testvectors_noalloc(n: int, rp_ptr: int, ci_ptr: int, val_ptr: int, diag_ptr: int, colour_ptr: int,
-                        ncol: int, level: int, seed: int, K: int, nu: int, X_ptr: int, stream: int = 0):
+                        ncol: int, level: int, seed: int, K: int, nu: int, X_ptr: int, stream: int = 0,
+                        order: int = TV_STRIDED):
     """lamg_testvectors_noalloc on caller-owned device memory (raw device pointers); queued on
     `stream`, returns without waiting. For callers that cannot allocate device memory."""
     _check(lib().lamg_testvectors_noalloc(n, C.c_void_p(rp_ptr), C.c_void_p(ci_ptr), C.c_void_p(val_ptr),
                                           C.c_void_p(diag_ptr), C.c_void_p(colour_ptr), ncol, level, seed,
-                                          K, nu, C.c_void_p(X_ptr), C.c_void_p(stream) if stream else None),
+                                          K, nu, C.c_void_p(X_ptr), C.c_void_p(stream) if stream else None,
+                                          order),
            "lamg_testvectors_noalloc")
 
 
@@ -484,7 +504,7 @@ def affinity(rp, ci, val, X, tau: float = 0.05):
     return aff, strong
 
 
-EXPORTS = ["lamg_options_default", "lamg_setup", "lamg_import", "lamg_solve", "lamg_solve_batch",
+EXPORTS = ["lamg_time_kernel_batch", "lamg_options_default", "lamg_setup", "lamg_import", "lamg_solve", "lamg_solve_batch",
            "lamg_cycle", "lamg_hier_info", "lamg_level_get", "lamg_destroy", "lamg_testvectors",
            "lamg_affinity", "lamg_strerror", "lamg_server_create", "lamg_serve", "lamg_serve_poll",
            "lamg_server_drain", "lamg_server_destroy", "lamg_time_kernel"]

@@ -430,11 +430,12 @@ __global__ void bk_elim_interp(int nc, int nF, int k, const int32_t *__restrict_
     x[e] = s + b[e] / d;
 }
 
-// Coarsest level against the projected pseudo-inverse in the cycle's type (FP64, or an FP32 copy
-// for the FP32 cycle, whose dense n^2 k products would otherwise run at the FP64 rate): one warp
-// per row, KL lanes per column times 32/KL lanes splitting the row.
+// Coarsest level: x = (I - J/n) A^+ b against the FP64 projected pseudo-inverse, accumulated in
+// FP64 for either cycle type (an FP32 cycle's right-hand side is widened, the FP64 sum rounded
+// to FP32 once at the end): one warp per row, KL lanes per column times 32/KL lanes splitting the
+// row.
 template <typename T, int KL>
-__global__ void __launch_bounds__(BBS) bk_coarse(int n, int k, const T *__restrict__ pinv,
+__global__ void __launch_bounds__(BBS) bk_coarse(int n, int k, const double *__restrict__ pinv,
                                                  const T *__restrict__ b, T *x) {
     b_trigger();
     b_wait();
@@ -443,10 +444,10 @@ __global__ void __launch_bounds__(BBS) bk_coarse(int n, int k, const T *__restri
     const int j = lane % KL, sub = lane / KL;
     const int wg = (blockIdx.x * BBS + threadIdx.x) >> 5, nwarps = (gridDim.x * BBS) >> 5;
     for (int i = wg; i < n; i += nwarps) {
-        const T *row = pinv + (size_t)i * n;
-        T s = T(0);
+        const double *row = pinv + (size_t)i * n;
+        double s = 0.0;
         if (j < k)
-            for (int m = sub; m < n; m += TPR) s += row[m] * b[(size_t)m * k + j];
+            for (int m = sub; m < n; m += TPR) s += row[m] * (double)b[(size_t)m * k + j];
 #pragma unroll
         for (int o = KL; o < 32; o <<= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
         if (sub == 0 && j < k) x[(size_t)i * k + j] = (T)s;
@@ -687,8 +688,12 @@ __global__ void __launch_bounds__(BBS) bk_true_resid(int n, int k, const int32_t
 
 // ------------------------------------------------------------------ launch helpers
 
+// kernels launched (or captured) by this thread through blaunch / blaunch_bs
+static thread_local int64_t t_blaunches = 0;
+
 template <typename... KArgs, typename... Args>
 static void blaunch(void (*kernel)(KArgs...), int64_t grid, cudaStream_t s, Args... args) {
+    t_blaunches++;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)(grid < 1 ? 1 : grid));
     cfg.blockDim = dim3(BBS);
@@ -703,6 +708,7 @@ static void blaunch(void (*kernel)(KArgs...), int64_t grid, cudaStream_t s, Args
 
 template <typename... KArgs, typename... Args>
 static void blaunch_bs(void (*kernel)(KArgs...), int64_t grid, unsigned bs, cudaStream_t s, Args... args) {
+    t_blaunches++;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)(grid < 1 ? 1 : grid));
     cfg.blockDim = dim3(bs);
@@ -774,7 +780,7 @@ struct BLev {
                   *pt_row = nullptr, *pf_col = nullptr, *pft_ptr = nullptr, *pft_f = nullptr;
     const void *val = nullptr, *diag = nullptr, *wt = nullptr, *pt_w = nullptr, *pf_val = nullptr,
                *dF = nullptr, *pft_val = nullptr;
-    const void *pinv = nullptr;  // coarsest (I - J/n) A^+ in the cycle's type
+    const double *pinv = nullptr;  // coarsest (I - J/n) A^+, FP64 for either cycle type
     void *x = nullptr, *b = nullptr, *r = nullptr;
 };
 
@@ -787,6 +793,7 @@ struct BatchCtx {
     BRed red{};
     double *h_sk = nullptr;  // pinned: B_COUNT x KMAX scalars + KMAX done flags
     cudaGraphExec_t g_tail = nullptr, g_head = nullptr;
+    int64_t n_tail = 0, n_head = 0;   // kernels in each captured graph
 };
 
 void batch_free(BatchCtx *b) {
@@ -829,7 +836,7 @@ static int build_ctx(lamg_hier *h, BatchCtx *c) {
         if (D.sell && (rc = typed_copy<T>(h, D.sl_val, D.sell_nnz, &B.sl_val))) return rc;
         B.rp = D.rp; B.ci = D.ci; B.agg = D.agg; B.agg2 = D.agg2; B.pt_ptr = D.pt_ptr; B.pt_row = D.pt_row;
         B.pf_col = D.pf_col; B.pft_ptr = D.pft_ptr; B.pft_f = D.pft_f;
-        if ((rc = typed_copy<T>(h, D.pinv, D.kind == KIND_COARSEST ? D.n * D.n : 0, &B.pinv))) return rc;
+        B.pinv = D.kind == KIND_COARSEST ? D.pinv : nullptr;
         const int64_t pte = (D.kind == KIND_AGG) ? (int64_t)h->host[l].A.n * 2 : 0;
         int32_t ent = 0;
         if (D.kind == KIND_AGG) {
@@ -987,7 +994,7 @@ static void bop(const Op &op, BatchCtx *c, cudaStream_t s, const Op *start) {
             break;
         }
         case OP_COARSE:
-#define C8(KLv, ...) case KLv: blaunch(bk_coarse<T, KLv>, rblocks((int64_t)n * 32), s, n, k, (const T *)L.pinv, (const T *)b, x); break;
+#define C8(KLv, ...) case KLv: blaunch(bk_coarse<T, KLv>, rblocks((int64_t)n * 32), s, n, k, L.pinv, (const T *)b, x); break;
             switch (KL) { K_CASES(C8) }
 #undef C8
             break;
@@ -1072,12 +1079,14 @@ static int capture_ctx(lamg_hier *h, BatchCtx *c) {
     for (int which = 0; which < 2; which++) {
         cudaGraph_t g = nullptr;
         CKR(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+        const int64_t l0 = t_blaunches;
         if (which == 0) {
             if (c->prec == LAMG_FP32) cg_tail<float>(h, c, cs);
             else cg_tail<double>(h, c, cs);
         } else {
             cg_head(h, c, cs);
         }
+        (which == 0 ? c->n_tail : c->n_head) = t_blaunches - l0;
         cudaError_t e = cudaStreamEndCapture(cs, &g);
         if (e != cudaSuccess) return cuda_status(e);
         e = cudaGraphInstantiate(which == 0 ? &c->g_tail : &c->g_head, g, 0);
@@ -1179,13 +1188,105 @@ int solve_batch_impl(lamg_hier *h, int k, const double *B, double *PHI, const la
             st[j].solve_ms = ms;
             st[j].kernel_ms = kms;
             st[j].alg_bytes = ((double)cycles * cyc + (double)it * per_it + once) / k;  // this column's share
-            st[j].launches = 0;
+            st[j].launches = 3 + (int64_t)cycles * c->n_tail + (int64_t)it * (c->n_head + 1);
         }
     }
     return all_done ? LAMG_OK : LAMG_ERR_NOT_CONVERGED;
 }
 
+// Cold-L2 device time of one k-column kernel of the cycle or the outer CG (lamg_time_kernel_batch):
+// which 0 residual at an aggregation level, 1 one smoothing sweep at an aggregation level (every
+// colour class of Gauss-Seidel, or the cheb_degree steps of the Chebyshev polynomial), 2 the outer
+// CG product q = A p with its dots (level 0, FP64). Algorithmic bytes count each operator array
+// once, each vector once per column (a gathered vector at most once per launch); flops count one
+// multiply-add (2 flops) per stored entry and column plus the per-row arithmetic.
+template <typename T>
+static int time_batch(lamg_hier *h, BatchCtx *c, int which, int level, int reps, double *out) {
+    const DevLevel &D = h->dev[level];
+    BLev &L = c->lv[level];
+    const double n = (double)D.n, z = (double)D.nnz, k = (double)c->k, sz = (double)sizeof(T);
+    std::vector<Op> seq;
+    double bytes = 0.0, flops = 0.0;
+    if (which == 0) {
+        seq.push_back({OP_RESID, level, 0});
+        bytes = (4 + sz) * z + 4 * (n + 1) + sz * n + k * sz * 3 * n;
+        flops = k * (2 * z + 4 * n);
+    } else if (which == 1 && D.cheb) {
+        const int m = h->opt.cheb_degree;
+        for (int q = 0; q < m; q++) {
+            seq.push_back({OP_CHEB, level, q});
+            bytes += (4 + sz) * z + 4 * (n + 1) + 2 * sz * n + k * sz * ((q ? 5 : 4) * n);
+            flops += k * (2 * z + (q ? 9 : 7) * n);
+        }
+        if (m & 1) {
+            seq.push_back({OP_CHEB_COPY, level, 0});
+            bytes += k * sz * 2 * n;
+        }
+    } else if (which == 1) {
+        std::vector<int32_t> rp(D.n + 1);
+        CKR(cudaMemcpy(rp.data(), D.rp, (D.n + 1) * sizeof(int32_t), cudaMemcpyDeviceToHost));
+        for (int col = 0; col < D.ncol; col++) {
+            const int64_t r0 = D.cptr[col], r1 = D.cptr[col + 1];
+            const double R = (double)(r1 - r0), zc = (double)(rp[r1] - rp[r0]);
+            seq.push_back({OP_GS, level, col});
+            bytes += (4 + sz) * zc + 4 * (R + 1) + sz * R + k * sz * (2 * R + std::min(zc, n));
+            flops += k * (2 * zc + 2 * R);
+        }
+    } else if (which == 2) {
+        bytes = 12 * z + 4 * (n + 1) + 8 * n + k * 8 * 2 * n;
+        flops = k * (2 * z + 4 * n);
+    } else {
+        return LAMG_ERR_INVALID;
+    }
+    cudaStream_t s = h->stream;
+    const size_t flush_bytes = (size_t)256 << 20;
+    void *flush = nullptr;
+    CKR(cudaMalloc(&flush, flush_bytes));
+    double total = 0.0;
+    int rc = LAMG_OK;
+    int64_t launches = 0;
+    for (int r = 0; r < reps && !rc; r++) {
+        cudaMemsetAsync(flush, r & 0xff, flush_bytes, s);
+        cudaEventRecord(h->ev_a, s);
+        const int64_t l0 = t_blaunches;
+        if (which == 2) cg_spmv_dot(h, c, s);
+        else for (const Op &op : seq) bop<T>(op, c, s, nullptr);
+        launches = t_blaunches - l0;
+        cudaEventRecord(h->ev_b, s);
+        rc = wait_event(h, h->ev_b);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, h->ev_a, h->ev_b);
+        total += ms;
+    }
+    (void)L;
+    cudaFree(flush);
+    if (rc) return rc;
+    CKR(cudaGetLastError());
+    out[0] = total / reps;
+    out[1] = bytes;
+    out[2] = (double)launches;
+    out[3] = flops;
+    return LAMG_OK;
+}
+
 }  // namespace lamg
+
+extern "C" int lamg_time_kernel_batch(lamg_hier *h, int32_t which, int32_t level, int32_t k, int32_t reps,
+                                      double *out) {
+    using namespace lamg;
+    if (!h || !out || reps < 1 || k < 1 || k > KMAX || level < 0 || level >= (int32_t)h->dev.size())
+        return LAMG_ERR_INVALID;
+    if ((which == 0 || which == 1) && h->dev[level].kind != KIND_AGG) return LAMG_ERR_INVALID;
+    if (which == 2 && level != 0) return LAMG_ERR_INVALID;
+    if (which < 0 || which > 2) return LAMG_ERR_INVALID;
+    CKR(cudaSetDevice(h->device));
+    const int prec = h->opt.precision == LAMG_FP32 ? LAMG_FP32 : LAMG_FP64;
+    BatchCtx *c = nullptr;
+    int rc = get_ctx(h, k, prec, &c);
+    if (rc) return rc;
+    return prec == LAMG_FP32 ? time_batch<float>(h, c, which, level, reps, out)
+                             : time_batch<double>(h, c, which, level, reps, out);
+}
 
 extern "C" int lamg_solve_batch(lamg_hier *h, int32_t k, const double *B, double *PHI, const lamg_solve_opts *so,
                                 lamg_stats *st) {

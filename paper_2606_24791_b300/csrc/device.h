@@ -137,13 +137,16 @@ struct PSolve {
     GridBar *bar;
     double *scal;                 // S_COUNT outputs
     double *hist;                 // relres per iteration
+    unsigned long long wait_ns;   // limit of one grid-barrier wait (set per launch)
 };
 
 size_t persistent_smem(int nlev, int nops, int ncptr);
 int persistent_grid(int device, size_t smem);
+constexpr unsigned long long WAIT_NS_DEFAULT = 2000000000ULL;   // 2 s
 cudaError_t launch_persistent(const PSolve *P, int grid, size_t smem, int mode, int maxit, double tol,
                               const double *b_in, double *phi_out, cudaStream_t s,
-                              unsigned long long *prof = nullptr);
+                              unsigned long long *prof = nullptr,
+                              unsigned long long wait_ns = WAIT_NS_DEFAULT);
 
 // A whole solve run by one thread-block cluster (lamg_solve_many): device pointers of one
 // hierarchy and its right-hand side.

@@ -87,7 +87,7 @@ double cycle_index(int64_t El, int64_t El1, int64_t E0);
 // the affinity / veto pass. All pointers are host pointers; the functions manage device
 // copies themselves. X is n x K row-major.
 int gpu_testvectors(const HostMat &A, const std::vector<int32_t> &colour, int level,
-                    uint64_t seed, int K, int nu, double *X);
+                    uint64_t seed, int K, int nu, double *X, int order);
 int gpu_affinity(const HostMat &A, const double *X, int K, double tau, double *aff,
                  uint8_t *strong);
 // ... and the guard of Eq. 4 per entry (adm[e]: strong and energy ratio <= Q), from the
@@ -114,7 +114,7 @@ int gpu_schur(const HostMat &A, const std::vector<uint8_t> &inF, const std::vect
 int gpu_validate_entries(const lamg_graph *g, bool *valid);
 int gpu_tv_and_affinity(const HostMat &A, const std::vector<int32_t> &colour, int level,
                         uint64_t seed, int K, int nu, double tau, int veto, double *X,
-                        double *aff, uint8_t *strong, double Q, double eps, uint8_t *adm);
+                        double *aff, uint8_t *strong, double Q, double eps, uint8_t *adm, int order);
 
 int cuda_status(cudaError_t e);
 

@@ -12,8 +12,9 @@
 // The level table, the colour-class offsets and the step list are copied into shared memory
 // at kernel start, so a step starts without a global-memory round trip.
 //
-// Each barrier wait is bounded: a CTA that waits longer than about two seconds marks the
-// barrier as failed and every CTA returns; the host then reports LAMG_ERR_TIMEOUT.
+// Each barrier wait is bounded: a CTA that waits longer than the solve's limit (2 s unless the
+// caller sets lamg_solve_opts.wait_us; %globaltimer nanoseconds) marks the barrier as failed and
+// every CTA returns at its next barrier; the host then reports LAMG_ERR_TIMEOUT.
 //
 // CG scalars (alpha, beta, r.z, ||r||) are replicated: every CTA adds the same per-block
 // partials in the same order, so every CTA holds bit-identical scalars and takes the same
@@ -32,7 +33,6 @@
 namespace lamg {
 
 constexpr int PBS = 512;
-constexpr long long BARRIER_LIMIT_CYCLES = 4000000000LL;  // ~2 s at 2 GHz
 
 __device__ __forceinline__ unsigned ld_relaxed(const unsigned *p) {
     unsigned v;
@@ -50,8 +50,15 @@ __device__ __forceinline__ unsigned atom_add_acq_rel(unsigned *p, unsigned v) {
     return old;
 }
 
-// Grid barrier (all CTAs co-resident by cooperative launch). Returns false on failure.
-__device__ __forceinline__ bool gsync(GridBar *bar, unsigned &gen) {
+__device__ __forceinline__ unsigned long long timer_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Grid barrier (all CTAs co-resident by cooperative launch). Returns false on failure: this
+// CTA waited longer than wait_ns, or another CTA's wait ran out.
+__device__ __forceinline__ bool gsync(GridBar *bar, unsigned &gen, unsigned long long wait_ns) {
     __shared__ int fail;
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -63,9 +70,9 @@ __device__ __forceinline__ bool gsync(GridBar *bar, unsigned &gen) {
             releaser = true;
         }
         if (!releaser) {
-            const long long t0 = clock64();
+            const unsigned long long t0 = timer_ns();
             while (ld_relaxed(&bar->gen) == gen) {
-                if (clock64() - t0 > BARRIER_LIMIT_CYCLES) {
+                if (timer_ns() - t0 >= wait_ns) {
                     atomicExch(&bar->err, 1u);
                     f = 1;
                     break;
@@ -92,7 +99,7 @@ __device__ __forceinline__ bool allreduce(double (&v)[NV], const PSolve &P, unsi
 #pragma unroll
         for (int k = 0; k < NV; k++) buf[k * gridDim.x + blockIdx.x] = v[k];
     }
-    if (!gsync(P.bar, gen)) return false;
+    if (!gsync(P.bar, gen, P.wait_ns)) return false;
 #pragma unroll
     for (int k = 0; k < NV; k++) {
         double s = 0.0;
@@ -304,7 +311,7 @@ __device__ __forceinline__ bool p_cycle(const PSolve &P, const Tables &T, unsign
             if (op.kind == OP_RESID) continue;
             p_op(op, T, grid);
         }
-        if (!gsync(P.bar, gen)) return false;
+        if (!gsync(P.bar, gen, P.wait_ns)) return false;
         if (prof && blockIdx.x == 0 && threadIdx.x == 0) {
             nrec++;
             prof[2 * nrec] = (unsigned long long)i;   // steps up to (not including) op i are done
@@ -387,17 +394,21 @@ __device__ __forceinline__ bool p_cg_tail(const PSolve &P, const Tables &T, unsi
         P.p[i] = zi + beta * P.p[i];
         P.zold[i] = zi;
     }
-    return gsync(P.bar, gen);
+    return gsync(P.bar, gen, P.wait_ns);
 }
 
 // mode 0: full solve of L phi = b_in (natural order) into phi_out.
 // mode 1: one preconditioner application z = M r (r = b_in, natural order), projected.
 __global__ void __launch_bounds__(PBS, 2) k_persistent(const PSolve *__restrict__ Pg, int mode, int maxit,
                                                        double tol, const double *__restrict__ b_in,
-                                                       double *phi_out, unsigned long long *prof) {
+                                                       double *phi_out, unsigned long long *prof,
+                                                       unsigned long long wait_ns) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ PSolve sP;
-    if (threadIdx.x == 0) sP = *Pg;
+    if (threadIdx.x == 0) {
+        sP = *Pg;
+        sP.wait_ns = wait_ns;
+    }
     __syncthreads();
     const PSolve &P = sP;
     // tables into shared memory
@@ -516,9 +527,10 @@ int persistent_grid(int device, size_t smem) {
 }
 
 cudaError_t launch_persistent(const PSolve *P, int grid, size_t smem, int mode, int maxit, double tol,
-                              const double *b_in, double *phi_out, cudaStream_t s, unsigned long long *prof) {
+                              const double *b_in, double *phi_out, cudaStream_t s, unsigned long long *prof,
+                              unsigned long long wait_ns) {
     void *args[] = {(void *)&P,    (void *)&mode,    (void *)&maxit, (void *)&tol,
-                    (void *)&b_in, (void *)&phi_out, (void *)&prof};
+                    (void *)&b_in, (void *)&phi_out, (void *)&prof,  (void *)&wait_ns};
     return cudaLaunchCooperativeKernel((const void *)k_persistent, dim3(grid), dim3(PBS), args, smem, s);
 }
 

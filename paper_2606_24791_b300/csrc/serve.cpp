@@ -346,6 +346,11 @@ struct lamg_server {
         for (Request *r : fresh) r->phase = 6;
         if (e != cudaSuccess) {
             cudaGetLastError();
+            // copies already queued on gstream may still read the requests' device inputs and
+            // pinned buffers: let them finish before those are released (phase 4 frees them)
+            cudaStreamSynchronize(gstream);
+            cudaGetLastError();
+            if (g.d_desc) cudaFreeAsync(g.d_desc, gstream);
             for (Request *r : fresh) { r->status = cuda_status(e); r->phase = 4; }
             if (g.ev) cudaEventDestroy(g.ev);
             pins.put(g.pin_out);

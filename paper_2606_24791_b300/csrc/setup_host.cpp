@@ -690,7 +690,7 @@ int build_hierarchy(const lamg_graph *g, const lamg_options &o, std::vector<Host
     };
     int rc = validate_graph(g);
     if (rc) return rc;
-    if (o.K < 1 || o.K > 16 || o.nu_tv < 0 || o.coarsest_max < 0 || o.max_levels < 1 || o.dense_rows < 0 ||
+    if (o.K < 1 || o.K > 16 || o.nu_tv < 0 || (o.tv_order != LAMG_TV_STRIDED && o.tv_order != LAMG_TV_STORED) || o.coarsest_max < 0 || o.max_levels < 1 || o.dense_rows < 0 ||
         o.dense_rows > 4096 || o.cheb_colours < 0 || (o.cheb_colours > 0 && (o.cheb_degree < 1 || o.cheb_degree > 8)))
         return LAMG_ERR_INVALID;
     levels.clear();
@@ -735,7 +735,7 @@ int build_hierarchy(const lamg_graph *g, const lamg_options &o, std::vector<Host
             L.adm.resize(L.A.nnz());
             rc = gpu_tv_and_affinity(L.A, L.colour, l, o.seed, o.K, o.nu_tv, o.tau_soc, o.veto,
                                      L.X.data(), L.aff.data(), L.strong.data(), o.Q, o.guard_eps,
-                                     L.adm.data());
+                                     L.adm.data(), o.tv_order);
             if (rc) return rc;
             lap(SETUP_TV_AFFINITY);
             std::vector<int32_t> status, seed;

@@ -34,10 +34,10 @@ int cuda_status(cudaError_t e) {
 
 // SplitMix64 (Steele, Lea and Flood 2014): state advanced by 0x9e3779b97f4a7c15, each state
 // mixed by two xor-shift-multiply rounds; output i of the stream from `seed` is
-// mix(seed + i * increment). The test-vector start of column k at node u of level `lvl` is
-// output 1 + ((lvl << 44) | (u << 2) | k) mapped to [-1, 1) through its top 53 bits.
+// mix(seed + i * increment). The test-vector start of column k (< 16) at node u of level `lvl`
+// is output 1 + ((lvl << 44) | (u << 4) | k) mapped to [-1, 1) through its top 53 bits.
 __device__ __forceinline__ double random_start(uint64_t seed, int lvl, int64_t u, int k) {
-    uint64_t c = ((uint64_t)lvl << 44) | ((uint64_t)u << 2) | (uint64_t)k;
+    uint64_t c = ((uint64_t)lvl << 44) | ((uint64_t)u << 4) | (uint64_t)k;
     uint64_t z = seed + (c + 1) * 0x9e3779b97f4a7c15ULL;
     z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ULL;
     z = (z ^ (z >> 27)) * 0x94d049bb133111ebULL;
@@ -54,9 +54,9 @@ __global__ void k_tv_start(int64_t n, int K, uint64_t seed, int lvl, double *X) 
 
 // One Gauss-Seidel colour class on A X = 0 for all K columns: X_u <- -(sum_v A_uv X_v) / A_uu.
 // Rows of one colour are pairwise non-adjacent, so they update independently. The neighbour sum
-// of a row of at most TV_STRIDE entries runs in stored order (one thread per row, these
-// kernels); a longer row is summed as TV_STRIDE strided partial sums added in order (one warp
-// per row, k_tv_long), the same order as the oracle's, which the paper leaves open.
+// runs in stored order (one thread per row, these kernels) for every row with LAMG_TV_STORED and
+// for rows of at most TV_STRIDE entries with LAMG_TV_STRIDED; with LAMG_TV_STRIDED a longer row
+// is summed as TV_STRIDE strided partial sums added in order (one warp per row, k_tv_long).
 constexpr int TV_STRIDE = 32;
 template <int K>
 __global__ void k_tv_colour(int64_t cnt, const int32_t *__restrict__ rows,
@@ -397,7 +397,7 @@ static inline unsigned nblk(int64_t work, int bs) { return (unsigned)((work + bs
 static int run_setup_kernels(const HostMat &A, const std::vector<int32_t> *colour, int level,
                              uint64_t seed, int K, int nu, double tau, int veto, double *X,
                              const double *Xin, double *aff, uint8_t *strong, double Q = 0.0,
-                             double eps = 0.0, uint8_t *adm = nullptr) {
+                             double eps = 0.0, uint8_t *adm = nullptr, int order = LAMG_TV_STRIDED) {
     int rc = LAMG_OK;
     const int64_t n = A.n, z = A.nnz();
     int64_t *d_rp = nullptr;
@@ -420,21 +420,23 @@ static int run_setup_kernels(const HostMat &A, const std::vector<int32_t> *colou
     if (z) CK(cudaMemcpyAsync(d_val, A.val.data(), z * sizeof(double), cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(d_diag, A.diag.data(), n * sizeof(double), cudaMemcpyHostToDevice, st));
     if (colour) {
-        // rows grouped by colour; within a colour the rows of at most TV_STRIDE entries, then
-        // the longer ones (from lptr[c]), each group ascending
+        // rows grouped by colour; within a colour the rows summed in stored order, then (with
+        // LAMG_TV_STRIDED) the rows of more than TV_STRIDE entries (from lptr[c]), each group
+        // ascending
+        auto short_row = [&](int64_t u) { return order == LAMG_TV_STORED || A.rp[u + 1] - A.rp[u] <= TV_STRIDE; };
         for (int32_t c : *colour) ncol = std::max(ncol, c + 1);
         cptr.assign(ncol + 1, 0);
         lptr.assign(ncol, 0);
         for (int32_t c : *colour) cptr[c + 1]++;
         for (int c = 0; c < ncol; c++) cptr[c + 1] += cptr[c];
         for (int64_t u = 0; u < n; u++)
-            if (A.rp[u + 1] - A.rp[u] <= TV_STRIDE) lptr[(*colour)[u]]++;
+            if (short_row(u)) lptr[(*colour)[u]]++;
         for (int c = 0; c < ncol; c++) lptr[c] += cptr[c];
         rows.resize(n);
         std::vector<int64_t> fill(cptr.begin(), cptr.end() - 1), lfill(lptr);
         for (int64_t u = 0; u < n; u++) {
             const int32_t c = (*colour)[u];
-            if (A.rp[u + 1] - A.rp[u] <= TV_STRIDE) rows[fill[c]++] = (int32_t)u;
+            if (short_row(u)) rows[fill[c]++] = (int32_t)u;
             else rows[lfill[c]++] = (int32_t)u;
         }
         CK(cudaMallocAsync((void **)&d_rows, n * sizeof(int32_t), st));
@@ -700,8 +702,9 @@ out:
 }
 
 int gpu_testvectors(const HostMat &A, const std::vector<int32_t> &colour, int level,
-                    uint64_t seed, int K, int nu, double *X) {
-    return run_setup_kernels(A, &colour, level, seed, K, nu, 0.0, 1, X, nullptr, nullptr, nullptr);
+                    uint64_t seed, int K, int nu, double *X, int order) {
+    return run_setup_kernels(A, &colour, level, seed, K, nu, 0.0, 1, X, nullptr, nullptr, nullptr, 0.0, 0.0,
+                             nullptr, order);
 }
 
 int gpu_affinity(const HostMat &A, const double *X, int K, double tau, double *aff,
@@ -711,8 +714,9 @@ int gpu_affinity(const HostMat &A, const double *X, int K, double tau, double *a
 
 int gpu_tv_and_affinity(const HostMat &A, const std::vector<int32_t> &colour, int level,
                         uint64_t seed, int K, int nu, double tau, int veto, double *X,
-                        double *aff, uint8_t *strong, double Q, double eps, uint8_t *adm) {
-    return run_setup_kernels(A, &colour, level, seed, K, nu, tau, veto, X, nullptr, aff, strong, Q, eps, adm);
+                        double *aff, uint8_t *strong, double Q, double eps, uint8_t *adm, int order) {
+    return run_setup_kernels(A, &colour, level, seed, K, nu, tau, veto, X, nullptr, aff, strong, Q, eps, adm,
+                             order);
 }
 
 }  // namespace lamg

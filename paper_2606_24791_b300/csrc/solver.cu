@@ -793,6 +793,7 @@ void lamg_options_default(lamg_options *o) {
     o->dense_rows = 4096;
     o->cheb_colours = 32;
     o->cheb_degree = 2;
+    o->tv_order = LAMG_TV_STRIDED;
 }
 
 const char *lamg_strerror(int c) {
@@ -1007,7 +1008,9 @@ static int solve_persistent(lamg_hier *h, const double *b, double *phi, const la
     }
     CKR(cudaMemsetAsync(h->bar, 0, sizeof(GridBar), s));
     CKR(cudaEventRecord(h->ev_k0, s));
-    CKR(launch_persistent(h->psolve, h->grid, h->smem, 0, so->maxit, so->tol, b_in, phi_out, s));
+    const unsigned long long wait_ns = so->wait_us == 0 ? WAIT_NS_DEFAULT
+                                       : so->wait_us < 0 ? 0ULL : 1000ULL * (unsigned long long)so->wait_us;
+    CKR(launch_persistent(h->psolve, h->grid, h->smem, 0, so->maxit, so->tol, b_in, phi_out, s, nullptr, wait_ns));
     CKR(cudaEventRecord(h->ev_k1, s));
     if (!devp) CKR(cudaMemcpyAsync(phi, h->nat_out, n * sizeof(double), cudaMemcpyDeviceToHost, s));
     CKR(cudaMemcpyAsync(h->h_scal, h->red.scal, S_COUNT * sizeof(double), cudaMemcpyDeviceToHost, s));
@@ -1379,8 +1382,13 @@ int lamg_level_get(const lamg_hier *h, int32_t level, const char *name, void *ds
 }
 
 int lamg_testvectors(int64_t n, const int64_t *rp, const int32_t *ci, const double *val, const double *diag,
-                     const int32_t *colour, int32_t level, uint64_t seed, int32_t K, int32_t nu, double *X) {
-    if (n < 1 || !rp || !diag || !colour || !X || K < 1 || nu < 0) return LAMG_ERR_INVALID;
+                     const int32_t *colour, int32_t level, uint64_t seed, int32_t K, int32_t nu, double *X,
+                     int32_t order) {
+    if (n < 1 || !rp || !diag || !colour || !X || K < 1 || K > 16 || nu < 0 ||
+        (order != LAMG_TV_STRIDED && order != LAMG_TV_STORED))
+        return LAMG_ERR_INVALID;
+    for (int64_t u = 0; u < n; u++)
+        if (colour[u] < 0) return LAMG_ERR_INVALID;
     int rc = set_device(0);
     if (rc) return rc;
     HostMat A;
@@ -1390,7 +1398,7 @@ int lamg_testvectors(int64_t n, const int64_t *rp, const int32_t *ci, const doub
     A.val.assign(val, val + rp[n]);
     A.diag.assign(diag, diag + n);
     std::vector<int32_t> col(colour, colour + n);
-    return gpu_testvectors(A, col, level, seed, K, nu, X);
+    return gpu_testvectors(A, col, level, seed, K, nu, X, order);
 }
 
 int lamg_affinity(int64_t n, const int64_t *rp, const int32_t *ci, const double *val, const double *X,

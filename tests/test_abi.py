@@ -43,6 +43,8 @@ def test_options_defaults_are_the_papers():
     assert (o.K, o.nu_tv, o.dmax, o.nu_pre, o.nu_post) == (4, 3, 4, 1, 2)
     assert o.Q == 2.5 and o.tau_soc == 0.05 and o.veto == 1 and o.caliber2 == 1
     assert ctypes.sizeof(lamg.Options) == 144   # the layout include/lamg.h states
+    assert ctypes.sizeof(lamg.SolveOpts) == 32
+    assert o.tv_order == lamg.TV_STRIDED == 0 and lamg.TV_STORED == 1
     # the readings' defaults, as include/lamg.h documents them: coarsest size by rule (0), dense
     # small levels up to 4096 nodes, Chebyshev above 32 colours with degree 2, no timing trials,
     # and the oracle's defaults agree wherever both have the option

@@ -35,7 +35,7 @@ GRAPHS = {
 def gcase(request):
     make, cm = GRAPHS[request.param]
     g = make()
-    return request.param, g, cm, lamg.setup(g, coarsest_max=cm), oracle.Hierarchy(g, coarsest_max=cm)
+    return request.param, g, cm, lamg.setup(g, coarsest_max=cm, tv_order=lamg.TV_STORED), oracle.Hierarchy(g, coarsest_max=cm)
 
 
 @pytest.mark.parametrize("k", [1, 3, 16])
@@ -118,3 +118,32 @@ def test_fp32_batch_matches_fp32_single():
         assert sts[j]["relres_true"] <= 2e-8
         assert st1["iters"] == sts[j]["iters"]
         assert rel(X[:, j], x1) <= 1e-6
+
+
+@pytest.mark.parametrize("k", [1, 5])
+def test_fp32_cycle_coarsest_solve_is_fp64(k):
+    # The FP32 cycle keeps the coarsest-level solve in FP64: its right-hand side (the FP32
+    # residual) is widened, multiplied by the FP64 (I - J/n) A^+ with FP64 accumulation, and the
+    # sum rounded to FP32 once. On a graph that is its own coarsest level the first CG step is
+    # x = alpha z with z that rounded product (then projected); its direction must match the
+    # product computed here from the oracle's pseudo-inverse to FP32 rounding of each entry
+    # (FP32 accumulation over ~1000 terms would miss by far more).
+    g = gg.grid2d_random(36, 30, seed=6)
+    P = lamg.setup(g, precision=lamg.FP32, coarsest_max=2048)
+    assert P.nlevels == 1
+    Ap = oracle.pinv(oracle.laplacian(g))
+    B = gg.rhs(g, seed=9, k=k)
+    B = B[:, None] if k == 1 else B
+    if k == 1:
+        x, st = P.solve(B[:, 0], tol=1e-300, maxit=1, allow_unconverged=True)
+        X = x[:, None]
+    else:
+        X, _ = P.solve_batch(B, tol=1e-300, maxit=1, allow_unconverged=True)
+    for j in range(k):
+        b32 = (B[:, j] - B[:, j].mean()).astype(np.float32).astype(np.float64)
+        zj = (Ap - Ap.mean(axis=0, keepdims=True)) @ b32          # (I - J/n) A^+ in FP64
+        zj = zj.astype(np.float32).astype(np.float64)
+        zj -= zj.mean()
+        xj = X[:, j] * (zj @ X[:, j]) / (X[:, j] @ X[:, j])      # remove the step length alpha
+        assert np.abs(xj - zj).max() <= 2e-7 * np.abs(zj).max(), (k, j)
+    P.close()

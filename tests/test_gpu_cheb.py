@@ -55,7 +55,7 @@ def test_cheb_setup_matches_oracle_and_solves():
     g = gg.chung_lu(20000, 2.1, 16, seed=1)
     b = gg.rhs(g, 2)
     H = oracle.Hierarchy(g)
-    P = lamg.setup(g)
+    P = lamg.setup(g, tv_order=lamg.TV_STORED)   # the oracle's hierarchy
     assert [i["n"] for i in P.info] == [L["n"] for L in H.levels]
     assert sum(L["cheb"] for L in H.levels) >= 1
     x, st = P.solve(b, 1e-8, 200)

@@ -29,7 +29,7 @@ def small_graphs():
 def test_many_systems_match_oracle_and_single_solves():
     gs = small_graphs()
     bs = [gg.rhs(g, seed=30 + i) for i, g in enumerate(gs)]
-    hs = [lamg.setup(g) for g in gs]
+    hs = [lamg.setup(g, tv_order=lamg.TV_STORED) for g in gs]   # the oracle's hierarchies
     xs, sts = lamg.solve_many(hs, bs, tol=1e-8, maxit=200, hist=True)
     for g, b, h, x, st in zip(gs, bs, hs, xs, sts):
         assert st["launches"] == 1 and st["relres_true"] <= 2e-8, (g.name, st)
