@@ -1,16 +1,18 @@
 """Benchmark of the LAMG+ solve phase on B300 (one JSON line on stdout).
 
-Workload (N=1 line): the 1024 x 1024 grid-aligned anisotropic 5-point Laplacian (x-edges 1,
-y-edges 1e-3; n = 1,048,576, nnz(L) = n + 2m = 5,238,784), one mean-zero Gaussian right-hand
-side b = L x (seeds: graph 1, RHS 2, test vectors 3), FP64 cycle inside FP64 flexible CG, run to
-||b - L phi|| / ||b|| <= 1e-8.
+Workload (N=1 line): the Chung-Lu power-law graph of 4,000,000 nodes (expected degrees from a
+Pareto density with exponent 2.1, mean degree 16, capped at sqrt(sum); largest connected
+component: 3,902,576 nodes, nnz(L) = n + 2m = 67,055,822), weights U(0.5, 1.5], 32 mean-zero
+Gaussian right-hand sides b = L x (seeds: graph 1, RHS 2, test vectors 3), solved together in
+SpMM form: FP64 cycle inside FP64 flexible CG, every column to ||b - L phi|| / ||b|| <= 1e-8.
 
-A step is one complete solve (projection of b, CG with one cycle per iteration, final true
-residual) with b and phi resident in device memory; the hierarchy is set up once before the
-timed region. The metric is ns per nonzero of L per digit of residual reduction,
-t_solve / (nnz(L) * log10(||b|| / ||b - L phi||)); lower is better.
+A step is one complete 32-column solve (projection of b, CG with one cycle per iteration, final
+true residuals) with B and PHI resident in device memory; the hierarchy is set up once before the
+timed region. The metric is ns per nonzero of L per digit of residual reduction per right-hand
+side, t_solve / sum_j (nnz(L) * log10(||b_j|| / ||b_j - L phi_j||)); lower is better.
 
---impl reference times the CPU oracle (serial FP64 C) on the same workload and metric.
+--impl reference times the CPU oracle (serial FP64 C) on a bounded sample of the same family
+(a 250,000-node Chung-Lu graph of the same generator, one right-hand side per step).
 """
 from __future__ import annotations
 
@@ -31,31 +33,47 @@ import numpy as np  # noqa: E402
 
 METRIC = "ns/nnz/digit to 1e-8 residual"
 UNIT = "ns/nnz/digit"
-WORKLOAD = ("aniso1024: 2D 5-point grid 1024x1024, x-weight 1, y-weight 1e-3, one mean-zero "
-            "N(0,1) RHS b = L x, FP64 cycle in FP64 flexible CG, tol 1e-8")
+K_RHS = 32
+WORKLOAD = ("chunglu4m x 32 RHS: Chung-Lu power-law graph n=4,000,000 (Pareto exponent 2.1, mean "
+            "degree 16, largest connected component), weights U(0.5,1.5], 32 mean-zero N(0,1) RHS "
+            "b = L x solved together (SpMM-form cycles), FP64 cycle in FP64 flexible CG, tol 1e-8 per "
+            "column; metric per right-hand side")
+ANISO = ("aniso1024: 2D 5-point grid 1024x1024, x-weight 1, y-weight 1e-3, one mean-zero N(0,1) RHS "
+         "b = L x, FP64 cycle in FP64 flexible CG, tol 1e-8")
+SAMPLE_N = 250_000
 TOL = 1e-8
+FP64_PEAK_TFLOPS = 1.25   # nominal B300 FP64 rate: 148 SMs x 2.032 GHz x ~4.16 flop/clock/SM
 
 
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-variants", action="store_true", help="the main line only (no other forms)")
     ap.add_argument("--tail-rows", type=int, default=8192,
                     help="levels with at most this many rows run inside one CTA (persistent path)")
     ap.add_argument("--serve", action="store_true", help="run the serving workload instead")
     ap.add_argument("--profile-cycle", action="store_true",
-                    help="per-step timing of one persistent-kernel cycle of the workload")
-    ap.add_argument("--solve-once", action="store_true",
-                    help="set up the workload and run one solve, nothing else (for a launch-list capture)")
+                    help="per-step timing of one persistent-kernel cycle of the aniso1024 workload")
+    ap.add_argument("--solve-once", default=None, choices=["main", "main-fp32", "aniso1024"],
+                    help="set up the named workload and run one solve, nothing else (for a launch-list capture)")
     ap.add_argument("--serve-requests", type=int, default=200)
     ap.add_argument("--serve-max-n", type=int, default=200000)
     ap.add_argument("--serve-threads", type=int, default=8)
     ap.add_argument("--profile-sweep", type=int, default=-1, metavar="LEVEL",
-                    help="set up the workload, run one cold-L2 Gauss-Seidel sweep at LEVEL, exit "
-                         "(a target for ncu)")
+                    help="set up aniso1024, run one cold-L2 Gauss-Seidel sweep at LEVEL, exit (a target for ncu)")
+    ap.add_argument("--profile-kernels", default=None, choices=["single", "batch", "batch16", "setup"],
+                    help="run each kernel of one family a few times after an L2 flush, nothing else (a target "
+                         "for one-kernel ncu captures): single = the one-RHS cycle and CG kernels on aniso1024, "
+                         "batch = the 32-column kernels on a 500k-node Chung-Lu graph, batch16 = the 16-column "
+                         "Gauss-Seidel kernels on a 512^2 anisotropic grid, setup = the setup kernels on a "
+                         "200k-node Barabasi-Albert graph")
+    ap.add_argument("--profile-batch", default=None, metavar="N:LEVEL:WHICH",
+                    help="set up a Chung-Lu graph of N nodes, run one cold-L2 32-column kernel sequence "
+                         "(WHICH: sweep, resid, spmv_dot) at LEVEL, exit (a target for ncu)")
     return ap.parse_args()
 
 
@@ -129,10 +147,10 @@ def serve_bench(args):
 
 def profile_cycle():
     """Per-step device time of one cycle of the persistent kernel (%globaltimer at every grid
-    barrier), grouped by (step kind, level), for the workload's hierarchy."""
+    barrier), grouped by (step kind, level), for the aniso1024 hierarchy."""
     import collections
     import paper_2606_24791_b300 as lamg
-    g, b = workload()
+    g, b = aniso_workload()
     P = lamg.setup(g)
     ops = P.op_list()
     for _ in range(3):
@@ -157,29 +175,103 @@ def profile_cycle():
         "iterations": st["iters"]}))
 
 
-def solve_once():
-    """Setup and exactly one solve of the workload (device buffers): the launch list of a
+def solve_once(which: str):
+    """Setup and exactly one solve of the named workload (device buffers): the launch list of a
     profiler run over this process is the setup kernels followed by one solve."""
     import torch
     import paper_2606_24791_b300 as lamg
-    g, b = workload()
-    P = lamg.setup(g)
-    bt = torch.from_numpy(b).cuda()
-    xt = torch.zeros_like(bt)
-    st = P.solve_ptr(bt.data_ptr(), xt.data_ptr(), TOL, 200)
+    if which == "aniso1024":
+        g, b = aniso_workload()
+        P = lamg.setup(g)
+        bt = torch.from_numpy(b).cuda()
+        xt = torch.zeros_like(bt)
+        sts = [P.solve_ptr(bt.data_ptr(), xt.data_ptr(), TOL, 200)]
+    else:
+        g, B = workload()
+        P = lamg.setup(g, precision=lamg.FP32 if which == "main-fp32" else lamg.FP64)
+        bt = torch.from_numpy(B).cuda()
+        xt = torch.zeros_like(bt)
+        sts = P.solve_batch_ptr(K_RHS, bt.data_ptr(), xt.data_ptr(), TOL, 200)
     torch.cuda.synchronize()
-    print(json.dumps({"iterations": st["iters"], "relres_true": st["relres_true"], "launches": st["launches"]}))
+    print(json.dumps({"iterations": max(s["iters"] for s in sts), "relres_true": max(s["relres_true"] for s in sts),
+                      "launches": sts[0]["launches"]}))
 
 
 def profile_sweep(level: int):
     import paper_2606_24791_b300 as lamg
-    g, b = workload()
+    g, b = aniso_workload()
     P = lamg.setup(g)
     # fill the level vectors with a real cycle iterate through the persistent kernel, so that
     # the only k_gs launches of this process are the profiled sweep
     P.cycle(b - b.mean(), persistent=True)
     r = P.time_kernel("gs_sweep", level, reps=1)
     print(json.dumps({"level": level, "info": P.info[level], "sweep": r}))
+
+
+def profile_batch(spec: str):
+    """One cold-L2 32-column kernel sequence on a Chung-Lu graph of N nodes (the workload's
+    generator at a size whose device memory suits a full ncu capture)."""
+    import torch
+    import graphgen as gg
+    import paper_2606_24791_b300 as lamg
+    n, level, which = spec.split(":")
+    g = gg.chung_lu(int(n), 2.1, 16.0, seed=1)
+    B = gg.rhs(g, seed=2, k=K_RHS)
+    P = lamg.setup(g)
+    bt = torch.from_numpy(B).cuda()
+    xt = torch.zeros_like(bt)
+    P.solve_batch_ptr(K_RHS, bt.data_ptr(), xt.data_ptr(), TOL, 2)   # vectors hold a real iterate
+    torch.cuda.synchronize()
+    r = P.time_kernel_batch(which, int(level), K_RHS, reps=1)
+    print(json.dumps({"n": g.n, "nnz_L": g.nnz_L, "level": int(level), "info": P.info[int(level)], "which": which,
+                      "kernel": r}))
+
+
+def profile_kernels(family: str):
+    """Each kernel of a family run a few times from a cold L2 (lamg_time_kernel*), plus one cycle or
+    one iteration for the transfer kernels; prints what ran."""
+    import torch
+    import graphgen as gg
+    import paper_2606_24791_b300 as lamg
+    out = {"family": family}
+    if family == "single":
+        g, b = aniso_workload()
+        P = lamg.setup(g)
+        P.cycle(b - b.mean())
+        for which, lvl in (("resid", 1), ("resid", 2), ("gs_sweep", 1), ("gs_sweep", 2), ("spmv_dot", 0),
+                           ("restrict", 1), ("prolong", 1)):
+            if which != "spmv_dot" and P.info[lvl]["kind"] != "agg":
+                continue
+            out[f"{which}@L{lvl}"] = P.time_kernel(which, lvl, reps=2)
+        P.solve(b, TOL, 2, allow_unconverged=True)
+        out["levels"] = [(i["kind"], i["n"], i["nnz"]) for i in P.info]
+        out["forms"] = P.schedule()["forms"]
+    elif family in ("batch", "batch16"):
+        if family == "batch":
+            g = gg.chung_lu(500_000, 2.1, 16.0, seed=1)
+            k = K_RHS
+        else:
+            g = gg.grid2d(512, 512, 1.0, 1e-3)
+            k = 16
+        B = gg.rhs(g, seed=2, k=k)
+        P = lamg.setup(g)
+        bt = torch.from_numpy(B).cuda()
+        xt = torch.zeros_like(bt)
+        P.solve_batch_ptr(k, bt.data_ptr(), xt.data_ptr(), TOL, 2)
+        torch.cuda.synchronize()
+        for l, L in enumerate(P.info):
+            if L["kind"] == "agg" and L["n"] >= 50_000:
+                out[f"sweep@L{l}"] = P.time_kernel_batch("sweep", l, k, reps=2)
+                out[f"resid@L{l}"] = P.time_kernel_batch("resid", l, k, reps=2)
+        out["spmv_dot@L0"] = P.time_kernel_batch("spmv_dot", 0, k, reps=2)
+        out["levels"] = [(i["kind"], i["n"], i["nnz"], i["ncol"]) for i in P.info]
+    else:
+        g = gg.barabasi_albert(200_000, 4, seed=1)
+        P = lamg.setup(g)
+        out["levels"] = [(i["kind"], i["n"], i["nnz"], i["ncol"]) for i in P.info]
+        out["setup_ms"] = P.setup_times()
+    torch.cuda.synchronize()
+    print(json.dumps(out, default=str))
 
 
 def dist_env():
@@ -243,42 +335,58 @@ class ClockSampler:
 
 
 def workload():
+    """The N=1 workload: the 4M-node Chung-Lu graph and its 32 right-hand sides (n x 32)."""
+    import graphgen as gg
+    g = gg.config_graph("chunglu4m")
+    return g, gg.rhs(g, seed=2, k=K_RHS)
+
+
+def aniso_workload():
     import graphgen as gg
     g = gg.config_graph("aniso1024")
-    b = gg.rhs(g, 2)
-    return g, b
+    return g, gg.rhs(g, 2)
 
 
 def digits(relres: float) -> float:
     return -math.log10(max(relres, 1e-300))
 
 
-def cpu_baseline(g, b, reps: int = 3) -> dict:
-    """The oracle as it stands (serial FP64 C, one thread) on the same workload."""
+def oracle_sample(reps: int, warmup: int = 0) -> dict:
+    """The oracle as it stands (serial FP64 C, one thread) on a bounded sample of the workload's
+    family: a Chung-Lu graph of SAMPLE_N nodes from the same generator, one right-hand side,
+    `reps` timed FCG solves to 1e-8 after an untimed setup (and `warmup` untimed solves)."""
+    import graphgen as gg
     import oracle
+    g = gg.chung_lu(SAMPLE_N, 2.1, 16.0, seed=1)
+    b = gg.rhs(g, 2)
     t0 = time.perf_counter()
     H = oracle.Hierarchy(g)
     setup_s = time.perf_counter() - t0
+    for _ in range(warmup):
+        H.fcg(b, TOL, 200)
     times, units = 0.0, 0.0
     for _ in range(reps):
         t0 = time.perf_counter()
         out = H.fcg(b, TOL, 200)
-        dt = time.perf_counter() - t0
-        x = out["x"]
-        import graphgen as gg
-        r = gg.laplacian_apply(g, x) - (b - b.mean())
-        rel = np.linalg.norm(r) / np.linalg.norm(b - b.mean())
-        times += dt
-        units += g.nnz_L * digits(rel)
+        times += time.perf_counter() - t0
+        r = gg.laplacian_apply(g, out["x"]) - (b - b.mean())
+        units += g.nnz_L * digits(np.linalg.norm(r) / np.linalg.norm(b - b.mean()))
     return {"value": times * 1e9 / units, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{reps} full solves of the aniso1024 workload (FCG to 1e-8) after a "
-                      f"{setup_s:.1f} s untimed oracle setup; single-threaded C, gcc -O2",
-            "setup_s": setup_s}
+            "sample": f"Chung-Lu n={SAMPLE_N} from the workload's generator (largest component {g.n} "
+                      f"nodes, nnz(L) = {g.nnz_L}), one RHS, {reps} FCG solves to 1e-8 after a "
+                      f"{setup_s:.1f} s untimed oracle setup; ns/nnz/digit is per nonzero and digit, so "
+                      f"it compares with the 4M workload's per-RHS figure; single-threaded C, gcc -O2",
+            "setup_s": round(setup_s, 2), "ms_per_solve": round(times * 1e3 / max(reps, 1), 2),
+            "n": g.n, "nnz_L": g.nnz_L}
 
 
-# the source a kernel's counters depend on: its own definition and the device helpers it calls
-KERNEL_SOURCES = {"k_gs": ["struct RowPre {", "RowPre row_pre(", "double row_finish(", "double block_row(",
-                           "void __launch_bounds__(BS) k_gs("]}
+# the source a kernel's counters depend on: its file, its own definition and the device helpers
+# it calls
+KERNEL_SOURCES = {
+    "k_gs": ("cycle_kernels.cu", ["struct RowPre {", "RowPre row_pre(", "double row_finish(", "double block_row(",
+                                  "void __launch_bounds__(BS) k_gs("]),
+    "bk_cheb": ("batch.cu", ["T rowsum_k(", "T block_row_k(", "__global__ void __launch_bounds__(BBS) bk_cheb("]),
+}
 
 
 def _definition(src: str, signature: str) -> str:
@@ -297,13 +405,15 @@ def _definition(src: str, signature: str) -> str:
 
 
 def kernel_source_sha(kernel: str) -> str:
-    src = open(os.path.join(ROOT, "paper_2606_24791_b300", "csrc", "cycle_kernels.cu")).read()
-    text = "\n".join(_definition(src, sig) for sig in KERNEL_SOURCES[kernel])
+    fname, sigs = KERNEL_SOURCES[kernel]
+    src = open(os.path.join(ROOT, "paper_2606_24791_b300", "csrc", fname)).read()
+    text = "\n".join(_definition(src, sig) for sig in sigs)
     return hashlib.sha256(text.encode()).hexdigest()
 
 
-def traffic_for(kernel: str):
-    """ncu DRAM bytes per launch recorded for `kernel`, if the kernel's source is unchanged."""
+def traffic_for(kernel: str, units: float = 1.0):
+    """ncu DRAM bytes per roofline unit recorded for `kernel` (scaled by `units` when the record
+    is per unit of a smaller capture), if the kernel's source is unchanged."""
     path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     if not os.path.exists(path) or kernel not in KERNEL_SOURCES:
         return None
@@ -311,6 +421,8 @@ def traffic_for(kernel: str):
     k = rec.get("kernels", {}).get(kernel)
     if not k or k.get("source_sha256") != kernel_source_sha(kernel):
         return None
+    if "dram_bytes_per_unit" in k:
+        return k["dram_bytes_per_unit"] * units
     return k.get("dram_bytes")
 
 
@@ -350,12 +462,36 @@ def combine_ranks(total_ms: float, units: float, device="cpu"):
     return float(tmax[0]), float(tsum[0])
 
 
+def timed_batch(P, Bt, Xt, k, stream, flush, reps, warm=1):
+    """Device-timed k-column solves (cold L2): per-solve ms, stats of the last solve, and the sum of
+    digits over the timed solves' columns."""
+    import torch
+    ms, units, sts = [], 0.0, None
+    for rep in range(warm + reps):
+        flush.fill_(rep & 0xff)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        if k == 1:
+            sts = [P.solve_ptr(Bt.data_ptr(), Xt.data_ptr(), TOL, 200, stream=stream.cuda_stream)]
+        else:
+            sts = P.solve_batch_ptr(k, Bt.data_ptr(), Xt.data_ptr(), TOL, 200, stream=stream.cuda_stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if rep >= warm:
+            ms.append(e0.elapsed_time(e1))
+            units += sum(digits(s_["relres_true"]) for s_ in sts)
+    return ms, sts, units
+
+
 def run_ours(args, ws, rank, local):
     import torch
+    import graphgen as gg
     import paper_2606_24791_b300 as lamg
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    g, b = workload()
+    t0 = time.perf_counter()
+    g, B = workload()
+    gen_s = time.perf_counter() - t0
     t0 = time.perf_counter()
     P = lamg.setup(g, device=local, tail_rows=args.tail_rows)
     setup_s = time.perf_counter() - t0
@@ -363,12 +499,12 @@ def run_ours(args, ws, rank, local):
     # interval covers exactly the work between its two events
     stream = torch.cuda.Stream(dev)
     torch.cuda.set_stream(stream)
-    bt = torch.from_numpy(b).to(dev)
-    xt = torch.zeros_like(bt)
+    Bt = torch.from_numpy(B).to(dev)
+    Xt = torch.zeros_like(Bt)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
 
     def solve():
-        return P.solve_ptr(bt.data_ptr(), xt.data_ptr(), TOL, 200, stream=stream.cuda_stream)
+        return P.solve_batch_ptr(K_RHS, Bt.data_ptr(), Xt.data_ptr(), TOL, 200, stream=stream.cuda_stream)
 
     for _ in range(max(args.warmup, 0)):
         flush.fill_(1)
@@ -395,142 +531,184 @@ def run_ours(args, ws, rank, local):
     clocks = sampler.stop()
     step_ms = [a.elapsed_time(bb) for a, bb in ev]
     total_ms = float(sum(step_ms))
-    units = float(sum(g.nnz_L * digits(s["relres_true"]) for s in stats))
-    iters = [s["iters"] for s in stats]
+    units = float(sum(g.nnz_L * digits(c["relres_true"]) for sts in stats for c in sts))
+    iters = [max(c["iters"] for c in sts) for sts in stats]
+    worst = max(c["relres_true"] for sts in stats for c in sts)
+    launches = int(sum(sts[0]["launches"] for sts in stats))
+    kern_ms = [sts[0]["kernel_ms"] for sts in stats]
+    alg_bytes = [sum(c["alg_bytes"] for c in sts) for sts in stats]
+    X64 = Xt.cpu().numpy()
 
-    # kernels launched in the timed region (the persistent solve kernel: one per solve)
-    launches = int(sum(s["launches"] for s in stats))
-    kern_ms = [s["kernel_ms"] for s in stats]
-    alg_bytes = [s["alg_bytes"] for s in stats]
-
-    # e2e: the same solve through the C ABI with host buffers (H2D of b, D2H of phi inside the
-    # timed interval), right after the device-timed steps, one untimed call first, the L2
-    # flushed before each call (outside the interval) as for the device steps
-    P.solve(b, TOL, 200)
+    # e2e: the same solves through the C ABI with host buffers (H2D of B, D2H of PHI inside the
+    # timed interval), right after the device-timed steps, one untimed call first, the L2 flushed
+    # before each call (outside the interval) as for the device steps
+    P.solve_batch(B, TOL, 200)
     e2e_t, e2e_units = 0.0, 0.0
-    for i in range(max(3, args.steps)):
+    for i in range(max(2, min(args.steps, 3))):
         flush.fill_(i & 0xff)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        x, st = P.solve(b, TOL, 200)
+        Xh, sth = P.solve_batch(B, TOL, 200)
         e2e_t += time.perf_counter() - t0
-        e2e_units += g.nnz_L * digits(st["relres_true"])
+        e2e_units += sum(g.nnz_L * digits(c["relres_true"]) for c in sth)
 
-    # the same solves as one persistent cooperative kernel, for comparison
-    graph_ms = []
-    for _ in range(3):
-        flush.fill_(7)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        P.solve_ptr(bt.data_ptr(), xt.data_ptr(), TOL, 200, stream=stream.cuda_stream, persistent=True)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        graph_ms.append(e0.elapsed_time(e1))
-
-
-    # roofline of the dominant kernel: cold-L2 timing of each candidate, weighted by how often
-    # a solve runs it
+    # roofline of the dominant kernel: cold-L2 time of each candidate sequence alone, weighted by
+    # how often a solve runs it; per level the same figures (the levels table)
     visits = schedule_counts(P, iters[0])
-    cand = []
-    it0 = iters[0]
+    o = lamg.options()
+    nsweeps = o.nu_pre + o.nu_post
+    cand, levels = [], []
+    cheb_levels = {lv for kind, lv, _ in P.op_list() if kind == "cheb"}
     for l, L in enumerate(P.info):
-        if L["kind"] != "agg" or L["n"] < 100_000:
+        if L["kind"] != "agg":
             continue
-        for k, per_cycle in (("gs_sweep", 3 * visits[l]), ("resid", visits[l])):
-            r = P.time_kernel(k, l, reps=10)
-            cand.append((r["ms"] * per_cycle * it0, f"{k}@L{l}", r))
-    r = P.time_kernel("spmv_dot", 0, reps=10)
-    cand.append((r["ms"] * it0, "spmv_dot@L0", r))
+        sw = P.time_kernel_batch("sweep", l, K_RHS, reps=3)
+        rs = P.time_kernel_batch("resid", l, K_RHS, reps=3)
+        smoother = "chebyshev" if l in cheb_levels else "gauss-seidel"
+        op_bytes = 12 * L["nnz"] + 20 * L["n"]
+        vec_bytes = 3 * 8 * K_RHS * L["n"]
+        levels.append({"level": l, "n": L["n"], "nnz": L["nnz"], "colours": L["ncol"], "smoother": smoother,
+                       "visits_per_cycle": visits[l],
+                       "sweep_ms": round(sw["ms"], 4), "sweep_tflops": round(sw["tflops"], 3),
+                       "sweep_gbs": round(sw["gbs"], 1), "resid_ms": round(rs["ms"], 4),
+                       "resid_tflops": round(rs["tflops"], 3), "resid_gbs": round(rs["gbs"], 1),
+                       "l2_resident": op_bytes + vec_bytes <= 126e6})
+        cand.append((sw["ms"] * nsweeps * visits[l] * iters[0], f"sweep@L{l}", sw, smoother))
+        cand.append((rs["ms"] * visits[l] * iters[0], f"resid@L{l}", rs, "residual"))
+    sp = P.time_kernel_batch("spmv_dot", 0, K_RHS, reps=3)
+    cand.append((sp["ms"] * iters[0], "spmv_dot@L0", sp, "outer CG product"))
     cand.sort(key=lambda t: -t[0])
     peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
         os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
-    peak = peaks.get("hbm_gbs", 6400.0)
-    # dominant kernel: the candidate with the largest estimated share of a solve (cold-L2 time
-    # alone x launches per solve); timed alone, so compared with the burst copy peak
-    _, dom_name, dom = cand[0]
-    kname = {"gs_sweep": "k_gs", "resid": "k_resid", "spmv_dot": "k_spmv_dot"}[dom_name.split("@")[0]]
-    roofline = {"bound": "hbm", "kernel": f"{kname} ({dom_name}: " +
-                ("one full colour-ordered sweep, all colour classes)" if kname == "k_gs" else "one launch)"),
-                "achieved": round(dom["gbs"], 1), "peak": peak, "unit": "GB/s",
-                "frac": round(dom["gbs"] / peak, 4), "traffic": traffic_for(kname),
-                "algorithmic_bytes": dom["bytes"], "launch_ms": round(dom["ms"], 5),
-                "launches_per_unit": dom["launches"],
-                "peak_source": "MEASURED_PEAKS.json hbm_gbs (burst copy), of measured" if peaks
-                else "fallback 6400 GB/s"}
-    # the whole solve: algorithmic bytes of every step / device time of the solve
+    hbm_peak = peaks.get("hbm_gbs", 6400.0)
+    share_ms, dom_name, dom, dom_kind = cand[0]
+    kname = {"chebyshev": "bk_cheb", "gauss-seidel": "bk_gs", "residual": "bk_resid",
+             "outer CG product": "bk_spmv_dot"}[dom_kind]
+    roofline = {"bound": "alu", "kernel": f"{kname}<double,32,1> ({dom_name}: {dom['launches']} launches, "
+                f"32 columns, {dom_kind})", "achieved": round(dom["tflops"], 4), "peak": FP64_PEAK_TFLOPS,
+                "unit": "TFLOP/s", "frac": round(dom["tflops"] / FP64_PEAK_TFLOPS, 4),
+                "traffic": traffic_for(kname, dom["flops"]),
+                "algorithmic_flops": dom["flops"], "algorithmic_bytes": dom["bytes"],
+                "launch_ms": round(dom["ms"], 5), "launches_per_unit": dom["launches"],
+                "estimated_share_of_solve": round(share_ms / float(np.mean(step_ms)), 3),
+                "peak_source": "nominal B300 FP64 rate (148 SMs x 2.032 GHz x ~4.16 flop/clock/SM); FP64 "
+                               "multiply-adds bound the 32-column kernels",
+                "hbm_view": {"achieved_gbs": round(dom["gbs"], 1), "peak_gbs": hbm_peak,
+                             "frac": round(dom["gbs"] / hbm_peak, 4),
+                             "peak_source": "MEASURED_PEAKS.json hbm_gbs (burst copy), of measured"}}
     ach = float(np.mean([bb / (ms * 1e-3) / 1e9 for bb, ms in zip(alg_bytes, kern_ms)]))
-    solve_roofline = {"achieved": round(ach, 1), "peak": peak, "unit": "GB/s", "frac": round(ach / peak, 4),
+    solve_roofline = {"achieved": round(ach, 1), "peak": hbm_peak, "unit": "GB/s", "frac": round(ach / hbm_peak, 4),
                       "algorithmic_bytes": float(np.mean(alg_bytes)), "ms": float(np.mean(kern_ms))}
-    kernels = {name + " (per-step kernel, cold L2, alone)": {"gbs": round(rr["gbs"], 1), "ms": round(rr["ms"], 4)}
-               for _, name, rr in cand}
-    kernels["persistent_path_ms_per_solve"] = round(float(np.median(graph_ms)), 3)
-    kernels["graph_path_launches_per_solve"] = launches // max(args.steps, 1)
-    kernels["schedule"] = P.schedule()
-    # the same solve with every cycle step its own kernel (no cluster sub-cycle)
-    Pq = lamg.setup(g, device=local, cluster_rows=-1)
-    qms = []
-    for _ in range(3):
-        flush.fill_(9)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        Pq.solve_ptr(bt.data_ptr(), xt.data_ptr(), TOL, 200, stream=stream.cuda_stream)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        qms.append(e0.elapsed_time(e1))
-    kernels["per_step_schedule_ms_per_solve"] = round(float(np.median(qms)), 3)
-    Pq.close()
+    kernels = {name: {"ms": round(rr["ms"], 4), "tflops": round(rr["tflops"], 3), "gbs": round(rr["gbs"], 1),
+                      "est_ms_per_solve": round(sh, 2)} for sh, name, rr, _ in cand}
+    kernels["launches_per_solve"] = launches // max(args.steps, 1)
+    P.close()
+    del Bt, Xt
 
-    # other forms of the same solve on the same workload (same metric, per right-hand side):
-    # FP32 cycle inside FP64 CG, and 16 right-hand sides per SpMM-form solve (FP64 / FP32 cycle)
     variants = {}
-    x64 = xt.cpu().numpy()
-    P32 = lamg.setup(g, device=local, precision=lamg.FP32)
-    for name, PP, k in (("fp32_cycle", P32, 1), ("batch16_fp64", P, 16), ("batch16_fp32_cycle", P32, 16)):
-        import graphgen as gg
-        # k independent mean-zero Gaussian right-hand sides b = L x (seed 2); k = 1 is the main b
-        Bk = torch.from_numpy(gg.rhs(g, seed=2, k=k) if k > 1 else b).to(dev)
-        Xk = torch.zeros_like(Bk)
-        ms, unit_sum, its, rts = [], 0.0, [], []
-        for rep in range(2 + 3):
-            flush.fill_(rep & 0xff)
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            if k == 1:
-                sts = [PP.solve_ptr(Bk.data_ptr(), Xk.data_ptr(), TOL, 200, stream=stream.cuda_stream)]
-            else:
-                sts = PP.solve_batch_ptr(k, Bk.data_ptr(), Xk.data_ptr(), TOL, 200, stream=stream.cuda_stream)
-            e1.record(stream)
-            torch.cuda.synchronize()
-            if rep >= 2:
-                ms.append(e0.elapsed_time(e1))
-                unit_sum += sum(g.nnz_L * digits(s["relres_true"]) for s in sts)
-                its.append(max(s["iters"] for s in sts))
-                rts.append(max(s["relres_true"] for s in sts))
-        v = {"value": round(float(np.sum(ms)) * 1e6 / unit_sum, 5), "unit": UNIT + " (per right-hand side)",
-             "rhs": k, "ms_per_solve": round(float(np.mean(ms)), 3), "iterations": its[-1],
-             "relres_true_max": max(rts),
-             "achieved_gbs": round(float(np.mean([s["alg_bytes"] for s in sts])) * k / (np.mean(ms) * 1e-3) / 1e9, 1)}
-        if k == 1:
-            v["rel_err_vs_fp64_solution"] = float(np.linalg.norm(Xk.cpu().numpy() - x64) / np.linalg.norm(x64))
-        variants[name] = v
-    P32.close()
+    if not args.no_variants:
+        variants.update(run_variants(g, B, X64, dev, stream, flush, local))
 
-    # the paper's own outer loop: stationary cycles with recombination of the last 4 iterates
-    # (host buffers; its convergence factor beside FCG's iteration count)
+    if ws > 1:
+        total_ms, units_all = combine_ranks(total_ms, units, dev)
+    else:
+        units_all = units
+    value = total_ms * 1e6 / units_all
+    out = {
+        "metric": METRIC, "value": round(value, 5), "unit": UNIT + " (per right-hand side)", "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(total_ms / args.steps, 3),
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n": g.n, "nnz_L": g.nnz_L, "rhs": K_RHS, "levels": len(P.info),
+                   "iterations": iters[0], "relres_true_max": worst,
+                   "digits_min": round(digits(worst), 3), "setup_s": round(setup_s, 2),
+                   "generation_s": round(gen_s, 1), "parallelism": f"replicas{ws}",
+                   "l2": "flushed between steps (256 MB write); the 32-column vectors alone exceed L2",
+                   "seeds": {"graph": 1, "rhs": 2, "test_vectors": 3},
+                   "hierarchy": [(i["kind"], i["n"], i["nnz"], i["ncol"]) for i in P.info]},
+        "e2e": {"value": round(e2e_t * 1e9 / e2e_units, 5), "unit": UNIT + " (per right-hand side)",
+                "h2d_bytes_per_step": 8 * g.n * K_RHS, "d2h_bytes_per_step": 8 * g.n * K_RHS + 128 * K_RHS},
+        "gpu_launches": launches,
+        "roofline": roofline,
+        "levels": levels,
+        "solve_roofline": solve_roofline,
+        "variants": variants,
+        "kernels": kernels,
+        "clocks": clocks,
+        "wall_s_timed": round(wall, 3),
+    }
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = oracle_sample(reps=3)
+    return out
+
+
+def run_variants(g, B, X64, dev, stream, flush, local) -> dict:
+    """Other forms of the solve, same metric (per right-hand side): the workload with the FP32
+    cycle inside FP64 CG (the precision the Chung-Lu configuration names), and the 1024^2
+    anisotropic grid (single RHS FP64 and FP32 cycle, 16 RHS), many small systems in one launch,
+    and the paper's own stationary loop."""
+    import torch
+    import graphgen as gg
+    import paper_2606_24791_b300 as lamg
+    variants = {}
+    t0 = time.perf_counter()
+    P32 = lamg.setup(g, device=local, precision=lamg.FP32)
+    s32 = time.perf_counter() - t0
+    Bt = torch.from_numpy(B).to(dev)
+    Xt = torch.zeros_like(Bt)
+    ms, sts, dsum = timed_batch(P32, Bt, Xt, K_RHS, stream, flush, reps=3)
+    X32 = Xt.cpu().numpy()
+    err = float(max(np.linalg.norm(X32[:, j] - X64[:, j]) / np.linalg.norm(X64[:, j]) for j in range(K_RHS)))
+    units = g.nnz_L * dsum
+    variants["chunglu4m_fp32_cycle"] = {
+        "value": round(float(np.sum(ms)) * 1e6 / units, 5), "unit": UNIT + " (per right-hand side)",
+        "rhs": K_RHS, "ms_per_solve": round(float(np.mean(ms)), 3), "iterations": max(c["iters"] for c in sts),
+        "relres_true_max": max(c["relres_true"] for c in sts), "setup_s": round(s32, 2),
+        "max_col_rel_err_vs_fp64_solution": err}
+    k32 = P32.time_kernel_batch("sweep", 2, K_RHS, reps=3) if P32.info[2]["kind"] == "agg" else None
+    if k32:
+        variants["chunglu4m_fp32_cycle"]["sweep_L2"] = {"ms": round(k32["ms"], 4), "gbs": round(k32["gbs"], 1),
+                                                       "tflops": round(k32["tflops"], 3)}
+    P32.close()
+    del Bt, Xt
+
+    ga, ba = aniso_workload()
+    Pa = lamg.setup(ga, device=local)
+    Pa32 = lamg.setup(ga, device=local, precision=lamg.FP32)
+    xa64 = None
+    for name, PP, k in (("aniso1024_fp64", Pa, 1), ("aniso1024_fp32_cycle", Pa32, 1),
+                        ("aniso1024_batch16_fp64", Pa, 16), ("aniso1024_batch16_fp32_cycle", Pa32, 16)):
+        Bk = torch.from_numpy(gg.rhs(ga, seed=2, k=k) if k > 1 else ba).to(dev)
+        Xk = torch.zeros_like(Bk)
+        ms, sts, dsum = timed_batch(PP, Bk, Xk, k, stream, flush, reps=3, warm=2)
+        units = ga.nnz_L * dsum
+        v = {"value": round(float(np.sum(ms)) * 1e6 / units, 5), "unit": UNIT + " (per right-hand side)",
+             "rhs": k, "ms_per_solve": round(float(np.mean(ms)), 3), "iterations": max(c["iters"] for c in sts),
+             "relres_true_max": max(c["relres_true"] for c in sts)}
+        if k == 1 and PP is Pa:
+            xa64 = Xk.cpu().numpy()
+            v["launches_per_solve"] = sts[0]["launches"]
+            # round 1's dominant kernel of this workload: one level-2 colour-ordered sweep
+            r = Pa.time_kernel("gs_sweep", 2, reps=10)
+            v["k_gs_sweep_L2"] = {"ms": round(r["ms"], 5), "gbs": round(r["gbs"], 1), "bytes": r["bytes"],
+                                  "traffic": traffic_for("k_gs")}
+        if k == 1 and PP is Pa32 and xa64 is not None:
+            v["rel_err_vs_fp64_solution"] = float(np.linalg.norm(Xk.cpu().numpy() - xa64) / np.linalg.norm(xa64))
+        variants[name] = v
     for _ in range(2):
-        xs_st, st_st = P.stationary(b, TOL, 200, kappa=4, allow_unconverged=True)
+        xs_st, st_st = Pa.stationary(ba, TOL, 200, kappa=4, allow_unconverged=True)
     h = np.asarray(st_st["hist"])
     kk = min(5, len(h) - 1)
-    variants["stationary_recombination_kappa4"] = {
-        "value": round(st_st["solve_ms"] * 1e6 / (g.nnz_L * digits(st_st["relres_true"])), 5),
+    variants["aniso1024_stationary_recombination_kappa4"] = {
+        "value": round(st_st["solve_ms"] * 1e6 / (ga.nnz_L * digits(st_st["relres_true"])), 5),
         "unit": UNIT + " (host buffers, copies included)", "cycles": st_st["iters"],
         "ms_per_solve": round(st_st["solve_ms"], 3), "relres_true": st_st["relres_true"],
         "acf_last5": round(float((h[-1] / h[-1 - kk]) ** (1.0 / kk)), 4) if kk > 0 else None}
+    Pa.close()
+    Pa32.close()
 
     # many small systems in one launch (one thread-block cluster per system): 64 systems shaped
     # like the 64x64 unit grid (seeded weights U(0.5,1.5], so each system has its own
     # hierarchy), against the same systems solved one after another
-    import graphgen as gg
     smalls = [gg.grid2d_random(64, 64, seed=100 + i) for i in range(64)]
     hs = [lamg.setup(gsm, device=local) for gsm in smalls]
     bsm = [gg.rhs(gsm, seed=2) for gsm in smalls]
@@ -555,66 +733,26 @@ def run_ours(args, ws, rank, local):
         "relres_true_max": max(x["relres_true"] for x in st_m)}
     for hh in hs:
         hh.close()
-
-    # whole-job value across ranks: max time over ranks / sum of units
-    if ws > 1:
-        total_ms, units_all = combine_ranks(total_ms, units, dev)
-    else:
-        units_all = units
-    value = total_ms * 1e6 / units_all
-    out = {
-        "metric": METRIC, "value": round(value, 5), "unit": UNIT, "n_gpus": ws, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": round(total_ms / args.steps, 4), "higher_is_better": False,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "n": g.n, "nnz_L": g.nnz_L, "levels": P.nlevels,
-                   "iterations": iters[0], "relres_true": stats[-1]["relres_true"],
-                   "digits": round(digits(stats[-1]["relres_true"]), 3), "setup_s": round(setup_s, 2),
-                   "parallelism": f"replicas{ws}", "l2": "flushed between steps (256 MB write)",
-                   "seeds": {"graph": 1, "rhs": 2, "test_vectors": 3}},
-        "e2e": {"value": round(e2e_t * 1e9 / e2e_units, 5), "unit": UNIT,
-                "h2d_bytes_per_step": 8 * g.n, "d2h_bytes_per_step": 8 * g.n + 128},
-        "gpu_launches": launches,
-        "roofline": roofline,
-        "solve_roofline": solve_roofline,
-        "variants": variants,
-        "kernels": kernels,
-        "clocks": clocks,
-        "wall_s_timed": round(wall, 3),
-    }
-    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        out["cpu_baseline"] = cpu_baseline(g, b)
-    P.close()
-    return out
+    return variants
 
 
 def run_reference(args, ws, rank):
-    """The oracle on the host cores, same workload and metric (rank 0 only)."""
+    """The oracle on the host cores (rank 0 only): one solve of the bounded sample per step."""
     if rank != 0:
         return None
-    import oracle
-    import graphgen as gg
-    g, b = workload()
-    H = oracle.Hierarchy(g)
-    for _ in range(max(args.warmup, 0)):
-        H.fcg(b, TOL, 200)
-    t_total, units = 0.0, 0.0
     t0w = time.perf_counter()
-    for _ in range(args.steps):
-        t0 = time.perf_counter()
-        out = H.fcg(b, TOL, 200)
-        t_total += time.perf_counter() - t0
-        r = gg.laplacian_apply(g, out["x"]) - (b - b.mean())
-        units += g.nnz_L * digits(np.linalg.norm(r) / np.linalg.norm(b - b.mean()))
-    value = t_total * 1e9 / units
+    cb = oracle_sample(reps=args.steps, warmup=max(args.warmup, 0))
+    value = cb["value"]
+    cb["value"] = round(value, 4)
     return {
-        "impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": UNIT,
+        "impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": UNIT + " (per right-hand side)",
         "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": round(t_total * 1e3 / args.steps, 2), "higher_is_better": False,
+        "ms_per_step": cb["ms_per_solve"], "higher_is_better": False,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "n": g.n, "nnz_L": g.nnz_L},
-        "cpu_baseline": {"value": round(value, 4), "unit": UNIT, "kind": "oracle", "cores": 1,
-                         "sample": f"{args.steps} full oracle solves of the workload after an untimed setup"},
-        "e2e": {"value": round(value, 4), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "config": {"workload": WORKLOAD, "sample": cb["sample"]},
+        "cpu_baseline": cb,
+        "e2e": {"value": round(value, 4), "unit": UNIT + " (per right-hand side)", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
         "wall_s_timed": round(time.perf_counter() - t0w, 2),
     }
 
@@ -629,7 +767,13 @@ def main():
         profile_cycle()
         return
     if args.solve_once:
-        solve_once()
+        solve_once(args.solve_once)
+        return
+    if args.profile_batch:
+        profile_batch(args.profile_batch)
+        return
+    if args.profile_kernels:
+        profile_kernels(args.profile_kernels)
         return
     if args.serve:
         if rank == 0:

@@ -63,7 +63,7 @@ typedef struct lamg_options {
     int32_t nu_tv;         /* GS sweeps per test vector: 3 (Section 2) */
     int32_t dmax;          /* elimination degree bound: 4 (Eq. 2) */
     int32_t nu_pre;        /* pre-smoothing sweeps: 1 */
-    int32_t nu_post;       /* post-smoothing sweeps: 2 ((1,2) cycle, Appendix A Table 4) */
+    int32_t nu_post;       /* post-smoothing sweeps: 2 ((1,2) cycle, Appendix A, Table 10) */
     int32_t coarsest_max;  /* a level with at most this many nodes is solved densely; 0 (default):
                               min(4096, max(1024, floor(sqrt(1.5 nnz(L))))) for the input's
                               nnz(L) = n + 2m, so the dense coarsest matrix holds about as many
@@ -105,10 +105,17 @@ typedef struct lamg_options {
                               (polynomial smoothers, the paper's Conclusion): 32; 0 never */
     int32_t cheb_degree;   /* degree of the Jacobi-preconditioned Chebyshev polynomial (interval
                               [lambda/30, lambda], lambda the Gershgorin bound of D^-1 A) that
-                              replaces one sweep: 2 (1..8) */
+                              replaces one sweep: 1 (1..8; degree 1 is Jacobi damped by
+                              1/theta, theta the interval's centre) */
     int32_t tv_order;      /* summation order of a test-vector row sum (Section 2 relaxation):
                               LAMG_TV_STRIDED (default) or LAMG_TV_STORED, see below */
-    int32_t reserved[2];
+    int32_t agg_gpu_rows;  /* aggregation levels with at least this many rows run the aggregation
+                              pass of Section 2 on the GPU (each node decided once its lower-
+                              numbered neighbours are: the sequential pass's exact result in
+                              parallel rounds); 0 (default): levels of >= 32768 rows with at
+                              most 32 stored entries per row on average (denser levels need
+                              thousands of rounds); < 0: always on the host */
+    int32_t reserved[1];
 } lamg_options;                    /* 144 bytes */
 
 /* Test-vector row sums (lamg_options.tv_order, lamg_testvectors, lamg_testvectors_noalloc).
@@ -334,7 +341,9 @@ int lamg_solve_stationary(lamg_hier *h, const double *b, double *phi, int32_t ka
  * validation and Laplacian; elimination (Eq. 2); colouring; test vectors and affinities on the
  * GPU (Section 2, Eq. 3, Eq. 9) with their copies; aggregation and caliber-2 (Eqs. 4, 13);
  * Galerkin products; dense pseudo-inverse of the coarsest level; device layout and uploads;
- * step list, timing trials and graph capture. cap >= 9. Errors: INVALID. */
+ * step list, timing trials and graph capture. cap >= 9; with cap >= 10, out[9] = the parallel
+ * rounds the GPU aggregation pass took, summed over levels (0 when every level aggregated on the
+ * host). Errors: INVALID. */
 int lamg_setup_times(const lamg_hier *h, double *out, int32_t cap);
 
 /* Solve G independent systems L_g phi_g = b_g (Eq. 1), each on its own hierarchy, with one

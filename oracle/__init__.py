@@ -23,7 +23,7 @@ _lib = None
 
 DEFAULTS = dict(K=4, nu_tv=3, dmax=4, nu_pre=1, nu_post=2, coarsest_max=0, max_levels=100,
                 veto=1, caliber2=1, tv_lex=0, symmetric=0, seed=3, dense_rows=4096,
-                cheb_colours=32, cheb_degree=2,
+                cheb_colours=32, cheb_degree=1,
                 Q=2.5, tau_soc=0.05, elim_min_frac=0.01, snap=1e-3, guard_eps=1e-10,
                 gamma_fixed=0.0)
 _IKEYS = ["K", "nu_tv", "dmax", "nu_pre", "nu_post", "coarsest_max", "max_levels", "veto",

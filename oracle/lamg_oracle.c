@@ -43,7 +43,7 @@ typedef struct {
     int K;              /* test vectors, Section 3.3: K = 4 fixed */
     int nu_tv;          /* GS sweeps per test vector, Section 2: nu = 3 */
     int dmax;           /* low-degree elimination bound, Eq. 2: d_max = 4 */
-    int nu_pre, nu_post;/* (1,2) cycle, Appendix A Table 4 */
+    int nu_pre, nu_post;/* (1,2) cycle, Appendix A, Table 10 */
     int coarsest_max;   /* dense coarsest level when n <= this; 0: the size rule of oracle_setup */
     int dense_rows;     /* dense coarsest level also when n <= this and the level has at least
                            n^2 / 8 off-diagonal entries (0: off) */

@@ -40,7 +40,7 @@ class Options(C.Structure):
                 ("elim_min_frac", C.c_double), ("snap", C.c_double), ("guard_eps", C.c_double),
                 ("gamma_fixed", C.c_double), ("device", C.c_int32), ("tail_rows", C.c_int32),
                 ("cluster_rows", C.c_int32), ("row_tpr", C.c_int32), ("sell", C.c_int32), ("autotune", C.c_int32), ("dense_rows", C.c_int32), ("cheb_colours", C.c_int32), ("cheb_degree", C.c_int32),
-                ("tv_order", C.c_int32), ("reserved", C.c_int32 * 2)]
+                ("tv_order", C.c_int32), ("agg_gpu_rows", C.c_int32), ("reserved", C.c_int32 * 1)]
 
 
 class Graph(C.Structure):
@@ -303,9 +303,11 @@ class Hierarchy:
 
     def setup_times(self) -> dict:
         """Wall milliseconds of each setup phase (lamg_setup hierarchies)."""
-        out = np.zeros(len(self.SETUP_PHASES))
+        out = np.zeros(len(self.SETUP_PHASES) + 1)
         _check(lib().lamg_setup_times(self._h, _p(out), out.size), "lamg_setup_times")
-        return {k: round(float(v), 3) for k, v in zip(self.SETUP_PHASES, out)}
+        d = {k: round(float(v), 3) for k, v in zip(self.SETUP_PHASES, out)}
+        d["gpu_aggregation_rounds"] = int(out[-1])
+        return d
 
     def schedule(self) -> dict:
         """Launch schedule of the graph path: first level of the cluster sub-cycle (-1: none),

@@ -432,25 +432,43 @@ __global__ void bk_elim_interp(int nc, int nF, int k, const int32_t *__restrict_
 
 // Coarsest level: x = (I - J/n) A^+ b against the FP64 projected pseudo-inverse, accumulated in
 // FP64 for either cycle type (an FP32 cycle's right-hand side is widened, the FP64 sum rounded
-// to FP32 once at the end): one warp per row, KL lanes per column times 32/KL lanes splitting the
-// row.
+// to FP32 once at the end). One block per row: KL lanes per column times BBS/KL lanes splitting
+// the row, each lane with four independent partial sums (a dependent FP64 add takes ~68 clocks
+// on this GPU, so one chain of n/2 adds per lane would set the kernel's time), combined in a
+// fixed order: the four partials, the lanes of a warp by a shuffle tree, then the warps in order.
 template <typename T, int KL>
 __global__ void __launch_bounds__(BBS) bk_coarse(int n, int k, const double *__restrict__ pinv,
                                                  const T *__restrict__ b, T *x) {
     b_trigger();
     b_wait();
-    constexpr int TPR = 32 / KL;
-    const int lane = threadIdx.x & 31;
-    const int j = lane % KL, sub = lane / KL;
-    const int wg = (blockIdx.x * BBS + threadIdx.x) >> 5, nwarps = (gridDim.x * BBS) >> 5;
-    for (int i = wg; i < n; i += nwarps) {
+    __shared__ double sh[BBS / 32][32];
+    constexpr int M = BBS / KL;
+    const int j = threadIdx.x % KL, m = threadIdx.x / KL;
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int i = blockIdx.x; i < n; i += gridDim.x) {
         const double *row = pinv + (size_t)i * n;
-        double s = 0.0;
-        if (j < k)
-            for (int m = sub; m < n; m += TPR) s += row[m] * (double)b[(size_t)m * k + j];
+        double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+        if (j < k) {
+            int c = m;
+            for (; c + 3 * M < n; c += 4 * M) {
+                s0 += row[c] * (double)b[(size_t)c * k + j];
+                s1 += row[c + M] * (double)b[(size_t)(c + M) * k + j];
+                s2 += row[c + 2 * M] * (double)b[(size_t)(c + 2 * M) * k + j];
+                s3 += row[c + 3 * M] * (double)b[(size_t)(c + 3 * M) * k + j];
+            }
+            for (; c < n; c += M) s0 += row[c] * (double)b[(size_t)c * k + j];
+        }
+        double s = (s0 + s1) + (s2 + s3);
 #pragma unroll
         for (int o = KL; o < 32; o <<= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-        if (sub == 0 && j < k) x[(size_t)i * k + j] = (T)s;
+        if (lane < KL) sh[w][lane] = s;
+        __syncthreads();
+        if ((int)threadIdx.x < KL && (int)threadIdx.x < k) {
+            double t = 0.0;
+            for (int q = 0; q < BBS / 32; q++) t += sh[q][threadIdx.x];
+            x[(size_t)i * k + threadIdx.x] = (T)t;
+        }
+        __syncthreads();
     }
 }
 
@@ -994,7 +1012,7 @@ static void bop(const Op &op, BatchCtx *c, cudaStream_t s, const Op *start) {
             break;
         }
         case OP_COARSE:
-#define C8(KLv, ...) case KLv: blaunch(bk_coarse<T, KLv>, rblocks((int64_t)n * 32), s, n, k, L.pinv, (const T *)b, x); break;
+#define C8(KLv, ...) case KLv: blaunch(bk_coarse<T, KLv>, std::min<int64_t>(n, 148 * 8), s, n, k, L.pinv, (const T *)b, x); break;
             switch (KL) { K_CASES(C8) }
 #undef C8
             break;

@@ -65,7 +65,7 @@ struct lamg_hier {
     // lamg_solve_many: cluster partial sums, results, residual history
     double *mg_part = nullptr, *mg_out = nullptr, *mg_hist = nullptr;
     int mg_hist_cap = 0;
-    double setup_ms[lamg::SETUP_NPHASE] = {0};
+    double setup_ms[lamg::SETUP_NPHASE + 1] = {0};   // + rounds of the GPU aggregation pass
     // multi-RHS / FP32 workspaces, one per (k, precision) used so far
     std::vector<lamg::BatchCtx *> batch;
     std::vector<void *> allocs;

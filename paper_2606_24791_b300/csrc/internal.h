@@ -114,7 +114,10 @@ int gpu_schur(const HostMat &A, const std::vector<uint8_t> &inF, const std::vect
 int gpu_validate_entries(const lamg_graph *g, bool *valid);
 int gpu_tv_and_affinity(const HostMat &A, const std::vector<int32_t> &colour, int level,
                         uint64_t seed, int K, int nu, double tau, int veto, double *X,
-                        double *aff, uint8_t *strong, double Q, double eps, uint8_t *adm, int order);
+                        double *aff, uint8_t *strong, double Q, double eps, uint8_t *adm, int order,
+                        int32_t *choice = nullptr, int *rounds = nullptr);
+// With choice != nullptr gpu_tv_and_affinity also runs the aggregation pass of Section 2 on the GPU
+// (k_agg_round): choice[u] = the node u joined, or -1 if u is a seed; *rounds = parallel rounds.
 
 int cuda_status(cudaError_t e);
 

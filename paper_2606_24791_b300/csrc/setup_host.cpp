@@ -325,6 +325,31 @@ static void aggregate(HostLevel &L, const lamg_options &o, std::vector<int32_t> 
     for (int64_t u = 0; u < n; u++) L.agg[u] = id[seed[u]];
 }
 
+// The aggregates of the GPU pass (choice[u]: the seed u joined, or -1: u is a seed), numbered by
+// ascending seed as aggregate() numbers them.
+static void aggregate_from_choice(HostLevel &L, const std::vector<int32_t> &choice, std::vector<int32_t> &status,
+                                  std::vector<int32_t> &seed) {
+    const int64_t n = L.A.n;
+    status.assign(n, SEED);
+    seed.resize(n);
+    std::vector<int32_t> id(n, -1);
+    int64_t nc = 0;
+    for (int64_t u = 0; u < n; u++) {
+        if (choice[u] >= 0) {
+            status[u] = ASSOCIATE;
+            seed[u] = choice[u];
+        } else {
+            seed[u] = (int32_t)u;
+            id[u] = (int32_t)nc++;
+        }
+    }
+    L.nc = nc;
+    L.agg.resize(n);
+    L.agg2.assign(n, -1);
+    L.wt.assign(n, 1.0);
+    for (int64_t u = 0; u < n; u++) L.agg[u] = id[seed[u]];
+}
+
 // Selective caliber-2 (Section 3.2, Eq. 13): a non-seed node whose strong edges reach exactly
 // one aggregate b besides its own a gets phi_u = w phi_a + (1-w) phi_b with the least-squares
 // weight over the test vectors taken at the two seeds, snapped to 0/1 within `snap`, kept
@@ -733,13 +758,23 @@ int build_hierarchy(const lamg_graph *g, const lamg_options &o, std::vector<Host
             L.aff.resize(L.A.nnz());
             L.strong.resize(L.A.nnz());
             L.adm.resize(L.A.nnz());
+            // the GPU pass takes as many rounds as the longest index-decreasing path, which on the
+            // dense Galerkin levels of power-law graphs (hundreds of entries per row) runs to
+            // thousands: those stay on the host, whose pass is one O(m) scan
+            const int64_t agg_rows = o.agg_gpu_rows == 0 ? 32768 : o.agg_gpu_rows;
+            const bool gpu_agg = o.agg_gpu_rows >= 0 && n >= agg_rows &&
+                                 (o.agg_gpu_rows > 0 || L.A.nnz() <= 32 * n);
+            std::vector<int32_t> choice(gpu_agg ? n : 0);
+            int rounds = 0;
             rc = gpu_tv_and_affinity(L.A, L.colour, l, o.seed, o.K, o.nu_tv, o.tau_soc, o.veto,
                                      L.X.data(), L.aff.data(), L.strong.data(), o.Q, o.guard_eps,
-                                     L.adm.data(), o.tv_order);
+                                     L.adm.data(), o.tv_order, gpu_agg ? choice.data() : nullptr, &rounds);
             if (rc) return rc;
+            if (times) times[SETUP_NPHASE] += rounds;
             lap(SETUP_TV_AFFINITY);
             std::vector<int32_t> status, seed;
-            aggregate(L, o, status, seed);
+            if (gpu_agg) aggregate_from_choice(L, choice, status, seed);
+            else aggregate(L, o, status, seed);
             if (o.caliber2) upgrade_caliber2(L, o, status, seed);
             lap(SETUP_AGGREGATE);
             if (L.nc >= n || ((double)L.nc > 0.9 * (double)n && n <= 4096)) {

@@ -207,6 +207,55 @@ __global__ void k_entry_affinity(int64_t n, int64_t z, int K, int veto, double Q
     adm[e] = worst <= Q ? 1 : 0;
 }
 
+// Caliber-1 aggregation (Section 2) on the GPU, with exactly the result of the sequential pass
+// (nodes visited in ascending order; an undecided node joins the admissible strong neighbour of
+// largest affinity, ties to the lower index, among seeds and undecided nodes; a chosen undecided
+// node becomes a seed). In that pass node u's decision depends only on the decisions of its
+// lower-numbered neighbours: u is skipped iff one of them chose u (it is already a seed), and a
+// lower-numbered neighbour s is a candidate iff s did not join anyone, while a higher-numbered
+// neighbour is not yet visited, so never an associate, and always a candidate if admissible.
+// Deciding u as soon as every lower-numbered neighbour is decided (Kahn's order on the DAG of
+// lower-to-higher edges) therefore reproduces the pass exactly, in as many parallel rounds as
+// the longest index-decreasing path.
+//   choice[u]: -2 pending, -1 decided without joining (a seed: chosen by an earlier node or
+//   left over), s >= 0 joined s.
+__global__ void k_agg_init(int64_t n, const int64_t *__restrict__ rp, const int32_t *__restrict__ ci,
+                           int32_t *cnt, int32_t *choice, int32_t *front, int32_t *fsize) {
+    const int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (u >= n) return;
+    int32_t c = 0;
+    for (int64_t e = rp[u]; e < rp[u + 1] && ci[e] < u; e++) c++;   // columns ascending
+    cnt[u] = c;
+    choice[u] = -2;
+    if (c == 0) front[atomicAdd(fsize, 1)] = (int32_t)u;
+}
+
+__global__ void k_agg_round(const int32_t *__restrict__ front, const int32_t *__restrict__ fsize,
+                            const int64_t *__restrict__ rp, const int32_t *__restrict__ ci,
+                            const double *__restrict__ aff, const uint8_t *__restrict__ adm, int32_t *cnt,
+                            int32_t *choice, int32_t *next, int32_t *nsize) {
+    const int32_t t = (int32_t)(blockIdx.x * blockDim.x + threadIdx.x);
+    if (t >= *fsize) return;
+    const int32_t u = front[t];
+    const int64_t e0 = rp[u], e1 = rp[u + 1];
+    bool skipped = false;
+    for (int64_t e = e0; e < e1 && ci[e] < u; e++)
+        if (choice[ci[e]] == u) skipped = true;
+    int32_t best = -1;
+    if (!skipped) {
+        double bestc = -1.0;
+        for (int64_t e = e0; e < e1; e++) {
+            const int32_t s = ci[e];
+            if (!adm[e] || (s < u && choice[s] >= 0)) continue;
+            const double c = aff[e];
+            if (c > bestc || (c == bestc && s < best)) { bestc = c; best = s; }
+        }
+    }
+    choice[u] = best;
+    for (int64_t e = e1 - 1; e >= e0 && ci[e] > u; e--)
+        if (atomicSub(&cnt[ci[e]], 1) == 1) next[atomicAdd(nsize, 1)] = ci[e];
+}
+
 // Galerkin coarse operator P^T A P (Section 2), row a by one thread, in the host's order: u
 // over the fine rows of aggregate a ascending (P_ua = pa), v over u's diagonal then u's
 // entries in stored order, b over v's row of P; each product (pa * A_uv) * P_vb is rounded
@@ -397,13 +446,15 @@ static inline unsigned nblk(int64_t work, int bs) { return (unsigned)((work + bs
 static int run_setup_kernels(const HostMat &A, const std::vector<int32_t> *colour, int level,
                              uint64_t seed, int K, int nu, double tau, int veto, double *X,
                              const double *Xin, double *aff, uint8_t *strong, double Q = 0.0,
-                             double eps = 0.0, uint8_t *adm = nullptr, int order = LAMG_TV_STRIDED) {
+                             double eps = 0.0, uint8_t *adm = nullptr, int order = LAMG_TV_STRIDED,
+                             int32_t *choice = nullptr, int *rounds = nullptr) {
     int rc = LAMG_OK;
     const int64_t n = A.n, z = A.nnz();
     int64_t *d_rp = nullptr;
     int32_t *d_ci = nullptr, *d_rows = nullptr;
     double *d_val = nullptr, *d_diag = nullptr, *d_X = nullptr, *d_aff = nullptr, *d_rs = nullptr;
     uint8_t *d_strong = nullptr, *d_adm = nullptr;
+    int32_t *d_agg = nullptr;
     const int bs = 128;
     cudaStream_t st = nullptr;
     std::vector<int32_t> rows;
@@ -476,11 +527,41 @@ static int run_setup_kernels(const HostMat &A, const std::vector<int32_t> *colou
         if (z) CK(cudaMemcpyAsync(aff, d_aff, z * sizeof(double), cudaMemcpyDeviceToHost, st));
         if (z) CK(cudaMemcpyAsync(strong, d_strong, z, cudaMemcpyDeviceToHost, st));
         if (moments && z) CK(cudaMemcpyAsync(adm, d_adm, z, cudaMemcpyDeviceToHost, st));
+        if (choice && moments) {
+            // the aggregation pass in dependency order (k_agg_round), one launch per round; the
+            // host reads the next frontier's size between rounds
+            CK(cudaMallocAsync((void **)&d_agg, (4 * n + 2) * sizeof(int32_t), st));
+            int32_t *cnt = d_agg, *dch = d_agg + n, *fa = d_agg + 2 * n, *fb = d_agg + 3 * n, *sz = d_agg + 4 * n;
+            int32_t *h_sz = nullptr;
+            CK(cudaHostAlloc((void **)&h_sz, sizeof(int32_t), cudaHostAllocDefault));
+            CK(cudaMemsetAsync(sz, 0, 2 * sizeof(int32_t), st));
+            k_agg_init<<<nblk(n, bs), bs, 0, st>>>(n, d_rp, d_ci, cnt, dch, fa, sz);
+            CK(cudaMemcpyAsync(h_sz, sz, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+            CK(cudaStreamSynchronize(st));
+            int64_t left = n, r = 0;
+            int cur = 0;
+            while (*h_sz > 0 && left > 0) {
+                const int32_t fn = *h_sz;
+                left -= fn;
+                int32_t *fin = cur ? fb : fa, *fout = cur ? fa : fb;
+                CK(cudaMemsetAsync(sz + 1 - cur, 0, sizeof(int32_t), st));
+                k_agg_round<<<nblk(fn, bs), bs, 0, st>>>(fin, sz + cur, d_rp, d_ci, d_aff, d_adm, cnt, dch, fout,
+                                                         sz + 1 - cur);
+                CK(cudaMemcpyAsync(h_sz, sz + 1 - cur, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+                CK(cudaStreamSynchronize(st));
+                cur = 1 - cur;
+                r++;
+            }
+            cudaFreeHost(h_sz);
+            if (left != 0) { rc = LAMG_ERR_SETUP; goto out; }   // every node is reached: an invariant
+            CK(cudaMemcpyAsync(choice, dch, n * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+            if (rounds) *rounds = (int)r;
+        }
     }
     CK(cudaStreamSynchronize(st));
 out:
     if (st) {
-        void *ptrs[] = {d_rp, d_ci, d_val, d_diag, d_X, d_rows, d_aff, d_strong, d_adm, d_rs};
+        void *ptrs[] = {d_rp, d_ci, d_val, d_diag, d_X, d_rows, d_aff, d_strong, d_adm, d_rs, d_agg};
         for (void *q : ptrs)
             if (q) cudaFreeAsync(q, st);
         cudaStreamSynchronize(st);
@@ -714,9 +795,10 @@ int gpu_affinity(const HostMat &A, const double *X, int K, double tau, double *a
 
 int gpu_tv_and_affinity(const HostMat &A, const std::vector<int32_t> &colour, int level,
                         uint64_t seed, int K, int nu, double tau, int veto, double *X,
-                        double *aff, uint8_t *strong, double Q, double eps, uint8_t *adm, int order) {
+                        double *aff, uint8_t *strong, double Q, double eps, uint8_t *adm, int order,
+                        int32_t *choice, int *rounds) {
     return run_setup_kernels(A, &colour, level, seed, K, nu, tau, veto, X, nullptr, aff, strong, Q, eps, adm,
-                             order);
+                             order, choice, rounds);
 }
 
 }  // namespace lamg

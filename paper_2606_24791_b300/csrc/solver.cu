@@ -792,7 +792,7 @@ void lamg_options_default(lamg_options *o) {
     o->autotune = 0;
     o->dense_rows = 4096;
     o->cheb_colours = 32;
-    o->cheb_degree = 2;
+    o->cheb_degree = 1;
     o->tv_order = LAMG_TV_STRIDED;
 }
 
@@ -1298,6 +1298,7 @@ int lamg_profile_schedule(lamg_hier *h, int32_t from_level, int64_t *out, int64_
 int lamg_setup_times(const lamg_hier *h, double *out, int32_t cap) {
     if (!h || !out || cap < SETUP_NPHASE) return LAMG_ERR_INVALID;
     for (int i = 0; i < SETUP_NPHASE; i++) out[i] = h->setup_ms[i];
+    if (cap > SETUP_NPHASE) out[SETUP_NPHASE] = h->setup_ms[SETUP_NPHASE];
     return LAMG_OK;
 }
 

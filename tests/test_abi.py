@@ -46,9 +46,9 @@ def test_options_defaults_are_the_papers():
     assert ctypes.sizeof(lamg.SolveOpts) == 32
     assert o.tv_order == lamg.TV_STRIDED == 0 and lamg.TV_STORED == 1
     # the readings' defaults, as include/lamg.h documents them: coarsest size by rule (0), dense
-    # small levels up to 4096 nodes, Chebyshev above 32 colours with degree 2, no timing trials,
+    # small levels up to 4096 nodes, Chebyshev above 32 colours with degree 1, no timing trials,
     # and the oracle's defaults agree wherever both have the option
-    assert (o.coarsest_max, o.dense_rows, o.cheb_colours, o.cheb_degree, o.autotune) == (0, 4096, 32, 2, 0)
+    assert (o.coarsest_max, o.dense_rows, o.cheb_colours, o.cheb_degree, o.autotune) == (0, 4096, 32, 1, 0)
     for key in ("K", "nu_tv", "dmax", "nu_pre", "nu_post", "coarsest_max", "dense_rows", "cheb_colours",
                 "cheb_degree"):
         assert oracle.DEFAULTS[key] == getattr(o, key), key

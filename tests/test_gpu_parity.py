@@ -134,6 +134,22 @@ def test_setup_matches_oracle(case):
     P.close()
 
 
+def test_gpu_aggregation_equals_the_sequential_pass(case):
+    # every aggregation level aggregated on the GPU (each node decided once its lower-numbered
+    # neighbours are decided): the same aggregates, caliber-2 parents, weights and coarse
+    # operators as the oracle's sequential pass, bit for bit
+    name, g, cm, H = case
+    P = lamg.setup(g, coarsest_max=cm, agg_gpu_rows=1, **STORED)
+    assert P.nlevels == H.nlevels, name
+    for l, L in enumerate(H.levels):
+        for key in ("ci", "val", "diag"):
+            assert np.array_equal(P.array(l, key), L[key]), (name, l, key)
+        if L["kind"] == "agg":
+            for key in ("agg", "agg2", "wt"):
+                assert np.array_equal(P.array(l, key), L[key]), (name, l, key)
+    P.close()
+
+
 def test_default_setup_matches_oracle_or_differs_by_rounding(case):
     # with the default strided order the hierarchy is the oracle's wherever no aggregation level
     # has rows over 32 entries; on hub graphs the first such level's test vectors agree to
@@ -183,6 +199,9 @@ def test_gpu_coarse_operators_match_oracle_bitwise(name):
         assert P.info[l]["n"] == L["n"], (name, l)
         for key in ("rp", "ci", "val", "diag"):
             assert np.array_equal(P.array(l, key), L[key]), (name, l, key)
+        if L["kind"] == "agg":   # levels of >= 32768 rows aggregate on the GPU by default
+            for key in ("agg", "agg2", "wt"):
+                assert np.array_equal(P.array(l, key), L[key]), (name, l, key)
     P.close()
 
 

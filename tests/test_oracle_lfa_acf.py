@@ -4,8 +4,8 @@
    against the explicitly assembled 2 x 2 symbol, against the explicit dense two-grid operator
    on a periodic grid, the closed forms of the energy fractions, the caliber-1 ceiling, and the
    printed suprema (caliber-1 about 0.48, caliber-2 0.08 / 0.09 / 0.09).
-2. Convergence factors the paper prints for its anisotropic grids (Table 2, Table 4, Section 3
-   and the grid128 row of the ACF table), compared in bands of +-35% (random test vectors, and
+2. Convergence factors the paper prints for its anisotropic grids (Table 2, Table 10, Section 3
+   and the grid128 row of the ACF table, Table 3), compared in bands of +-35% (random test vectors, and
    readings where the paper is silent). Cases whose band the oracle misses are marked xfail
    with the reading responsible; strict, so that a change that brings one into its band shows.
 3. The measured two-level factors of Section 3.2 (exact coarse solve, per aggregation level)
@@ -114,7 +114,7 @@ def test_lfa_caliber1_ceiling():
 
 
 def test_lfa_printed_suprema():
-    # Appendix A.1 and Table 4: sup rho_c1 about 0.48 (the 1/2 ceiling), sup rho_c2 0.08 / 0.09 /
+    # Appendix A.1 and Table 10: sup rho_c1 about 0.48 (the 1/2 ceiling), sup rho_c2 0.08 / 0.09 /
     # 0.09 at eps = 1e-1 / 1e-2 / 1e-4
     for eps in (1e-1, 1e-2, 1e-4):
         assert 0.47 <= lfa.sup_rho(eps, 1) <= 0.50
@@ -143,7 +143,7 @@ READING_ML = ("the oracle's cycle is the gamma-cycle of Eq. 5 with per-cycle vis
 
 @pytest.mark.parametrize("eps,paper", [(1.0, 0.74), (1e-1, 0.76), (1e-2, 0.77), (1e-4, 0.77)])
 def test_flat_vcycle_caliber1_factor(eps, paper):
-    # Table 4, caliber-1 "V-cycle": gamma = 1, (1,2) sweeps, no recombination, no caliber-2
+    # Table 10, caliber-1 "V-cycle": gamma = 1, (1,2) sweeps, no recombination, no caliber-2
     v = stationary_acf(gg.grid2d(64, 64, 1.0, eps), 0, caliber2=0, gamma_fixed=1.0)
     assert band(paper, v), v
 
@@ -155,7 +155,7 @@ def test_flat_vcycle_caliber1_factor(eps, paper):
     (1e-4, 0.391),
 ])
 def test_multilevel_caliber1_factor(eps, paper):
-    # Table 4, caliber-1 "ML": gamma of Eq. 5 and recombination
+    # Table 10, caliber-1 "ML": gamma of Eq. 5 and recombination
     v = stationary_acf(gg.grid2d(64, 64, 1.0, eps), 4, caliber2=0)
     assert band(paper, v), v
 
@@ -169,7 +169,7 @@ def test_multilevel_caliber1_factor(eps, paper):
                              "(single seeds 0.126-0.144) against the printed 0.100")),
 ])
 def test_multilevel_caliber2_factor(eps, paper):
-    # Table 4, caliber-2 "ML": the full LAMG+ solver
+    # Table 10, caliber-2 "ML": the full LAMG+ solver
     v = stationary_acf(gg.grid2d(64, 64, 1.0, eps), 4)
     assert band(paper, v), v
 
