@@ -109,12 +109,11 @@ typedef struct lamg_options {
                               1/theta, theta the interval's centre) */
     int32_t tv_order;      /* summation order of a test-vector row sum (Section 2 relaxation):
                               LAMG_TV_STRIDED (default) or LAMG_TV_STORED, see below */
-    int32_t agg_gpu_rows;  /* aggregation levels with at least this many rows run the aggregation
-                              pass of Section 2 on the GPU (each node decided once its lower-
-                              numbered neighbours are: the sequential pass's exact result in
-                              parallel rounds); 0 (default): levels of >= 32768 rows with at
-                              most 32 stored entries per row on average (denser levels need
-                              thousands of rounds); < 0: always on the host */
+    int32_t agg_gpu_rows;  /* > 0: aggregation levels with at least this many rows run the
+                              aggregation pass of Section 2 on the GPU (each node decided once
+                              its lower-numbered neighbours are: the sequential pass's exact
+                              result, in as many parallel rounds as the longest index-decreasing
+                              path); 0 (default): on the host (one O(m) scan, measured faster) */
     int32_t reserved[1];
 } lamg_options;                    /* 144 bytes */
 
@@ -423,7 +422,9 @@ int lamg_server_drain(lamg_server *s, double timeout_s);
  * waiting for admission, out[3] requests not yet finished, out[4] grouped launches so far (the
  * requests that became ready since the executor's previous pass and that the cluster kernel
  * takes are solved together, one thread-block cluster each, as in lamg_solve_many), out[5]
- * requests solved in such launches, out[6] the largest group. 7 entries. */
+ * requests solved in such launches, out[6] the largest group, out[7] solves whose first launch
+ * the executor issued while another request's device work was still in flight (requests sharing
+ * the device). 8 entries. */
 int lamg_server_stats(lamg_server *s, int64_t *out);
 /* Stop the threads and release everything; unfinished requests are dropped. */
 void lamg_server_destroy(lamg_server *s);

@@ -241,13 +241,20 @@ class Hierarchy:
         _check(rc, "lamg_solve", (LAMG_OK, 5))
         return _stats(st, h)
 
-    def solve_batch(self, B, tol: float = 1e-8, maxit: int = 100, allow_unconverged: bool = False):
-        """k right-hand sides (B: n x k) in one SpMM-form solve; returns (PHI, [stats per column])."""
+    def solve_batch(self, B, tol: float = 1e-8, maxit: int = 100, allow_unconverged: bool = False, out=None):
+        """k right-hand sides (B: n x k) in one SpMM-form solve; returns (PHI, [stats per column]).
+        out: an optional C-contiguous float64 n x k array that receives PHI (reused between calls,
+        it saves the first-touch cost of a fresh output array)."""
         B = _c(B, np.float64)
         if B.ndim != 2 or B.shape[0] != self.n:
             raise ValueError("B must be n x k")
         k = B.shape[1]
-        PHI = np.zeros_like(B)
+        if out is not None:
+            if out.shape != B.shape or out.dtype != np.float64 or not out.flags["C_CONTIGUOUS"]:
+                raise ValueError("out must be a C-contiguous float64 array shaped like B")
+            PHI = out
+        else:
+            PHI = np.zeros_like(B)
         hists = [np.zeros(maxit + 1) for _ in range(k)]
         st = (Stats * k)()
         for j in range(k):
@@ -415,11 +422,11 @@ class Server:
         _check(lib().lamg_server_drain(self._s, timeout_s), "lamg_server_drain")
 
     def stats(self) -> dict:
-        out = np.zeros(7, np.int64)
+        out = np.zeros(8, np.int64)
         lib().lamg_server_stats(self._s, _p(out))
         return dict(bytes_in_flight=int(out[0]), inflight=int(out[1]), waiting=int(out[2]),
                     unfinished=int(out[3]), grouped_launches=int(out[4]), grouped_requests=int(out[5]),
-                    largest_group=int(out[6]))
+                    largest_group=int(out[6]), overlapped_starts=int(out[7]))
 
     def close(self):
         if getattr(self, "_s", None):

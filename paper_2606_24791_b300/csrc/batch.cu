@@ -1141,7 +1141,13 @@ int solve_batch_impl(lamg_hier *h, int k, const double *B, double *PHI, const la
     const int n = (int)h->dev[0].n;
     const int64_t cnt = (int64_t)n * k;
     CKR(cudaEventRecord(h->ev_a, s));
-    CKR(cudaMemcpyAsync(c->nat_in, B, cnt * sizeof(double), devp ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+    // host vectors of a few hundred MB and more: pipelined pinned chunks with threaded host copies
+    const bool staged = !devp && (size_t)cnt * sizeof(double) >= staged_copy_min_bytes();
+    if (staged) {
+        if ((rc = h2d_staged(c->nat_in, B, cnt * sizeof(double), s, h->wait_timeout_s))) return rc;
+    } else {
+        CKR(cudaMemcpyAsync(c->nat_in, B, cnt * sizeof(double), devp ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+    }
     c->h_sk[B_TOL2 * KMAX] = so->tol * so->tol;
     CKR(cudaMemcpyAsync(c->red.sk + B_TOL2 * KMAX, c->h_sk + B_TOL2 * KMAX, sizeof(double), cudaMemcpyHostToDevice, s));
     KL_SWITCH(c->KL, blaunch(bk_gather_rows<KLc>, nblocks((int64_t)n * KLc), s, n, k, (const int32_t *)h->perm0,
@@ -1179,9 +1185,11 @@ int solve_batch_impl(lamg_hier *h, int k, const double *B, double *PHI, const la
     cg_true_resid(h, c, s);
     KL_SWITCH(c->KL, blaunch(bk_scatter_rows<KLc>, nblocks((int64_t)n * KLc), s, n, k, (const int32_t *)h->perm0,
                              (const double *)c->xs, c->nat_out));
-    CKR(cudaMemcpyAsync(PHI, c->nat_out, cnt * sizeof(double), devp ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
+    if (!staged)
+        CKR(cudaMemcpyAsync(PHI, c->nat_out, cnt * sizeof(double), devp ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
     CKR(cudaMemcpyAsync(c->h_sk, c->red.sk, B_COUNT * KMAX * sizeof(double), cudaMemcpyDeviceToHost, s));
     CKR(cudaMemcpyAsync(c->h_sk + B_COUNT * KMAX, c->red.done, KMAX * sizeof(int), cudaMemcpyDeviceToHost, s));
+    if (staged && (rc = d2h_staged(PHI, c->nat_out, cnt * sizeof(double), s, h->wait_timeout_s))) return rc;
     CKR(cudaEventRecord(h->ev_b, s));
     if ((rc = wait_event(h, h->ev_b))) return rc;
     CKR(cudaGetLastError());

@@ -137,6 +137,14 @@ inline int wait_event(lamg_hier *h, cudaEvent_t ev) {
     }
 }
 
+// Host <-> device copies of large caller vectors through pipelined pinned chunks (host_copy.cpp);
+// d2h_staged returns once dst holds the data, h2d_staged once every chunk's DMA is queued and
+// its staging buffer released. Waits are bounded by timeout_s. Worth it from
+// staged_copy_min_bytes() on.
+size_t staged_copy_min_bytes();
+int h2d_staged(void *dst, const void *src, size_t bytes, cudaStream_t s, double timeout_s);
+int d2h_staged(void *dst, const void *src, size_t bytes, cudaStream_t s, double timeout_s);
+
 void op_bytes(const lamg_hier *h, const Op &op, double s, double *mat, double *vec);
 bool many_eligible(const lamg_hier *h, size_t *smem);
 // step i is a restriction that also performs step i + 1, the row-local start of the coarse

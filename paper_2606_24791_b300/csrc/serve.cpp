@@ -178,6 +178,19 @@ struct lamg_server {
     cudaStream_t gstream = nullptr;
     std::vector<Group> groups;
     int64_t n_groups = 0, n_grouped = 0, max_group = 0;
+    // solves whose first launch was issued while another request's device work was in flight
+    // (the executor's own record of requests sharing the device)
+    int64_t n_overlap_starts = 0;
+
+    // the executor's current pass over the ready requests (executor thread only)
+    std::vector<Request *> pass;
+
+    // another admitted request has launched work not yet seen complete (executor thread)
+    bool device_busy_except(const Request *r) const {
+        for (const Request *q : pass)
+            if (q != r && (q->phase == 1 || q->phase == 2 || q->phase == 6)) return true;
+        return !groups.empty();
+    }
 
     double now_ms() const {
         return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
@@ -247,6 +260,10 @@ struct lamg_server {
         cudaError_t e = cudaSuccess;
         switch (r->phase) {
             case 0: {
+                if (device_busy_except(r)) {
+                    std::lock_guard<std::mutex> lock(mu);
+                    n_overlap_starts++;
+                }
                 r->pin_b = pins.get(n);
                 r->pin_x = pins.get(n);
                 if (!r->pin_b || !r->pin_x) { r->phase = 4; r->status = LAMG_ERR_OOM; return true; }
@@ -308,6 +325,14 @@ struct lamg_server {
     void launch_group(std::vector<Request *> &fresh) {
         Group g;
         std::vector<MGraph> desc(fresh.size());
+        int64_t overlapped = 0;
+        {
+            bool busy = !groups.empty();
+            for (const Request *q : pass)
+                if (std::find(fresh.begin(), fresh.end(), q) == fresh.end() && (q->phase == 1 || q->phase == 2 || q->phase == 6))
+                    busy = true;
+            overlapped = busy ? (int64_t)fresh.size() : 0;
+        }
         int cl = 16;
         size_t smem = 0;
         cudaError_t e = cudaSuccess;
@@ -360,6 +385,7 @@ struct lamg_server {
             std::lock_guard<std::mutex> lock(mu);
             n_groups++;
             n_grouped += (int64_t)fresh.size();
+            n_overlap_starts += overlapped;
             max_group = std::max<int64_t>(max_group, (int64_t)fresh.size());
         }
         groups.push_back(std::move(g));
@@ -406,6 +432,7 @@ struct lamg_server {
                 if (stop) break;
                 act = running;
             }
+            pass = act;
             // continuous batching: every request whose setup finished since the last pass and
             // that the cluster kernel takes joins one launch
             fresh.clear();
@@ -535,6 +562,7 @@ int lamg_server_stats(lamg_server *s, int64_t *out) {
     out[4] = s->n_groups;
     out[5] = s->n_grouped;
     out[6] = s->max_group;
+    out[7] = s->n_overlap_starts;
     return LAMG_OK;
 }
 

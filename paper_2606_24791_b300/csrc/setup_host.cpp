@@ -758,12 +758,10 @@ int build_hierarchy(const lamg_graph *g, const lamg_options &o, std::vector<Host
             L.aff.resize(L.A.nnz());
             L.strong.resize(L.A.nnz());
             L.adm.resize(L.A.nnz());
-            // the GPU pass takes as many rounds as the longest index-decreasing path, which on the
-            // dense Galerkin levels of power-law graphs (hundreds of entries per row) runs to
-            // thousands: those stay on the host, whose pass is one O(m) scan
-            const int64_t agg_rows = o.agg_gpu_rows == 0 ? 32768 : o.agg_gpu_rows;
-            const bool gpu_agg = o.agg_gpu_rows >= 0 && n >= agg_rows &&
-                                 (o.agg_gpu_rows > 0 || L.A.nnz() <= 32 * n);
+            // the GPU pass takes as many rounds as the longest index-decreasing path (thousands
+            // per level on natural-order meshes and dense power-law levels), so the host's one
+            // O(m) scan stays the default
+            const bool gpu_agg = o.agg_gpu_rows > 0 && n >= o.agg_gpu_rows;
             std::vector<int32_t> choice(gpu_agg ? n : 0);
             int rounds = 0;
             rc = gpu_tv_and_affinity(L.A, L.colour, l, o.seed, o.K, o.nu_tv, o.tau_soc, o.veto,

@@ -190,7 +190,7 @@ GALERKIN_CASES = {
 def test_gpu_coarse_operators_match_oracle_bitwise(name):
     g = GALERKIN_CASES[name]()
     H = oracle.Hierarchy(g)
-    P = lamg.setup(g, **STORED)
+    P = lamg.setup(g, agg_gpu_rows=32768, **STORED)   # large levels also aggregate on the GPU
     assert P.nlevels == H.nlevels, name
     assert any(L["kind"] == "agg" and L["n"] >= 32768 for L in H.levels), name
     if name != "grid3d40_hetero":  # the others start with an elimination level of >= 32768 rows
@@ -199,7 +199,7 @@ def test_gpu_coarse_operators_match_oracle_bitwise(name):
         assert P.info[l]["n"] == L["n"], (name, l)
         for key in ("rp", "ci", "val", "diag"):
             assert np.array_equal(P.array(l, key), L[key]), (name, l, key)
-        if L["kind"] == "agg":   # levels of >= 32768 rows aggregate on the GPU by default
+        if L["kind"] == "agg":   # levels of >= 32768 rows aggregated on the GPU
             for key in ("agg", "agg2", "wt"):
                 assert np.array_equal(P.array(l, key), L[key]), (name, l, key)
     P.close()
