@@ -216,12 +216,9 @@ def profile_batch(spec: str):
     import paper_2606_24791_b300 as lamg
     n, level, which = spec.split(":")
     g = gg.chung_lu(int(n), 2.1, 16.0, seed=1)
-    B = gg.rhs(g, seed=2, k=K_RHS)
     P = lamg.setup(g)
-    bt = torch.from_numpy(B).cuda()
-    xt = torch.zeros_like(bt)
-    P.solve_batch_ptr(K_RHS, bt.data_ptr(), xt.data_ptr(), TOL, 2)   # vectors hold a real iterate
-    torch.cuda.synchronize()
+    # the kernel sequence runs once, on the batch context's vectors as allocated (values do not
+    # change the work or the traffic), so it is the only launch of its kind in the process
     r = P.time_kernel_batch(which, int(level), K_RHS, reps=1)
     print(json.dumps({"n": g.n, "nnz_L": g.nnz_L, "level": int(level), "info": P.info[int(level)], "which": which,
                       "kernel": r}))

@@ -24,9 +24,12 @@ namespace {
 // A fixed set of worker threads running one parallel memcpy at a time.
 class CopyPool {
   public:
+    // Created on first use and never destroyed: its detached workers wait on the condition
+    // variable for the life of the process, and destroying a condition variable that has waiters
+    // would block (glibc waits for them) when the process exits.
     static CopyPool &get() {
-        static CopyPool pool;
-        return pool;
+        static CopyPool *pool = new CopyPool();
+        return *pool;
     }
     // dst[0, bytes) = src[0, bytes), split into nthreads() slices copied concurrently.
     void copy(void *dst, const void *src, size_t bytes) {

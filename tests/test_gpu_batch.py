@@ -170,3 +170,20 @@ def test_large_host_batch_goes_through_staged_copies_unchanged():
         assert X2 is out and np.array_equal(out, Xh)
     assert all(s["relres_true"] <= 2e-8 for s in sts)
     P.close()
+
+
+def test_a_process_that_used_the_staged_copies_exits():
+    # the copy threads of the staged host transfers live for the whole process; the process must
+    # still exit normally afterwards (a pool destroyed at exit with waiting threads would block)
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    code = ("import sys; sys.path.insert(0, %r)\n"
+            "import numpy as np, graphgen as gg, paper_2606_24791_b300 as lamg\n"
+            "g = gg.grid2d(1024, 1024, 1.0, 1e-2)\n"
+            "P = lamg.setup(g)\n"
+            "X, st = P.solve_batch(gg.rhs(g, seed=4, k=17), 1e-8, 200)\n"
+            "print('solved', max(s['relres_true'] for s in st))\n" % root)
+    out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=300)
+    assert out.returncode == 0 and "solved" in out.stdout, out.stderr[-2000:]
