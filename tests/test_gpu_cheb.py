@@ -16,7 +16,12 @@ pytestmark = pytest.mark.gpu
 
 
 def rel(a, b):
-    return np.linalg.norm(np.asarray(a) - np.asarray(b)) / max(np.linalg.norm(b), 1e-300)
+    """max(norm ratio, largest element difference / largest element): bounds the whole vector
+    and every entry."""
+    a, b = np.asarray(a), np.asarray(b)
+    d = a - b
+    return max(np.linalg.norm(d) / max(np.linalg.norm(b), 1e-300),
+               np.abs(d).max(initial=0.0) / max(np.abs(b).max(initial=0.0), 1e-300))
 
 
 CASES = {
