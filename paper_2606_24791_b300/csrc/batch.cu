@@ -265,14 +265,16 @@ __global__ void __launch_bounds__(BBS) bk_resid_sell(int n, const int32_t *__res
 }
 
 // One step of the Chebyshev smoothing polynomial for k columns (as k_cheb): every row from the
-// previous iterate xin, d <- c1 d + c2 (b - A xin) / A_uu (first step: c1 term absent),
-// xout = xin + d. Blocks b < nl take the long rows lr[b].
+// previous iterate xin, d <- c1 d + c2 (b - A xin) / A_uu (first step, flags bit 0: c1 term
+// absent), xout = xin + d; d not stored on the last step (flags bit 1). Blocks b < nl take the
+// long rows lr[b].
 template <typename T, int KL, int TPR>
 __global__ void __launch_bounds__(BBS) bk_cheb(int n, int k, const int32_t *__restrict__ rp,
                                                const int32_t *__restrict__ ci, const T *__restrict__ val,
                                                const T *__restrict__ diag, const T *__restrict__ idiag,
                                                const T *__restrict__ b, const T *xin, T *xout, T *d, T c1, T c2,
-                                               int first, const int32_t *__restrict__ lr, int nl) {
+                                               int flags, const int32_t *__restrict__ lr, int nl) {
+    const bool first = flags & 1, last = flags & 2;
     b_trigger();
     if ((int)blockIdx.x < nl) {
         const int row = lr[blockIdx.x];
@@ -284,7 +286,7 @@ __global__ void __launch_bounds__(BBS) bk_cheb(int n, int k, const int32_t *__re
             const size_t i = (size_t)row * k + threadIdx.x;
             const T r = b[i] - (dg * xin[i] + s);
             const T dn = (first ? T(0) : c1 * d[i]) + c2 * r * id;
-            d[i] = dn;
+            if (!last) d[i] = dn;
             xout[i] = xin[i] + dn;
         }
         return;
@@ -303,7 +305,7 @@ __global__ void __launch_bounds__(BBS) bk_cheb(int n, int k, const int32_t *__re
         const size_t i = (size_t)row * k + j;
         const T r = b[i] - (dg * xin[i] + s);
         const T dn = (first ? T(0) : c1 * d[i]) + c2 * r * id;
-        d[i] = dn;
+        if (!last) d[i] = dn;
         xout[i] = xin[i] + dn;
     }
 }
@@ -791,7 +793,7 @@ struct BLev {
     const void *idiag = nullptr;
     const int32_t *sl_ptr = nullptr, *sl_col = nullptr;
     const void *sl_val = nullptr;
-    int cheb = 0;
+    int cheb = 0, cheb_m = 0;
     double cheb_c1[8] = {0}, cheb_c2[8] = {0};
     void *t = nullptr, *d = nullptr;   // Chebyshev second iterate and direction, n x k
     const int32_t *rp = nullptr, *ci = nullptr, *agg = nullptr, *agg2 = nullptr, *pt_ptr = nullptr,
@@ -850,6 +852,7 @@ static int build_ctx(lamg_hier *h, BatchCtx *c) {
         B.nlong = D.nlong; B.lptr = D.lptr; B.lrows = D.lrows;
         B.gs_tpr = D.gs_tpr; B.rs_tpr = D.rs_tpr; B.sl_ptr = D.sl_ptr; B.sl_col = D.sl_col;
         B.cheb = D.cheb;
+        B.cheb_m = D.cheb_m;
         for (int q = 0; q < 8; q++) { B.cheb_c1[q] = D.cheb_c1[q]; B.cheb_c2[q] = D.cheb_c2[q]; }
         if (D.sell && (rc = typed_copy<T>(h, D.sl_val, D.sell_nnz, &B.sl_val))) return rc;
         B.rp = D.rp; B.ci = D.ci; B.agg = D.agg; B.agg2 = D.agg2; B.pt_ptr = D.pt_ptr; B.pt_row = D.pt_row;
@@ -1022,7 +1025,7 @@ static void bop(const Op &op, BatchCtx *c, cudaStream_t s, const Op *start) {
             T *xout = (q & 1) ? x : (T *)L.t;
             const int tpr = row_tpr(KL, L.tpr);
             const T c1 = (T)L.cheb_c1[q], c2 = (T)L.cheb_c2[q];
-#define C11(KLv, TPRv, ...) case KT_CODE(KLv, TPRv): blaunch(bk_cheb<T, KLv, TPRv>, L.nlong + nblocks((int64_t)n * KLv * TPRv), s, n, k, L.rp, L.ci, val, diag, idiag, (const T *)b, xin, xout, (T *)L.d, c1, c2, q == 0 ? 1 : 0, L.lrows, (int)L.nlong); break;
+#define C11(KLv, TPRv, ...) case KT_CODE(KLv, TPRv): blaunch(bk_cheb<T, KLv, TPRv>, L.nlong + nblocks((int64_t)n * KLv * TPRv), s, n, k, L.rp, L.ci, val, diag, idiag, (const T *)b, xin, xout, (T *)L.d, c1, c2, (q == 0 ? 1 : 0) | (q == L.cheb_m - 1 ? 2 : 0), L.lrows, (int)L.nlong); break;
             switch (KT_CODE(KL, tpr)) { KT_CASES(C11) }
 #undef C11
             break;

@@ -280,14 +280,16 @@ __global__ void __launch_bounds__(BS) k_resid(int n, const int32_t *__restrict__
 }
 
 // One step of the Chebyshev smoothing polynomial: every row from the previous iterate xin,
-// r_u = b_u - (A xin)_u, d_u <- c1 d_u + c2 r_u / A_uu (first step: d_u = c2 r_u / A_uu),
-// xout_u = xin_u + d_u. Blocks b < nl take the long rows lr[b].
+// r_u = b_u - (A xin)_u, d_u <- c1 d_u + c2 r_u / A_uu (first step, flags bit 0: d_u = c2 r_u /
+// A_uu), xout_u = xin_u + d_u; d is not stored on the last step of the polynomial (flags bit 1),
+// where nothing reads it. Blocks b < nl take the long rows lr[b].
 template <int TPR>
 __global__ void __launch_bounds__(BS) k_cheb(int n, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
                                              const double *__restrict__ val, const double *__restrict__ diag,
                                              const double *__restrict__ idiag, const double *__restrict__ b,
                                              const double *xin, double *xout, double *d, double c1, double c2,
-                                             int first, const int32_t *__restrict__ lr, int nl) {
+                                             int flags, const int32_t *__restrict__ lr, int nl) {
+    const bool first = flags & 1, last = flags & 2;
     pdl_trigger();
     if ((int)blockIdx.x < nl) {
         const int row = lr[blockIdx.x];
@@ -298,7 +300,7 @@ __global__ void __launch_bounds__(BS) k_cheb(int n, const int32_t *__restrict__ 
         if (threadIdx.x == 0) {
             const double r = b[row] - (dg * xin[row] + s);
             const double dn = (first ? 0.0 : c1 * d[row]) + c2 * r * id;
-            d[row] = dn;
+            if (!last) d[row] = dn;
             xout[row] = xin[row] + dn;
         }
         return;
@@ -314,7 +316,7 @@ __global__ void __launch_bounds__(BS) k_cheb(int n, const int32_t *__restrict__ 
     if (ok && sub == 0) {
         const double r = b[g] - (dg * xin[g] + s);
         const double dn = (first ? 0.0 : c1 * d[g]) + c2 * r * id;
-        d[g] = dn;
+        if (!last) d[g] = dn;
         xout[g] = xin[g] + dn;
     }
 }
@@ -811,7 +813,8 @@ void launch_op(const Op &op, std::vector<DevLevel> &lv, const Reduce &red, cudaS
 #define GRID_C(T) (unsigned)L.nlong + blocks((int64_t)n * (T))
             TPR_DISPATCH(tpr, k_cheb, GRID_C, n, (const int32_t *)L.rp, (const int32_t *)L.ci, (const double *)L.val,
                          (const double *)L.diag, (const double *)L.idiag, (const double *)L.b, xin, xout, L.d,
-                         L.cheb_c1[k], L.cheb_c2[k], k == 0 ? 1 : 0, (const int32_t *)L.lrows, (int)L.nlong);
+                         L.cheb_c1[k], L.cheb_c2[k], (k == 0 ? 1 : 0) | (k == L.cheb_m - 1 ? 2 : 0),
+                         (const int32_t *)L.lrows, (int)L.nlong);
 #undef GRID_C
             break;
         }

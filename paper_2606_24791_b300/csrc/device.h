@@ -43,7 +43,7 @@ struct DevLevel {
     int gs_tpr = 1, rs_tpr = 1;
     // Chebyshev smoothing (levels with many colours): coefficients of each step, the second
     // iterate buffer and the step direction
-    int cheb = 0;
+    int cheb = 0, cheb_m = 0;    // Chebyshev smoothing on this level, polynomial degree
     double cheb_c1[8] = {0}, cheb_c2[8] = {0};
     double *t = nullptr, *d = nullptr;
     int32_t *sl_ptr = nullptr, *sl_col = nullptr;

@@ -227,6 +227,7 @@ int upload_level(lamg_hier *h, int l) {
         D.pt_tpr = choose_tpr(H.nc ? (double)cnt[H.nc] / (double)H.nc : 1.0);
         if ((rc = dalloc(h, &D.r, n))) return rc;
         D.cheb = H.cheb;
+        D.cheb_m = H.cheb ? h->opt.cheb_degree : 0;
         if (H.cheb) {
             for (int k = 0; k < 8; k++) { D.cheb_c1[k] = H.cheb_c1[k]; D.cheb_c2[k] = H.cheb_c2[k]; }
             if ((rc = dalloc(h, &D.t, n)) || (rc = dalloc(h, &D.d, n))) return rc;
