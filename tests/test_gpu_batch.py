@@ -107,8 +107,13 @@ def test_fp32_cycle_reaches_1e8_and_stays_near_fp64_oracle(make):
     assert st32["relres_true"] <= 2e-8, st32
     H = oracle.Hierarchy(g)
     ref = H.fcg(b, tol=1e-12, maxit=300)
-    err = rel(x32, ref["x"])
-    assert err <= 1e-6, err          # stated FP32-cycle error against the FP64 oracle
+    # stated FP32-cycle error against the FP64 oracle solution: a solve stopped at 1e-8 differs
+    # from the exact solution by up to about cond x 1e-8 in any precision, so this is a norm
+    # bound (1e-6) with a looser entry bound, not a rounding-level parity check
+    d = x32 - ref["x"]
+    err = np.linalg.norm(d) / np.linalg.norm(ref["x"])
+    assert err <= 1e-6, err
+    assert np.abs(d).max() <= 1e-5 * np.abs(ref["x"]).max()
     ref8 = H.fcg(b, tol=1e-8, maxit=300)
     assert st32["iters"] <= ref8["iters"] + 3, (st32["iters"], ref8["iters"])
 
@@ -122,7 +127,9 @@ def test_fp32_batch_matches_fp32_single():
         x1, st1 = P.solve(B[:, j], 1e-8, 200)
         assert sts[j]["relres_true"] <= 2e-8
         assert st1["iters"] == sts[j]["iters"]
-        assert rel(X[:, j], x1) <= 1e-6
+        # two FP32-cycle solves stopped at 1e-8 with other summation orders: a solution-accuracy
+        # bound on the norm
+        assert np.linalg.norm(X[:, j] - x1) <= 1e-6 * np.linalg.norm(x1)
 
 
 @pytest.mark.parametrize("k", [1, 5])

@@ -75,7 +75,8 @@ def test_cheb_setup_matches_oracle_and_solves():
         assert sts[j]["iters"] == stj["iters"] and rel(X[:, j], xj) <= 1e-10
     P32 = lamg.setup(g, precision=lamg.FP32)
     x32, st32 = P32.solve(b, 1e-8, 200)
-    assert st32["relres_true"] <= 2e-8 and rel(x32, ref["x"]) <= 1e-5
+    assert st32["relres_true"] <= 2e-8
+    assert np.linalg.norm(x32 - ref["x"]) <= 1e-5 * np.linalg.norm(ref["x"])   # solution accuracy, FP32 cycle
     P.close()
     P32.close()
 
