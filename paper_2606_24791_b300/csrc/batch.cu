@@ -105,12 +105,28 @@ struct Lanes {
     }
 };
 
+// A row's entries e0, e0 + TPR, ... for column j, accumulated in entry order. Four entries are
+// loaded before their products are added (column ids, values, then the four gathers), so a lane
+// has four independent gathers in flight instead of one; the sum is the same sequence of
+// multiply-adds as a one-entry-at-a-time loop.
 template <typename T, int KL, int TPR>
 __device__ __forceinline__ T rowsum_k(int e0, int e1, int k, int j, const int32_t *__restrict__ ci,
                                       const T *__restrict__ val, const T *x) {
     T s = T(0);
-    if (j < k)
-        for (int e = e0; e < e1; e += TPR) s += val[e] * x[(size_t)ci[e] * k + j];
+    if (j < k) {
+        int e = e0;
+        for (; e + 3 * TPR < e1; e += 4 * TPR) {
+            const int c0 = ci[e], c1 = ci[e + TPR], c2 = ci[e + 2 * TPR], c3 = ci[e + 3 * TPR];
+            const T v0 = val[e], v1 = val[e + TPR], v2 = val[e + 2 * TPR], v3 = val[e + 3 * TPR];
+            const T x0 = x[(size_t)c0 * k + j], x1 = x[(size_t)c1 * k + j];
+            const T x2 = x[(size_t)c2 * k + j], x3 = x[(size_t)c3 * k + j];
+            s += v0 * x0;
+            s += v1 * x1;
+            s += v2 * x2;
+            s += v3 * x3;
+        }
+        for (; e < e1; e += TPR) s += val[e] * x[(size_t)ci[e] * k + j];
+    }
 #pragma unroll
     for (int o = KL; o < KL * TPR; o <<= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     return s;
