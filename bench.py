@@ -382,7 +382,8 @@ def oracle_sample(reps: int, warmup: int = 0) -> dict:
 KERNEL_SOURCES = {
     "k_gs": ("cycle_kernels.cu", ["struct RowPre {", "RowPre row_pre(", "double row_finish(", "double block_row(",
                                   "void __launch_bounds__(BS) k_gs("]),
-    "bk_cheb": ("batch.cu", ["T rowsum_k(", "T block_row_k(", "__global__ void __launch_bounds__(BBS) bk_cheb("]),
+    "bk_cheb": ("batch.cu", ["T rowsum_k(", "T block_row_k(", "__global__ void __launch_bounds__(BBS) bk_cheb(",
+                             "__global__ void bk_copy("]),
 }
 
 
@@ -585,7 +586,7 @@ def run_ours(args, ws, rank, local):
     roofline = {"bound": "alu", "kernel": f"{kname}<double,32,1> ({dom_name}: {dom['launches']} launches, "
                 f"32 columns, {dom_kind})", "achieved": round(dom["tflops"], 4), "peak": FP64_PEAK_TFLOPS,
                 "unit": "TFLOP/s", "frac": round(dom["tflops"] / FP64_PEAK_TFLOPS, 4),
-                "traffic": traffic_for(kname, dom["flops"]),
+                "traffic": traffic_for(kname) if dom_name == "sweep@L2" else None,
                 "algorithmic_flops": dom["flops"], "algorithmic_bytes": dom["bytes"],
                 "launch_ms": round(dom["ms"], 5), "launches_per_unit": dom["launches"],
                 "estimated_share_of_solve": round(share_ms / float(np.mean(step_ms)), 3),

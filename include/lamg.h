@@ -310,7 +310,8 @@ int lamg_profile_cycle(lamg_hier *h, int64_t *out, int64_t cap, int64_t *count);
 /* The static step list of one cycle: 3 int32 per step (kind, level, colour); kinds 0 first
  * GS colour from zero, 1 GS colour class, 2 zero, 3 residual, 4 restriction, 5 prolongation,
  * 6 elimination restriction, 7 elimination interpolation, 8 coarsest solve, 9 Chebyshev
- * smoothing step (colour = step index), 10 copy after a polynomial of odd degree. out may be NULL
+ * smoothing step (colour = step index), 10 copy after a polynomial of odd degree, 11 the first
+ * Chebyshev step of a first visit (from a zero iterate: no product with A). out may be NULL
  * to query *count. Errors: INVALID. */
 int lamg_op_list(const lamg_hier *h, int32_t *out, int64_t cap, int64_t *count);
 

@@ -296,7 +296,7 @@ class Hierarchy:
                     gbs=float(out[1]) / (ms * 1e-3) / 1e9, tflops=float(out[3]) / (ms * 1e-3) / 1e12)
 
     OP_KINDS = ["gs_first", "gs", "zero", "resid", "restrict", "prolong", "elim_restrict",
-                "elim_interp", "coarse", "cheb", "cheb_copy"]
+                "elim_interp", "coarse", "cheb", "cheb_copy", "cheb_first"]
 
     def op_list(self) -> list:
         cnt = C.c_int64()

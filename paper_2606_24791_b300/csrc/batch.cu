@@ -326,6 +326,20 @@ __global__ void __launch_bounds__(BBS) bk_cheb(int n, int k, const int32_t *__re
     }
 }
 
+// First Chebyshev step from x = 0 for k columns (as k_cheb_first): out = (c2 b) / A_uu, and the
+// direction d = out when the polynomial continues.
+template <typename T>
+__global__ void bk_cheb_first(int64_t cnt, int k, const T *__restrict__ idiag, const T *__restrict__ b, T c2,
+                              T *out, T *d) {
+    b_trigger();
+    b_wait();
+    const int64_t t = (int64_t)blockIdx.x * BBS + threadIdx.x;
+    if (t >= cnt) return;
+    const T v = c2 * b[t] * idiag[t / k];
+    out[t] = v;
+    if (d) d[t] = v;
+}
+
 template <typename T>
 __global__ void bk_copy(int64_t cnt, const T *__restrict__ src, T *dst) {
     b_trigger();
@@ -1048,6 +1062,10 @@ static void bop(const Op &op, BatchCtx *c, cudaStream_t s, const Op *start) {
         }
         case OP_CHEB_COPY:
             blaunch(bk_copy<T>, nblocks((int64_t)n * k), s, (int64_t)n * k, (const T *)L.t, x);
+            break;
+        case OP_CHEB_FIRST:
+            blaunch(bk_cheb_first<T>, nblocks((int64_t)n * k), s, (int64_t)n * k, k, idiag, (const T *)b,
+                    (T)L.cheb_c2[0], L.cheb_m > 1 ? (T *)L.t : x, L.cheb_m > 1 ? (T *)L.d : (T *)nullptr);
             break;
     }
 }

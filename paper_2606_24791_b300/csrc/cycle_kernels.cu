@@ -321,6 +321,19 @@ __global__ void __launch_bounds__(BS) k_cheb(int n, const int32_t *__restrict__ 
     }
 }
 
+// First Chebyshev step from x = 0: out = (c2 b) / A_uu as the reciprocal product of k_cheb with
+// r = b (the step's direction d = out is stored when the polynomial continues).
+__global__ void k_cheb_first(int n, const double *__restrict__ idiag, const double *__restrict__ b, double c2,
+                             double *out, double *d) {
+    pdl_trigger();
+    pdl_wait();
+    const int i = blockIdx.x * BS + threadIdx.x;
+    if (i >= n) return;
+    const double v = c2 * b[i] * idiag[i];
+    out[i] = v;
+    if (d) d[i] = v;
+}
+
 __global__ void k_copy(int n, const double *__restrict__ src, double *dst) {
     pdl_trigger();
     pdl_wait();
@@ -820,6 +833,10 @@ void launch_op(const Op &op, std::vector<DevLevel> &lv, const Reduce &red, cudaS
         }
         case OP_CHEB_COPY:
             launch(k_copy, blocks(n), s, n, (const double *)L.t, L.x);
+            break;
+        case OP_CHEB_FIRST:
+            launch(k_cheb_first, blocks(n), s, n, (const double *)L.idiag, (const double *)L.b, L.cheb_c2[0],
+                   L.cheb_m > 1 ? L.t : L.x, L.cheb_m > 1 ? L.d : (double *)nullptr);
             break;
     }
 }

@@ -78,6 +78,8 @@ enum OpKind {
     OP_COARSE,        // x = A^+ b, then the mean-zero projection
     OP_CHEB,          // step `colour` of the Chebyshev smoothing polynomial (x <-> t alternate)
     OP_CHEB_COPY,     // x = t (after a polynomial of odd degree)
+    OP_CHEB_FIRST,    // the first Chebyshev step from x == 0 (first visit): no product with A,
+                      // out = c2[0] b / d into x (degree 1) or into t and d (degree > 1)
 };
 
 struct Op {

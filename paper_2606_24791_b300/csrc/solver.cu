@@ -298,8 +298,19 @@ void emit_visit(lamg_hier *h, std::vector<int64_t> &visits, int l, bool first) {
         if (m & 1) h->ops.push_back({OP_CHEB_COPY, l, 0});
     };
     if (D.cheb) {
-        if (first) h->ops.push_back({OP_ZERO, l, 0});
-        for (int s = 0; s < npre; s++) cheb_poly();
+        // a first visit starts from x = 0, so the first step of the first polynomial needs no
+        // product with A: x1 = c2[0] D^-1 b (the same operations as that step with x = 0)
+        const int m = h->opt.cheb_degree;
+        if (first && npre == 0) h->ops.push_back({OP_ZERO, l, 0});
+        for (int s = 0; s < npre; s++) {
+            if (s == 0 && first) {
+                h->ops.push_back({OP_CHEB_FIRST, l, 0});
+                for (int k = 1; k < m; k++) h->ops.push_back({OP_CHEB, l, k});
+                if (m > 1 && (m & 1)) h->ops.push_back({OP_CHEB_COPY, l, 0});
+            } else {
+                cheb_poly();
+            }
+        }
     } else {
         if (first && npre == 0) h->ops.push_back({OP_ZERO, l, 0});
         for (int s = 0; s < npre; s++) {
@@ -413,6 +424,7 @@ void lamg::op_bytes(const lamg_hier *h, const Op &op, double s, double *mat, dou
         case OP_COARSE: m = 8 * n * n; v = 2 * s * n; break;
         case OP_CHEB: m = (4 + s) * z + 4 * (n + 1) + 2 * s * n; v = s * (n + std::min(z, n)) + 3 * s * n; break;
         case OP_CHEB_COPY: v = 2 * s * n; break;
+        case OP_CHEB_FIRST: m = s * n; v = (h->opt.cheb_degree > 1 ? 3 : 2) * s * n; break;
     }
     *mat = m;
     *vec = v;
