@@ -53,8 +53,10 @@ class CopyPool {
 
   private:
     CopyPool() {
-        const unsigned hw = std::max(2u, std::thread::hardware_concurrency());
-        const int n = (int)std::min(7u, hw / 2);
+        // one thread per four hardware threads, at most 16 copying threads in all: a host
+        // memcpy runs at ~5-10 GB/s per thread, so a dozen or so keep up with the link
+        const unsigned hw = std::max(4u, std::thread::hardware_concurrency());
+        const int n = (int)std::min(15u, hw / 4);
         for (int i = 0; i < n; i++) workers_.emplace_back([this, i] { loop(i + 1); });
         for (auto &t : workers_) t.detach();   // process-lifetime pool
     }
