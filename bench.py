@@ -209,9 +209,9 @@ def profile_sweep(level: int):
 
 
 def profile_batch(spec: str):
-    """One cold-L2 32-column kernel sequence on a Chung-Lu graph of N nodes (the workload's
-    generator at a size whose device memory suits a full ncu capture)."""
-    import torch
+    """One cold-L2 32-column kernel sequence on a Chung-Lu graph of N nodes from the workload's
+    generator: a small N for multi-pass captures (a few GB on the device), N = 4,000,000 (the
+    workload itself) for one-pass counters."""
     import graphgen as gg
     import paper_2606_24791_b300 as lamg
     n, level, which = spec.split(":")

@@ -1266,7 +1266,6 @@ int solve_batch_impl(lamg_hier *h, int k, const double *B, double *PHI, const la
 template <typename T>
 static int time_batch(lamg_hier *h, BatchCtx *c, int which, int level, int reps, double *out) {
     const DevLevel &D = h->dev[level];
-    BLev &L = c->lv[level];
     const double n = (double)D.n, z = (double)D.nnz, k = (double)c->k, sz = (double)sizeof(T);
     std::vector<Op> seq;
     double bytes = 0.0, flops = 0.0;
@@ -1321,7 +1320,6 @@ static int time_batch(lamg_hier *h, BatchCtx *c, int which, int level, int reps,
         cudaEventElapsedTime(&ms, h->ev_a, h->ev_b);
         total += ms;
     }
-    (void)L;
     cudaFree(flush);
     if (rc) return rc;
     CKR(cudaGetLastError());
