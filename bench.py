@@ -58,7 +58,7 @@ def parse():
     ap.add_argument("--serve", action="store_true", help="run the serving workload instead")
     ap.add_argument("--profile-cycle", action="store_true",
                     help="per-step timing of one persistent-kernel cycle of the aniso1024 workload")
-    ap.add_argument("--solve-once", default=None, choices=["main", "main-fp32", "aniso1024"],
+    ap.add_argument("--solve-once", default=None, choices=["main", "main-fp32", "aniso1024", "aniso1024-fp32"],
                     help="set up the named workload and run one solve, nothing else (for a launch-list capture)")
     ap.add_argument("--serve-requests", type=int, default=200)
     ap.add_argument("--serve-max-n", type=int, default=200000)
@@ -180,9 +180,9 @@ def solve_once(which: str):
     profiler run over this process is the setup kernels followed by one solve."""
     import torch
     import paper_2606_24791_b300 as lamg
-    if which == "aniso1024":
+    if which in ("aniso1024", "aniso1024-fp32"):
         g, b = aniso_workload()
-        P = lamg.setup(g)
+        P = lamg.setup(g, precision=lamg.FP32 if which == "aniso1024-fp32" else lamg.FP64)
         bt = torch.from_numpy(b).cuda()
         xt = torch.zeros_like(bt)
         sts = [P.solve_ptr(bt.data_ptr(), xt.data_ptr(), TOL, 200)]
@@ -382,8 +382,7 @@ def oracle_sample(reps: int, warmup: int = 0) -> dict:
 KERNEL_SOURCES = {
     "k_gs": ("cycle_kernels.cu", ["struct RowPre {", "RowPre row_pre(", "double row_finish(", "double block_row(",
                                   "void __launch_bounds__(BS) k_gs("]),
-    "bk_cheb": ("batch.cu", ["T rowsum_k(", "T block_row_k(", "__global__ void __launch_bounds__(BBS) bk_cheb(",
-                             "__global__ void bk_copy("]),
+    "bk_cheb": ("batch.cu", ["T rowsum_k(", "T block_row_k(", "__global__ void __launch_bounds__(BBS) bk_cheb("]),
 }
 
 
@@ -552,18 +551,28 @@ def run_ours(args, ws, rank, local):
         e2e_units += sum(g.nnz_L * digits(c["relres_true"]) for c in sth)
 
     # roofline of the dominant kernel: cold-L2 time of each candidate sequence alone, weighted by
-    # how often a solve runs it; per level the same figures (the levels table)
+    # how often a solve runs it (the cycle's static step list times the iterations); per level
+    # the same figures (the levels table)
     visits = schedule_counts(P, iters[0])
     o = lamg.options()
     nsweeps = o.nu_pre + o.nu_post
     cand, levels = [], []
-    cheb_levels = {lv for kind, lv, _ in P.op_list() if kind == "cheb"}
+    per_cycle = {}
+    for kind, lv, _ in P.op_list():
+        per_cycle[(kind, lv)] = per_cycle.get((kind, lv), 0) + 1
+    cheb_levels = {lv for kind, lv in per_cycle if kind == "cheb"}
     for l, L in enumerate(P.info):
         if L["kind"] != "agg":
             continue
         sw = P.time_kernel_batch("sweep", l, K_RHS, reps=3)
         rs = P.time_kernel_batch("resid", l, K_RHS, reps=3)
         smoother = "chebyshev" if l in cheb_levels else "gauss-seidel"
+        if l in cheb_levels:
+            # one Chebyshev step (bk_cheb alone) as the unit: a cycle runs per_cycle of them here
+            cs = P.time_kernel_batch("cheb_step", l, K_RHS, reps=3)
+            cand.append((cs["ms"] * per_cycle[("cheb", l)] * iters[0], f"cheb_step@L{l}", cs, smoother))
+        else:
+            cand.append((sw["ms"] * nsweeps * visits[l] * iters[0], f"sweep@L{l}", sw, smoother))
         op_bytes = 12 * L["nnz"] + 20 * L["n"]
         vec_bytes = 3 * 8 * K_RHS * L["n"]
         levels.append({"level": l, "n": L["n"], "nnz": L["nnz"], "colours": L["ncol"], "smoother": smoother,
@@ -572,7 +581,12 @@ def run_ours(args, ws, rank, local):
                        "sweep_gbs": round(sw["gbs"], 1), "resid_ms": round(rs["ms"], 4),
                        "resid_tflops": round(rs["tflops"], 3), "resid_gbs": round(rs["gbs"], 1),
                        "l2_resident": op_bytes + vec_bytes <= 126e6})
-        cand.append((sw["ms"] * nsweeps * visits[l] * iters[0], f"sweep@L{l}", sw, smoother))
+        if l in cheb_levels:
+            levels[-1].update({"cheb_steps_per_cycle": per_cycle[("cheb", l)],
+                               "first_steps_per_cycle": per_cycle.get(("cheb_first", l), 0),
+                               "copies_per_cycle": per_cycle.get(("cheb_copy", l), 0),
+                               "cheb_step_ms": round(cs["ms"], 4), "cheb_step_tflops": round(cs["tflops"], 3),
+                               "cheb_step_gbs": round(cs["gbs"], 1)})
         cand.append((rs["ms"] * visits[l] * iters[0], f"resid@L{l}", rs, "residual"))
     sp = P.time_kernel_batch("spmv_dot", 0, K_RHS, reps=3)
     cand.append((sp["ms"] * iters[0], "spmv_dot@L0", sp, "outer CG product"))
@@ -586,7 +600,7 @@ def run_ours(args, ws, rank, local):
     roofline = {"bound": "alu", "kernel": f"{kname}<double,32,1> ({dom_name}: {dom['launches']} launches, "
                 f"32 columns, {dom_kind})", "achieved": round(dom["tflops"], 4), "peak": FP64_PEAK_TFLOPS,
                 "unit": "TFLOP/s", "frac": round(dom["tflops"] / FP64_PEAK_TFLOPS, 4),
-                "traffic": traffic_for(kname) if dom_name == "sweep@L2" else None,
+                "traffic": traffic_for(kname) if dom_name == "cheb_step@L2" else None,
                 "algorithmic_flops": dom["flops"], "algorithmic_bytes": dom["bytes"],
                 "launch_ms": round(dom["ms"], 5), "launches_per_unit": dom["launches"],
                 "estimated_share_of_solve": round(share_ms / float(np.mean(step_ms)), 3),

@@ -84,16 +84,19 @@ typedef struct lamg_options {
                               persistent solve kernel (no grid barrier per step): 8192 */
     int32_t cluster_rows;  /* graph path: a visit of the first level from which on every level
                               has at most this many rows, with all its sub-visits, runs as one
-                              launch of a thread-block cluster. 0 (default): chosen at setup by
+                              launch of a thread-block cluster (a dense coarsest solve larger
+                              than 512 x 512 stays a launch over the whole GPU, between two
+                              cluster launches). 0 (default): chosen at setup by
                               timing one cycle of each candidate and of the per-step schedule
                               when autotune is 1, else off; < 0: off. Results are bit-identical
                               whatever the choice. */
     int32_t row_tpr;       /* lanes per CSR row in the operator kernels: 0 (default) picks per
                               level from the mean row length; 1, 2, 4, ..., 32 forces it */
     int32_t sell;          /* operator kernels: 0 (default) one thread per row on a sliced
-                              ELLPACK copy (32-row slices) where rows have at most 64 entries and
-                              padding adds at most 50%, else lane groups on CSR; 1 sliced ELLPACK
-                              wherever rows have at most 64 entries; -1 CSR only */
+                              ELLPACK copy (32-row slices, rows padded to a multiple of four
+                              entries, read with 16-byte loads) where rows have at most 64
+                              entries and padding adds at most 50%, else lane groups on CSR; 1
+                              sliced ELLPACK wherever rows have at most 64 entries; -1 CSR only */
     int32_t autotune;      /* 1: setup times the kernel form of each level's sweep and residual
                               (lanes per row, or one thread per row) and, with cluster_rows = 0,
                               the cluster schedule; 0 (default): rules only (measured within
@@ -273,7 +276,8 @@ int lamg_time_kernel(lamg_hier *h, int32_t which, int32_t level, int32_t reps, d
  * stream, each after a 256 MB device write that evicts the L2, timed with CUDA events. which: 0
  * residual at an aggregation level, 1 one smoothing sweep at an aggregation level (all colour
  * classes of Gauss-Seidel, or the degree-m Chebyshev polynomial on levels with many colours),
- * 2 the outer CG product A p with its dot products (level 0, FP64). 1 <= k <= 32.
+ * 2 the outer CG product A p with its dot products (level 0, FP64), 3 one step of the Chebyshev
+ * polynomial alone (Chebyshev levels only). 1 <= k <= 32.
  * out[0] = mean device ms per launch sequence, out[1] = its algorithmic DRAM bytes (operator once,
  * each vector once per column), out[2] = kernels per sequence, out[3] = its algorithmic flops (a
  * multiply-add per stored entry and column, plus per-row arithmetic). No counterpart in the
@@ -310,9 +314,11 @@ int lamg_profile_cycle(lamg_hier *h, int64_t *out, int64_t cap, int64_t *count);
 /* The static step list of one cycle: 3 int32 per step (kind, level, colour); kinds 0 first
  * GS colour from zero, 1 GS colour class, 2 zero, 3 residual, 4 restriction, 5 prolongation,
  * 6 elimination restriction, 7 elimination interpolation, 8 coarsest solve, 9 Chebyshev
- * smoothing step (colour = step index), 10 copy after a polynomial of odd degree, 11 the first
- * Chebyshev step of a first visit (from a zero iterate: no product with A). out may be NULL
- * to query *count. Errors: INVALID. */
+ * smoothing step (colour = step index within its polynomial, + 256 when it reads the level's
+ * second buffer instead of the iterate), 10 copy of the second buffer into the iterate after an
+ * odd number of steps, 11 the first Chebyshev step of a first visit (from a zero iterate: no
+ * product with A; colour 1 when it writes the second buffer). out may be NULL to query *count.
+ * Errors: INVALID. */
 int lamg_op_list(const lamg_hier *h, int32_t *out, int64_t cap, int64_t *count);
 
 /* The launch schedule of the graph path (no counterpart in the paper: it records how the
@@ -364,7 +370,8 @@ int lamg_solve_many(int32_t G, lamg_hier *const *hs, const double *const *b, dou
                     const lamg_solve_opts *so, lamg_stats *st);
 
 /* Per-step device time of one cycle (r = 0) with the steps on levels >= from_level run as
- * cluster launches (from_level < 0: none), outside any graph: out receives 3 int64 per step
+ * cluster launches as cluster_rows forms them (from_level < 0: none), outside any graph: out
+ * receives 3 int64 per step
  * (step index, 1 if the step ran inside a cluster launch, nanoseconds). A step inside a
  * cluster is timed by %globaltimer in its first CTA, from before the step to after the
  * barrier that ends it; any other step by CUDA events around its own launch (no overlap with

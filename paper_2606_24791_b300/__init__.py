@@ -283,7 +283,7 @@ class Hierarchy:
         return dict(ms=float(out[0]), bytes=float(out[1]), launches=int(out[2]),
                     gbs=float(out[1]) / (float(out[0]) * 1e-3) / 1e9)
 
-    BATCH_KERNELS = {"resid": 0, "sweep": 1, "spmv_dot": 2}
+    BATCH_KERNELS = {"resid": 0, "sweep": 1, "spmv_dot": 2, "cheb_step": 3}
 
     def time_kernel_batch(self, which: str, level: int, k: int, reps: int = 5) -> dict:
         """Cold-L2 device time of one k-column kernel sequence (``BATCH_KERNELS``), its

@@ -43,6 +43,32 @@ struct BRed {
 
 // ------------------------------------------------------------------ per-column reductions
 
+// Column totals over the block: the value v of thread t belongs to column t % KL. The lanes of a
+// warp that share a column are added by a fixed shuffle tree (none when KL = 32), then the warps
+// in order; thread j < KL returns with column j's total. sh is the caller's NV x BBS scratch.
+template <int KL, int NV>
+__device__ __forceinline__ void block_col_total(double (&v)[NV], double (*sh)[BBS]) {
+#pragma unroll
+    for (int o = 16; o >= KL; o >>= 1)
+#pragma unroll
+        for (int q = 0; q < NV; q++) v[q] += __shfl_xor_sync(0xffffffffu, v[q], o);
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    __syncthreads();   // the scratch may still be read by a previous use
+    if (lane < KL) {
+#pragma unroll
+        for (int q = 0; q < NV; q++) sh[q][w * KL + lane] = v[q];
+    }
+    __syncthreads();
+    if ((int)threadIdx.x < KL) {
+#pragma unroll
+        for (int q = 0; q < NV; q++) {
+            double s = 0.0;
+            for (int ww = 0; ww < BBS / 32; ww++) s += sh[q][ww * KL + threadIdx.x];
+            v[q] = s;
+        }
+    }
+}
+
 // Each thread contributes to column threadIdx.x % KL. Deterministic: per-block column sums in a
 // fixed order, then the last block to finish adds the blocks in a fixed order. Returns true in
 // the last block, where threads j < KL hold column j's totals.
@@ -51,16 +77,10 @@ __device__ bool col_sum(double (&v)[NV], const BRed R) {
     __shared__ double sh[NV][BBS];
     __shared__ bool last;
     __threadfence();
+    block_col_total<KL, NV>(v, sh);
+    if ((int)threadIdx.x < KL) {
 #pragma unroll
-    for (int q = 0; q < NV; q++) sh[q][threadIdx.x] = v[q];
-    __syncthreads();
-    if (threadIdx.x < KL) {
-#pragma unroll
-        for (int q = 0; q < NV; q++) {
-            double s = 0.0;
-            for (int m = threadIdx.x; m < BBS; m += KL) s += sh[q][m];
-            R.part[(q * KMAX + threadIdx.x) * RED_MAXG + blockIdx.x] = s;
-        }
+        for (int q = 0; q < NV; q++) R.part[(q * KMAX + threadIdx.x) * RED_MAXG + blockIdx.x] = v[q];
         __threadfence();
     }
     __syncthreads();
@@ -68,24 +88,16 @@ __device__ bool col_sum(double (&v)[NV], const BRed R) {
     __syncthreads();
     if (!last) return false;
     __threadfence();
-    // threads t = j + KL * m sum blocks m, m + BBS/KL, ... of column j; then fixed-order combine
+    // threads t = j + KL * m sum blocks m, m + BBS/KL, ... of column j; then the block total
     constexpr int PER = BBS / KL;
     const int j = threadIdx.x % KL, m = threadIdx.x / KL;
 #pragma unroll
     for (int q = 0; q < NV; q++) {
         double s = 0.0;
         for (int b = m; b < (int)gridDim.x; b += PER) s += __ldcg(&R.part[(q * KMAX + j) * RED_MAXG + b]);
-        sh[q][threadIdx.x] = s;
+        v[q] = s;
     }
-    __syncthreads();
-    if (threadIdx.x < KL) {
-#pragma unroll
-        for (int q = 0; q < NV; q++) {
-            double s = 0.0;
-            for (int mm = 0; mm < PER; mm++) s += sh[q][threadIdx.x + KL * mm];
-            v[q] = s;
-        }
-    }
+    block_col_total<KL, NV>(v, sh);
     if (threadIdx.x == 0) *R.ticket = 0u;
     return true;
 }
@@ -221,30 +233,30 @@ __global__ void __launch_bounds__(BBS) bk_resid(int n, int k, const int32_t *__r
     }
 }
 
-// One right-hand side, one thread per row on the sliced-ELLPACK copy (entry j of row 32 s + l
-// at sp[s] + 32 j + l, value-0 padding at a valid column); entries summed in order.
+// One right-hand side, one thread per row on the sliced-ELLPACK copy in four-entry blocks
+// (sell_col_at / sell_val_at: four column ids in one int4, the values two at a time); entries
+// summed in order, padding (value 0 at a valid column) included.
+template <typename T> struct Pair;
+template <> struct Pair<double> { using V = double2; };
+template <> struct Pair<float> { using V = float2; };
+
 template <typename T>
 __device__ __forceinline__ T sell_row1(int row, const int32_t *__restrict__ sp, const int32_t *__restrict__ sc,
-                                       const T *__restrict__ sv, const T *x, int &e, int &w) {
-    const int s = row >> 5;
+                                       const T *__restrict__ sv, const T *x) {
+    using V = typename Pair<T>::V;
+    const int s = row >> 5, l = row & 31;
     const int a = sp[s];
-    e = a + (row & 31);
-    w = (sp[s + 1] - a) >> 5;
+    const int nq = (sp[s + 1] - a) >> 7;
     T acc = T(0);
-    for (int j = 0; j < w; j += 4) {
-        int c[4];
-        T v[4], xv[4];
-#pragma unroll
-        for (int q = 0; q < 4; q++) {
-            const bool h = j + q < w;
-            c[q] = h ? sc[e + 32 * (j + q)] : 0;
-            v[q] = h ? sv[e + 32 * (j + q)] : T(0);
-        }
-#pragma unroll
-        for (int q = 0; q < 4; q++) xv[q] = j + q < w ? x[c[q]] : T(0);
-#pragma unroll
-        for (int q = 0; q < 4; q++)
-            if (j + q < w) acc += v[q] * xv[q];
+    for (int q = 0; q < nq; q++) {
+        const int4 c = __ldg(reinterpret_cast<const int4 *>(sc + a + 128 * q + 4 * l));
+        const V va = __ldg(reinterpret_cast<const V *>(sv + a + 128 * q + 2 * l));
+        const V vb = __ldg(reinterpret_cast<const V *>(sv + a + 128 * q + 64 + 2 * l));
+        const T x0 = x[c.x], x1 = x[c.y], x2 = x[c.z], x3 = x[c.w];
+        acc += va.x * x0;
+        acc += va.y * x1;
+        acc += vb.x * x2;
+        acc += vb.y * x3;
     }
     return acc;
 }
@@ -259,8 +271,7 @@ __global__ void __launch_bounds__(64) bk_gs_sell(int r0, int r1, int s0, const i
     const T id = ok ? idiag[row] : T(1);
     b_wait();
     if (!ok) return;
-    int e, w;
-    const T s = sell_row1<T>(row, sp, sc, sv, x, e, w);
+    const T s = sell_row1<T>(row, sp, sc, sv, x);
     x[row] = (b[row] - s) * id;
 }
 
@@ -275,8 +286,7 @@ __global__ void __launch_bounds__(BBS) bk_resid_sell(int n, const int32_t *__res
     const T d = ok ? diag[row] : T(0);
     b_wait();
     if (!ok) return;
-    int e, w;
-    const T s = sell_row1<T>(row, sp, sc, sv, x, e, w);
+    const T s = sell_row1<T>(row, sp, sc, sv, x);
     r[row] = b[row] - (d * x[row] + s);
 }
 
@@ -463,14 +473,14 @@ __global__ void bk_elim_interp(int nc, int nF, int k, const int32_t *__restrict_
 }
 
 // Coarsest level: x = (I - J/n) A^+ b against the FP64 projected pseudo-inverse, accumulated in
-// FP64 for either cycle type (an FP32 cycle's right-hand side is widened, the FP64 sum rounded
-// to FP32 once at the end). One block per row: KL lanes per column times BBS/KL lanes splitting
+// FP64 for either cycle type (b in FP64: an FP32 cycle's right-hand side widened beforehand; the
+// FP64 sum rounded to FP32 once at the end). One block per row: KL lanes per column times BBS/KL lanes splitting
 // the row, each lane with four independent partial sums (a dependent FP64 add takes ~68 clocks
 // on this GPU, so one chain of n/2 adds per lane would set the kernel's time), combined in a
 // fixed order: the four partials, the lanes of a warp by a shuffle tree, then the warps in order.
 template <typename T, int KL>
 __global__ void __launch_bounds__(BBS) bk_coarse(int n, int k, const double *__restrict__ pinv,
-                                                 const T *__restrict__ b, T *x) {
+                                                 const double *__restrict__ b, T *x) {
     b_trigger();
     b_wait();
     __shared__ double sh[BBS / 32][32];
@@ -483,12 +493,12 @@ __global__ void __launch_bounds__(BBS) bk_coarse(int n, int k, const double *__r
         if (j < k) {
             int c = m;
             for (; c + 3 * M < n; c += 4 * M) {
-                s0 += row[c] * (double)b[(size_t)c * k + j];
-                s1 += row[c + M] * (double)b[(size_t)(c + M) * k + j];
-                s2 += row[c + 2 * M] * (double)b[(size_t)(c + 2 * M) * k + j];
-                s3 += row[c + 3 * M] * (double)b[(size_t)(c + 3 * M) * k + j];
+                s0 += row[c] * b[(size_t)c * k + j];
+                s1 += row[c + M] * b[(size_t)(c + M) * k + j];
+                s2 += row[c + 2 * M] * b[(size_t)(c + 2 * M) * k + j];
+                s3 += row[c + 3 * M] * b[(size_t)(c + 3 * M) * k + j];
             }
-            for (; c < n; c += M) s0 += row[c] * (double)b[(size_t)c * k + j];
+            for (; c < n; c += M) s0 += row[c] * b[(size_t)c * k + j];
         }
         double s = (s0 + s1) + (s2 + s3);
 #pragma unroll
@@ -625,6 +635,28 @@ __global__ void __launch_bounds__(BBS) bk_spmv_dot(int n, int k, const int32_t *
         const int c = threadIdx.x;
         const double rz = R.sk[B_RZ * KMAX + c];
         R.sk[B_ALPHA * KMAX + c] = (R.done[c] || pq[0] == 0.0) ? 0.0 : rz / pq[0];
+    }
+}
+
+// One right-hand side on a level with the sliced copy: q = A p one thread per row (as
+// k_spmv_dot_sell), alpha = r.z / (p . q).
+__global__ void __launch_bounds__(BBS) bk_spmv_dot_sell(int n, const int32_t *__restrict__ sp,
+                                                        const int32_t *__restrict__ sc,
+                                                        const double *__restrict__ sv,
+                                                        const double *__restrict__ diag,
+                                                        const double *__restrict__ p, double *q, const BRed R) {
+    b_trigger();
+    b_wait();
+    double pq[1] = {0.0};
+    for (int row = blockIdx.x * BBS + threadIdx.x; row < n; row += gridDim.x * BBS) {
+        const double s = sell_row1<double>(row, sp, sc, sv, p);
+        const double qi = diag[row] * p[row] + s;
+        q[row] = qi;
+        pq[0] += p[row] * qi;
+    }
+    if (col_sum<1, 1>(pq, R) && threadIdx.x == 0) {
+        const double rz = R.sk[B_RZ * KMAX];
+        R.sk[B_ALPHA * KMAX] = (R.done[0] || pq[0] == 0.0) ? 0.0 : rz / pq[0];
     }
 }
 
@@ -831,6 +863,7 @@ struct BLev {
     const void *val = nullptr, *diag = nullptr, *wt = nullptr, *pt_w = nullptr, *pf_val = nullptr,
                *dF = nullptr, *pft_val = nullptr;
     const double *pinv = nullptr;  // coarsest (I - J/n) A^+, FP64 for either cycle type
+    double *b64 = nullptr;         // coarsest, FP32 cycle: the right-hand side widened to FP64
     void *x = nullptr, *b = nullptr, *r = nullptr;
 };
 
@@ -935,6 +968,7 @@ static int build_ctx(lamg_hier *h, BatchCtx *c) {
             x = (T *)c->lv[l - 1].x;
         }
         if (B.kind == KIND_AGG && (rc = dalloc(h, &r, B.n * k))) return rc;
+        if (B.kind == KIND_COARSEST && c->prec == LAMG_FP32 && (rc = dalloc(h, &B.b64, B.n * k))) return rc;
         B.x = x; B.b = b; B.r = r;
         if (B.cheb) {
             T *tt = nullptr, *dd = nullptr;
@@ -1044,15 +1078,25 @@ static void bop(const Op &op, BatchCtx *c, cudaStream_t s, const Op *start) {
 #undef C7
             break;
         }
-        case OP_COARSE:
-#define C8(KLv, ...) case KLv: blaunch(bk_coarse<T, KLv>, std::min<int64_t>(n, 148 * 8), s, n, k, L.pinv, (const T *)b, x); break;
+        case OP_COARSE: {
+            // an FP32 cycle's right-hand side is widened once (n k conversions) instead of at
+            // every product: FP64 conversions share the FP64 pipe with the n^2 k multiply-adds
+            const double *b64 = (const double *)b;
+            if (sizeof(T) != sizeof(double)) {
+                blaunch(bk_cast<T, double>, nblocks((int64_t)n * k), s, (int64_t)n * k, (const T *)b, L.b64);
+                b64 = L.b64;
+            }
+#define C8(KLv, ...) case KLv: blaunch(bk_coarse<T, KLv>, std::min<int64_t>(n, 148 * 8), s, n, k, L.pinv, b64, x); break;
             switch (KL) { K_CASES(C8) }
 #undef C8
             break;
+        }
         case OP_CHEB: {
-            const int q = op.colour;
-            const T *xin = (q & 1) ? (const T *)L.t : (const T *)x;
-            T *xout = (q & 1) ? x : (T *)L.t;
+            // colour: step index within the polynomial, + 256 when the step reads t
+            const int q = op.colour & 255;
+            const bool from_t = op.colour >= 256;
+            const T *xin = from_t ? (const T *)L.t : (const T *)x;
+            T *xout = from_t ? x : (T *)L.t;
             const int tpr = row_tpr(KL, L.tpr);
             const T c1 = (T)L.cheb_c1[q], c2 = (T)L.cheb_c2[q];
 #define C11(KLv, TPRv, ...) case KT_CODE(KLv, TPRv): blaunch(bk_cheb<T, KLv, TPRv>, L.nlong + nblocks((int64_t)n * KLv * TPRv), s, n, k, L.rp, L.ci, val, diag, idiag, (const T *)b, xin, xout, (T *)L.d, c1, c2, (q == 0 ? 1 : 0) | (q == L.cheb_m - 1 ? 2 : 0), L.lrows, (int)L.nlong); break;
@@ -1065,7 +1109,7 @@ static void bop(const Op &op, BatchCtx *c, cudaStream_t s, const Op *start) {
             break;
         case OP_CHEB_FIRST:
             blaunch(bk_cheb_first<T>, nblocks((int64_t)n * k), s, (int64_t)n * k, k, idiag, (const T *)b,
-                    (T)L.cheb_c2[0], L.cheb_m > 1 ? (T *)L.t : x, L.cheb_m > 1 ? (T *)L.d : (T *)nullptr);
+                    (T)L.cheb_c2[0], op.colour ? (T *)L.t : x, L.cheb_m > 1 ? (T *)L.d : (T *)nullptr);
             break;
     }
 }
@@ -1083,6 +1127,11 @@ static void bop(const Op &op, BatchCtx *c, cudaStream_t s, const Op *start) {
 static void cg_spmv_dot(lamg_hier *h, BatchCtx *c, cudaStream_t s) {
     const DevLevel &F = h->dev[0];
     const int n = (int)F.n, k = c->k;
+    if (c->KL == 1 && F.rs_tpr == 0) {
+        blaunch(bk_spmv_dot_sell, rblocks(n), s, n, (const int32_t *)F.sl_ptr, (const int32_t *)F.sl_col,
+                (const double *)F.sl_val, (const double *)F.diag, (const double *)c->p, c->q, c->red);
+        return;
+    }
     const int tpr = row_tpr(c->KL, F.tpr);
 #define C9(KLv, TPRv, ...) case KT_CODE(KLv, TPRv): blaunch(bk_spmv_dot<KLv, TPRv>, rblocks((int64_t)n * KLv * TPRv), s, n, k, F.rp, F.ci, (const double *)F.val, (const double *)F.diag, (const double *)c->p, c->q, c->red, (const int32_t *)F.lrows, (int)F.nlong); break;
     switch (KT_CODE(c->KL, tpr)) { KT_CASES(C9) }
@@ -1260,7 +1309,7 @@ int solve_batch_impl(lamg_hier *h, int k, const double *B, double *PHI, const la
 // Cold-L2 device time of one k-column kernel of the cycle or the outer CG (lamg_time_kernel_batch):
 // which 0 residual at an aggregation level, 1 one smoothing sweep at an aggregation level (every
 // colour class of Gauss-Seidel, or the cheb_degree steps of the Chebyshev polynomial), 2 the outer
-// CG product q = A p with its dots (level 0, FP64). Algorithmic bytes count each operator array
+// CG product q = A p with its dots (level 0, FP64), 3 one Chebyshev step (Chebyshev levels). Algorithmic bytes count each operator array
 // once, each vector once per column (a gathered vector at most once per launch); flops count one
 // multiply-add (2 flops) per stored entry and column plus the per-row arithmetic.
 template <typename T>
@@ -1273,14 +1322,21 @@ static int time_batch(lamg_hier *h, BatchCtx *c, int which, int level, int reps,
         seq.push_back({OP_RESID, level, 0});
         bytes = (4 + sz) * z + 4 * (n + 1) + sz * n + k * sz * 3 * n;
         flops = k * (2 * z + 4 * n);
-    } else if (which == 1 && D.cheb) {
-        const int m = h->opt.cheb_degree;
-        for (int q = 0; q < m; q++) {
-            seq.push_back({OP_CHEB, level, q});
-            bytes += (4 + sz) * z + 4 * (n + 1) + 2 * sz * n + k * sz * ((q ? 5 : 4) * n);
-            flops += k * (2 * z + (q ? 9 : 7) * n);
+    } else if ((which == 1 || which == 3) && D.cheb) {
+        // which 1: one polynomial from x back into x (steps alternate x -> t -> x ..., a copy
+        // t -> x after an odd count); which 3: its first step alone (bk_cheb, x -> t). Per row
+        // and column a step reads b and the iterate (its own entry and the gathered ones count
+        // once) and writes the new iterate, reads the direction d after the first step and
+        // writes it before the last; flops: the product (2 per entry), r = b - (A_uu x + s) (3),
+        // d = c1 d + c2 r / A_uu (2 on the first step, 4 after it), x + d (1).
+        const int m = h->opt.cheb_degree, steps = which == 3 ? 1 : m;
+        for (int q = 0; q < steps; q++) {
+            seq.push_back({OP_CHEB, level, q + 256 * (q & 1)});
+            const double vecs = 3 + (q > 0 ? 1 : 0) + (q < m - 1 ? 1 : 0);
+            bytes += (4 + sz) * z + 4 * (n + 1) + 2 * sz * n + k * sz * vecs * n;
+            flops += k * (2 * z + (q ? 8 : 6) * n);
         }
-        if (m & 1) {
+        if (which == 1 && (m & 1)) {
             seq.push_back({OP_CHEB_COPY, level, 0});
             bytes += k * sz * 2 * n;
         }
@@ -1337,9 +1393,10 @@ extern "C" int lamg_time_kernel_batch(lamg_hier *h, int32_t which, int32_t level
     using namespace lamg;
     if (!h || !out || reps < 1 || k < 1 || k > KMAX || level < 0 || level >= (int32_t)h->dev.size())
         return LAMG_ERR_INVALID;
-    if ((which == 0 || which == 1) && h->dev[level].kind != KIND_AGG) return LAMG_ERR_INVALID;
+    if ((which == 0 || which == 1 || which == 3) && h->dev[level].kind != KIND_AGG) return LAMG_ERR_INVALID;
+    if (which == 3 && !h->dev[level].cheb) return LAMG_ERR_INVALID;
     if (which == 2 && level != 0) return LAMG_ERR_INVALID;
-    if (which < 0 || which > 2) return LAMG_ERR_INVALID;
+    if (which < 0 || which > 3) return LAMG_ERR_INVALID;
     CKR(cudaSetDevice(h->device));
     const int prec = h->opt.precision == LAMG_FP32 ? LAMG_FP32 : LAMG_FP64;
     BatchCtx *c = nullptr;

@@ -49,13 +49,13 @@ struct CPos {
 // e1 = the slice width, the entries e0, e0 + 32. d = reciprocal diagonal (sweep) or diagonal
 // (residual).
 struct CPre {
-    int e0, e1, c0, c1;
+    int e0, e1, c0, c1, sub;
     double v0, v1, d;
 };
 
 __device__ __forceinline__ CPre cpre_empty() {
     CPre q;
-    q.e0 = q.e1 = 0;
+    q.e0 = q.e1 = q.sub = 0;
     q.c0 = q.c1 = -1;
     q.v0 = q.v1 = 0.0;
     q.d = 1.0;
@@ -76,15 +76,22 @@ __device__ __forceinline__ CPre cpre_csr(bool ok, int row, int sub, const int32_
     return q;
 }
 
+// Sliced ELLPACK in four-entry blocks (sell_col_at / sell_val_at): e0 holds the slice base,
+// e1 the slice width, sub the lane in the slice; the first two entries come with the prefetch.
 __device__ __forceinline__ CPre cpre_sell(bool ok, int row, const PLevel &L, const double *__restrict__ dg) {
     CPre q = cpre_empty();
     if (!ok) return q;
     const int sl = row >> 5;
     const int a = __ldg(&L.sl_ptr[sl]);
-    q.e0 = a + (row & 31);
+    q.e0 = a;
     q.e1 = (__ldg(&L.sl_ptr[sl + 1]) - a) >> 5;
-    if (q.e1 > 0) { q.c0 = __ldg(&L.sl_col[q.e0]); q.v0 = __ldg(&L.sl_val[q.e0]); }
-    if (q.e1 > 1) { q.c1 = __ldg(&L.sl_col[q.e0 + 32]); q.v1 = __ldg(&L.sl_val[q.e0 + 32]); }
+    q.sub = row & 31;
+    if (q.e1 > 0) {
+        const int2 c = __ldg(reinterpret_cast<const int2 *>(L.sl_col + a + 4 * q.sub));
+        const double2 v = __ldg(reinterpret_cast<const double2 *>(L.sl_val + a + 2 * q.sub));
+        q.c0 = c.x; q.v0 = v.x;
+        q.c1 = c.y; q.v1 = v.y;
+    }
     q.d = __ldg(&dg[row]);
     return q;
 }
@@ -108,7 +115,8 @@ __device__ __forceinline__ double cl_sell_pre(const CPre &q, const PLevel &L, co
     double acc = 0.0;
     if (q.c0 >= 0) acc += q.v0 * __ldcg(&x[q.c0]);
     if (q.c1 >= 0) acc += q.v1 * __ldcg(&x[q.c1]);
-    for (int j = 2; j < q.e1; j++) acc += __ldg(&L.sl_val[q.e0 + 32 * j]) * __ldcg(&x[__ldg(&L.sl_col[q.e0 + 32 * j])]);
+    for (int j = 2; j < q.e1; j++)
+        acc += __ldg(&L.sl_val[sell_val_at(q.e0, q.sub, j)]) * __ldcg(&x[__ldg(&L.sl_col[sell_col_at(q.e0, q.sub, j)])]);
     return acc;
 }
 

@@ -28,6 +28,12 @@ constexpr int BS = 256;
 __device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 
+// The outer CG's vectors are the hierarchy's own allocations (256-byte aligned), so their
+// element pairs (2 i, 2 i + 1) are read and written as one 16-byte double2; an odd n leaves a
+// last single element. Pair i of a grid-stride loop belongs to thread i mod (grid x BS).
+__device__ __forceinline__ double2 ld2(const double *v, int e) { return *reinterpret_cast<const double2 *>(v + e); }
+__device__ __forceinline__ void st2(double *v, int e, double2 a) { *reinterpret_cast<double2 *>(v + e) = a; }
+
 // Grid-wide deterministic sum: every block publishes its partials, the last block to arrive
 // adds all partials in block order. Returns true in the last block, whose thread 0 holds the
 // totals in v. Must be reached by every thread of every block.
@@ -144,55 +150,81 @@ __global__ void __launch_bounds__(BS) k_gs(int r0, int r1, int nl, const int32_t
 
 // --------------------------------------------------- sliced ELLPACK, one thread per row
 //
-// Rows in 32-row slices; entry j of row 32 s + l sits at sl_ptr[s] + 32 j + l, so the loads
-// of a warp (one slice) are contiguous. Every row is summed by one thread in entry order,
-// without a shuffle tree: on a part with few FP64 units the FP64 instruction count per row is
-// what bounds these kernels. Padding entries hold value 0 at a valid column. The slice
-// bounds and the first SELL_PRE entries are loaded before the dependency wait.
-constexpr int SELL_PRE = 4;
-
+// Rows in 32-row slices stored in four-entry blocks (sell_col_at / sell_val_at): a thread reads
+// its row's column ids four at a time (one int4) and its values two at a time (two double2 per
+// block), and every such load of a warp is 512 contiguous bytes. Every row is summed by one
+// thread in entry order, without a shuffle tree: on a part with few FP64 units the FP64
+// instruction count per row is what bounds these kernels. Padding entries hold value 0 at a
+// valid column (adding 0 * x to a sum that started at +0 leaves its bits unchanged). The slice
+// bounds and the first block of four entries are loaded before the dependency wait.
 struct SellPre {
-    int e, w;
-    int c[SELL_PRE];
-    double v[SELL_PRE];
+    int a, l, w;        // slice base, lane in the slice, slice width (a multiple of 4)
+    int4 c;             // the first four column ids
+    double2 v01, v23;   // the first four values
 };
+
+__device__ __forceinline__ int4 sell_ids(const int32_t *__restrict__ sc, int a, int l, int q) {
+    return __ldg(reinterpret_cast<const int4 *>(sc + a + 128 * q + 4 * l));
+}
+__device__ __forceinline__ double2 sell_vals(const double *__restrict__ sv, int a, int l, int q, int h) {
+    return __ldg(reinterpret_cast<const double2 *>(sv + a + 128 * q + 64 * h + 2 * l));
+}
 
 __device__ __forceinline__ SellPre sell_pre(bool ok, int row, const int32_t *__restrict__ sp,
                                             const int32_t *__restrict__ sc, const double *__restrict__ sv) {
     SellPre p;
     const int s = row >> 5;
-    const int a = ok ? sp[s] : 0, bnd = ok ? sp[s + 1] : 0;
-    p.e = a + (row & 31);
-    p.w = (bnd - a) >> 5;
-#pragma unroll
-    for (int k = 0; k < SELL_PRE; k++) {
-        const bool h = k < p.w;
-        p.c[k] = h ? sc[p.e + 32 * k] : 0;
-        p.v[k] = h ? sv[p.e + 32 * k] : 0.0;
+    p.l = row & 31;
+    p.a = ok ? sp[s] : 0;
+    p.w = ok ? (sp[s + 1] - p.a) >> 5 : 0;
+    if (p.w > 0) {
+        p.c = sell_ids(sc, p.a, p.l, 0);
+        p.v01 = sell_vals(sv, p.a, p.l, 0, 0);
+        p.v23 = sell_vals(sv, p.a, p.l, 0, 1);
+    } else {
+        p.c = make_int4(0, 0, 0, 0);
+        p.v01 = p.v23 = make_double2(0.0, 0.0);
     }
     return p;
+}
+
+// The whole row after the dependency wait (kernels with nothing to load before it).
+__device__ __forceinline__ double sell_row(int row, const int32_t *__restrict__ sp, const int32_t *__restrict__ sc,
+                                           const double *__restrict__ sv, const double *x) {
+    const int sl = row >> 5, l = row & 31;
+    const int a = sp[sl], nq = (sp[sl + 1] - a) >> 7;
+    double s = 0.0;
+    for (int q = 0; q < nq; q++) {
+        const int4 c = sell_ids(sc, a, l, q);
+        const double2 va = sell_vals(sv, a, l, q, 0), vb = sell_vals(sv, a, l, q, 1);
+        const double x0 = x[c.x], x1 = x[c.y], x2 = x[c.z], x3 = x[c.w];
+        s += va.x * x0;
+        s += va.y * x1;
+        s += vb.x * x2;
+        s += vb.y * x3;
+    }
+    return s;
 }
 
 __device__ __forceinline__ double sell_finish(const SellPre &p, const int32_t *__restrict__ sc,
                                               const double *__restrict__ sv, const double *x) {
     double s = 0.0;
-#pragma unroll
-    for (int k = 0; k < SELL_PRE; k++)
-        if (k < p.w) s += p.v[k] * x[p.c[k]];
-    for (int j = SELL_PRE; j < p.w; j += 4) {
-        int c[4];
-        double v[4], xv[4];
-#pragma unroll
-        for (int k = 0; k < 4; k++) {
-            const bool h = j + k < p.w;
-            c[k] = h ? sc[p.e + 32 * (j + k)] : 0;
-            v[k] = h ? sv[p.e + 32 * (j + k)] : 0.0;
-        }
-#pragma unroll
-        for (int k = 0; k < 4; k++) xv[k] = j + k < p.w ? x[c[k]] : 0.0;
-#pragma unroll
-        for (int k = 0; k < 4; k++)
-            if (j + k < p.w) s += v[k] * xv[k];
+    if (p.w <= 0) return s;
+    {
+        const double x0 = x[p.c.x], x1 = x[p.c.y], x2 = x[p.c.z], x3 = x[p.c.w];
+        s += p.v01.x * x0;
+        s += p.v01.y * x1;
+        s += p.v23.x * x2;
+        s += p.v23.y * x3;
+    }
+    for (int q = 1; q < (p.w >> 2); q++) {
+        const int4 c = sell_ids(sc, p.a, p.l, q);
+        const double2 va = sell_vals(sv, p.a, p.l, q, 0), vb = sell_vals(sv, p.a, p.l, q, 1);
+        const double x0 = x[c.x], x1 = x[c.y], x2 = x[c.z], x3 = x[c.w];
+        s += va.x * x0;
+        s += va.y * x1;
+        s += vb.x * x2;
+        s += vb.y * x3;
     }
     return s;
 }
@@ -481,7 +513,16 @@ __global__ void __launch_bounds__(BS) k_sum(int n, const double *__restrict__ v,
     pdl_trigger();
     pdl_wait();
     double s[1] = {0.0};
-    for (int i = blockIdx.x * BS + threadIdx.x; i < n; i += gridDim.x * BS) s[0] += v[i];
+    for (int i = blockIdx.x * BS + threadIdx.x; 2 * i < n; i += gridDim.x * BS) {
+        const int e = 2 * i;
+        if (e + 1 < n) {
+            const double2 a = ld2(v, e);
+            s[0] += a.x;
+            s[0] += a.y;
+        } else {
+            s[0] += v[e];
+        }
+    }
     if (grid_sum<1>(s, red) && threadIdx.x == 0) red.scal[S_MEAN] = s[0] / (double)n;
 }
 
@@ -499,14 +540,29 @@ __global__ void __launch_bounds__(BS) k_init_b(int n, double *r, double *bkeep, 
     pdl_wait();
     const double m = red.scal[S_MEAN];
     double s[1] = {0.0};
-    for (int i = blockIdx.x * BS + threadIdx.x; i < n; i += gridDim.x * BS) {
-        const double v = r[i] - m;
-        r[i] = v;
-        bkeep[i] = v;
-        x[i] = 0.0;
-        p[i] = 0.0;
-        zold[i] = 0.0;
-        s[0] += v * v;
+    const double2 z2 = make_double2(0.0, 0.0);
+    for (int i = blockIdx.x * BS + threadIdx.x; 2 * i < n; i += gridDim.x * BS) {
+        const int e = 2 * i;
+        if (e + 1 < n) {
+            double2 v = ld2(r, e);
+            v.x -= m;
+            v.y -= m;
+            st2(r, e, v);
+            st2(bkeep, e, v);
+            st2(x, e, z2);
+            st2(p, e, z2);
+            st2(zold, e, z2);
+            s[0] += v.x * v.x;
+            s[0] += v.y * v.y;
+        } else {
+            const double v = r[e] - m;
+            r[e] = v;
+            bkeep[e] = v;
+            x[e] = 0.0;
+            p[e] = 0.0;
+            zold[e] = 0.0;
+            s[0] += v * v;
+        }
     }
     if (grid_sum<1>(s, red) && threadIdx.x == 0) {
         red.scal[S_BN2] = s[0];
@@ -555,7 +611,7 @@ __global__ void __launch_bounds__(BS) k_spmv_dot(int n, const int32_t *__restric
 }
 
 // q = A p, S_ALPHA = S_RZ / (p . q), one thread per row (sliced ELLPACK)
-__global__ void __launch_bounds__(BS) k_spmv_dot_sell(int n, const int32_t *__restrict__ sp,
+__global__ void __launch_bounds__(BS, 8) k_spmv_dot_sell(int n, const int32_t *__restrict__ sp,
                                                       const int32_t *__restrict__ sc,
                                                       const double *__restrict__ sv,
                                                       const double *__restrict__ diag,
@@ -565,8 +621,7 @@ __global__ void __launch_bounds__(BS) k_spmv_dot_sell(int n, const int32_t *__re
     pdl_wait();
     double pq[1] = {0.0};
     for (int row = blockIdx.x * BS + threadIdx.x; row < n; row += gridDim.x * BS) {
-        const SellPre pre = sell_pre(true, row, sp, sc, sv);
-        const double s = sell_finish(pre, sc, sv, p);
+        const double s = sell_row(row, sp, sc, sv, p);
         const double qi = diag[row] * p[row] + s;
         q[row] = qi;
         pq[0] += p[row] * qi;
@@ -582,27 +637,54 @@ __global__ void __launch_bounds__(BS) k_update_xr(int n, double *x, double *r, c
     pdl_wait();
     const double a = red.scal[S_ALPHA];
     double s[1] = {0.0};
-    for (int i = blockIdx.x * BS + threadIdx.x; i < n; i += gridDim.x * BS) {
-        x[i] += a * p[i];
-        const double ri = r[i] - a * q[i];
-        r[i] = ri;
-        s[0] += ri * ri;
+    for (int i = blockIdx.x * BS + threadIdx.x; 2 * i < n; i += gridDim.x * BS) {
+        const int e = 2 * i;
+        if (e + 1 < n) {
+            double2 xv = ld2(x, e), rv = ld2(r, e);
+            const double2 pv = ld2(p, e), qv = ld2(q, e);
+            xv.x += a * pv.x;
+            xv.y += a * pv.y;
+            rv.x = rv.x - a * qv.x;
+            rv.y = rv.y - a * qv.y;
+            st2(x, e, xv);
+            st2(r, e, rv);
+            s[0] += rv.x * rv.x;
+            s[0] += rv.y * rv.y;
+        } else {
+            x[e] += a * p[e];
+            const double ri = r[e] - a * q[e];
+            r[e] = ri;
+            s[0] += ri * ri;
+        }
     }
     if (grid_sum<1>(s, red) && threadIdx.x == 0) red.scal[S_RR] = s[0];
 }
 
 // z -= mean(z); beta = r.(z - zold) / rz_old; rz = r.z (flexible CG, Polak-Ribiere form)
-__global__ void __launch_bounds__(BS) k_proj_dots(int n, double *z, const double *__restrict__ zold,
+__global__ void __launch_bounds__(BS, 8) k_proj_dots(int n, double *z, const double *__restrict__ zold,
                                                   const double *__restrict__ r, const Reduce red) {
     pdl_trigger();
     pdl_wait();
     const double m = red.scal[S_MEAN];
     double s[2] = {0.0, 0.0};
-    for (int i = blockIdx.x * BS + threadIdx.x; i < n; i += gridDim.x * BS) {
-        const double zi = z[i] - m;
-        z[i] = zi;
-        s[0] += r[i] * (zi - zold[i]);
-        s[1] += r[i] * zi;
+    for (int i = blockIdx.x * BS + threadIdx.x; 2 * i < n; i += gridDim.x * BS) {
+        const int e = 2 * i;
+        if (e + 1 < n) {
+            double2 zv = ld2(z, e);
+            const double2 rv = ld2(r, e), ov = ld2(zold, e);
+            zv.x -= m;
+            zv.y -= m;
+            st2(z, e, zv);
+            s[0] += rv.x * (zv.x - ov.x);
+            s[1] += rv.x * zv.x;
+            s[0] += rv.y * (zv.y - ov.y);
+            s[1] += rv.y * zv.y;
+        } else {
+            const double zi = z[e] - m;
+            z[e] = zi;
+            s[0] += r[e] * (zi - zold[e]);
+            s[1] += r[e] * zi;
+        }
     }
     if (grid_sum<2>(s, red) && threadIdx.x == 0) {
         red.scal[S_BETA] = red.scal[S_RZ] != 0.0 ? s[0] / red.scal[S_RZ] : 0.0;
@@ -614,12 +696,21 @@ __global__ void __launch_bounds__(BS) k_proj_dots(int n, double *z, const double
 __global__ void k_update_p(int n, const double *__restrict__ z, double *p, double *zold, const Reduce red) {
     pdl_trigger();
     pdl_wait();
-    const int i = blockIdx.x * BS + threadIdx.x;
-    if (i >= n) return;
+    const int e = 2 * (blockIdx.x * BS + threadIdx.x);
+    if (e >= n) return;
     const double beta = red.scal[S_BETA];
-    const double zi = z[i];
-    p[i] = zi + beta * p[i];
-    zold[i] = zi;
+    if (e + 1 < n) {
+        const double2 zv = ld2(z, e);
+        double2 pv = ld2(p, e);
+        pv.x = zv.x + beta * pv.x;
+        pv.y = zv.y + beta * pv.y;
+        st2(p, e, pv);
+        st2(zold, e, zv);
+    } else {
+        const double zi = z[e];
+        p[e] = zi + beta * p[e];
+        zold[e] = zi;
+    }
 }
 
 // S_TRUE_RR = ||b - A x||^2; long rows as in k_spmv_dot
@@ -660,7 +751,7 @@ __global__ void __launch_bounds__(BS) k_true_resid(int n, const int32_t *__restr
 }
 
 // S_TRUE_RR = ||b - A x||^2, one thread per row (sliced ELLPACK)
-__global__ void __launch_bounds__(BS) k_true_resid_sell(int n, const int32_t *__restrict__ sp,
+__global__ void __launch_bounds__(BS, 8) k_true_resid_sell(int n, const int32_t *__restrict__ sp,
                                                         const int32_t *__restrict__ sc,
                                                         const double *__restrict__ sv,
                                                         const double *__restrict__ diag,
@@ -670,8 +761,7 @@ __global__ void __launch_bounds__(BS) k_true_resid_sell(int n, const int32_t *__
     pdl_wait();
     double acc[1] = {0.0};
     for (int row = blockIdx.x * BS + threadIdx.x; row < n; row += gridDim.x * BS) {
-        const SellPre pre = sell_pre(true, row, sp, sc, sv);
-        const double s = sell_finish(pre, sc, sv, x);
+        const double s = sell_row(row, sp, sc, sv, x);
         const double ri = b[row] - (diag[row] * x[row] + s);
         acc[0] += ri * ri;
     }
@@ -819,9 +909,11 @@ void launch_op(const Op &op, std::vector<DevLevel> &lv, const Reduce &red, cudaS
             launch(k_coarse, red_blocks((int64_t)n * 32), s, n, (const double *)L.pinv, (const double *)L.b, L.x);
             break;
         case OP_CHEB: {
-            const int k = op.colour;
-            const double *xin = (k & 1) ? L.t : L.x;
-            double *xout = (k & 1) ? L.x : L.t;
+            // colour: step index within the polynomial, + 256 when the step reads t
+            const int k = op.colour & 255;
+            const bool from_t = op.colour >= 256;
+            const double *xin = from_t ? L.t : L.x;
+            double *xout = from_t ? L.x : L.t;
             const int tpr = L.gs_tpr > 0 ? L.gs_tpr : L.tpr;
 #define GRID_C(T) (unsigned)L.nlong + blocks((int64_t)n * (T))
             TPR_DISPATCH(tpr, k_cheb, GRID_C, n, (const int32_t *)L.rp, (const int32_t *)L.ci, (const double *)L.val,
@@ -836,7 +928,7 @@ void launch_op(const Op &op, std::vector<DevLevel> &lv, const Reduce &red, cudaS
             break;
         case OP_CHEB_FIRST:
             launch(k_cheb_first, blocks(n), s, n, (const double *)L.idiag, (const double *)L.b, L.cheb_c2[0],
-                   L.cheb_m > 1 ? L.t : L.x, L.cheb_m > 1 ? L.d : (double *)nullptr);
+                   op.colour ? L.t : L.x, L.cheb_m > 1 ? L.d : (double *)nullptr);
             break;
     }
 }
@@ -850,7 +942,7 @@ void launch_scatter(int64_t n, const int32_t *perm, const double *src, double *d
 }
 
 void launch_sum(int64_t n, const double *v, const Reduce &red, cudaStream_t s) {
-    launch(k_sum, red_blocks(n), s, (int)n, v, red);
+    launch(k_sum, red_blocks((n + 1) / 2), s, (int)n, v, red);
 }
 
 void launch_sub_mean(int64_t n, double *v, const Reduce &red, cudaStream_t s) {
@@ -859,7 +951,7 @@ void launch_sub_mean(int64_t n, double *v, const Reduce &red, cudaStream_t s) {
 
 void launch_init_b(int64_t n, double *r, double *bkeep, double *x, double *p, double *zold,
                    const Reduce &red, cudaStream_t s) {
-    launch(k_init_b, red_blocks(n), s, (int)n, r, bkeep, x, p, zold, red);
+    launch(k_init_b, red_blocks((n + 1) / 2), s, (int)n, r, bkeep, x, p, zold, red);
 }
 
 void launch_spmv_dot(const DevLevel &L, const double *p, double *q, const Reduce &red, cudaStream_t s) {
@@ -878,17 +970,17 @@ void launch_spmv_dot(const DevLevel &L, const double *p, double *q, const Reduce
 
 void launch_update_xr(int64_t n, double *x, double *r, const double *p, const double *q,
                       const Reduce &red, cudaStream_t s) {
-    launch(k_update_xr, red_blocks(n), s, (int)n, x, r, p, q, red);
+    launch(k_update_xr, red_blocks((n + 1) / 2), s, (int)n, x, r, p, q, red);
 }
 
 void launch_proj_dots(int64_t n, double *z, const double *zold, const double *r, const Reduce &red,
                       cudaStream_t s) {
-    launch(k_proj_dots, red_blocks(n), s, (int)n, z, zold, r, red);
+    launch(k_proj_dots, red_blocks((n + 1) / 2), s, (int)n, z, zold, r, red);
 }
 
 void launch_update_p(int64_t n, const double *z, double *p, double *zold, const Reduce &red,
                      cudaStream_t s) {
-    launch(k_update_p, blocks(n), s, (int)n, z, p, zold, red);
+    launch(k_update_p, blocks((n + 1) / 2), s, (int)n, z, p, zold, red);
 }
 
 void launch_true_resid(const DevLevel &L, const double *x, const double *b, const Reduce &red,

@@ -26,9 +26,8 @@ struct DevLevel {
     // operator: off-diagonal CSR + diagonal and its reciprocal (FP64), int32 row pointers
     int32_t *rp = nullptr, *ci = nullptr;
     double *val = nullptr, *diag = nullptr, *idiag = nullptr;
-    // the same off-diagonal entries as sliced ELLPACK (sell = 1): 32-row slices, entry j of
-    // row 32 s + l at sl_ptr[s] + 32 j + l, padding (value 0, the row's own column) up to the
-    // slice's longest row
+    // the same off-diagonal entries as sliced ELLPACK (sell = 1) in four-entry blocks: see
+    // sell_col_at / sell_val_at
     int sell = 0;
     int64_t sell_nnz = 0;
     // rows with more than LONG_ROW off-diagonal entries, summed by a whole thread block: their
@@ -99,6 +98,14 @@ struct Reduce {
     double *scal = nullptr;       // S_COUNT
 };
 
+// Sliced ELLPACK in four-entry blocks. Rows come in slices of 32; every row of slice s is
+// padded to the slice's width w (its longest row rounded up to a multiple of 4) with value 0 at
+// the row's own column (the last row for the slots past n), and the slice occupies 32 w slots
+// from sl_ptr[s]. Entry j of row 32 s + l: column id at sell_col_at, value at sell_val_at, so a
+// lane reads its row's ids four at a time (one 16-byte int4) and its values two at a time (one
+// 16-byte double2), and each such load of a warp covers 512 contiguous bytes.
+__host__ __device__ inline int64_t sell_col_at(int64_t base, int l, int j) { return base + 128 * (j >> 2) + 4 * l + (j & 3); }
+__host__ __device__ inline int64_t sell_val_at(int64_t base, int l, int j) { return base + 64 * (j >> 1) + 2 * l + (j & 1); }
 constexpr int SELL_MAX_ROW = 64;   // longer rows keep the level on the lane-group CSR kernels
 constexpr int LONG_ROW = 256;      // longer rows are summed by a whole thread block
 

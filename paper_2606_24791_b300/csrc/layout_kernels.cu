@@ -33,10 +33,9 @@ __global__ void k_layout_rows(int64_t n, const int32_t *__restrict__ perm, const
     }
 }
 
-// Sliced ELLPACK: entry j of row 32 s + l at sp[s] + 32 j + l for j below the slice's widest
-// row; padding (rows shorter than that, and the rows past n in the last slice) holds value 0 at
-// the row's own column (the last row for rows past n). One thread per slot row, so a warp
-// writes 32 consecutive words per entry index.
+// Sliced ELLPACK in four-entry blocks (sell_col_at / sell_val_at) for j below the slice's width;
+// padding (rows shorter than that, and the rows past n in the last slice) holds value 0 at the
+// row's own column (the last row for rows past n). One thread per slot row.
 __global__ void k_layout_sell(int64_t n, int64_t ns, const int32_t *__restrict__ sp,
                               const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
                               const double *__restrict__ val, int32_t *__restrict__ sc, double *__restrict__ sv) {
@@ -48,13 +47,13 @@ __global__ void k_layout_sell(int64_t n, int64_t ns, const int32_t *__restrict__
     const int64_t e0 = real ? rp[i] : 0, len = real ? rp[i + 1] - e0 : 0;
     const int32_t self = (int32_t)(real ? i : n - 1);
     for (int64_t j = 0; j < w; j++) {
-        const int64_t e = base + 32 * j + l;
+        const int64_t ec = sell_col_at(base, (int)l, (int)j), ev = sell_val_at(base, (int)l, (int)j);
         if (j < len) {
-            sc[e] = ci[e0 + j];
-            sv[e] = val[e0 + j];
+            sc[ec] = ci[e0 + j];
+            sv[ev] = val[e0 + j];
         } else {
-            sc[e] = self;
-            sv[e] = 0.0;
+            sc[ec] = self;
+            sv[ev] = 0.0;
         }
     }
 }

@@ -33,6 +33,16 @@ bool lamg::start_fusable(const lamg_hier *h, int i, bool clusters) {
     return b.kind == OP_ZERO || h->dev[b.level].ncol >= 1;
 }
 
+// True when step i runs inside a cluster segment of the graph path: a step on a level >=
+// cluster_from, except a dense coarsest solve larger than 512 x 512, which stays one launch over
+// the whole GPU (on a cluster's 16 SMs its FP64 products take several times longer) and splits
+// the segment around it.
+bool lamg::in_cluster_segment(const lamg_hier *h, int i) {
+    const Op &op = h->ops[i];
+    if (h->cluster_from < 0 || op.level < h->cluster_from) return false;
+    return !(op.kind == OP_COARSE && h->dev[op.level].n > 512);
+}
+
 namespace {
 
 // Device orders of all levels, from the coarsest up (see DevLevel).
@@ -139,9 +149,8 @@ int upload_level(lamg_hier *h, int l) {
         if ((rc = t.finish())) return rc;
     }
     D.tpr = h->opt.row_tpr > 0 ? h->opt.row_tpr : choose_tpr(n ? (double)H.A.nnz() / (double)n : 1.0);
-    // sliced ELLPACK copy of the operator (32-row slices, entry j of row 32 s + l at
-    // sl_ptr[s] + 32 j + l, padded with value 0 at the row's own column), used by the
-    // one-thread-per-row kernels when rows are short and padding is small
+    // sliced ELLPACK copy of the operator in four-entry blocks (sell_col_at / sell_val_at),
+    // used by the one-thread-per-row kernels when rows are short and padding is small
     {
         const int64_t ns = (n + 31) / 32;
         std::vector<int32_t> sp(ns + 1, 0);
@@ -150,6 +159,7 @@ int upload_level(lamg_hier *h, int l) {
             int64_t w = 0;
             for (int64_t i = 32 * sl; i < std::min(n, 32 * sl + 32); i++) w = std::max<int64_t>(w, rp[i + 1] - rp[i]);
             maxlen = std::max(maxlen, w);
+            w = (w + 3) & ~(int64_t)3;
             sp[sl] = (int32_t)tot;
             tot += 32 * w;
         }
@@ -291,26 +301,26 @@ void emit_visit(lamg_hier *h, std::vector<int64_t> &visits, int l, bool first) {
         return;
     }
     const int npre = h->opt.nu_pre, npost = h->opt.nu_post;
-    // one Chebyshev polynomial: m steps alternating between x and t, back into x
-    auto cheb_poly = [&]() {
-        const int m = h->opt.cheb_degree;
-        for (int k = 0; k < m; k++) h->ops.push_back({OP_CHEB, l, k});
-        if (m & 1) h->ops.push_back({OP_CHEB_COPY, l, 0});
+    // one smoothing phase of `sweeps` Chebyshev polynomials of degree m: its T = m sweeps steps
+    // alternate between the iterate x and the level's second buffer t (a step reads one and
+    // writes the other; colour = step index within its polynomial + 256 when it reads t). A
+    // phase that continues from x starts by reading x and ends with one copy t -> x when T is
+    // odd; a phase that starts from a zero iterate (first visit: the first step needs no product
+    // with A) writes its first result into whichever buffer makes the last step land in x.
+    auto cheb_phase = [&](int sweeps, bool from_zero) {
+        const int m = h->opt.cheb_degree, T = m * sweeps;
+        auto buf = [&](int i) { return from_zero ? ((T - i) & 1) : (i & 1); };   // 0 x, 1 t
+        for (int p = 0; p < T; p++) {
+            if (p == 0 && from_zero) h->ops.push_back({OP_CHEB_FIRST, l, buf(1)});
+            else h->ops.push_back({OP_CHEB, l, (p % m) + 256 * buf(p)});
+        }
+        if (buf(T)) h->ops.push_back({OP_CHEB_COPY, l, 0});
     };
     if (D.cheb) {
         // a first visit starts from x = 0, so the first step of the first polynomial needs no
         // product with A: x1 = c2[0] D^-1 b (the same operations as that step with x = 0)
-        const int m = h->opt.cheb_degree;
         if (first && npre == 0) h->ops.push_back({OP_ZERO, l, 0});
-        for (int s = 0; s < npre; s++) {
-            if (s == 0 && first) {
-                h->ops.push_back({OP_CHEB_FIRST, l, 0});
-                for (int k = 1; k < m; k++) h->ops.push_back({OP_CHEB, l, k});
-                if (m > 1 && (m & 1)) h->ops.push_back({OP_CHEB_COPY, l, 0});
-            } else {
-                cheb_poly();
-            }
-        }
+        if (npre > 0) cheb_phase(npre, first);
     } else {
         if (first && npre == 0) h->ops.push_back({OP_ZERO, l, 0});
         for (int s = 0; s < npre; s++) {
@@ -326,9 +336,10 @@ void emit_visit(lamg_hier *h, std::vector<int64_t> &visits, int l, bool first) {
     const int64_t nv = (int64_t)std::floor((double)(j + 1) * g) - (int64_t)std::floor((double)j * g);
     for (int64_t i = 0; i < nv; i++) emit_visit(h, visits, l + 1, i == 0);
     h->ops.push_back({OP_PROLONG, l, 0});
-    for (int s = 0; s < npost; s++) {
-        if (D.cheb) cheb_poly();
-        else
+    if (D.cheb) {
+        if (npost > 0) cheb_phase(npost, false);
+    } else {
+        for (int s = 0; s < npost; s++)
             for (int c = D.ncol - 1; c >= 0; c--) h->ops.push_back({OP_GS, l, c});
     }
 }
@@ -342,9 +353,9 @@ int capture(lamg_hier *h, cudaGraphExec_t *out, int which) {
     if (which == 0 || which == 1) {
         const int nops = (int)h->ops.size(), nlev = (int)h->dev.size();
         for (int i = 0; i < nops;) {
-            if (h->cluster_from >= 0 && h->ops[i].level >= h->cluster_from) {
+            if (in_cluster_segment(h, i)) {
                 int j = i;
-                while (j < nops && h->ops[j].level >= h->cluster_from) j++;
+                while (j < nops && in_cluster_segment(h, j)) j++;
                 launch_cluster(h->d_lv, nlev, h->d_cptr, h->ncptr, h->d_ops + i, j - i, h->cl_dim,
                                pdl_enabled(), cs);
                 i = j;
@@ -589,8 +600,8 @@ int64_t count_cycle_launches(const lamg_hier *h) {
     const int nops = (int)h->ops.size();
     for (int i = 0; i < nops;) {
         const Op &op = h->ops[i];
-        if (h->cluster_from >= 0 && op.level >= h->cluster_from) {
-            while (i < nops && h->ops[i].level >= h->cluster_from) i++;
+        if (in_cluster_segment(h, i)) {
+            while (i < nops && in_cluster_segment(h, i)) i++;
             k++;
             continue;
         }
@@ -657,9 +668,19 @@ int choose_cluster(lamg_hier *h) {
         smax[l] = std::max(smax[l + 1], h->dev[l].n);
         lng[l] = lng[l + 1] + h->dev[l].nlong + (h->dev[l].cheb ? 1 : 0);   // nor Chebyshev levels
     }
+    // a candidate must leave some step inside a cluster segment (a level holding only a dense
+    // coarsest that stays outside would give the per-step schedule again)
+    auto has_segment = [&](int from) {
+        const int keep = h->cluster_from;
+        h->cluster_from = from;
+        bool any = false;
+        for (int i = 0; i < (int)h->ops.size() && !any; i++) any = in_cluster_segment(h, i);
+        h->cluster_from = keep;
+        return any;
+    };
     std::vector<int> cand;
     for (int l = 0; l < L; l++)
-        if (smax[l] <= limit && lng[l] == 0) cand.push_back(l);
+        if (smax[l] <= limit && lng[l] == 0 && has_segment(l)) cand.push_back(l);
     if (cand.empty()) return LAMG_OK;
     if (rows > 0) {
         h->cluster_from = cand[0];
@@ -1267,10 +1288,15 @@ int lamg_profile_schedule(lamg_hier *h, int32_t from_level, int64_t *out, int64_
     std::vector<cudaEvent_t> ev(2 * (size_t)nops, nullptr);
     std::vector<uint8_t> in_cl(nops, 0);
     cudaError_t e = cudaMemsetAsync(h->r, 0, h->dev[0].n * sizeof(double), s);
+    // segments as the graph path forms them for cluster_from = from_level
+    auto in_seg = [&](int i) {
+        const Op &op = h->ops[i];
+        return from_level >= 0 && op.level >= from_level && !(op.kind == OP_COARSE && h->dev[op.level].n > 512);
+    };
     for (int i = 0; i < nops && e == cudaSuccess;) {
-        if (from_level >= 0 && h->ops[i].level >= from_level) {
+        if (in_seg(i)) {
             int j = i;
-            while (j < nops && h->ops[j].level >= from_level) in_cl[j++] = 1;
+            while (j < nops && in_seg(j)) in_cl[j++] = 1;
             launch_cluster(h->d_lv, nlev, h->d_cptr, h->ncptr, h->d_ops + i, j - i, h->cl_dim, false, s,
                            dprof + 2 * (size_t)i);
             i = j;

