@@ -53,10 +53,12 @@ class CopyPool {
 
   private:
     CopyPool() {
-        // one thread per four hardware threads, at most 16 copying threads in all: a host
-        // memcpy runs at ~5-10 GB/s per thread, so a dozen or so keep up with the link
-        const unsigned hw = std::max(4u, std::thread::hardware_concurrency());
-        const int n = (int)std::min(15u, hw / 4);
+        // one copying thread per hardware thread (the caller included), at most 32: a host
+        // memcpy from pageable memory runs at ~10 GB/s on one thread and the host's memory
+        // system saturates near 43 GB/s with 16 (measured on a 16-thread B300 host, where the
+        // pinned DMA runs at 55 GB/s each way); the caller waits for the copy anyway
+        const unsigned hw = std::max(2u, std::thread::hardware_concurrency());
+        const int n = (int)std::min(31u, hw - 1);
         for (int i = 0; i < n; i++) workers_.emplace_back([this, i] { loop(i + 1); });
         for (auto &t : workers_) t.detach();   // process-lifetime pool
     }
