@@ -65,10 +65,10 @@ def parse():
     ap.add_argument("--serve-threads", type=int, default=8)
     ap.add_argument("--profile-sweep", type=int, default=-1, metavar="LEVEL",
                     help="set up aniso1024, run one cold-L2 Gauss-Seidel sweep at LEVEL, exit (a target for ncu)")
-    ap.add_argument("--profile-kernels", default=None, choices=["single", "batch", "batch16", "setup"],
+    ap.add_argument("--profile-kernels", default=None, choices=["single", "single32", "batch", "batch16", "setup"],
                     help="run each kernel of one family a few times after an L2 flush, nothing else (a target "
                          "for one-kernel ncu captures): single = the one-RHS cycle and CG kernels on aniso1024, "
-                         "batch = the 32-column kernels on a 500k-node Chung-Lu graph, batch16 = the 16-column "
+                         "single32 = two FP32-cycle iterations on aniso1024, batch = the 32-column kernels on a 500k-node Chung-Lu graph, batch16 = the 16-column "
                          "Gauss-Seidel kernels on a 512^2 anisotropic grid, setup = the setup kernels on a "
                          "200k-node Barabasi-Albert graph")
     ap.add_argument("--profile-batch", default=None, metavar="N:LEVEL:WHICH",
@@ -243,6 +243,13 @@ def profile_kernels(family: str):
         P.solve(b, TOL, 2, allow_unconverged=True)
         out["levels"] = [(i["kind"], i["n"], i["nnz"]) for i in P.info]
         out["forms"] = P.schedule()["forms"]
+    elif family == "single32":
+        # the FP32 cycle with one right-hand side (the multi-column kernels at one column) and
+        # its FP64 outer CG: two iterations
+        g, b = aniso_workload()
+        P = lamg.setup(g, precision=lamg.FP32)
+        P.solve(b, TOL, 2, allow_unconverged=True)
+        out["levels"] = [(i["kind"], i["n"], i["nnz"]) for i in P.info]
     elif family in ("batch", "batch16"):
         if family == "batch":
             g = gg.chung_lu(500_000, 2.1, 16.0, seed=1)
@@ -704,6 +711,26 @@ def run_variants(g, B, X64, dev, stream, flush, local) -> dict:
             r = Pa.time_kernel("gs_sweep", 2, reps=10)
             v["k_gs_sweep_L2"] = {"ms": round(r["ms"], 5), "gbs": round(r["gbs"], 1), "bytes": r["bytes"],
                                   "traffic": traffic_for("k_gs")}
+            # per-level table of the one-column cycle passes (cold L2, of the measured copy peak)
+            peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+                os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+            hbm = peaks.get("hbm_gbs", 6400.0)
+            sp = Pa.time_kernel("spmv_dot", 0, reps=5)
+            rows = [{"level": 0, "kind": Pa.info[0]["kind"], "n": Pa.info[0]["n"], "nnz": Pa.info[0]["nnz"],
+                     "spmv_dot_ms": round(sp["ms"], 5), "spmv_dot_gbs": round(sp["gbs"], 1),
+                     "spmv_dot_frac": round(sp["gbs"] / hbm, 3)}]
+            for l, L in enumerate(Pa.info):
+                if L["kind"] != "agg":
+                    continue
+                sw = Pa.time_kernel("gs_sweep", l, reps=5)
+                rs = Pa.time_kernel("resid", l, reps=5)
+                rows.append({"level": l, "kind": "agg", "n": L["n"], "nnz": L["nnz"], "colours": L["ncol"],
+                             "sweep_ms": round(sw["ms"], 5), "sweep_gbs": round(sw["gbs"], 1),
+                             "sweep_frac": round(sw["gbs"] / hbm, 3), "sweep_launches": sw["launches"],
+                             "resid_ms": round(rs["ms"], 5), "resid_gbs": round(rs["gbs"], 1),
+                             "resid_frac": round(rs["gbs"] / hbm, 3),
+                             "l2_resident": 12 * L["nnz"] + 48 * L["n"] <= 126e6})
+            v["levels"] = rows
         if k == 1 and PP is Pa32 and xa64 is not None:
             v["rel_err_vs_fp64_solution"] = float(np.linalg.norm(Xk.cpu().numpy() - xa64) / np.linalg.norm(xa64))
         variants[name] = v

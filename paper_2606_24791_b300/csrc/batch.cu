@@ -71,12 +71,13 @@ __device__ __forceinline__ void block_col_total(double (&v)[NV], double (*sh)[BB
 
 // Each thread contributes to column threadIdx.x % KL. Deterministic: per-block column sums in a
 // fixed order, then the last block to finish adds the blocks in a fixed order. Returns true in
-// the last block, where threads j < KL hold column j's totals.
+// the last block, where threads j < KL hold column j's totals. The last block reads only the
+// partials (fenced before the ticket); the kernel's other writes reach the next kernel through
+// the launch boundary.
 template <int KL, int NV>
 __device__ bool col_sum(double (&v)[NV], const BRed R) {
     __shared__ double sh[NV][BBS];
     __shared__ bool last;
-    __threadfence();
     block_col_total<KL, NV>(v, sh);
     if ((int)threadIdx.x < KL) {
 #pragma unroll
@@ -511,6 +512,34 @@ __global__ void __launch_bounds__(BBS) bk_coarse(int n, int k, const double *__r
             x[(size_t)i * k + threadIdx.x] = (T)t;
         }
         __syncthreads();
+    }
+}
+
+// One column: a warp per row, each lane with four partial sums over the columns lane, lane + 32,
+// ..., then the warp's shuffle tree (a block per row would spend half as many FP64 adds on its
+// 256-lane reduction as on the row's n multiply-adds).
+template <typename T>
+__global__ void __launch_bounds__(BBS) bk_coarse1(int n, const double *__restrict__ pinv,
+                                                  const double *__restrict__ b, T *x) {
+    b_trigger();
+    b_wait();
+    const int lane = threadIdx.x & 31;
+    const int wg = (int)((blockIdx.x * BBS + threadIdx.x) >> 5), nw = (int)((gridDim.x * BBS) >> 5);
+    for (int i = wg; i < n; i += nw) {
+        const double *row = pinv + (size_t)i * n;
+        double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+        int c = lane;
+        for (; c + 96 < n; c += 128) {
+            s0 += row[c] * b[c];
+            s1 += row[c + 32] * b[c + 32];
+            s2 += row[c + 64] * b[c + 64];
+            s3 += row[c + 96] * b[c + 96];
+        }
+        for (; c < n; c += 32) s0 += row[c] * b[c];
+        double s = (s0 + s1) + (s2 + s3);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) x[i] = (T)s;
     }
 }
 
@@ -1085,6 +1114,10 @@ static void bop(const Op &op, BatchCtx *c, cudaStream_t s, const Op *start) {
             if (sizeof(T) != sizeof(double)) {
                 blaunch(bk_cast<T, double>, nblocks((int64_t)n * k), s, (int64_t)n * k, (const T *)b, L.b64);
                 b64 = L.b64;
+            }
+            if (KL == 1) {
+                blaunch(bk_coarse1<T>, std::min<int64_t>((n + BBS / 32 - 1) / (BBS / 32), 148 * 8), s, n, L.pinv, b64, x);
+                break;
             }
 #define C8(KLv, ...) case KLv: blaunch(bk_coarse<T, KLv>, std::min<int64_t>(n, 148 * 8), s, n, k, L.pinv, b64, x); break;
             switch (KL) { K_CASES(C8) }

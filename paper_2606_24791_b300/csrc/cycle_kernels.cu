@@ -28,19 +28,16 @@ constexpr int BS = 256;
 __device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 
-// The outer CG's vectors are the hierarchy's own allocations (256-byte aligned), so their
-// element pairs (2 i, 2 i + 1) are read and written as one 16-byte double2; an odd n leaves a
-// last single element. Pair i of a grid-stride loop belongs to thread i mod (grid x BS).
-__device__ __forceinline__ double2 ld2(const double *v, int e) { return *reinterpret_cast<const double2 *>(v + e); }
-__device__ __forceinline__ void st2(double *v, int e, double2 a) { *reinterpret_cast<double2 *>(v + e) = a; }
 
 // Grid-wide deterministic sum: every block publishes its partials, the last block to arrive
 // adds all partials in block order. Returns true in the last block, whose thread 0 holds the
-// totals in v. Must be reached by every thread of every block.
+// totals in v. Must be reached by every thread of every block. The last block reads only the
+// partials (published by a fence before the ticket); the kernel's other writes reach the next
+// kernel through the launch boundary (its griddepcontrol.wait returns once this grid's memory
+// operations are complete and visible), so threads do not fence them here.
 template <int NV>
 __device__ bool grid_sum(double (&v)[NV], const Reduce red) {
     __shared__ bool last;
-    __threadfence();  // publish this thread's global writes before the block signals
     block_sum<NV>(v);
     if (threadIdx.x == 0) {
 #pragma unroll
@@ -513,16 +510,7 @@ __global__ void __launch_bounds__(BS) k_sum(int n, const double *__restrict__ v,
     pdl_trigger();
     pdl_wait();
     double s[1] = {0.0};
-    for (int i = blockIdx.x * BS + threadIdx.x; 2 * i < n; i += gridDim.x * BS) {
-        const int e = 2 * i;
-        if (e + 1 < n) {
-            const double2 a = ld2(v, e);
-            s[0] += a.x;
-            s[0] += a.y;
-        } else {
-            s[0] += v[e];
-        }
-    }
+    for (int i = blockIdx.x * BS + threadIdx.x; i < n; i += gridDim.x * BS) s[0] += v[i];
     if (grid_sum<1>(s, red) && threadIdx.x == 0) red.scal[S_MEAN] = s[0] / (double)n;
 }
 
@@ -540,29 +528,14 @@ __global__ void __launch_bounds__(BS) k_init_b(int n, double *r, double *bkeep, 
     pdl_wait();
     const double m = red.scal[S_MEAN];
     double s[1] = {0.0};
-    const double2 z2 = make_double2(0.0, 0.0);
-    for (int i = blockIdx.x * BS + threadIdx.x; 2 * i < n; i += gridDim.x * BS) {
-        const int e = 2 * i;
-        if (e + 1 < n) {
-            double2 v = ld2(r, e);
-            v.x -= m;
-            v.y -= m;
-            st2(r, e, v);
-            st2(bkeep, e, v);
-            st2(x, e, z2);
-            st2(p, e, z2);
-            st2(zold, e, z2);
-            s[0] += v.x * v.x;
-            s[0] += v.y * v.y;
-        } else {
-            const double v = r[e] - m;
-            r[e] = v;
-            bkeep[e] = v;
-            x[e] = 0.0;
-            p[e] = 0.0;
-            zold[e] = 0.0;
-            s[0] += v * v;
-        }
+    for (int i = blockIdx.x * BS + threadIdx.x; i < n; i += gridDim.x * BS) {
+        const double v = r[i] - m;
+        r[i] = v;
+        bkeep[i] = v;
+        x[i] = 0.0;
+        p[i] = 0.0;
+        zold[i] = 0.0;
+        s[0] += v * v;
     }
     if (grid_sum<1>(s, red) && threadIdx.x == 0) {
         red.scal[S_BN2] = s[0];
@@ -637,54 +610,27 @@ __global__ void __launch_bounds__(BS) k_update_xr(int n, double *x, double *r, c
     pdl_wait();
     const double a = red.scal[S_ALPHA];
     double s[1] = {0.0};
-    for (int i = blockIdx.x * BS + threadIdx.x; 2 * i < n; i += gridDim.x * BS) {
-        const int e = 2 * i;
-        if (e + 1 < n) {
-            double2 xv = ld2(x, e), rv = ld2(r, e);
-            const double2 pv = ld2(p, e), qv = ld2(q, e);
-            xv.x += a * pv.x;
-            xv.y += a * pv.y;
-            rv.x = rv.x - a * qv.x;
-            rv.y = rv.y - a * qv.y;
-            st2(x, e, xv);
-            st2(r, e, rv);
-            s[0] += rv.x * rv.x;
-            s[0] += rv.y * rv.y;
-        } else {
-            x[e] += a * p[e];
-            const double ri = r[e] - a * q[e];
-            r[e] = ri;
-            s[0] += ri * ri;
-        }
+    for (int i = blockIdx.x * BS + threadIdx.x; i < n; i += gridDim.x * BS) {
+        x[i] += a * p[i];
+        const double ri = r[i] - a * q[i];
+        r[i] = ri;
+        s[0] += ri * ri;
     }
     if (grid_sum<1>(s, red) && threadIdx.x == 0) red.scal[S_RR] = s[0];
 }
 
 // z -= mean(z); beta = r.(z - zold) / rz_old; rz = r.z (flexible CG, Polak-Ribiere form)
-__global__ void __launch_bounds__(BS, 8) k_proj_dots(int n, double *z, const double *__restrict__ zold,
+__global__ void __launch_bounds__(BS) k_proj_dots(int n, double *z, const double *__restrict__ zold,
                                                   const double *__restrict__ r, const Reduce red) {
     pdl_trigger();
     pdl_wait();
     const double m = red.scal[S_MEAN];
     double s[2] = {0.0, 0.0};
-    for (int i = blockIdx.x * BS + threadIdx.x; 2 * i < n; i += gridDim.x * BS) {
-        const int e = 2 * i;
-        if (e + 1 < n) {
-            double2 zv = ld2(z, e);
-            const double2 rv = ld2(r, e), ov = ld2(zold, e);
-            zv.x -= m;
-            zv.y -= m;
-            st2(z, e, zv);
-            s[0] += rv.x * (zv.x - ov.x);
-            s[1] += rv.x * zv.x;
-            s[0] += rv.y * (zv.y - ov.y);
-            s[1] += rv.y * zv.y;
-        } else {
-            const double zi = z[e] - m;
-            z[e] = zi;
-            s[0] += r[e] * (zi - zold[e]);
-            s[1] += r[e] * zi;
-        }
+    for (int i = blockIdx.x * BS + threadIdx.x; i < n; i += gridDim.x * BS) {
+        const double zi = z[i] - m;
+        z[i] = zi;
+        s[0] += r[i] * (zi - zold[i]);
+        s[1] += r[i] * zi;
     }
     if (grid_sum<2>(s, red) && threadIdx.x == 0) {
         red.scal[S_BETA] = red.scal[S_RZ] != 0.0 ? s[0] / red.scal[S_RZ] : 0.0;
@@ -696,21 +642,12 @@ __global__ void __launch_bounds__(BS, 8) k_proj_dots(int n, double *z, const dou
 __global__ void k_update_p(int n, const double *__restrict__ z, double *p, double *zold, const Reduce red) {
     pdl_trigger();
     pdl_wait();
-    const int e = 2 * (blockIdx.x * BS + threadIdx.x);
-    if (e >= n) return;
+    const int i = blockIdx.x * BS + threadIdx.x;
+    if (i >= n) return;
     const double beta = red.scal[S_BETA];
-    if (e + 1 < n) {
-        const double2 zv = ld2(z, e);
-        double2 pv = ld2(p, e);
-        pv.x = zv.x + beta * pv.x;
-        pv.y = zv.y + beta * pv.y;
-        st2(p, e, pv);
-        st2(zold, e, zv);
-    } else {
-        const double zi = z[e];
-        p[e] = zi + beta * p[e];
-        zold[e] = zi;
-    }
+    const double zi = z[i];
+    p[i] = zi + beta * p[i];
+    zold[i] = zi;
 }
 
 // S_TRUE_RR = ||b - A x||^2; long rows as in k_spmv_dot
@@ -942,7 +879,7 @@ void launch_scatter(int64_t n, const int32_t *perm, const double *src, double *d
 }
 
 void launch_sum(int64_t n, const double *v, const Reduce &red, cudaStream_t s) {
-    launch(k_sum, red_blocks((n + 1) / 2), s, (int)n, v, red);
+    launch(k_sum, red_blocks(n), s, (int)n, v, red);
 }
 
 void launch_sub_mean(int64_t n, double *v, const Reduce &red, cudaStream_t s) {
@@ -951,7 +888,7 @@ void launch_sub_mean(int64_t n, double *v, const Reduce &red, cudaStream_t s) {
 
 void launch_init_b(int64_t n, double *r, double *bkeep, double *x, double *p, double *zold,
                    const Reduce &red, cudaStream_t s) {
-    launch(k_init_b, red_blocks((n + 1) / 2), s, (int)n, r, bkeep, x, p, zold, red);
+    launch(k_init_b, red_blocks(n), s, (int)n, r, bkeep, x, p, zold, red);
 }
 
 void launch_spmv_dot(const DevLevel &L, const double *p, double *q, const Reduce &red, cudaStream_t s) {
@@ -970,17 +907,17 @@ void launch_spmv_dot(const DevLevel &L, const double *p, double *q, const Reduce
 
 void launch_update_xr(int64_t n, double *x, double *r, const double *p, const double *q,
                       const Reduce &red, cudaStream_t s) {
-    launch(k_update_xr, red_blocks((n + 1) / 2), s, (int)n, x, r, p, q, red);
+    launch(k_update_xr, red_blocks(n), s, (int)n, x, r, p, q, red);
 }
 
 void launch_proj_dots(int64_t n, double *z, const double *zold, const double *r, const Reduce &red,
                       cudaStream_t s) {
-    launch(k_proj_dots, red_blocks((n + 1) / 2), s, (int)n, z, zold, r, red);
+    launch(k_proj_dots, red_blocks(n), s, (int)n, z, zold, r, red);
 }
 
 void launch_update_p(int64_t n, const double *z, double *p, double *zold, const Reduce &red,
                      cudaStream_t s) {
-    launch(k_update_p, blocks((n + 1) / 2), s, (int)n, z, p, zold, red);
+    launch(k_update_p, blocks(n), s, (int)n, z, p, zold, red);
 }
 
 void launch_true_resid(const DevLevel &L, const double *x, const double *b, const Reduce &red,
