@@ -156,8 +156,22 @@ __device__ __forceinline__ T block_row_k(int e0, int e1, int k, const int32_t *_
     constexpr int M = BBS / KL;
     const int j = threadIdx.x % KL, m = threadIdx.x / KL;
     T s = T(0);
-    if (j < k)
-        for (int e = e0 + m; e < e1; e += M) s += val[e] * x[(size_t)ci[e] * k + j];
+    if (j < k) {
+        // four entries of the lane loaded before their products are added (as rowsum_k): the
+        // same sequence of multiply-adds as one entry at a time, four gathers in flight
+        int e = e0 + m;
+        for (; e + 3 * M < e1; e += 4 * M) {
+            const int c0 = ci[e], c1 = ci[e + M], c2 = ci[e + 2 * M], c3 = ci[e + 3 * M];
+            const T v0 = val[e], v1 = val[e + M], v2 = val[e + 2 * M], v3 = val[e + 3 * M];
+            const T x0 = x[(size_t)c0 * k + j], x1 = x[(size_t)c1 * k + j];
+            const T x2 = x[(size_t)c2 * k + j], x3 = x[(size_t)c3 * k + j];
+            s += v0 * x0;
+            s += v1 * x1;
+            s += v2 * x2;
+            s += v3 * x3;
+        }
+        for (; e < e1; e += M) s += val[e] * x[(size_t)ci[e] * k + j];
+    }
 #pragma unroll
     for (int o = KL; o < 32; o <<= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
