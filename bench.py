@@ -65,10 +65,12 @@ def parse():
     ap.add_argument("--serve-threads", type=int, default=8)
     ap.add_argument("--profile-sweep", type=int, default=-1, metavar="LEVEL",
                     help="set up aniso1024, run one cold-L2 Gauss-Seidel sweep at LEVEL, exit (a target for ncu)")
-    ap.add_argument("--profile-kernels", default=None, choices=["single", "single32", "batch", "batch16", "setup"],
+    ap.add_argument("--profile-kernels", default=None,
+                    choices=["single", "single32", "single_powerlaw", "batch", "batch16", "setup"],
                     help="run each kernel of one family a few times after an L2 flush, nothing else (a target "
                          "for one-kernel ncu captures): single = the one-RHS cycle and CG kernels on aniso1024, "
-                         "single32 = two FP32-cycle iterations on aniso1024, batch = the 32-column kernels on a 500k-node Chung-Lu graph, batch16 = the 16-column "
+                         "single32 = two FP32-cycle iterations on aniso1024, single_powerlaw = two one-RHS "
+                         "iterations on a 500k-node Chung-Lu graph (Chebyshev levels), batch = the 32-column kernels on a 500k-node Chung-Lu graph, batch16 = the 16-column "
                          "Gauss-Seidel kernels on a 512^2 anisotropic grid, setup = the setup kernels on a "
                          "200k-node Barabasi-Albert graph")
     ap.add_argument("--profile-batch", default=None, metavar="N:LEVEL:WHICH",
@@ -250,6 +252,12 @@ def profile_kernels(family: str):
         P = lamg.setup(g, precision=lamg.FP32)
         P.solve(b, TOL, 2, allow_unconverged=True)
         out["levels"] = [(i["kind"], i["n"], i["nnz"]) for i in P.info]
+    elif family == "single_powerlaw":
+        g = gg.chung_lu(500_000, 2.1, 16.0, seed=1)
+        b = gg.rhs(g, seed=2)
+        P = lamg.setup(g)
+        P.solve(b, TOL, 2, allow_unconverged=True)
+        out["levels"] = [(i["kind"], i["n"], i["nnz"], i["ncol"]) for i in P.info]
     elif family in ("batch", "batch16"):
         if family == "batch":
             g = gg.chung_lu(500_000, 2.1, 16.0, seed=1)
