@@ -150,6 +150,9 @@ bool many_eligible(const lamg_hier *h, size_t *smem);
 // step i is a restriction that also performs step i + 1, the row-local start of the coarse
 // level's first visit (with clusters: not when that step belongs to a cluster segment)
 bool start_fusable(const lamg_hier *h, int i, bool clusters = true);
+// Step i runs inside a cluster segment when the sub-cycle starts at level `from` (the
+// hierarchy's own cluster_from in the two-argument form).
+bool in_cluster_segment(const lamg_hier *h, int i, int from);
 bool in_cluster_segment(const lamg_hier *h, int i);
 int many_prepare(lamg_hier *h, int maxit, double tol, const double *b_in, double *phi_out, MGraph *M);
 int solve_batch_impl(lamg_hier *h, int k, const double *B, double *PHI, const lamg_solve_opts *so,

@@ -37,11 +37,13 @@ bool lamg::start_fusable(const lamg_hier *h, int i, bool clusters) {
 // cluster_from, except a dense coarsest solve larger than 512 x 512, which stays one launch over
 // the whole GPU (on a cluster's 16 SMs its FP64 products take several times longer) and splits
 // the segment around it.
-bool lamg::in_cluster_segment(const lamg_hier *h, int i) {
+bool lamg::in_cluster_segment(const lamg_hier *h, int i, int from) {
     const Op &op = h->ops[i];
-    if (h->cluster_from < 0 || op.level < h->cluster_from) return false;
+    if (from < 0 || op.level < from) return false;
     return !(op.kind == OP_COARSE && h->dev[op.level].n > 512);
 }
+
+bool lamg::in_cluster_segment(const lamg_hier *h, int i) { return in_cluster_segment(h, i, h->cluster_from); }
 
 namespace {
 
@@ -671,12 +673,9 @@ int choose_cluster(lamg_hier *h) {
     // a candidate must leave some step inside a cluster segment (a level holding only a dense
     // coarsest that stays outside would give the per-step schedule again)
     auto has_segment = [&](int from) {
-        const int keep = h->cluster_from;
-        h->cluster_from = from;
-        bool any = false;
-        for (int i = 0; i < (int)h->ops.size() && !any; i++) any = in_cluster_segment(h, i);
-        h->cluster_from = keep;
-        return any;
+        for (int i = 0; i < (int)h->ops.size(); i++)
+            if (in_cluster_segment(h, i, from)) return true;
+        return false;
     };
     std::vector<int> cand;
     for (int l = 0; l < L; l++)
@@ -1289,10 +1288,7 @@ int lamg_profile_schedule(lamg_hier *h, int32_t from_level, int64_t *out, int64_
     std::vector<uint8_t> in_cl(nops, 0);
     cudaError_t e = cudaMemsetAsync(h->r, 0, h->dev[0].n * sizeof(double), s);
     // segments as the graph path forms them for cluster_from = from_level
-    auto in_seg = [&](int i) {
-        const Op &op = h->ops[i];
-        return from_level >= 0 && op.level >= from_level && !(op.kind == OP_COARSE && h->dev[op.level].n > 512);
-    };
+    auto in_seg = [&](int i) { return in_cluster_segment(h, i, from_level); };
     for (int i = 0; i < nops && e == cudaSuccess;) {
         if (in_seg(i)) {
             int j = i;
