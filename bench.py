@@ -397,7 +397,8 @@ def oracle_sample(reps: int, warmup: int = 0) -> dict:
 KERNEL_SOURCES = {
     "k_gs": ("cycle_kernels.cu", ["struct RowPre {", "RowPre row_pre(", "double row_finish(", "double block_row(",
                                   "void __launch_bounds__(BS) k_gs("]),
-    "bk_cheb": ("batch.cu", ["T rowsum_k(", "T block_row_k(", "__global__ void __launch_bounds__(BBS) bk_cheb("]),
+    "bk_cheb": ("batch.cu", ["void add_entries(", "T rowsum_k(", "T block_row_k(",
+                             "__global__ void __launch_bounds__(BBS) bk_cheb("]),
 }
 
 

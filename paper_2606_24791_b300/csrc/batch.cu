@@ -118,26 +118,37 @@ struct Lanes {
     }
 };
 
-// A row's entries e0, e0 + TPR, ... for column j, accumulated in entry order. Four entries are
-// loaded before their products are added (column ids, values, then the four gathers), so a lane
-// has four independent gathers in flight instead of one; the sum is the same sequence of
-// multiply-adds as a one-entry-at-a-time loop.
+// D entries e, e + TPR, ... of a row for column j added to s in order, their column ids, values
+// and gathers all loaded first.
+template <int D, typename T, int TPR>
+__device__ __forceinline__ void add_entries(T &s, int e, int k, int j, const int32_t *__restrict__ ci,
+                                            const T *__restrict__ val, const T *x) {
+    int c[D];
+    T v[D], xv[D];
+#pragma unroll
+    for (int q = 0; q < D; q++) c[q] = ci[e + q * TPR];
+#pragma unroll
+    for (int q = 0; q < D; q++) v[q] = val[e + q * TPR];
+#pragma unroll
+    for (int q = 0; q < D; q++) xv[q] = x[(size_t)c[q] * k + j];
+#pragma unroll
+    for (int q = 0; q < D; q++) s += v[q] * xv[q];
+}
+
+// A row's entries e0, e0 + TPR, ... for column j, accumulated in entry order. Entries are loaded
+// in groups before their products are added, so a lane has several independent gathers in
+// flight instead of one; the sum is the same sequence of multiply-adds as a one-entry-at-a-time
+// loop. FP32 rows take groups of eight first (their kernels wait on the gathers), FP64 rows
+// groups of four (their kernels wait on the FP64 unit, and eight would cost registers).
 template <typename T, int KL, int TPR>
 __device__ __forceinline__ T rowsum_k(int e0, int e1, int k, int j, const int32_t *__restrict__ ci,
                                       const T *__restrict__ val, const T *x) {
     T s = T(0);
     if (j < k) {
         int e = e0;
-        for (; e + 3 * TPR < e1; e += 4 * TPR) {
-            const int c0 = ci[e], c1 = ci[e + TPR], c2 = ci[e + 2 * TPR], c3 = ci[e + 3 * TPR];
-            const T v0 = val[e], v1 = val[e + TPR], v2 = val[e + 2 * TPR], v3 = val[e + 3 * TPR];
-            const T x0 = x[(size_t)c0 * k + j], x1 = x[(size_t)c1 * k + j];
-            const T x2 = x[(size_t)c2 * k + j], x3 = x[(size_t)c3 * k + j];
-            s += v0 * x0;
-            s += v1 * x1;
-            s += v2 * x2;
-            s += v3 * x3;
-        }
+        if constexpr (sizeof(T) == 4)
+            for (; e + 7 * TPR < e1; e += 8 * TPR) add_entries<8, T, TPR>(s, e, k, j, ci, val, x);
+        for (; e + 3 * TPR < e1; e += 4 * TPR) add_entries<4, T, TPR>(s, e, k, j, ci, val, x);
         for (; e < e1; e += TPR) s += val[e] * x[(size_t)ci[e] * k + j];
     }
 #pragma unroll
@@ -145,10 +156,6 @@ __device__ __forceinline__ T rowsum_k(int e0, int e1, int k, int j, const int32_
     return s;
 }
 
-// A row longer than LONG_ROW entries, all k columns, summed by the whole block: column
-// j = threadIdx.x % KL, entry lane m = threadIdx.x / KL taking entries e0 + m, e0 + m + BBS/KL,
-// ...; the lanes of one column are combined by a shuffle tree inside each warp, then the warps
-// in order. Column j's total is returned in thread j (j < KL).
 template <typename T, int KL>
 __device__ __forceinline__ T block_row_k(int e0, int e1, int k, const int32_t *__restrict__ ci,
                                          const T *__restrict__ val, const T *x) {
