@@ -58,7 +58,8 @@ def parse():
     ap.add_argument("--serve", action="store_true", help="run the serving workload instead")
     ap.add_argument("--profile-cycle", action="store_true",
                     help="per-step timing of one persistent-kernel cycle of the aniso1024 workload")
-    ap.add_argument("--solve-once", default=None, choices=["main", "main-fp32", "aniso1024", "aniso1024-fp32"],
+    ap.add_argument("--solve-once", default=None,
+                    choices=["main", "main-fp32", "aniso1024", "aniso1024-fp32", "grid192", "grid192-fp32"],
                     help="set up the named workload and run one solve, nothing else (for a launch-list capture)")
     ap.add_argument("--serve-requests", type=int, default=200)
     ap.add_argument("--serve-max-n", type=int, default=200000)
@@ -188,6 +189,15 @@ def solve_once(which: str):
         bt = torch.from_numpy(b).cuda()
         xt = torch.zeros_like(bt)
         sts = [P.solve_ptr(bt.data_ptr(), xt.data_ptr(), TOL, 200)]
+    elif which in ("grid192", "grid192-fp32"):
+        # the 192^3 heterogeneous 3D grid with 16 right-hand sides
+        import graphgen as gg
+        g = gg.config_graph("grid3d192_hetero")
+        B = gg.rhs(g, seed=2, k=16)
+        P = lamg.setup(g, precision=lamg.FP32 if which == "grid192-fp32" else lamg.FP64)
+        bt = torch.from_numpy(B).cuda()
+        xt = torch.zeros_like(bt)
+        sts = P.solve_batch_ptr(16, bt.data_ptr(), xt.data_ptr(), TOL, 200)
     else:
         g, B = workload()
         P = lamg.setup(g, precision=lamg.FP32 if which == "main-fp32" else lamg.FP64)
