@@ -887,8 +887,15 @@ static int pow2_at_least(int k) {
     X(16, 2, __VA_ARGS__)             \
     X(32, 1, __VA_ARGS__)
 
+// Lanes per row for each column of a k-column kernel: from four columns on, one lane per row
+// and column, which sums its row's entries in a chain without a shuffle tree (the tree's FP64
+// adds and the lanes it idles cost more than the chain's latency; measured on B300, 16-column
+// solves: 1024^2 anisotropic grid 75.3 -> 64.2 ms, 192^3 heterogeneous grid 699 -> 508 ms; 8
+// columns on a 128^3 grid 159 -> 90 ms, 4 columns 89 -> 65 ms); at two columns the level's lane
+// groups stay (56 against 60 ms); one column uses the single-RHS rule of the level.
 static int row_tpr(int KL, int level_tpr) {
     if (KL == 1) return level_tpr;
+    if (KL >= 4) return 1;
     return std::max(1, std::min(level_tpr, std::min(4, 32 / KL)));
 }
 
