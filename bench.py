@@ -576,6 +576,21 @@ def run_ours(args, ws, rank, local):
         e2e_t += time.perf_counter() - t0
         e2e_units += sum(g.nnz_L * digits(c["relres_true"]) for c in sth)
 
+    # one right-hand side of the same workload (the graph path, FP64): column 0, device buffers
+    b0 = Bt[:, 0].contiguous()
+    x0 = torch.zeros_like(b0)
+    one = []
+    for i in range(4):
+        flush.fill_(i & 0xff)
+        st1 = P.solve_ptr(b0.data_ptr(), x0.data_ptr(), TOL, 200, stream=stream.cuda_stream)
+        one.append(st1)
+    torch.cuda.synchronize()
+    ms1 = float(np.median([c["solve_ms"] for c in one[1:]]))
+    single_rhs = {"value": round(ms1 * 1e6 / (g.nnz_L * digits(one[-1]["relres_true"])), 5), "unit": UNIT,
+                  "rhs": 1, "ms_per_solve": round(ms1, 3), "iterations": one[-1]["iters"],
+                  "relres_true": one[-1]["relres_true"]}
+    del b0, x0
+
     # roofline of the dominant kernel: cold-L2 time of each candidate sequence alone, weighted by
     # how often a solve runs it (the cycle's static step list times the iterations); per level
     # the same figures (the levels table)
@@ -644,7 +659,7 @@ def run_ours(args, ws, rank, local):
     P.close()
     del Bt, Xt
 
-    variants = {}
+    variants = {"chunglu4m_1rhs_fp64": single_rhs}
     if not args.no_variants:
         variants.update(run_variants(g, B, X64, dev, stream, flush, local))
 

@@ -205,6 +205,15 @@ int upload_level(lamg_hier *h, int l) {
     D.gs_tpr = (D.sell && h->opt.row_tpr == 0 && n >= (1 << 18) && avg <= 8.0) ? 0 : D.tpr;
     D.rs_tpr = (D.sell && (h->opt.sell > 0 || n >= 65536)) ? 0 : D.tpr;
     if (D.sell && h->opt.sell > 0) D.gs_tpr = 0;
+    // Chebyshev levels (power-law Galerkin levels, long rows): a step is one pass over all rows
+    // and is bound by FP64 instructions rather than latency, so a lane takes about eight entries
+    // of its row before the shuffle tree instead of two (the tree's adds and idle lanes cost more
+    // than the longer chain)
+    if (H.kind == KIND_AGG && H.cheb && h->opt.row_tpr == 0 && !D.sell) {
+        int t = 1;
+        while (t < 32 && 8.0 * t < avg) t *= 2;
+        D.gs_tpr = D.rs_tpr = t;
+    }
     if (H.kind == KIND_AGG) {
         const std::vector<int32_t> &ip = h->dev[l + 1].perm;
         std::vector<int32_t> ipc(H.nc);
