@@ -573,10 +573,13 @@ int tune_kernels(lamg_hier *h) {
         std::vector<int> cand;
         if (D.sell) cand.push_back(0);
         for (int t = 1; t <= 32; t *= 2)
-            if (4 * t >= D.tpr && t <= 2 * D.tpr) cand.push_back(t);
+            if ((4 * t >= D.tpr && t <= 2 * D.tpr) || (D.cheb && t <= 2 * D.tpr)) cand.push_back(t);
         if (D.kind == KIND_AGG) {
+            // the level's smoothing pass: one colour-ordered sweep, or one Chebyshev step
             std::vector<Op> sweep;
-            for (int c = 0; c < D.ncol; c++) sweep.push_back({OP_GS, l, c});
+            if (D.cheb) sweep.push_back({OP_CHEB, l, 0});
+            else
+                for (int c = 0; c < D.ncol; c++) sweep.push_back({OP_GS, l, c});
             double best = -1.0;
             int pick = D.gs_tpr;
             for (int t : cand) {
