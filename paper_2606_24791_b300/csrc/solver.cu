@@ -205,6 +205,14 @@ int upload_level(lamg_hier *h, int l) {
     D.gs_tpr = (D.sell && h->opt.row_tpr == 0 && n >= (1 << 18) && avg <= 8.0) ? 0 : D.tpr;
     D.rs_tpr = (D.sell && (h->opt.sell > 0 || n >= 65536)) ? 0 : D.tpr;
     if (D.sell && h->opt.sell > 0) D.gs_tpr = 0;
+    // A colour class of >= 2^16 rows on average (large mesh-like levels without the sliced form)
+    // is bound by FP64 instructions rather than latency: a lane takes about four entries before
+    // the shuffle tree instead of two
+    if (h->opt.row_tpr == 0 && D.gs_tpr > 0 && H.kind == KIND_AGG && H.ncol > 0 && n / H.ncol >= (1 << 16)) {
+        int t = 1;
+        while (t < 32 && 4.0 * t < avg) t *= 2;
+        D.gs_tpr = std::min(D.gs_tpr, t);
+    }
     // Chebyshev levels (power-law Galerkin levels, long rows): a step is one pass over all rows
     // and is bound by FP64 instructions rather than latency, so a lane takes about eight entries
     // of its row before the shuffle tree instead of two (the tree's adds and idle lanes cost more
