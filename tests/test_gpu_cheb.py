@@ -109,3 +109,21 @@ def test_cheb_rejects_bad_degree():
         lamg.setup(g, cheb_degree=9)
     with pytest.raises(lamg.LamgError):
         lamg.setup(g, cheb_degree=0)
+
+
+def test_cheb_step_timer_reports_one_launch_and_its_work():
+    # lamg_time_kernel_batch's one-step unit on a Chebyshev level: one bk_cheb launch, a
+    # multiply-add per stored entry and column plus six flops per row and column
+    g = gg.chung_lu(20000, 2.1, 16, seed=1)
+    P = lamg.setup(g)
+    lv = [l for l, L in enumerate(P.info) if L["kind"] == "agg" and L["ncol"] > 32]
+    assert lv
+    B = gg.rhs(g, seed=3, k=4)
+    P.solve_batch(B, 1e-8, 200)
+    L = P.info[lv[0]]
+    r = P.time_kernel_batch("cheb_step", lv[0], 4, reps=2)
+    assert r["launches"] == 1 and r["ms"] > 0
+    assert r["flops"] == pytest.approx(4 * (2 * L["nnz"] + 6 * L["n"]))
+    with pytest.raises(Exception):
+        P.time_kernel_batch("cheb_step", 0, 4, reps=1)   # level 0 is not a Chebyshev level
+    P.close()
