@@ -496,10 +496,11 @@ __global__ void bk_elim_interp(int nc, int nF, int k, const int32_t *__restrict_
 
 // Coarsest level: x = (I - J/n) A^+ b against the FP64 projected pseudo-inverse, accumulated in
 // FP64 for either cycle type (b in FP64: an FP32 cycle's right-hand side widened beforehand; the
-// FP64 sum rounded to FP32 once at the end). One block per row: KL lanes per column times BBS/KL lanes splitting
-// the row, each lane with four independent partial sums (a dependent FP64 add takes ~68 clocks
-// on this GPU, so one chain of n/2 adds per lane would set the kernel's time), combined in a
-// fixed order: the four partials, the lanes of a warp by a shuffle tree, then the warps in order.
+// FP64 sum rounded to FP32 once at the end). One block per row: KL lanes per column times BBS/KL
+// lanes splitting the row, each lane with four independent partial sums (a dependent FP64 add
+// takes ~68 clocks on this GPU, so one chain of n/2 adds per lane would set the kernel's time),
+// combined in a fixed order: the four partials, the lanes of a warp by a shuffle tree, then the
+// warps in order.
 template <typename T, int KL>
 __global__ void __launch_bounds__(BBS) bk_coarse(int n, int k, const double *__restrict__ pinv,
                                                  const double *__restrict__ b, T *x) {
