@@ -450,19 +450,38 @@ __global__ void bk_prolong(int n, int k, const int32_t *__restrict__ agg, const 
     x[(size_t)u * k + j] += s;
 }
 
+// b^c = b_C + P_F^T b_F (and with xc set the coarse level's row-local first-visit start, as
+// bk_restrict). Blocks b < nl take the C rows lr[b] that gather more than LONG_ROW F entries (the
+// hubs of power-law graphs), summed by the whole block (as block_row_k) and added to b_C; every
+// other C row is summed by its lanes in entry order.
 template <typename T, int KL>
 __global__ void bk_elim_restrict(int nc, int k, const int32_t *__restrict__ ptr, const int32_t *__restrict__ f,
                                  const T *__restrict__ pv, const T *__restrict__ b, T *bc, T *xc, int c1,
-                                 const T *__restrict__ idc) {
+                                 const T *__restrict__ idc, const int32_t *__restrict__ lr, int nl) {
     b_trigger();
-    int i, j;
-    elem_pos<KL>(i, j);
-    const bool ok = i < nc;
+    const T *bF = b + (size_t)nc * k;
+    if ((int)blockIdx.x < nl) {
+        const int i = lr[blockIdx.x];
+        const int e0 = ptr[i], e1 = ptr[i + 1];
+        const T id = (xc && i < c1) ? idc[i] : T(0);
+        b_wait();
+        const T sF = block_row_k<T, KL>(e0, e1, k, f, pv, bF);
+        if ((int)threadIdx.x < k) {
+            const size_t e = (size_t)i * k + threadIdx.x;
+            const T s = b[e] + sF;
+            bc[e] = s;
+            if (xc) xc[e] = i < c1 ? s * id : T(0);
+        }
+        return;
+    }
+    const int t = (blockIdx.x - nl) * BBS + threadIdx.x;
+    const int i = t / KL, j = t % KL;
+    bool ok = i < nc;
     const int e0 = ok ? ptr[i] : 0, e1 = ok ? ptr[i + 1] : 0;
+    if (e1 - e0 > LONG_ROW) ok = false;
     const T id = (xc && ok && i < c1) ? idc[i] : T(0);
     b_wait();
     if (!ok || j >= k) return;
-    const T *bF = b + (size_t)nc * k;
     T s = b[(size_t)i * k + j];
     for (int e = e0; e < e1; e++) s += pv[e] * bF[(size_t)f[e] * k + j];
     bc[(size_t)i * k + j] = s;
@@ -471,7 +490,7 @@ __global__ void bk_elim_restrict(int nc, int k, const int32_t *__restrict__ ptr,
 
 template <typename T, int KL>
 __global__ void bk_elim_interp(int nc, int nF, int k, const int32_t *__restrict__ col, const T *__restrict__ pv,
-                               const T *__restrict__ dF, const T *__restrict__ b, T *x) {
+                               const T *__restrict__ idF, const T *__restrict__ b, T *x) {
     b_trigger();
     int t, j;
     elem_pos<KL>(t, j);
@@ -483,7 +502,7 @@ __global__ void bk_elim_interp(int nc, int nF, int k, const int32_t *__restrict_
         c[q] = ok ? col[4 * t + q] : -1;
         p[q] = ok ? pv[4 * t + q] : T(0);
     }
-    const T d = ok ? dF[t] : T(1);
+    const T id = ok ? idF[t] : T(1);
     b_wait();
     if (!ok || j >= k) return;
     T s = T(0);
@@ -491,7 +510,7 @@ __global__ void bk_elim_interp(int nc, int nF, int k, const int32_t *__restrict_
     for (int q = 0; q < 4; q++)
         if (c[q] >= 0) s += p[q] * x[(size_t)c[q] * k + j];
     const size_t e = (size_t)(nc + t) * k + j;
-    x[e] = s + b[e] / d;
+    x[e] = s + b[e] * id;
 }
 
 // Coarsest level: x = (I - J/n) A^+ b against the FP64 projected pseudo-inverse, accumulated in
@@ -919,7 +938,9 @@ struct BLev {
     const int32_t *rp = nullptr, *ci = nullptr, *agg = nullptr, *agg2 = nullptr, *pt_ptr = nullptr,
                   *pt_row = nullptr, *pf_col = nullptr, *pft_ptr = nullptr, *pft_f = nullptr;
     const void *val = nullptr, *diag = nullptr, *wt = nullptr, *pt_w = nullptr, *pf_val = nullptr,
-               *dF = nullptr, *pft_val = nullptr;
+               *dF = nullptr, *idF = nullptr, *pft_val = nullptr;
+    const int32_t *pft_long = nullptr;   // elimination: C rows with more than LONG_ROW F entries
+    int64_t npft_long = 0;
     const double *pinv = nullptr;  // coarsest (I - J/n) A^+, FP64 for either cycle type
     double *b64 = nullptr;         // coarsest, FP32 cycle: the right-hand side widened to FP64
     void *x = nullptr, *b = nullptr, *r = nullptr;
@@ -978,6 +999,7 @@ static int build_ctx(lamg_hier *h, BatchCtx *c) {
         if (D.sell && (rc = typed_copy<T>(h, D.sl_val, D.sell_nnz, &B.sl_val))) return rc;
         B.rp = D.rp; B.ci = D.ci; B.agg = D.agg; B.agg2 = D.agg2; B.pt_ptr = D.pt_ptr; B.pt_row = D.pt_row;
         B.pf_col = D.pf_col; B.pft_ptr = D.pft_ptr; B.pft_f = D.pft_f;
+        B.pft_long = D.pft_long; B.npft_long = D.npft_long;
         B.pinv = D.kind == KIND_COARSEST ? D.pinv : nullptr;
         const int64_t pte = (D.kind == KIND_AGG) ? (int64_t)h->host[l].A.n * 2 : 0;
         int32_t ent = 0;
@@ -997,6 +1019,7 @@ static int build_ctx(lamg_hier *h, BatchCtx *c) {
             (rc = typed_copy<T>(h, D.pt_w, ent, &B.pt_w)) ||
             (rc = typed_copy<T>(h, D.pf_val, D.kind == KIND_ELIM ? 4 * D.nF : 0, &B.pf_val)) ||
             (rc = typed_copy<T>(h, D.dF, D.kind == KIND_ELIM ? D.nF : 0, &B.dF)) ||
+            (rc = typed_copy<T>(h, D.idF, D.kind == KIND_ELIM ? D.nF : 0, &B.idF)) ||
             (rc = typed_copy<T>(h, D.pft_val, fent, &B.pft_val)))
             return rc;
     }
@@ -1123,7 +1146,7 @@ static void bop(const Op &op, BatchCtx *c, cudaStream_t s, const Op *start) {
         case OP_ELIM_RESTRICT: {
             T *bc = (T *)c->lv[op.level + 1].b;
             const int nc = (int)L.nc;
-#define C6(KLv, ...) case KLv: blaunch(bk_elim_restrict<T, KLv>, nblocks((int64_t)nc * KLv), s, nc, k, L.pft_ptr, L.pft_f, (const T *)L.pft_val, (const T *)b, bc, xs, c1, ids); break;
+#define C6(KLv, ...) case KLv: blaunch(bk_elim_restrict<T, KLv>, L.npft_long + nblocks((int64_t)nc * KLv), s, nc, k, L.pft_ptr, L.pft_f, (const T *)L.pft_val, (const T *)b, bc, xs, c1, ids, L.pft_long, (int)L.npft_long); break;
             switch (KL) { K_CASES(C6) }
 #undef C6
             break;
@@ -1131,7 +1154,7 @@ static void bop(const Op &op, BatchCtx *c, cudaStream_t s, const Op *start) {
         case OP_ELIM_INTERP: {
             if (L.nF <= 0) break;
             const int nF = (int)L.nF;
-#define C7(KLv, ...) case KLv: blaunch(bk_elim_interp<T, KLv>, nblocks((int64_t)nF * KLv), s, (int)L.nc, nF, k, L.pf_col, (const T *)L.pf_val, (const T *)L.dF, (const T *)b, x); break;
+#define C7(KLv, ...) case KLv: blaunch(bk_elim_interp<T, KLv>, nblocks((int64_t)nF * KLv), s, (int)L.nc, nF, k, L.pf_col, (const T *)L.pf_val, (const T *)L.idF, (const T *)b, x); break;
             switch (KL) { K_CASES(C7) }
 #undef C7
             break;

@@ -53,11 +53,13 @@ struct DevLevel {
     int32_t *pt_ptr = nullptr, *pt_row = nullptr;
     double *pt_w = nullptr;
     int pt_tpr = 1;
-    // elimination: F rows as ELL-4 (coarse columns < nc, -1 padding), P_F^T over C rows
+    // elimination: F rows as ELL-4 (coarse columns < nc, -1 padding), P_F^T over C rows; for
+    // the multi-column kernels also 1 / A_FF and the C rows with more than LONG_ROW F entries
     int32_t *pf_col = nullptr;
-    double *pf_val = nullptr, *dF = nullptr;
-    int32_t *pft_ptr = nullptr, *pft_f = nullptr;
+    double *pf_val = nullptr, *dF = nullptr, *idF = nullptr;
+    int32_t *pft_ptr = nullptr, *pft_f = nullptr, *pft_long = nullptr;
     double *pft_val = nullptr;
+    int64_t npft_long = 0;
     // coarsest: dense pseudo-inverse, row-major
     double *pinv = nullptr;
     // iterate, right-hand side, residual

@@ -294,6 +294,16 @@ int upload_level(lamg_hier *h, int l) {
         if ((rc = dupload(h, &D.pf_col, pfc)) || (rc = dupload(h, &D.pf_val, pfv)) || (rc = dupload(h, &D.dF, dF)) ||
             (rc = dupload(h, &D.pft_ptr, ptr)) || (rc = dupload(h, &D.pft_f, fidx)) || (rc = dupload(h, &D.pft_val, fval)))
             return rc;
+        // for the multi-column kernels: 1 / A_FF (an FP64 division per element and column cost more
+        // than the interpolation's memory traffic) and the C rows that gather more than LONG_ROW
+        // F entries (hubs of power-law graphs), which a whole block sums
+        std::vector<double> idF(nF);
+        for (int64_t t = 0; t < nF; t++) idF[t] = 1.0 / dF[t];
+        std::vector<int32_t> lng;
+        for (int64_t i = 0; i < nc; i++)
+            if (ptr[i + 1] - ptr[i] > LONG_ROW) lng.push_back((int32_t)i);
+        D.npft_long = (int64_t)lng.size();
+        if ((rc = dupload(h, &D.idF, idF)) || (D.npft_long && (rc = dupload(h, &D.pft_long, lng)))) return rc;
     } else {
         // (I - J/n) A^+: the coarsest solve and its mean-zero projection as one matrix
         std::vector<double> P(n * n), colmean(n, 0.0);
