@@ -323,23 +323,25 @@ __device__ __forceinline__ void cl_op(const Op &op, const PLevel *lv, const int3
             }
             break;
         case OP_COARSE:
-            // same summation order as the per-step kernel (lane j, j + 32, ...); eight loads
-            // per lane are issued before they are used, so one warp keeps 2 KB in flight
+            // same summation order as the per-step kernel: four partial sums per lane over the
+            // columns lane, lane + 32, lane + 64, lane + 96, then every 128th, added as
+            // (s0 + s1) + (s2 + s3), then the warp's shuffle tree
             for (int i = p.warp; i < L.n; i += p.nwarps) {
                 const double *row = L.pinv + (size_t)i * L.n;
-                double s = 0.0;
-                for (int j0 = p.lane; j0 < L.n; j0 += 32 * 8) {
-                    double a[8], v[8];
-#pragma unroll
-                    for (int k = 0; k < 8; k++) {
-                        const int j = j0 + 32 * k;
-                        a[k] = j < L.n ? __ldg(&row[j]) : 0.0;
-                        v[k] = j < L.n ? __ldcg(&L.b[j]) : 0.0;
-                    }
-#pragma unroll
-                    for (int k = 0; k < 8; k++)
-                        if (j0 + 32 * k < L.n) s += a[k] * v[k];
+                double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+                int j = p.lane;
+                for (; j + 96 < L.n; j += 128) {
+                    const double a0 = __ldg(&row[j]), a1 = __ldg(&row[j + 32]);
+                    const double a2 = __ldg(&row[j + 64]), a3 = __ldg(&row[j + 96]);
+                    const double v0 = __ldcg(&L.b[j]), v1 = __ldcg(&L.b[j + 32]);
+                    const double v2 = __ldcg(&L.b[j + 64]), v3 = __ldcg(&L.b[j + 96]);
+                    s0 += a0 * v0;
+                    s1 += a1 * v1;
+                    s2 += a2 * v2;
+                    s3 += a3 * v3;
                 }
+                for (; j < L.n; j += 32) s0 += __ldg(&row[j]) * __ldcg(&L.b[j]);
+                double s = (s0 + s1) + (s2 + s3);
                 s = warp_sum(s);
                 if (p.lane == 0) L.x[i] = s;
             }

@@ -477,9 +477,20 @@ __global__ void __launch_bounds__(BS) k_coarse(int n, const double *__restrict__
     const int lane = threadIdx.x & 31;
     const int wg = (blockIdx.x * BS + threadIdx.x) >> 5, nwarps = (gridDim.x * BS) >> 5;
     for (int i = wg; i < n; i += nwarps) {
+        // four partial sums per lane (columns lane, lane + 32, lane + 64, lane + 96, then every
+        // 128th), added as (s0 + s1) + (s2 + s3) before the warp's shuffle tree: four
+        // independent FP64 chains per lane instead of one n/32 long
         const double *row = pinv + (int64_t)i * n;
-        double s = 0.0;
-        for (int j = lane; j < n; j += 32) s += row[j] * b[j];
+        double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+        int j = lane;
+        for (; j + 96 < n; j += 128) {
+            s0 += row[j] * b[j];
+            s1 += row[j + 32] * b[j + 32];
+            s2 += row[j + 64] * b[j + 64];
+            s3 += row[j + 96] * b[j + 96];
+        }
+        for (; j < n; j += 32) s0 += row[j] * b[j];
+        double s = (s0 + s1) + (s2 + s3);
         s = warp_sum(s);
         if (lane == 0) x[i] = s;
     }
