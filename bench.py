@@ -741,7 +741,7 @@ def run_variants(g, B, X64, dev, stream, flush, local) -> dict:
         if k == 1 and PP is Pa:
             xa64 = Xk.cpu().numpy()
             v["launches_per_solve"] = sts[0]["launches"]
-            # round 1's dominant kernel of this workload: one level-2 colour-ordered sweep
+            # the one-column path's dominant kernel on this workload: one level-2 colour-ordered sweep
             r = Pa.time_kernel("gs_sweep", 2, reps=10)
             v["k_gs_sweep_L2"] = {"ms": round(r["ms"], 5), "gbs": round(r["gbs"], 1), "bytes": r["bytes"],
                                   "traffic": traffic_for("k_gs")}
