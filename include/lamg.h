@@ -219,7 +219,10 @@ int lamg_solve(lamg_hier *h, const double *b, double *phi, const lamg_solve_opts
 
 /* k right-hand sides at once: B and PHI are n x k, row-major (entry (u, j) at u*k + j).
  * Each column is an independent solve with its own CG scalars and stopping test; the cycles
- * run in SpMM form over all still-active columns. st: NULL or an array of k stats.
+ * run in SpMM form over all still-active columns. st: NULL or an array of k stats. Host
+ * matrices of at least 128 MB move through 64 MB pinned chunks, copied on the host by a pool of
+ * threads (one per hardware thread, created on first use and kept for the life of the process)
+ * while the previous chunk's DMA runs.
  * Errors: as lamg_solve (NOT_CONVERGED if any column did not converge). */
 int lamg_solve_batch(lamg_hier *h, int32_t k, const double *B, double *PHI,
                      const lamg_solve_opts *so, lamg_stats *st);
